@@ -1,0 +1,721 @@
+/*
+ * woi_oracle.c -- plain, slow FP64 CPU oracle of the Walk-on-Interfaces (WoI)
+ * estimator (Ding & Stinchcombe, "Walk-on-Interfaces", arXiv 2508.16767).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library; the two agree only on the documented
+ * random-number protocol (Philox4x32-10, written here from its published
+ * definition) and on the input format.
+ *
+ * What it computes (section numbers are the paper's):
+ *   - Sec. 3: unit-coefficient system gamma_i - alpha_i sum_j K*_ij gamma_j =
+ *     beta_i and its truncated Neumann series with weights
+ *     w_i = 1 - delta_{iM}/2.  alpha, beta scaling and the schedule
+ *     thresholds are prepared by oracle.py and passed in.
+ *   - Sec. 4.2.1, Eqs. naive_woi_p0 / naive_woi_p: the transition densities
+ *     (uniform start; line-isotropic if h_{i-1} = h_i; ray-isotropic if
+ *     h_{i-1} is a descendant of h_i; uniform otherwise).
+ *   - Sec. 4.2.2, Eqs. naive_woi_Q / naive_woi_T: the Q and T factors.
+ *   - Sec. 4.3.1, Thm 4.2 and Eq. woi_estimator: scheduled interfaces
+ *     H_0 ~ U{1..N}, H_i ~ |alpha_n| / ||alpha||_1, the weight
+ *     N ||alpha||_1^i prod_{m=1}^{i} sign(alpha_{H_m}).
+ *   - Algorithms 1-2 (plain walk), Algorithm 3 and Eq.
+ *     variance_reduced_woi_estimator (two chains from the beta >= 0 and
+ *     beta < 0 parts of the first interface).
+ *   - Sec. 4.5, Eq. naive_woi_grad_estimator: the gradient tally uses
+ *     grad_x Phi on the same trajectory.
+ *
+ * Readings of the paper taken here (each one is listed with its reason in
+ * the design notes of the repository):
+ *   R1 the alpha-sign product runs over m = 1..i (Thm 4.2), not m = 0..i;
+ *   R2 in the "otherwise" (uniform) transition T is left unchanged: the sign
+ *      already lives in the signed K* inside Q (Thm 4.1 needs Q*T = prod K* / p);
+ *   R3 K* is evaluated as K*(y_i, y_{i-1}) with the normal at the new point;
+ *   R4 "descendant" means strict descendant at any depth;
+ *   R5 a line/ray that finds no admissible intersection (q = 0, a tangency of
+ *      measure zero) ends the walk: T = 0 from then on.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_DIM 6
+#define OR_MAX_STAR 16
+#define OR_MAX_ROOTS 64
+#define OR_STAR_SCAN 4096
+#define OR_STAR_PANELS 256
+
+enum { OR_SPHERE = 0, OR_STAR = 1 };
+enum { OR_FLUX_ZERO = 0, OR_FLUX_FOURIER = 1, OR_FLUX_REAL_SH = 2, OR_FLUX_HARMONIC_POLY = 3 };
+enum { OR_REL_SAME = 0, OR_REL_DESC = 1, OR_REL_OTHER = 2 };
+
+/* Planted-mistake switch.  Only the tests that show that the pins detect
+ * plausible errors set it (on the CPU); it is 0 in every other use.
+ *   1 uniform transition also multiplies T by the sign (|K*| instead of K*)
+ *   2 alpha-sign product over m = 0..i          3 no half weight at i = M
+ *   4 no factor N                               5 K* with the normal at the old point
+ *   6 beta_i scaled by +2/(sigma_p + sigma_i)   7 line case keeps Q (no 1/2)
+ *   8 gradient of Phi with the wrong sign       9 H_0 drawn like H_i (by |alpha|) */
+static int or_mutant = 0;
+void or_set_mutant(int m) { or_mutant = m; }
+
+/* Problem description.  All arrays are owned by the caller (oracle.py). */
+typedef struct {
+    int dim;
+    int n_surf;
+    const int *type;          /* [n_surf] OR_SPHERE or OR_STAR (star: dim 2 only) */
+    const double *center;     /* [n_surf][OR_MAX_DIM] */
+    const double *radius;     /* [n_surf] sphere radius, or star base radius R */
+    const int *star_K;        /* [n_surf] star Fourier degree */
+    const double *star_a;     /* [n_surf][OR_MAX_STAR+1] r = R(1 + sum a_k cos k t + b_k sin k t) */
+    const double *star_b;
+    const double *star_s;     /* [n_surf][OR_STAR_PANELS+1] arc length at t_j = 2 pi j / panels */
+    const double *star_scan;  /* [n_surf][OR_STAR_SCAN+1][2] curve points at t_j = 2 pi j / OR_STAR_SCAN */
+    const double *area;       /* [n_surf] |dOmega_i| */
+    const int *is_desc;       /* [n_surf*n_surf] is_desc[a*n+b] = 1 iff a is a strict descendant of b */
+    const double *alpha;      /* [n_surf] Sec. 3 */
+    const double *beta_scale; /* [n_surf] beta_i = beta_scale_i * b_i */
+    const uint64_t *thresh;   /* [n_surf] schedule thresholds, thresh[N-1] = 2^32 */
+    double alpha_l1;          /* ||alpha||_1 */
+    const int *flux_basis;    /* [n_surf] */
+    const int *flux_off;      /* [n_surf] offset into flux_coef */
+    const int *flux_n;        /* [n_surf] */
+    const double *flux_coef;
+    const int *arc_off;       /* [n_surf] first arc of the surface (2D variance reduction) */
+    const int *arc_n;         /* [n_surf] number of arcs */
+    const double *arc_t0;     /* parameter angle where the arc starts */
+    const double *arc_t1;     /* parameter angle where the arc ends */
+    const int *arc_sign;      /* +1: part of dOmega^+ (beta >= 0), -1: dOmega^- */
+    const double *arc_len;
+    const double *part_len;   /* [n_surf][2] |dOmega^+|, |dOmega^-| */
+} or_problem;
+
+typedef struct {
+    int M;            /* truncation: steps 0..M */
+    int variant;      /* 0 plain (Alg. 2), 1 variance reduced (Alg. 3) */
+    int sched_group;  /* walkers per schedule (Alg. 1): 1 or 32 */
+} or_opts;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random numbers:  */
+/* as easy as 1, 2, 3", SC'11: ten rounds of two 32x32->64 multiplies with   */
+/* the round keys bumped by the Weyl constants between rounds.               */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Random-number protocol (documented in the design notes; both sides follow it):
+ *   key     = (seed_lo ^ point_id, seed_hi ^ instance)
+ *   counter = (walk_lo, walk_hi, step, (chain << 4) | sub)      per-walk words
+ *   counter = (group_lo, group_hi, step, 0x100)                 shared schedule words
+ * Word k of a (step, chain) stream is word k % 4 of sub-call k / 4. */
+typedef struct {
+    uint32_t key[2];
+    uint64_t walk;
+    int cached_step, cached_chain, cached_sub;
+    uint32_t words[4];
+} or_rng;
+
+static uint32_t or_word(or_rng *r, int step, int chain, int k)
+{
+    int sub = k >> 2;
+    if (r->cached_step != step || r->cached_chain != chain || r->cached_sub != sub) {
+        uint32_t ctr[4] = {(uint32_t)r->walk, (uint32_t)(r->walk >> 32), (uint32_t)step,
+                           (uint32_t)((chain << 4) | sub)};
+        or_philox4x32_10(ctr, r->key, r->words);
+        r->cached_step = step; r->cached_chain = chain; r->cached_sub = sub;
+    }
+    return r->words[k & 3];
+}
+
+/* uniform on (0,1) from the top 24 bits; the same value is exact in FP32 */
+static double or_u01(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------------ */
+/* constants and Green's function (Sec. 2)                                   */
+/* ------------------------------------------------------------------------ */
+static double or_omega(int d) /* surface area of the unit sphere in R^d: d * alpha(d) */
+{
+    return 2.0 * pow(M_PI, 0.5 * d) / tgamma(0.5 * d);
+}
+
+static double or_dist(int d, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s += (a[k] - b[k]) * (a[k] - b[k]);
+    return sqrt(s);
+}
+
+/* Phi(x,y) = -ln|x-y| / (2 pi) in 2D, |x-y|^{2-d} / (d (d-2) alpha(d)) otherwise */
+static double or_phi(int d, const double *x, const double *y)
+{
+    double r = or_dist(d, x, y);
+    if (d == 2) return -log(r) / (2.0 * M_PI);
+    return pow(r, 2.0 - d) / ((d - 2) * or_omega(d));
+}
+
+/* grad_x Phi(x,y) = -(x - y) / (d alpha(d) |x-y|^d)  (Sec. 4.5) */
+static void or_grad_phi(int d, const double *x, const double *y, double *g)
+{
+    double r = or_dist(d, x, y);
+    double c = (or_mutant == 8 ? 1.0 : -1.0) / (or_omega(d) * pow(r, (double)d));
+    for (int k = 0; k < d; ++k) g[k] = c * (x[k] - y[k]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* geometry                                                                  */
+/* ------------------------------------------------------------------------ */
+static const double *or_center(const or_problem *P, int h) { return P->center + (size_t)h * OR_MAX_DIM; }
+
+/* star radius r(t) and r'(t) */
+static void or_star_r(const or_problem *P, int h, double t, double *r, double *dr)
+{
+    const double *a = P->star_a + (size_t)h * (OR_MAX_STAR + 1);
+    const double *b = P->star_b + (size_t)h * (OR_MAX_STAR + 1);
+    double R = P->radius[h], s = 1.0, ds = 0.0;
+    for (int k = 1; k <= P->star_K[h]; ++k) {
+        s += a[k] * cos(k * t) + b[k] * sin(k * t);
+        ds += k * (-a[k] * sin(k * t) + b[k] * cos(k * t));
+    }
+    *r = R * s;
+    *dr = R * ds;
+}
+
+static void or_star_point(const or_problem *P, int h, double t, double *y)
+{
+    double r, dr;
+    or_star_r(P, h, t, &r, &dr);
+    const double *c = or_center(P, h);
+    y[0] = c[0] + r * cos(t);
+    y[1] = c[1] + r * sin(t);
+}
+
+/* |gamma'(t)| and the outward unit normal of the counter-clockwise star */
+static double or_star_speed_normal(const or_problem *P, int h, double t, double *n)
+{
+    double r, dr;
+    or_star_r(P, h, t, &r, &dr);
+    double tx = dr * cos(t) - r * sin(t);
+    double ty = dr * sin(t) + r * cos(t);
+    double sp = sqrt(tx * tx + ty * ty);
+    if (n) { n[0] = ty / sp; n[1] = -tx / sp; }
+    return sp;
+}
+
+/* arc length from 0 to t (t in [0, 2 pi]): stored panel sums + 16-point Gauss-Legendre */
+static const double or_gl16_x[8] = {0.0950125098376374, 0.2816035507792589, 0.4580167776572274,
+                                    0.6178762444026438, 0.7554044083550030, 0.8656312023878318,
+                                    0.9445750230732326, 0.9894009349916499};
+static const double or_gl16_w[8] = {0.1894506104550685, 0.1826034150449236, 0.1691565193950025,
+                                    0.1495959888165767, 0.1246289712555339, 0.0951585116824928,
+                                    0.0622535239386479, 0.0271524594117541};
+
+static double or_star_arclen(const or_problem *P, int h, double t)
+{
+    const double H = 2.0 * M_PI / OR_STAR_PANELS;
+    int j = (int)floor(t / H);
+    if (j < 0) j = 0;
+    if (j >= OR_STAR_PANELS) j = OR_STAR_PANELS - 1;
+    double a = j * H, half = 0.5 * (t - a), mid = a + half, s = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        s += or_gl16_w[q] * (or_star_speed_normal(P, h, mid - half * or_gl16_x[q], NULL) +
+                             or_star_speed_normal(P, h, mid + half * or_gl16_x[q], NULL));
+    }
+    return P->star_s[(size_t)h * (OR_STAR_PANELS + 1) + j] + half * s;
+}
+
+/* parameter t in [t_lo, t_hi] with arclen(t) = s, by bisection */
+static double or_star_invert(const or_problem *P, int h, double s, double t_lo, double t_hi)
+{
+    for (int it = 0; it < 200 && t_hi - t_lo > 1e-15; ++it) {
+        double m = 0.5 * (t_lo + t_hi);
+        if (or_star_arclen(P, h, m) < s) t_lo = m; else t_hi = m;
+    }
+    return 0.5 * (t_lo + t_hi);
+}
+
+static double or_param_angle(const or_problem *P, int h, const double *y)
+{
+    const double *c = or_center(P, h);
+    double t = atan2(y[1] - c[1], y[0] - c[0]);
+    if (t < 0) t += 2.0 * M_PI;
+    return t;
+}
+
+/* outward unit normal at a point y of surface h */
+static void or_normal(const or_problem *P, int h, const double *y, double *n)
+{
+    int d = P->dim;
+    if (P->type[h] == OR_SPHERE) {
+        const double *c = or_center(P, h);
+        for (int k = 0; k < d; ++k) n[k] = (y[k] - c[k]) / P->radius[h];
+    } else {
+        or_star_speed_normal(P, h, or_param_angle(P, h, y), n);
+    }
+}
+
+/* isotropic unit direction from the words 1.. of a (step, chain) stream */
+static void or_direction(or_rng *r, int d, int step, int chain, double *z)
+{
+    if (d == 2) {
+        double phi = 2.0 * M_PI * or_u01(or_word(r, step, chain, 1));
+        z[0] = cos(phi); z[1] = sin(phi);
+        return;
+    }
+    if (d == 3) {
+        double zz = 1.0 - 2.0 * or_u01(or_word(r, step, chain, 1));
+        double phi = 2.0 * M_PI * or_u01(or_word(r, step, chain, 2));
+        double rho = sqrt(1.0 - zz * zz);
+        z[0] = rho * cos(phi); z[1] = rho * sin(phi); z[2] = zz;
+        return;
+    }
+    /* d >= 4: Box-Muller on pairs of words (1,2), (3,4), (5,6), then normalise */
+    double g[OR_MAX_DIM + 1], nrm = 0.0;
+    for (int j = 0; 2 * j < d; ++j) {
+        double ua = or_u01(or_word(r, step, chain, 1 + 2 * j));
+        double ub = or_u01(or_word(r, step, chain, 2 + 2 * j));
+        double rho = sqrt(-2.0 * log(ua));
+        g[2 * j] = rho * cos(2.0 * M_PI * ub);
+        g[2 * j + 1] = rho * sin(2.0 * M_PI * ub);
+    }
+    for (int k = 0; k < d; ++k) nrm += g[k] * g[k];
+    nrm = sqrt(nrm);
+    for (int k = 0; k < d; ++k) z[k] = g[k] / nrm;
+}
+
+/* index of the word that picks one of q intersections */
+static int or_choice_word(int d) { return d == 2 ? 2 : (d == 3 ? 3 : (d == 4 ? 5 : 7)); }
+
+/* uniform point on dOmega_h (Eq. naive_woi_p0; by surface measure) */
+static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, int chain, double *y)
+{
+    int d = P->dim;
+    if (P->type[h] == OR_SPHERE) {
+        double z[OR_MAX_DIM];
+        or_direction(r, d, step, chain, z);
+        const double *c = or_center(P, h);
+        for (int k = 0; k < d; ++k) y[k] = c[k] + P->radius[h] * z[k];
+    } else {
+        double s = or_u01(or_word(r, step, chain, 1)) * P->area[h];
+        double t = or_star_invert(P, h, s, 0.0, 2.0 * M_PI);
+        or_star_point(P, h, t, y);
+    }
+}
+
+/* uniform point on dOmega_h^+ (part = 0) or dOmega_h^- (part = 1): the arcs of
+ * the requested sign are concatenated in increasing parameter angle */
+static void or_uniform_part_point(const or_problem *P, int h, int part, or_rng *r, int step, int chain,
+                                  double *y)
+{
+    double s = or_u01(or_word(r, step, chain, 1)) * P->part_len[2 * h + part];
+    int want = part == 0 ? 1 : -1, last = -1;
+    for (int a = P->arc_off[h]; a < P->arc_off[h] + P->arc_n[h]; ++a) {
+        if (P->arc_sign[a] != want) continue;
+        last = a;
+        if (s < P->arc_len[a]) break;
+        s -= P->arc_len[a];
+    }
+    int a = last;
+    if (s > P->arc_len[a]) s = P->arc_len[a];
+    double t;
+    if (P->type[h] == OR_SPHERE) {
+        t = P->arc_t0[a] + s / P->radius[h];
+        const double *c = or_center(P, h);
+        y[0] = c[0] + P->radius[h] * cos(t);
+        y[1] = c[1] + P->radius[h] * sin(t);
+    } else {
+        double s0 = or_star_arclen(P, h, P->arc_t0[a]);
+        t = or_star_invert(P, h, s0 + s, P->arc_t0[a], P->arc_t1[a]);
+        or_star_point(P, h, t, y);
+    }
+}
+
+/* intersections y + t z of the line (ray = 0) or ray (ray = 1) with dOmega_h.
+ * Line: t != 0 (the start point itself is excluded), ray: t > 0.  Returns q
+ * and the parameters sorted increasingly. */
+static int or_intersections(const or_problem *P, int h, const double *y, const double *z, int ray,
+                            double *ts)
+{
+    int d = P->dim, q = 0;
+    const double tiny = 1e-9;
+    if (P->type[h] == OR_SPHERE) {
+        const double *c = or_center(P, h);
+        double b = 0.0, c0 = 0.0, R = P->radius[h];
+        for (int k = 0; k < d; ++k) {
+            b += z[k] * (y[k] - c[k]);
+            c0 += (y[k] - c[k]) * (y[k] - c[k]);
+        }
+        c0 -= R * R;
+        double disc = b * b - c0;
+        if (disc < 0.0) return 0;
+        double sq = sqrt(disc);
+        double qq = -(b + (b >= 0 ? sq : -sq));     /* stable quadratic roots */
+        double r1 = qq, r2 = (qq != 0.0) ? c0 / qq : 0.0;
+        double cand[2] = {r1 < r2 ? r1 : r2, r1 < r2 ? r2 : r1};
+        for (int j = 0; j < 2; ++j) {
+            double t = cand[j];
+            if (ray ? (t > tiny * R) : (fabs(t) > tiny * R)) ts[q++] = t;
+        }
+        return q;
+    }
+    /* star: roots in the parameter angle of cross(gamma(t) - y, z) = 0, by a
+     * dense sign scan and bisection, then the line parameter of each root */
+    double f_prev = 0.0, t_prev = 0.0;
+    double pt[2];
+    const double *scan = P->star_scan + (size_t)h * (OR_STAR_SCAN + 1) * 2;
+    for (int j = 0; j <= OR_STAR_SCAN; ++j) {
+        double th = 2.0 * M_PI * j / OR_STAR_SCAN;
+        double f = (scan[2 * j] - y[0]) * z[1] - (scan[2 * j + 1] - y[1]) * z[0];
+        if (j > 0 && ((f_prev < 0.0) != (f < 0.0))) {
+            double lo = t_prev, hi = th, flo = f_prev;
+            for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+                double m = 0.5 * (lo + hi);
+                or_star_point(P, h, m, pt);
+                double fm = (pt[0] - y[0]) * z[1] - (pt[1] - y[1]) * z[0];
+                if ((fm < 0.0) == (flo < 0.0)) { lo = m; flo = fm; } else hi = m;
+            }
+            double tr = 0.5 * (lo + hi);
+            or_star_point(P, h, tr, pt);
+            double t = (pt[0] - y[0]) * z[0] + (pt[1] - y[1]) * z[1];
+            if ((ray ? (t > tiny) : (fabs(t) > tiny)) && q < OR_MAX_ROOTS) ts[q++] = t;
+        }
+        f_prev = f; t_prev = th;
+    }
+    /* insertion sort by t */
+    for (int a = 1; a < q; ++a) {
+        double v = ts[a];
+        int b = a - 1;
+        while (b >= 0 && ts[b] > v) { ts[b + 1] = ts[b]; --b; }
+        ts[b + 1] = v;
+    }
+    return q;
+}
+
+/* ------------------------------------------------------------------------ */
+/* boundary data b_i and beta_i (Sec. 1, Sec. 3)                             */
+/* ------------------------------------------------------------------------ */
+
+/* orthonormal real spherical harmonic Y_l^m at a unit vector u (3D), with
+ * the convention sin(phi) cos(theta) = sqrt(4 pi / 3) Y_1^1 (Example 3, 3D):
+ * no Condon-Shortley phase, theta azimuth, phi polar. */
+static double or_real_sh(int l, int m, const double *u)
+{
+    int am = m < 0 ? -m : m;
+    double x = u[2];                       /* cos(phi) */
+    double sx = sqrt(fmax(0.0, 1.0 - x * x));
+    double pmm = 1.0;                      /* P_am^am without the (-1)^m phase */
+    for (int k = 1; k <= am; ++k) pmm *= (2.0 * k - 1.0) * sx;
+    double plm;
+    if (l == am) {
+        plm = pmm;
+    } else {
+        double p1 = x * (2.0 * am + 1.0) * pmm, p0 = pmm;
+        plm = p1;
+        for (int ll = am + 2; ll <= l; ++ll) {
+            plm = ((2.0 * ll - 1.0) * x * p1 - (ll + am - 1.0) * p0) / (ll - am);
+            p0 = p1; p1 = plm;
+        }
+    }
+    double ratio = 1.0;                    /* (l-am)! / (l+am)! */
+    for (int k = l - am + 1; k <= l + am; ++k) ratio /= k;
+    double nlm = sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * ratio);
+    double az = atan2(u[1], u[0]);
+    if (m == 0) return nlm * plm;
+    if (m > 0) return sqrt(2.0) * nlm * plm * cos(am * az);
+    return sqrt(2.0) * nlm * plm * sin(am * az);
+}
+
+/* flux datum b_h(y) at a point y of dOmega_h */
+static double or_flux(const or_problem *P, int h, const double *y)
+{
+    int d = P->dim, n = P->flux_n[h];
+    const double *c = P->flux_coef + P->flux_off[h];
+    switch (P->flux_basis[h]) {
+    case OR_FLUX_FOURIER: { /* [a0, a1, b1, ..., aK, bK] in the local parameter angle */
+        double t = (P->type[h] == OR_SPHERE)
+                       ? atan2(y[1] - or_center(P, h)[1], y[0] - or_center(P, h)[0])
+                       : or_param_angle(P, h, y);
+        double v = c[0];
+        for (int k = 1; 2 * k <= n - 1; ++k) v += c[2 * k - 1] * cos(k * t) + c[2 * k] * sin(k * t);
+        return v;
+    }
+    case OR_FLUX_REAL_SH: { /* coef[l*l + l + m] */
+        double u[3];
+        const double *cc = or_center(P, h);
+        for (int k = 0; k < 3; ++k) u[k] = (y[k] - cc[k]) / P->radius[h];
+        double nn = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        for (int k = 0; k < 3; ++k) u[k] /= nn;
+        double v = 0.0;
+        for (int idx = 0; idx < n; ++idx) {
+            if (c[idx] == 0.0) continue;
+            int l = (int)floor(sqrt((double)idx) + 1e-9);
+            int m = idx - l * l - l;
+            v += c[idx] * or_real_sh(l, m, u);
+        }
+        return v;
+    }
+    case OR_FLUX_HARMONIC_POLY: { /* [s, T, (c, e_1..e_d) x T]: b = s n . grad P */
+        double s = c[0];
+        int T = (int)c[1];
+        double nrm[OR_MAX_DIM], grad[OR_MAX_DIM] = {0};
+        or_normal(P, h, y, nrm);
+        for (int t = 0; t < T; ++t) {
+            const double *row = c + 2 + t * (d + 1);
+            for (int k = 0; k < d; ++k) {
+                int ek = (int)row[1 + k];
+                if (ek == 0) continue;
+                double term = row[0] * ek;
+                for (int j = 0; j < d; ++j) {
+                    int e = (int)row[1 + j] - (j == k ? 1 : 0);
+                    for (int p = 0; p < e; ++p) term *= y[j];
+                }
+                grad[k] += term;
+            }
+        }
+        double v = 0.0;
+        for (int k = 0; k < d; ++k) v += nrm[k] * grad[k];
+        return s * v;
+    }
+    default:
+        return 0.0;
+    }
+}
+
+static double or_beta(const or_problem *P, int h, const double *y)
+{
+    double sc = P->beta_scale[h];
+    if (or_mutant == 6 && h > 0) sc = -sc;
+    return sc * or_flux(P, h, y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* one walk (Algorithm 2; Algorithm 3 when variant = 1)                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int *H;          /* [M+1] scheduled interfaces (0-based), or NULL */
+    double *Y;       /* [2][M+1][dim] states of each chain, or NULL */
+    double *scale;   /* [2]: sum_i |c_i Phi_i| and sum_i |c_i| (both chains) */
+} or_trace;
+
+/* H_i: 0-based index; i = 0 uniform over the N surfaces, i >= 1 by |alpha| */
+static int or_schedule_from_word(const or_problem *P, int i, uint32_t w)
+{
+    if (i == 0 && or_mutant != 9) return (int)(((uint64_t)w * (uint64_t)P->n_surf) >> 32);
+    for (int n = 0; n < P->n_surf; ++n)
+        if ((uint64_t)w < P->thresh[n]) return n;
+    return P->n_surf - 1;
+}
+
+static int or_relation(const or_problem *P, int prev, int cur)
+{
+    if (prev == cur) return OR_REL_SAME;
+    if (P->is_desc[prev * P->n_surf + cur]) return OR_REL_DESC;
+    return OR_REL_OTHER;
+}
+
+void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t point_id, uint32_t instance,
+             uint64_t walk, uint64_t seed, double *out_u, double *out_g, or_trace *tr)
+{
+    const int d = P->dim, M = o->M, N = P->n_surf;
+    const int n_chain = o->variant == 1 ? 2 : 1;
+    or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32) ^ instance}, walk, -1, -1, -1, {0}};
+    uint64_t group = walk / (uint64_t)o->sched_group;
+    double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0}, sc_phi = 0.0, sc_c = 0.0;
+
+    double y[2][OR_MAX_DIM], Q[2], T[2];
+    int alive[2] = {1, 1};
+    double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m})  (reading R1) */
+    double Ai = 1.0;         /* ||alpha||_1^i */
+    int h_prev = -1;
+
+    for (int i = 0; i <= M; ++i) {
+        const double weight = (i == M && or_mutant != 3) ? 0.5 : 1.0; /* w_i = 1 - delta_{iM}/2 */
+        uint32_t hw;
+        if (o->sched_group == 1) {
+            hw = or_word(&rng, i, 0, 0);
+        } else {
+            uint32_t ctr[4] = {(uint32_t)group, (uint32_t)(group >> 32), (uint32_t)i, 0x100u}, w4[4];
+            or_philox4x32_10(ctr, rng.key, w4);
+            hw = w4[0];
+        }
+        const int h = or_schedule_from_word(P, i, hw);
+        if (tr && tr->H) tr->H[i] = h;
+
+        if (i > 0 || or_mutant == 2) {
+            if (i > 0) Ai *= P->alpha_l1;
+            S *= (P->alpha[h] > 0.0) ? 1.0 : ((P->alpha[h] < 0.0) ? -1.0 : 0.0);
+        }
+
+        for (int k = 0; k < n_chain; ++k) {
+            if (i == 0) {
+                /* p0: uniform on dOmega_{h0} (plain) or on dOmega^{+/-} (Alg. 3) */
+                T[k] = 1.0;
+                if (o->variant == 0) {
+                    or_uniform_point(P, h, &rng, 0, k, y[k]);
+                    Q[k] = or_beta(P, h, y[k]) * P->area[h];
+                } else {
+                    double L = P->part_len[2 * h + k];
+                    if (L <= 0.0 || P->flux_basis[h] == OR_FLUX_ZERO) {
+                        /* empty part, or beta = 0 on the whole surface: the chain carries no weight */
+                        alive[k] = 0; Q[k] = 0.0;
+                        for (int c = 0; c < d; ++c) y[k][c] = 0.0;
+                    } else {
+                        or_uniform_part_point(P, h, k, &rng, 0, k, y[k]);
+                        Q[k] = or_beta(P, h, y[k]) * L;
+                    }
+                }
+            } else if (alive[k]) {
+                const int rel = or_relation(P, h_prev, h);
+                double ynew[OR_MAX_DIM];
+                if (rel == OR_REL_OTHER) {
+                    /* uniform on dOmega_h; Q *= K*(y_i, y_{i-1}) |dOmega_h|; T unchanged (R2, R3) */
+                    or_uniform_point(P, h, &rng, i, k, ynew);
+                    double nrm[OR_MAX_DIM], dot = 0.0;
+                    if (or_mutant == 5) {
+                        or_normal(P, h_prev, y[k], nrm);
+                        for (int c = 0; c < d; ++c) dot += (y[k][c] - ynew[c]) * nrm[c];
+                    } else {
+                        or_normal(P, h, ynew, nrm);
+                        for (int c = 0; c < d; ++c) dot += (ynew[c] - y[k][c]) * nrm[c];
+                    }
+                    double r = or_dist(d, ynew, y[k]);
+                    double kstar = dot / (or_omega(d) * pow(r, (double)d));
+                    Q[k] *= kstar * P->area[h];
+                    if (or_mutant == 1) T[k] *= dot > 0.0 ? 1.0 : -1.0;
+                } else {
+                    /* isotropic line (same interface) or ray (from a descendant) */
+                    double z[OR_MAX_DIM], ts[OR_MAX_ROOTS];
+                    or_direction(&rng, d, i, k, z);
+                    int q = or_intersections(P, h, y[k], z, rel == OR_REL_DESC, ts);
+                    if (q == 0) {            /* reading R5 */
+                        alive[k] = 0; T[k] = 0.0;
+                        continue;
+                    }
+                    uint32_t cw = or_word(&rng, i, k, or_choice_word(d));
+                    int j = (int)(((uint64_t)cw * (uint64_t)q) >> 32);
+                    for (int c = 0; c < d; ++c) ynew[c] = y[k][c] + ts[j] * z[c];
+                    double nrm[OR_MAX_DIM], dot = 0.0;
+                    or_normal(P, h, ynew, nrm);
+                    for (int c = 0; c < d; ++c) dot += (ynew[c] - y[k][c]) * nrm[c];
+                    double sg = dot > 0.0 ? 1.0 : (dot < 0.0 ? -1.0 : 0.0);
+                    if (rel == OR_REL_SAME && or_mutant != 7) Q[k] *= 0.5;
+                    T[k] *= (double)q * sg;
+                }
+                for (int c = 0; c < d; ++c) y[k][c] = ynew[c];
+            }
+            if (tr && tr->Y)
+                for (int c = 0; c < d; ++c) tr->Y[((size_t)k * (M + 1) + i) * d + c] = y[k][c];
+            if (!alive[k]) continue;
+            /* tally: N w_i ||alpha||^i prod sign(alpha) Q T Phi(x, y_i), and grad_x Phi */
+            double coef = (or_mutant == 4 ? 1.0 : (double)N) * weight * Ai * S * Q[k] * T[k];
+            double phi = or_phi(d, x, y[k]), g[OR_MAX_DIM];
+            or_grad_phi(d, x, y[k], g);
+            acc_u += coef * phi;
+            for (int c = 0; c < d; ++c) acc_g[c] += coef * g[c];
+            sc_phi += fabs(coef * phi);
+            sc_c += fabs(coef);
+        }
+        h_prev = h;
+    }
+    *out_u = acc_u;
+    for (int c = 0; c < d; ++c) out_g[c] = acc_g[c];
+    if (tr && tr->scale) { tr->scale[0] = sc_phi; tr->scale[1] = sc_c; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* estimator over points (Algorithm 1): per point the walk sum and the       */
+/* sums of the schedule-group means and of their squares                    */
+/* ------------------------------------------------------------------------ */
+int or_estimate(const or_problem *P, const or_opts *o, const double *points, int64_t n_pts, uint32_t instance,
+                uint64_t walk_begin, uint64_t walk_end, uint64_t seed, double *sum_f /* [n_pts][d+1] */,
+                double *sum_gm /* [n_pts][d+1] */, double *sum_gm2 /* [n_pts][d+1] */, int64_t *n_groups)
+{
+    const int d = P->dim, W_g = o->sched_group;
+    if (W_g < 1 || walk_begin % (uint64_t)W_g != 0 || walk_end % (uint64_t)W_g != 0) return 1;
+    int64_t G = (int64_t)((walk_end - walk_begin) / (uint64_t)W_g);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < n_pts; ++p) {
+        const double *x = points + (size_t)p * d;
+        double sf[OR_MAX_DIM + 1] = {0}, sm[OR_MAX_DIM + 1] = {0}, sm2[OR_MAX_DIM + 1] = {0};
+        for (uint64_t g0 = walk_begin; g0 < walk_end; g0 += (uint64_t)W_g) {
+            double gs[OR_MAX_DIM + 1] = {0};
+            for (int j = 0; j < W_g; ++j) {
+                double fu, fg[OR_MAX_DIM];
+                or_walk(P, o, x, (uint32_t)p, instance, g0 + (uint64_t)j, seed, &fu, fg, NULL);
+                gs[0] += fu;
+                for (int c = 0; c < d; ++c) gs[1 + c] += fg[c];
+            }
+            for (int c = 0; c <= d; ++c) {
+                double m = gs[c] / W_g;
+                sf[c] += gs[c];
+                sm[c] += m;
+                sm2[c] += m * m;
+            }
+        }
+        for (int c = 0; c <= d; ++c) {
+            sum_f[p * (d + 1) + c] = sf[c];
+            sum_gm[p * (d + 1) + c] = sm[c];
+            sum_gm2[p * (d + 1) + c] = sm2[c];
+        }
+    }
+    *n_groups = G;
+    return 0;
+}
+
+/* per-walk values for pathwise replay: walks[w] for one point */
+void or_walks(const or_problem *P, const or_opts *o, const double *x, uint32_t point_id, uint32_t instance,
+              const uint64_t *walks, int64_t n_walks, uint64_t seed, double *out_u, double *out_g, int *out_H,
+              double *out_Y, double *out_scale)
+{
+    const int d = P->dim, M = o->M;
+    for (int64_t w = 0; w < n_walks; ++w) {
+        or_trace tr = {out_H ? out_H + w * (M + 1) : NULL, out_Y ? out_Y + (size_t)w * 2 * (M + 1) * d : NULL,
+                       out_scale ? out_scale + 2 * w : NULL};
+        or_walk(P, o, x, point_id, instance, walks[w], seed, out_u + w, out_g + w * d, &tr);
+    }
+}
+
+/* exposed for the tests of the building blocks */
+double or_test_real_sh(int l, int m, const double *u) { return or_real_sh(l, m, u); }
+double or_test_star_arclen(const or_problem *P, int h, double t) { return or_star_arclen(P, h, t); }
+int or_test_intersections(const or_problem *P, int h, const double *y, const double *z, int ray, double *ts)
+{
+    return or_intersections(P, h, y, z, ray, ts);
+}
+double or_test_flux(const or_problem *P, int h, const double *y) { return or_flux(P, h, y); }
+void or_test_uniform_point(const or_problem *P, int h, uint64_t seed, uint32_t point_id, uint64_t walk, int step,
+                           double *y)
+{
+    or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32)}, walk, -1, -1, -1, {0}};
+    or_uniform_point(P, h, &rng, step, 0, y);
+}
+void or_test_uniform_part_point(const or_problem *P, int h, int part, uint64_t seed, uint64_t walk, double *y)
+{
+    or_rng rng = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, walk, -1, -1, -1, {0}};
+    or_uniform_part_point(P, h, part, &rng, 0, part, y);
+}
+void or_test_direction(int d, uint64_t seed, uint64_t walk, int step, double *z)
+{
+    or_rng rng = {{(uint32_t)seed, (uint32_t)(seed >> 32)}, walk, -1, -1, -1, {0}};
+    or_direction(&rng, d, step, 0, z);
+}

@@ -1,0 +1,357 @@
+"""Seeded synthetic inputs for the Walk-on-Interfaces estimator.
+
+This module only builds problem descriptions (geometry, conductivities,
+boundary/interface flux data) and evaluation points.  It holds none of the
+estimator's arithmetic: no alpha/beta scaling, no schedule, no sampling.  The
+CUDA library and the CPU oracle both consume what it returns, each converting
+it with its own code.
+
+Problem dictionary (JSON-compatible):
+
+    dim       int, 2..6
+    surfaces  list of {"kind": "sphere" | "star", "center": [dim], "radius": R,
+              "star_a": [K+1], "star_b": [K+1]}  (star: 2D only,
+              r(t) = R (1 + sum_k a_k cos kt + b_k sin kt), index 0 unused)
+    parent    list of int, parent[0] = -1 (the outer boundary dOmega_1),
+              parent[i] = index of the region that contains region i
+    sigma     list of float, conductivity inside each region (sigma_1 > 0)
+    flux      list of {"basis": ..., "coef": [...]}:
+              "zero"           b = 0
+              "fourier"        [a0, a1, b1, ..., aK, bK] in the local parameter
+                               angle of a 2D circle or star
+              "real_sh"        coef[l*l + l + m], orthonormal real spherical
+                               harmonics of the unit direction from the centre (3D)
+              "harmonic_poly"  [s, T, (c, e_1..e_dim) x T]: b(y) = s n(y).grad P(y)
+                               with P(y) = sum c prod y_k^e_k harmonic
+    M         default truncation for this workload
+
+The recipes follow the synthetic workloads used to measure the estimator:
+nested layers (2D, 3D, 6D), a star-shaped domain with many small inclusions,
+and a batch of heterogeneous manufactured-solution instances.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def _sphere(center, radius):
+    return {"kind": "sphere", "center": [float(c) for c in center], "radius": float(radius)}
+
+
+def _star(center, radius, a, b):
+    return {"kind": "star", "center": [float(c) for c in center], "radius": float(radius),
+            "star_a": [float(v) for v in a], "star_b": [float(v) for v in b]}
+
+
+def fourier(coefs_cos, coefs_sin, a0=0.0):
+    """[a0, a1, b1, ..., aK, bK] from cos / sin coefficient lists (k = 1..K)."""
+    out = [float(a0)]
+    for a, b in zip(coefs_cos, coefs_sin):
+        out += [float(a), float(b)]
+    return {"basis": "fourier", "coef": out}
+
+
+def real_sh(coef_by_lm, lmax):
+    """coef[l*l + l + m] from a {(l, m): value} dict."""
+    out = [0.0] * ((lmax + 1) ** 2)
+    for (l, m), v in coef_by_lm.items():
+        out[l * l + l + m] = float(v)
+    return {"basis": "real_sh", "coef": out}
+
+
+def harmonic_poly(scale, terms, dim):
+    """b = scale * n . grad P with P = sum c * prod y_k^e_k; terms = [(c, (e_1..e_d)), ...]."""
+    out = [float(scale), float(len(terms))]
+    for c, e in terms:
+        assert len(e) == dim
+        out += [float(c)] + [float(v) for v in e]
+    return {"basis": "harmonic_poly", "coef": out}
+
+
+def zero_flux():
+    return {"basis": "zero", "coef": []}
+
+
+# ---------------------------------------------------------------------------
+# layered workloads
+# ---------------------------------------------------------------------------
+
+def concentric_2d_problem():
+    """Unit disk with a concentric inclusion r = 0.5, sigma = (1, 2), Neumann
+    flux cos(theta) on |x| = 1 and flux jump 0.5 cos(theta) on r = 0.5."""
+    return {
+        "name": "2d-concentric", "dim": 2,
+        "surfaces": [_sphere([0, 0], 1.0), _sphere([0, 0], 0.5)],
+        "parent": [-1, 0], "sigma": [1.0, 2.0],
+        "flux": [fourier([1.0], [0.0]), fourier([0.5], [0.0])],
+        "M": 4,
+    }
+
+
+def concentric_2d_points():
+    """64 points on a polar grid: r_k = (2k+1)/16, theta_j = pi/8 + j pi/4."""
+    pts = []
+    for k in range(8):
+        r = (2 * k + 1) / 16.0
+        for j in range(8):
+            t = math.pi / 8 + j * math.pi / 4
+            pts.append([r * math.cos(t), r * math.sin(t)])
+    return np.asarray(pts, dtype=np.float64)
+
+
+def nested_3d_problem(seed=2):
+    """Spheres r = 1, 0.8, 0.5 nested, sigma = (1, 5, 0.2); Neumann flux
+    Y_1^0 + 0.3 Y_2^1; flux jumps sum_m a_m Y_2^m with a ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    a2 = rng.standard_normal(5)
+    a3 = rng.standard_normal(5)
+    return {
+        "name": "3d-nested", "dim": 3,
+        "surfaces": [_sphere([0, 0, 0], 1.0), _sphere([0, 0, 0], 0.8), _sphere([0, 0, 0], 0.5)],
+        "parent": [-1, 0, 1], "sigma": [1.0, 5.0, 0.2],
+        "flux": [real_sh({(1, 0): 1.0, (2, 1): 0.3}, 2),
+                 real_sh({(2, m): a2[m + 2] for m in range(-2, 3)}, 2),
+                 real_sh({(2, m): a3[m + 2] for m in range(-2, 3)}, 2)],
+        "M": 6,
+    }
+
+
+def ball_points(n, dim, seed, radius=1.0):
+    """n points uniform in the ball of the given radius (r = R U^{1/d})."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n, dim))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    r = radius * rng.random(n) ** (1.0 / dim)
+    return g * r[:, None]
+
+
+def nested_6d_problem():
+    """6D hyperspheres r = 1, 0.6, sigma = (1, 4); Neumann flux x_1 on |x| = 1
+    and flux jump x_2 on the inner sphere (0.6 x_2/|x| there)."""
+    d = 6
+    e1 = tuple(1 if k == 0 else 0 for k in range(d))
+    e2 = tuple(1 if k == 1 else 0 for k in range(d))
+    return {
+        "name": "6d-nested", "dim": d,
+        "surfaces": [_sphere([0] * d, 1.0), _sphere([0] * d, 0.6)],
+        "parent": [-1, 0], "sigma": [1.0, 4.0],
+        "flux": [harmonic_poly(1.0, [(1.0, e1)], d), harmonic_poly(0.6, [(1.0, e2)], d)],
+        "M": 8,
+    }
+
+
+# ---------------------------------------------------------------------------
+# star-shaped domain with many inclusions
+# ---------------------------------------------------------------------------
+
+def _star_radius(a, b, t):
+    s = np.ones_like(t)
+    for k in range(1, len(a)):
+        s = s + a[k] * np.cos(k * t) + b[k] * np.sin(k * t)
+    return s
+
+
+def _star_curve(a, b, n=4096):
+    t = np.linspace(0.0, 2 * np.pi, n, endpoint=False)
+    r = _star_radius(a, b, t)
+    return t, np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
+
+
+def _inside_star(a, b, p):
+    t = np.arctan2(p[..., 1], p[..., 0])
+    return np.linalg.norm(p, axis=-1) < _star_radius(a, b, t)
+
+
+def star_inclusions_problem(seed=3, n_incl=32, star_amp=0.15, star_k=5):
+    """Star r(t) = 1 + 0.15 cos 5t with 32 circles (radii U[0.03, 0.08], a
+    gap >= 0.02 to each other and to the star), sigma_1 = 1, sigma_i
+    log-uniform on [0.1, 10]; flux jumps are random trig polynomials of degree
+    <= 4 with N(0,1) coefficients in the local angle (zero mean); the Neumann
+    flux is the same in the global angle minus its arc-length mean."""
+    rng = np.random.default_rng(seed)
+    a = [0.0] * (star_k + 1)
+    b = [0.0] * (star_k + 1)
+    a[star_k] = star_amp
+    _, curve = _star_curve(a, b)
+    circles = []
+    tries = 0
+    while len(circles) < n_incl and tries < 200000:
+        tries += 1
+        rad = rng.uniform(0.03, 0.08)
+        c = rng.uniform(-1.2, 1.2, size=2)
+        if not _inside_star(a, b, c):
+            continue
+        if np.min(np.linalg.norm(curve - c, axis=1)) < rad + 0.02:
+            continue
+        if any(np.linalg.norm(c - c2) < rad + r2 + 0.02 for c2, r2 in circles):
+            continue
+        circles.append((c, rad))
+    surfaces = [_star([0, 0], 1.0, a, b)] + [_sphere(c, r) for c, r in circles]
+    n = len(surfaces)
+    sigma = [1.0] + list(np.exp(rng.uniform(math.log(0.1), math.log(10.0), n - 1)))
+    flux = []
+    # Neumann flux in the global angle, projected to zero arc-length mean
+    ca, cb = rng.standard_normal(4), rng.standard_normal(4)
+    t = np.linspace(0.0, 2 * np.pi, 8192, endpoint=False)
+    r = _star_radius(a, b, t)
+    dr = sum(-k * a[k] * np.sin(k * t) + k * b[k] * np.cos(k * t) for k in range(1, len(a)))
+    speed = np.sqrt(r * r + dr * dr)
+    bt = sum(ca[k - 1] * np.cos(k * t) + cb[k - 1] * np.sin(k * t) for k in range(1, 5))
+    mean = float(np.sum(bt * speed) / np.sum(speed))
+    flux.append(fourier(ca, cb, a0=-mean))
+    for _ in range(n - 1):
+        flux.append(fourier(rng.standard_normal(4), rng.standard_normal(4)))
+    return {"name": "2d-star-inclusions", "dim": 2, "surfaces": surfaces,
+            "parent": [-1] + [0] * (n - 1), "sigma": [float(s) for s in sigma], "flux": flux, "M": 4}
+
+
+def star_inclusions_points(problem, n, seed=13, near_frac=0.3, band=0.01):
+    """n points in the star domain: (1 - near_frac) uniform by rejection and
+    near_frac within `band` of a surface (a random surface chosen by length, a
+    random point on it, a normal offset U[-band, band]), all kept inside."""
+    rng = np.random.default_rng(seed)
+    star = problem["surfaces"][0]
+    a, b = star["star_a"], star["star_b"]
+    n_near = int(round(near_frac * n))
+    n_far = n - n_near
+    pts = []
+    while len(pts) < n_far:
+        p = rng.uniform(-1.2, 1.2, size=(4 * n_far, 2))
+        pts += list(p[_inside_star(a, b, p)])
+    pts = pts[:n_far]
+    lengths = []
+    for s in problem["surfaces"]:
+        if s["kind"] == "star":
+            t, c = _star_curve(a, b)
+            lengths.append(float(np.sum(np.linalg.norm(np.roll(c, -1, 0) - c, axis=1))))
+        else:
+            lengths.append(2 * np.pi * s["radius"])
+    prob = np.asarray(lengths) / np.sum(lengths)
+    near = []
+    while len(near) < n_near:
+        i = rng.choice(len(lengths), p=prob)
+        s = problem["surfaces"][i]
+        t = rng.uniform(0, 2 * np.pi)
+        off = rng.uniform(-band, band)
+        if s["kind"] == "star":
+            rr = _star_radius(a, b, np.array([t]))[0]
+            p = np.array([rr * np.cos(t), rr * np.sin(t)])
+            q = _star_radius(a, b, np.array([t + 1e-6]))[0]
+            tang = np.array([q * np.cos(t + 1e-6), q * np.sin(t + 1e-6)]) - p
+            nrm = np.array([tang[1], -tang[0]]) / np.linalg.norm(tang)
+        else:
+            nrm = np.array([np.cos(t), np.sin(t)])
+            p = np.asarray(s["center"]) + s["radius"] * nrm
+        p = p + off * nrm
+        if _inside_star(a, b, p[None, :])[0]:
+            near.append(p)
+    out = np.asarray(pts + near, dtype=np.float64)
+    return out[rng.permutation(len(out))]
+
+
+# ---------------------------------------------------------------------------
+# batch of heterogeneous manufactured-solution instances
+# ---------------------------------------------------------------------------
+
+def _harmonic_basis(dim):
+    """Monomial expansions of a basis of harmonic polynomials of degree 1..3."""
+    def mono(*pairs):
+        return [(c, e) for c, e in pairs]
+    if dim == 2:
+        return [mono((1.0, (1, 0))), mono((1.0, (0, 1))),
+                mono((1.0, (2, 0)), (-1.0, (0, 2))), mono((2.0, (1, 1))),
+                mono((1.0, (3, 0)), (-3.0, (1, 2))), mono((3.0, (2, 1)), (-1.0, (0, 3)))]
+    return [mono((1.0, (1, 0, 0))), mono((1.0, (0, 1, 0))), mono((1.0, (0, 0, 1))),
+            mono((1.0, (2, 0, 0)), (-1.0, (0, 2, 0))), mono((1.0, (2, 0, 0)), (-1.0, (0, 0, 2))),
+            mono((1.0, (1, 1, 0))), mono((1.0, (1, 0, 1))), mono((1.0, (0, 1, 1))),
+            mono((1.0, (1, 1, 1))),
+            mono((1.0, (3, 0, 0)), (-3.0, (1, 2, 0))), mono((1.0, (3, 0, 0)), (-3.0, (1, 0, 2))),
+            mono((1.0, (0, 3, 0)), (-3.0, (2, 1, 0))), mono((1.0, (0, 3, 0)), (-3.0, (0, 1, 2))),
+            mono((1.0, (0, 0, 3)), (-3.0, (2, 0, 1))), mono((1.0, (0, 0, 3)), (-3.0, (0, 2, 1)))]
+
+
+def random_harmonic_poly(dim, rng):
+    """A random harmonic polynomial of degree <= 3 as merged monomial terms."""
+    terms = {}
+    for poly in _harmonic_basis(dim):
+        w = rng.standard_normal()
+        for c, e in poly:
+            terms[e] = terms.get(e, 0.0) + w * c
+    return [(c, e) for e, c in sorted(terms.items()) if c != 0.0]
+
+
+def eval_poly(terms, x):
+    """P(x) and grad P(x) of a monomial expansion at points x [n, dim]."""
+    x = np.atleast_2d(x)
+    n, d = x.shape
+    v = np.zeros(n)
+    g = np.zeros((n, d))
+    for c, e in terms:
+        v += c * np.prod(x ** np.asarray(e), axis=1)
+        for k in range(d):
+            if e[k] == 0:
+                continue
+            ee = list(e)
+            ee[k] -= 1
+            g[:, k] += c * e[k] * np.prod(x ** np.asarray(ee), axis=1)
+    return v, g
+
+
+def manufactured_instance(dim, rng, k_max=64, r_lo=0.02, r_hi=0.15, gap=0.01, max_tries=10000):
+    """Unit disk/ball with k ~ U{1..k_max} non-overlapping circles/spheres
+    (radii U[r_lo, r_hi]; on rejection failure the count is reduced and
+    recorded), sigma_1 = 1, sigma_i log-uniform on [0.05, 20], and flux data
+    of the manufactured solution u_h (harmonic, degree <= 3):
+    b_1 = sigma_1 dn u_h, b_i = (sigma_parent - sigma_i) dn u_h."""
+    k_req = int(rng.integers(1, k_max + 1))
+    incl = []
+    tries = 0
+    while len(incl) < k_req and tries < max_tries:
+        tries += 1
+        rad = rng.uniform(r_lo, r_hi)
+        g = rng.standard_normal(dim)
+        g /= np.linalg.norm(g)
+        c = g * (1.0 - rad - gap) * rng.random() ** (1.0 / dim)
+        if np.linalg.norm(c) + rad + gap > 1.0:
+            continue
+        if any(np.linalg.norm(c - c2) < rad + r2 + gap for c2, r2 in incl):
+            continue
+        incl.append((c, rad))
+    n = 1 + len(incl)
+    sigma = [1.0] + list(np.exp(rng.uniform(math.log(0.05), math.log(20.0), n - 1)))
+    uh = random_harmonic_poly(dim, rng)
+    flux = [harmonic_poly(sigma[0], uh, dim)]
+    for i in range(1, n):
+        flux.append(harmonic_poly(sigma[0] - sigma[i], uh, dim))
+    return {"name": f"batch-{dim}d", "dim": dim,
+            "surfaces": [_sphere([0.0] * dim, 1.0)] + [_sphere(c, r) for c, r in incl],
+            "parent": [-1] + [0] * (n - 1), "sigma": [float(s) for s in sigma], "flux": flux,
+            "M": 4 if dim == 2 else 6, "u_h": uh, "k_requested": k_req}
+
+
+def batch_instances(n_inst=256, seed=5, k_max=64, p_range=(16, 4096), w_range=(1e4, 1e5), point_seed=15):
+    """n_inst instances, alternating 2D / 3D, with per-instance point counts
+    log-uniform on p_range and walk counts log-uniform on w_range (rounded to a
+    multiple of 32)."""
+    rng = np.random.default_rng(seed)
+    prng = np.random.default_rng(point_seed)
+    out = []
+    for i in range(n_inst):
+        dim = 2 if i % 2 == 0 else 3
+        prob = manufactured_instance(dim, rng, k_max=k_max)
+        P = int(round(math.exp(rng.uniform(math.log(p_range[0]), math.log(p_range[1])))))
+        W = int(round(math.exp(rng.uniform(math.log(w_range[0]), math.log(w_range[1]))) / 32.0)) * 32
+        pts = ball_points(P, dim, int(prng.integers(0, 2**31)))
+        out.append({"problem": prob, "points": pts, "n_walks": max(W, 32)})
+    return out
+
+
+CONFIGS = {
+    "2d-concentric": "unit disk + r=0.5 inclusion, 64 polar-grid points, W=1e4, M=4",
+    "3d-nested": "spheres 1/0.8/0.5, sigma 1/5/0.2, 4096 ball points, W=1e5, M=6",
+    "2d-star-inclusions": "star + 32 circles, 16384 points (30% near surfaces), W=1e5, M=4",
+    "6d-nested": "hyperspheres 1/0.6, sigma 1/4, 1024 ball points, W=1e6, M=8",
+    "batch": "256 manufactured 2D/3D instances, 1-64 inclusions, P 16..4096, W 1e4..1e5",
+}

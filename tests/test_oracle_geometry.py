@@ -1,0 +1,176 @@
+"""Pins of the oracle's geometric and boundary-data building blocks (CPU):
+intersections against brute force, arc length against adaptive quadrature,
+uniform sampling by surface measure, real spherical harmonics against scipy
+and the identity printed for Example 3 (3D), harmonic-polynomial flux against
+a finite-difference normal derivative."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize, special, stats
+
+from paper_2508_16767_gb300 import workloads as wl
+
+
+def star_problem(amp=0.15, k=5):
+    a = [0.0] * (k + 1)
+    b = [0.0] * (k + 1)
+    a[k] = amp
+    b[2] = 0.05
+    return {"name": "star", "dim": 2,
+            "surfaces": [{"kind": "star", "center": [0.1, -0.2], "radius": 1.0, "star_a": a, "star_b": b},
+                         {"kind": "sphere", "center": [0.3, 0.1], "radius": 0.2}],
+            "parent": [-1, 0], "sigma": [1.0, 3.0],
+            "flux": [wl.fourier([0.3, -0.2], [0.5, 0.1], a0=0.0), wl.fourier([1.0, 0.5], [-0.3, 0.2])],
+            "M": 3}
+
+
+def star_xy(s, t):
+    a, b = s["star_a"], s["star_b"]
+    r = s["radius"] * (1 + sum(a[k] * np.cos(k * t) + b[k] * np.sin(k * t) for k in range(1, len(a))))
+    return np.asarray(s["center"])[:, None] + np.stack([r * np.cos(t), r * np.sin(t)])
+
+
+def brute_star_line(s, y, z, ray):
+    """All intersections by a 400k-sample scan of the curve and Brent refinement."""
+    t = np.linspace(0, 2 * np.pi, 400001)
+    p = star_xy(s, t)
+    f = (p[0] - y[0]) * z[1] - (p[1] - y[1]) * z[0]
+    out = []
+    for j in np.nonzero(np.signbit(f[:-1]) != np.signbit(f[1:]))[0]:
+        g = lambda th: float((star_xy(s, np.array([th]))[0, 0] - y[0]) * z[1]
+                             - (star_xy(s, np.array([th]))[1, 0] - y[1]) * z[0])
+        th = optimize.brentq(g, t[j], t[j + 1], xtol=1e-15)
+        q = star_xy(s, np.array([th]))[:, 0]
+        tt = float(np.dot(q - y, z))
+        if (tt > 1e-9) if ray else (abs(tt) > 1e-9):
+            out.append(tt)
+    return np.sort(out)
+
+
+def test_star_intersections_match_brute_force(oracle_core):
+    prob = star_problem(amp=0.3)
+    s = prob["surfaces"][0]
+    prep = oracle_core.Prepared(prob)
+    rng = np.random.default_rng(0)
+    n_multi = 0
+    for trial in range(100):
+        z = rng.standard_normal(2)
+        z /= np.linalg.norm(z)
+        if trial % 2 == 0:        # line through a point of the curve
+            th = rng.uniform(0, 2 * np.pi)
+            y = star_xy(s, np.array([th]))[:, 0]
+            ray = False
+        else:                     # ray from an interior point
+            y = np.asarray(s["center"]) + rng.uniform(-0.5, 0.5, 2)
+            ray = True
+        ts = oracle_core.intersections(prob, 0, y, z, ray, prepared=prep)
+        ref = brute_star_line(s, y, z, ray)
+        assert len(ts) == len(ref)
+        assert np.allclose(ts, ref, atol=1e-10)
+        n_multi += len(ts) > 1
+    assert n_multi > 5   # the star is non-convex: several crossings occur
+
+
+def test_sphere_intersections(oracle_core):
+    for d in [2, 3, 6]:
+        prob = {"dim": d, "surfaces": [{"kind": "sphere", "center": [0.1] * d, "radius": 0.7}],
+                "parent": [-1], "sigma": [1.0], "flux": [wl.zero_flux()], "M": 1}
+        rng = np.random.default_rng(d)
+        c = np.full(d, 0.1)
+        for _ in range(20):
+            z = rng.standard_normal(d); z /= np.linalg.norm(z)
+            u = rng.standard_normal(d); u /= np.linalg.norm(u)
+            y = c + 0.7 * u                            # on the sphere: the line hits once more
+            ts = oracle_core.intersections(prob, 0, y, z, False)
+            assert len(ts) == 1
+            assert abs(np.linalg.norm(y + ts[0] * z - c) - 0.7) < 1e-12
+            assert abs(ts[0] + 2 * np.dot(z, y - c)) < 1e-12
+            y2 = c + 0.3 * u                           # inside: the ray exits once
+            ts = oracle_core.intersections(prob, 0, y2, z, True)
+            assert len(ts) == 1 and ts[0] > 0
+            assert abs(np.linalg.norm(y2 + ts[0] * z - c) - 0.7) < 1e-12
+
+
+def test_star_arclength_matches_quadrature(oracle_core):
+    prob = star_problem()
+    s = prob["surfaces"][0]
+    prep = oracle_core.Prepared(prob)
+    speed = lambda t: np.linalg.norm(np.gradient(star_xy(s, np.array([t - 1e-6, t, t + 1e-6])), 1e-6, axis=1)[:, 1])
+    for t in [0.3, 1.7, 3.1, 4.9, 2 * np.pi]:
+        ref, _ = integrate.quad(speed, 0, t, epsabs=1e-12, limit=400)
+        assert abs(oracle_core.star_arclen(prob, 0, t, prepared=prep) - ref) < 1e-7
+    assert abs(prep.area[0] - oracle_core.star_arclen(prob, 0, 2 * np.pi, prepared=prep)) < 1e-12
+
+
+def test_uniform_on_star_by_arclength(oracle_core):
+    """Eq. naive_woi_p0: y_0 uniform by surface measure; the arc-length
+    coordinate of the samples is U(0, L) (KS test)."""
+    prob = star_problem()
+    prep = oracle_core.Prepared(prob)
+    y = oracle_core.uniform_points(prob, 0, 4000, seed=5, prepared=prep)
+    c = np.asarray(prob["surfaces"][0]["center"])
+    th = np.mod(np.arctan2(y[:, 1] - c[1], y[:, 0] - c[0]), 2 * np.pi)
+    s = np.array([oracle_core.star_arclen(prob, 0, t, prepared=prep) for t in th]) / prep.area[0]
+    assert stats.kstest(s, "uniform").pvalue > 1e-3
+    # the samples lie on the curve
+    assert np.allclose(star_xy(prob["surfaces"][0], th).T, y, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [3, 6])
+def test_uniform_on_sphere(oracle_core, d):
+    prob = {"dim": d, "surfaces": [{"kind": "sphere", "center": [0.2] * d, "radius": 0.5}],
+            "parent": [-1], "sigma": [1.0], "flux": [wl.zero_flux()], "M": 1}
+    y = oracle_core.uniform_points(prob, 0, 5000, seed=3)
+    u = (y - 0.2) / 0.5
+    assert np.allclose(np.linalg.norm(u, axis=1), 1.0, atol=1e-12)
+    # the first coordinate of a uniform point on S^{d-1} has density ∝ (1-x^2)^{(d-3)/2}
+    x = u[:, 0]
+    cdf = lambda v: stats.beta.cdf((v + 1) / 2, (d - 1) / 2, (d - 1) / 2)
+    assert stats.kstest(x, cdf).pvalue > 1e-3
+
+
+def test_real_sh_against_scipy_and_example3(oracle_core):
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        u = rng.standard_normal(3); u /= np.linalg.norm(u)
+        polar = math.acos(u[2]); az = math.atan2(u[1], u[0])
+        for l in range(0, 5):
+            for m in range(-l, l + 1):
+                Yc = special.sph_harm_y(l, abs(m), polar, az)  # complex, with the (-1)^m phase
+                if m == 0:
+                    ref = Yc.real
+                elif m > 0:
+                    ref = math.sqrt(2) * (-1) ** m * Yc.real
+                else:
+                    ref = math.sqrt(2) * (-1) ** m * Yc.imag
+                assert abs(oracle_core.real_sh(l, m, u) - ref) < 1e-12
+        # Example 3 (3D): sin(phi) cos(theta) = sqrt(4 pi / 3) Y_1^1
+        assert abs(math.sin(polar) * math.cos(az) - math.sqrt(4 * math.pi / 3) * oracle_core.real_sh(1, 1, u)) < 1e-13
+
+
+def test_harmonic_poly_flux_is_normal_derivative(oracle_core):
+    rng = np.random.default_rng(4)
+    for d in [2, 3]:
+        terms = wl.random_harmonic_poly(d, rng)
+        prob = {"dim": d, "surfaces": [{"kind": "sphere", "center": [0.1] * d, "radius": 0.8}],
+                "parent": [-1], "sigma": [1.0], "flux": [wl.harmonic_poly(1.7, terms, d)], "M": 1}
+        for _ in range(5):
+            u = rng.standard_normal(d); u /= np.linalg.norm(u)
+            y = 0.1 + 0.8 * u
+            h = 1e-6
+            fd = (wl.eval_poly(terms, y + h * u)[0] - wl.eval_poly(terms, y - h * u)[0]) / (2 * h)
+            assert abs(oracle_core.flux_at(prob, 0, y) - 1.7 * fd[0]) < 1e-6
+
+
+def test_vr_arcs(oracle_core):
+    """Sec. 4.4: dOmega^+ = {beta >= 0}, dOmega^- = {beta < 0}; the arcs cover
+    the surface and the uniform samples of each part carry the right sign."""
+    prob = star_problem()
+    prep = oracle_core.Prepared(prob, "vr")
+    for h in range(2):
+        assert abs(prep.part_len[h].sum() - prep.area[h]) < 1e-8
+        for part in (0, 1):
+            y = oracle_core.uniform_part_points(prob, h, part, 300, seed=7 + h, prepared=prep)
+            beta = np.array([prep.beta_scale[h] * oracle_core.flux_at(prob, h, yy, prepared=prep) for yy in y])
+            assert np.all(beta >= -1e-9) if part == 0 else np.all(beta < 1e-9)
