@@ -148,8 +148,9 @@ static uint32_t or_word(or_rng *r, int step, int chain, int k)
     return r->words[k & 3];
 }
 
-/* uniform on (0,1) from the top 24 bits; the same value is exact in FP32 */
-static double or_u01(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* uniform on (0,1) from the top 23 bits: (2k+1) / 2^24 with k < 2^23, a value
+ * that FP32 and FP64 both represent exactly */
+static double or_u01(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* ------------------------------------------------------------------------ */
 /* constants and Green's function (Sec. 2)                                   */
