@@ -1,0 +1,315 @@
+"""Benchmark of the Walk-on-Interfaces hot path on GB300.
+
+One step = one woi_estimate over the whole workload (every point, every walk,
+all M+1 steps of each walk, the u and grad u tallies, the per-point reduction
+and the finalize), inputs resident in HBM.  Default workload: 3D nested spheres
+(radii 1 / 0.8 / 0.5, sigma 1 / 5 / 0.2), 4096 points uniform in the ball,
+1e5 walks per point, M = 6, FP32 walks with FP64 reductions.
+
+Metric: accurate u + grad u estimates per second at the RMS standard error the
+estimator reaches with 1e5 walks per point (every path computes the same
+estimator, so equal walks mean equal error).  Also reported: walk-steps/s, the
+roofline of the walk kernel against the FP32 peak, the end-to-end figure
+through the C ABI with host buffers, and the CPU oracle timed on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload 3d-nested|2d-concentric|2d-star-inclusions|6d-nested]
+                    [--precision mixed|fp64]
+
+Multi-GPU (torchrun): each rank runs the full workload on its own GPU with its
+own walk range (weak scaling, no data-path collective); timing is the max over
+ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP32 flops per walk-step (FMA = 2) of the walk on circles /
+# d-spheres: 11 d + 15 (direction sampling, one transition and the Phi /
+# grad Phi tally); 2D circles 30.  Derivation in the design notes.
+def alg_flops_per_walk_step(dim: int) -> float:
+    return 30.0 if dim == 2 else 11.0 * dim + 15.0
+
+
+# DRAM bytes per launch of the walk kernel from the ncu capture of the
+# workload named as key, scaled to one full launch (None once the kernel has
+# changed since the counters were taken).
+TRAFFIC = {}
+
+WORKLOADS = {
+    "3d-nested": dict(points=4096, walks=100_000, M=6),
+    "2d-concentric": dict(points=64, walks=10_000, M=4),
+    "2d-star-inclusions": dict(points=16384, walks=100_000, M=4),
+    "6d-nested": dict(points=1024, walks=1_000_000, M=8),
+}
+
+
+def make_workload(name):
+    from paper_2508_16767_gb300 import workloads as wl
+    if name == "3d-nested":
+        return wl.nested_3d_problem(), wl.ball_points(4096, 3, 12)
+    if name == "2d-concentric":
+        return wl.concentric_2d_problem(), wl.concentric_2d_points()
+    if name == "2d-star-inclusions":
+        p = wl.star_inclusions_problem()
+        return p, wl.star_inclusions_points(p, 16384)
+    if name == "6d-nested":
+        return wl.nested_6d_problem(), wl.ball_points(1024, 6, 14)
+    raise ValueError(name)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0):
+    """The CPU oracle as it stands on a bounded sample of the workload: all host
+    threads, a subset of points and walks sized to ~target_s seconds; returns
+    estimates/s at W_full walks per point (time is linear in walks)."""
+    from oracle import core
+    prep = core.Prepared(problem)
+    n_pts, w = 16, 2048
+    t0 = time.perf_counter()
+    core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep)
+    t1 = time.perf_counter() - t0
+    scale = max(1.0, target_s / max(t1, 1e-3))
+    n_pts = int(min(len(points), max(16, n_pts * math.sqrt(scale))))
+    w = int(max(2048, 2048 * scale * 16 / n_pts)) // 32 * 32
+    t0 = time.perf_counter()
+    core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep)
+    t = time.perf_counter() - t0
+    est_per_s = n_pts / (t * W_full / w)
+    return {"value": est_per_s, "cores": core.threads_used(), "kind": "oracle",
+            "sample": f"{n_pts} points x {w} walks (of {len(points)} x {W_full}), {t:.1f} s, "
+                      f"extrapolated linearly in walks", "seconds": t,
+            "walk_steps_per_s": n_pts * w * (M + 1) / t}
+
+
+def run_reference(args, workload):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    problem, points = make_workload(workload)
+    cfg = WORKLOADS[workload]
+    times = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(problem, points, cfg["M"], cfg["walks"], target_s=max(2.0, 60.0 / max(args.steps, 1)))
+        if s >= args.warmup:
+            times.append(r)
+    v = float(np.mean([r["value"] for r in times]))
+    line = {"impl": "reference", "metric": "accurate u+grad u estimates/s at fixed RMS error", "value": v,
+            "unit": "estimates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * cfg["points"] / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "points": cfg["points"], "walks_per_point": cfg["walks"], "M": cfg["M"]},
+            "cpu_baseline": {"value": v, "unit": "estimates/s", "cores": times[-1]["cores"], "kind": "oracle",
+                             "sample": times[-1]["sample"]},
+            "e2e": {"value": v, "unit": "estimates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--workload", default="3d-nested", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--walks-per-lane", type=int, default=0)
+    ap.add_argument("--sched-group", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_16767_gb300 import build
+    build.build()
+    from paper_2508_16767_gb300 import woi
+
+    cfg = WORKLOADS[args.workload]
+    problem, points = make_workload(args.workload)
+    P, d, Wk, M = len(points), problem["dim"], cfg["walks"], cfg["M"]
+    geom = woi.Geometry(problem)
+    stream = torch.cuda.Stream()
+    xd = torch.from_numpy(points).cuda()
+    outs = (torch.empty(P, dtype=torch.float64, device="cuda"), torch.empty(P, d, dtype=torch.float64, device="cuda"),
+            torch.empty(P, dtype=torch.float64, device="cuda"), torch.empty(P, d, dtype=torch.float64, device="cuda"))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    opt = dict(M=M, precision=args.precision, sched_group=args.sched_group, block_size=args.block,
+               walks_per_lane=args.walks_per_lane)
+
+    def step(timing):
+        # each rank runs its own walk range: rank r takes walks [r W, (r + 1) W)
+        if ws == 1:
+            return woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, timing=timing, **opt)
+        mom = woi.woi_estimate_range(geom, xd, rank * Wk, Wk, seed=0, stream=stream.cuda_stream, timing=timing, **opt)
+        return mom
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[k][0].record(stream)
+            step(True)
+            ev[k][1].record(stream)
+            kernel_ms.append(woi.woi_last_kernel_ms(geom))
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1000.0
+    if ws > 1:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    ms_per_step = 1000.0 * t_total / args.steps
+    value = ws * P / (t_total / args.steps)
+    walk_steps = ws * P * Wk * (M + 1)
+    wsps = walk_steps / (t_total / args.steps)
+
+    # roofline of the walk kernel: algorithmic FP32 flops per launch / kernel time
+    pk, src = peaks()
+    props = torch.cuda.get_device_properties(local)
+    peak_tflops = props.multi_processor_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    k_ms = float(np.mean(kernel_ms))
+    flops = P * Wk * (M + 1) * alg_flops_per_walk_step(d)
+    achieved = flops / (k_ms / 1000.0) / 1e12
+    rms_se = float(torch.sqrt(torch.mean(outs[2] ** 2)).item()) if ws == 1 else None
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0:
+        hp = torch.from_numpy(points).pin_memory()
+        ho = (torch.empty(P, dtype=torch.float64).pin_memory(), torch.empty(P, d, dtype=torch.float64).pin_memory(),
+              torch.empty(P, dtype=torch.float64).pin_memory(), torch.empty(P, d, dtype=torch.float64).pin_memory())
+        woi.woi_estimate(geom, hp, Wk, seed=0, out=ho, stream=stream.cuda_stream, **opt)
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            woi.woi_estimate(geom, hp, Wk, seed=0, out=ho, stream=stream.cuda_stream, **opt)
+        te = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": P / te, "unit": "estimates/s", "h2d_bytes_per_step": P * d * 8,
+               "d2h_bytes_per_step": P * (2 + 2 * d) * 8}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(problem, points, M, Wk)
+        cpu = {k: cpu[k] for k in ("value", "cores", "kind", "sample")} | {"unit": "estimates/s"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": "accurate u+grad u estimates/s at fixed RMS error", "value": value, "unit": "estimates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "points": P, "walks_per_point": Wk, "M": M, "dim": d,
+                       "precision": args.precision, "sched_group": args.sched_group,
+                       "l2": "flushed between steps (512 MiB write outside the step events)",
+                       "parallelism": f"replicas x{ws}, disjoint walk ranges"},
+            "walk_steps_per_s": wsps, "rms_se_u": rms_se,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": TRAFFIC.get(args.workload),
+                         "peak_source": f"FP32: SMs x 128 lanes x 2 x sm_max_mhz ({src})",
+                         "kernel_ms": k_ms, "alg_flops_per_walk_step": alg_flops_per_walk_step(d)},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps * (2 if args.precision == "mixed" else P + 1),
+        }
+        print(json.dumps(line))
+    geom.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -61,7 +61,7 @@ def lib():
         _lib = ctypes.CDLL(LIB)
         P = ctypes.POINTER
         _lib.or_estimate.argtypes = [P(OrProblem), P(OrOpts), ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
-                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                     ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_estimate.restype = ctypes.c_int
         _lib.or_walks.argtypes = [P(OrProblem), P(OrOpts), ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
@@ -332,9 +332,10 @@ def _opts(M, variant, sched_group):
 
 
 def estimate(problem, points, n_walks, seed=0, M=None, variant="plain", sched_group=1, walk_begin=0,
-             instance=0, prepared=None):
+             instance=0, prepared=None, point_offset=0):
     """Algorithm 1 over every point: mean of N * (walk sum), and the standard
     error from the schedule-group means (groups of `sched_group` walkers).
+    Point p uses the random stream of point id point_offset + p.
     Returns a dict with u [P], grad [P, d], se_u, se_grad and raw sums."""
     prep = prepared or Prepared(problem, variant)
     M = problem["M"] if M is None else M
@@ -346,7 +347,7 @@ def estimate(problem, points, n_walks, seed=0, M=None, variant="plain", sched_gr
     sm2 = np.zeros((P, d + 1))
     G = ctypes.c_int64(0)
     o = _opts(M, variant, sched_group)
-    rc = lib().or_estimate(ctypes.byref(prep.struct), ctypes.byref(o), pts.ctypes.data, P, instance,
+    rc = lib().or_estimate(ctypes.byref(prep.struct), ctypes.byref(o), pts.ctypes.data, P, point_offset, instance,
                            walk_begin, walk_begin + n_walks, seed, sf.ctypes.data, sm.ctypes.data,
                            sm2.ctypes.data, ctypes.byref(G))
     if rc != 0:
@@ -377,7 +378,7 @@ def walks(problem, x, walk_ids, seed=0, M=None, variant="plain", sched_group=1, 
     fg = np.zeros((n, d))
     H = np.zeros((n, M + 1), dtype=np.int32)
     Y = np.zeros((n, 2, M + 1, d))
-    sc = np.zeros((n, 2))
+    sc = np.zeros((n, 3))
     o = _opts(M, variant, sched_group)
     lib().or_walks(ctypes.byref(prep.struct), ctypes.byref(o), x.ctypes.data, point_id, instance, ids.ctypes.data,
                    n, seed, fu.ctypes.data, fg.ctypes.data, H.ctypes.data, Y.ctypes.data, sc.ctypes.data)

@@ -515,7 +515,7 @@ static double or_beta(const or_problem *P, int h, const double *y)
 typedef struct {
     int *H;          /* [M+1] scheduled interfaces (0-based), or NULL */
     double *Y;       /* [2][M+1][dim] states of each chain, or NULL */
-    double *scale;   /* [2]: sum_i |c_i Phi_i| and sum_i |c_i| (both chains) */
+    double *scale;   /* [3]: sum_i |c_i Phi_i|, sum_i |c_i| and sum_i |c_i| |grad Phi_i| (both chains) */
 } or_trace;
 
 /* H_i: 0-based index; i = 0 uniform over the N surfaces, i >= 1 by |alpha| */
@@ -541,7 +541,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     const int n_chain = o->variant == 1 ? 2 : 1;
     or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32) ^ instance}, walk, -1, -1, -1, {0}};
     uint64_t group = walk / (uint64_t)o->sched_group;
-    double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0}, sc_phi = 0.0, sc_c = 0.0;
+    double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0}, sc_phi = 0.0, sc_c = 0.0, sc_g = 0.0;
 
     double y[2][OR_MAX_DIM], Q[2], T[2];
     int alive[2] = {1, 1};
@@ -635,20 +635,23 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
             for (int c = 0; c < d; ++c) acc_g[c] += coef * g[c];
             sc_phi += fabs(coef * phi);
             sc_c += fabs(coef);
+            double gn = 0.0;
+            for (int c = 0; c < d; ++c) gn += g[c] * g[c];
+            sc_g += fabs(coef) * sqrt(gn);
         }
         h_prev = h;
     }
     *out_u = acc_u;
     for (int c = 0; c < d; ++c) out_g[c] = acc_g[c];
-    if (tr && tr->scale) { tr->scale[0] = sc_phi; tr->scale[1] = sc_c; }
+    if (tr && tr->scale) { tr->scale[0] = sc_phi; tr->scale[1] = sc_c; tr->scale[2] = sc_g; }
 }
 
 /* ------------------------------------------------------------------------ */
 /* estimator over points (Algorithm 1): per point the walk sum and the       */
 /* sums of the schedule-group means and of their squares                    */
 /* ------------------------------------------------------------------------ */
-int or_estimate(const or_problem *P, const or_opts *o, const double *points, int64_t n_pts, uint32_t instance,
-                uint64_t walk_begin, uint64_t walk_end, uint64_t seed, double *sum_f /* [n_pts][d+1] */,
+int or_estimate(const or_problem *P, const or_opts *o, const double *points, int64_t n_pts, uint32_t point_offset,
+                uint32_t instance, uint64_t walk_begin, uint64_t walk_end, uint64_t seed, double *sum_f /* [n_pts][d+1] */,
                 double *sum_gm /* [n_pts][d+1] */, double *sum_gm2 /* [n_pts][d+1] */, int64_t *n_groups)
 {
     const int d = P->dim, W_g = o->sched_group;
@@ -662,7 +665,7 @@ int or_estimate(const or_problem *P, const or_opts *o, const double *points, int
             double gs[OR_MAX_DIM + 1] = {0};
             for (int j = 0; j < W_g; ++j) {
                 double fu, fg[OR_MAX_DIM];
-                or_walk(P, o, x, (uint32_t)p, instance, g0 + (uint64_t)j, seed, &fu, fg, NULL);
+                or_walk(P, o, x, point_offset + (uint32_t)p, instance, g0 + (uint64_t)j, seed, &fu, fg, NULL);
                 gs[0] += fu;
                 for (int c = 0; c < d; ++c) gs[1 + c] += fg[c];
             }
@@ -691,7 +694,7 @@ void or_walks(const or_problem *P, const or_opts *o, const double *x, uint32_t p
     const int d = P->dim, M = o->M;
     for (int64_t w = 0; w < n_walks; ++w) {
         or_trace tr = {out_H ? out_H + w * (M + 1) : NULL, out_Y ? out_Y + (size_t)w * 2 * (M + 1) * d : NULL,
-                       out_scale ? out_scale + 2 * w : NULL};
+                       out_scale ? out_scale + 3 * w : NULL};
         or_walk(P, o, x, point_id, instance, walks[w], seed, out_u + w, out_g + w * d, &tr);
     }
 }

@@ -1,0 +1,951 @@
+// woi_api.cu -- the C ABI of libwoi (include/woi.h): validation, the
+// pre-processing of Sec. 3 (alpha, beta, schedule thresholds of Thm 4.2),
+// geometry tables (areas, star arc lengths, beta-sign arcs of Sec. 4.4),
+// device staging and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/woi.h"
+#include "woi_kernels.h"
+#include "woi_layout.h"
+
+using namespace woi;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+woi_status fail(woi_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define WOI_CUDA(call)                                                                               \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(WOI_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+double omega_d(int d) { return 2.0 * std::pow(kPi, 0.5 * d) / std::tgamma(0.5 * d); }
+
+// star curve r(t), r'(t)
+struct StarCurve {
+    double R = 1.0;
+    int K = 0;
+    double a[kMaxStar + 1] = {0}, b[kMaxStar + 1] = {0};
+    double c[2] = {0, 0};
+    void eval(double t, double *r, double *dr) const
+    {
+        double s = 1.0, ds = 0.0;
+        for (int k = 1; k <= K; ++k) {
+            s += a[k] * std::cos(k * t) + b[k] * std::sin(k * t);
+            ds += k * (b[k] * std::cos(k * t) - a[k] * std::sin(k * t));
+        }
+        *r = R * s;
+        *dr = R * ds;
+    }
+    double speed(double t) const
+    {
+        double r, dr;
+        eval(t, &r, &dr);
+        return std::sqrt(r * r + dr * dr);
+    }
+    void point(double t, double *p) const
+    {
+        double r, dr;
+        eval(t, &r, &dr);
+        p[0] = c[0] + r * std::cos(t);
+        p[1] = c[1] + r * std::sin(t);
+    }
+};
+
+// composite 8-point Gauss-Legendre of |gamma'| on [a, b] with m sub-panels
+double star_length(const StarCurve &s, double a, double b, int m = 8)
+{
+    static const double x[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double w[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    double tot = 0.0, h = (b - a) / m;
+    for (int j = 0; j < m; ++j) {
+        double mid = a + (j + 0.5) * h, half = 0.5 * h, acc = 0.0;
+        for (int q = 0; q < 4; ++q) acc += w[q] * (s.speed(mid - half * x[q]) + s.speed(mid + half * x[q]));
+        tot += half * acc;
+    }
+    return tot;
+}
+
+double fourier_eval(const std::vector<double> &c, double t)
+{
+    double v = c.empty() ? 0.0 : c[0];
+    for (size_t k = 1; 2 * k <= c.size() - 1; ++k) v += c[2 * k - 1] * std::cos(k * t) + c[2 * k] * std::sin(k * t);
+    return v;
+}
+
+bool pointer_on_device(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the geometry handle
+// ---------------------------------------------------------------------------
+struct woi_geometry {
+    int dim = 0, n = 0;
+    std::vector<woi_surface_desc> surf;
+    std::vector<int> parent, tin, tout;
+    std::vector<double> area;
+    int star_idx = -1;
+    StarCurve star;
+    std::vector<double> star_panel_s;          // kStarPanels + 1
+    std::vector<double> star_scan;             // kStarScan * 2
+    double star_lmax = 0.0;
+
+    bool data_ready = false;
+    std::vector<double> sigma, alpha, beta_scale, flux_coef;
+    std::vector<uint64_t> thresh;
+    double alpha_l1 = 0.0;
+    std::vector<int> flux_basis, flux_off, flux_n;
+    bool vr_ok = false;
+    std::vector<double> arc_t0, arc_t1, arc_len, part_len;
+    std::vector<int> arc_sign, arc_off, arc_n;
+
+    // device side
+    int device = -1;
+    bool dev_dirty = true;
+    DevGeom blob{};
+    DevGeom *d_blob = nullptr;
+    double *d_flux = nullptr, *d_arc_t0 = nullptr, *d_arc_t1 = nullptr, *d_arc_len = nullptr;
+    int *d_arc_sign = nullptr;
+    int blob_M = -1;
+    // grow-only scratch
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int num_sms = 0;
+    std::map<long long, int> occ_cache;        // (dim, vr, star, block) -> blocks per SM
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    bool timed = false;
+
+    ~woi_geometry() { release(); }
+    void release()
+    {
+        if (device < 0) return;
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        cudaFree(d_blob);
+        cudaFree(d_flux);
+        cudaFree(d_arc_t0);
+        cudaFree(d_arc_t1);
+        cudaFree(d_arc_len);
+        cudaFree(d_arc_sign);
+        cudaFree(d_scratch);
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_stop) cudaEventDestroy(ev_stop);
+        ev_start = ev_stop = nullptr;
+        timed = false;
+        if (cur >= 0) cudaSetDevice(cur);
+        d_blob = nullptr;
+        d_flux = d_arc_t0 = d_arc_t1 = d_arc_len = nullptr;
+        d_arc_sign = nullptr;
+        d_scratch = nullptr;
+        scratch_bytes = 0;
+        device = -1;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// geometry validation helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+double dist(int d, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s += (a[k] - b[k]) * (a[k] - b[k]);
+    return std::sqrt(s);
+}
+
+// a dense sample of surface i (2D only: circles and stars), used for star checks
+std::vector<double> sample_curve(const woi_geometry &g, int i, int m)
+{
+    std::vector<double> p(2 * m);
+    for (int j = 0; j < m; ++j) {
+        double t = 2.0 * kPi * j / m;
+        if (g.surf[i].type == WOI_STAR) {
+            g.star.point(t, &p[2 * j]);
+        } else {
+            p[2 * j] = g.surf[i].center[0] + g.surf[i].radius * std::cos(t);
+            p[2 * j + 1] = g.surf[i].center[1] + g.surf[i].radius * std::sin(t);
+        }
+    }
+    return p;
+}
+
+// is point x strictly inside the region bounded by surface i?
+bool inside_surface(const woi_geometry &g, int i, const double *x)
+{
+    const woi_surface_desc &s = g.surf[i];
+    if (s.type == WOI_SPHERE) return dist(g.dim, x, s.center) < s.radius;
+    double t = std::atan2(x[1] - s.center[1], x[0] - s.center[0]);
+    double r, dr;
+    g.star.eval(t, &r, &dr);
+    return std::hypot(x[0] - s.center[0], x[1] - s.center[1]) < r;
+}
+
+woi_status check_nesting(const woi_geometry &g)
+{
+    const int n = g.n, d = g.dim;
+    const int M = 4096;
+    for (int i = 1; i < n; ++i) {
+        const int p = g.parent[i];
+        const woi_surface_desc &si = g.surf[i], &sp = g.surf[p];
+        // i strictly inside its parent
+        if (si.type == WOI_SPHERE && sp.type == WOI_SPHERE) {
+            if (!(dist(d, si.center, sp.center) + si.radius < sp.radius))
+                return fail(WOI_E_GEOMETRY, "surface %d is not strictly inside its parent %d", i, p);
+        } else {
+            std::vector<double> pts = sample_curve(g, i, M);
+            for (int j = 0; j < M; ++j)
+                if (!inside_surface(g, p, &pts[2 * j]))
+                    return fail(WOI_E_GEOMETRY, "surface %d is not strictly inside its parent %d", i, p);
+            if (sp.type == WOI_STAR) {
+                std::vector<double> q = sample_curve(g, p, M);
+                for (int j = 0; j < M; ++j)
+                    if (inside_surface(g, i, &q[2 * j]))
+                        return fail(WOI_E_GEOMETRY, "surface %d crosses its parent %d", i, p);
+            }
+        }
+        // disjoint from its siblings
+        for (int j = i + 1; j < n; ++j) {
+            if (g.parent[j] != p) continue;
+            const woi_surface_desc &sj = g.surf[j];
+            if (si.type == WOI_SPHERE && sj.type == WOI_SPHERE) {
+                if (!(dist(d, si.center, sj.center) > si.radius + sj.radius))
+                    return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
+            } else {
+                std::vector<double> a = sample_curve(g, i, M), b = sample_curve(g, j, M);
+                for (int k = 0; k < M; ++k)
+                    if (inside_surface(g, j, &a[2 * k]) || inside_surface(g, i, &b[2 * k]))
+                        return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
+            }
+        }
+    }
+    return WOI_OK;
+}
+
+// Laplacian of a monomial expansion is identically zero?
+bool poly_is_harmonic(int d, int T, const double *rows, double *scale)
+{
+    std::map<std::vector<int>, double> lap;
+    double tot = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const double *row = rows + t * (d + 1);
+        tot += std::fabs(row[0]);
+        for (int k = 0; k < d; ++k) {
+            int e = (int)row[1 + k];
+            if (e < 2) continue;
+            std::vector<int> key(d);
+            for (int j = 0; j < d; ++j) key[j] = (int)row[1 + j];
+            key[k] -= 2;
+            lap[key] += row[0] * e * (e - 1);
+        }
+    }
+    *scale = tot;
+    for (auto &kv : lap)
+        if (std::fabs(kv.second) > 1e-12 * std::max(tot, 1.0)) return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *woi_version(void) { return "woi-gb300 1.0 (sm_103a)"; }
+
+const char *woi_last_error(void) { return g_last_error.c_str(); }
+
+void woi_default_opts(woi_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->M = 4;
+    o->variant = WOI_PLAIN;
+    o->precision = WOI_MIXED;
+    o->sched_group = 1;
+}
+
+woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surfaces, const int *parent,
+                               woi_geometry **out)
+{
+    g_last_error.clear();
+    if (!out || !surfaces || !parent) return fail(WOI_E_INVALID_ARG, "null argument");
+    if (dim < 2 || dim > WOI_MAX_DIM) return fail(WOI_E_INVALID_ARG, "dim %d outside [2, %d]", dim, WOI_MAX_DIM);
+    if (n_surf < 1 || n_surf > WOI_MAX_SURF)
+        return fail(WOI_E_INVALID_ARG, "n_surf %d outside [1, %d]", n_surf, WOI_MAX_SURF);
+    if (parent[0] != -1) return fail(WOI_E_INVALID_ARG, "parent[0] must be -1 (surface 0 is the outer boundary)");
+    for (int i = 1; i < n_surf; ++i) {
+        if (parent[i] < 0 || parent[i] >= n_surf || parent[i] == i)
+            return fail(WOI_E_INVALID_ARG, "parent[%d] = %d is not a surface index", i, parent[i]);
+        int p = parent[i], steps = 0;          // the chain of parents must reach 0 without a cycle
+        while (p != 0 && steps <= n_surf) { p = parent[p]; ++steps; }
+        if (p != 0) return fail(WOI_E_INVALID_ARG, "parent array has a cycle through surface %d", i);
+    }
+    auto *g = new (std::nothrow) woi_geometry();
+    if (!g) return fail(WOI_E_OOM, "host allocation failed");
+    g->dim = dim;
+    g->n = n_surf;
+    g->surf.assign(surfaces, surfaces + n_surf);
+    g->parent.assign(parent, parent + n_surf);
+    for (int i = 0; i < n_surf; ++i) {
+        woi_surface_desc &s = g->surf[i];
+        s.star_a = s.star_b = nullptr;         // deep copy below; no pointer retained
+        if (s.type == WOI_SPHERE) {
+            if (!(s.radius > 0.0) || !std::isfinite(s.radius)) {
+                delete g;
+                return fail(WOI_E_INVALID_ARG, "surface %d: radius must be positive", i);
+            }
+        } else if (s.type == WOI_STAR) {
+            if (dim != 2) { delete g; return fail(WOI_E_UNSUPPORTED, "star surfaces exist only in 2D"); }
+            if (g->star_idx >= 0) { delete g; return fail(WOI_E_UNSUPPORTED, "at most one star surface per geometry"); }
+            const int K = surfaces[i].star_degree;
+            if (K < 0 || K > WOI_MAX_STAR_DEGREE || (K > 0 && (!surfaces[i].star_a || !surfaces[i].star_b))) {
+                delete g;
+                return fail(WOI_E_INVALID_ARG, "surface %d: bad star degree or coefficients", i);
+            }
+            if (!(s.radius > 0.0)) { delete g; return fail(WOI_E_INVALID_ARG, "surface %d: radius must be positive", i); }
+            g->star_idx = i;
+            g->star.R = s.radius;
+            g->star.K = K;
+            g->star.c[0] = s.center[0];
+            g->star.c[1] = s.center[1];
+            for (int k = 1; k <= K; ++k) {
+                g->star.a[k] = surfaces[i].star_a[k];
+                g->star.b[k] = surfaces[i].star_b[k];
+            }
+            for (int j = 0; j < 8192; ++j) {
+                double r, dr;
+                g->star.eval(2.0 * kPi * j / 8192, &r, &dr);
+                if (!(r > 0.0)) { delete g; return fail(WOI_E_GEOMETRY, "surface %d: star radius not positive", i); }
+            }
+        } else {
+            delete g;
+            return fail(WOI_E_INVALID_ARG, "surface %d: unknown type %d", i, s.type);
+        }
+    }
+    woi_status st = check_nesting(*g);
+    if (st != WOI_OK) { delete g; return st; }
+    // Euler tour of the tree: a is a strict descendant of b iff tin[b] < tin[a] < tout[b]
+    {
+        std::vector<std::vector<int>> ch(n_surf);
+        for (int i = 1; i < n_surf; ++i) ch[g->parent[i]].push_back(i);
+        g->tin.assign(n_surf, 0);
+        g->tout.assign(n_surf, 0);
+        int clock = 0;
+        std::vector<std::pair<int, size_t>> stack{{0, 0}};
+        g->tin[0] = clock++;
+        while (!stack.empty()) {
+            auto &top = stack.back();
+            if (top.second < ch[top.first].size()) {
+                int c = ch[top.first][top.second++];
+                g->tin[c] = clock++;
+                stack.push_back({c, 0});
+            } else {
+                g->tout[top.first] = clock++;
+                stack.pop_back();
+            }
+        }
+    }
+    // areas, star tables
+    g->area.resize(n_surf);
+    for (int i = 0; i < n_surf; ++i) {
+        if (g->surf[i].type == WOI_SPHERE) {
+            g->area[i] = omega_d(dim) * std::pow(g->surf[i].radius, dim - 1);
+        }
+    }
+    if (g->star_idx >= 0) {
+        g->star_panel_s.assign(kStarPanels + 1, 0.0);
+        const double H = 2.0 * kPi / kStarPanels;
+        for (int j = 0; j < kStarPanels; ++j)
+            g->star_panel_s[j + 1] = g->star_panel_s[j] + star_length(g->star, j * H, (j + 1) * H, 4);
+        g->area[g->star_idx] = g->star_panel_s[kStarPanels];
+        g->star_scan.assign(2 * kStarScan, 0.0);
+        for (int j = 0; j < kStarScan; ++j) {
+            double r, dr, t = 2.0 * kPi * j / kStarScan;
+            g->star.eval(t, &r, &dr);
+            g->star_scan[2 * j] = r * std::cos(t);
+            g->star_scan[2 * j + 1] = r * std::sin(t);
+        }
+        double lm = 0.0;
+        for (int j = 0; j < 16384; ++j) lm = std::max(lm, g->star.speed(2.0 * kPi * j / 16384));
+        g->star_lmax = lm * 1.02 + 1e-12;
+    }
+    *out = g;
+    return WOI_OK;
+}
+
+woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const woi_flux_desc *flux)
+{
+    g_last_error.clear();
+    if (!g || !sigma || !flux) return fail(WOI_E_INVALID_ARG, "null argument");
+    const int n = g->n, d = g->dim;
+    if (!(sigma[0] > 0.0)) return fail(WOI_E_INVALID_ARG, "sigma_1 must be positive");
+    for (int i = 0; i < n; ++i) {
+        if (!(sigma[i] >= 0.0) || !std::isfinite(sigma[i])) return fail(WOI_E_INVALID_ARG, "sigma[%d] must be >= 0", i);
+        if (i > 0 && !(sigma[i] + sigma[g->parent[i]] > 0.0))
+            return fail(WOI_E_INVALID_ARG, "sigma[%d] + sigma[parent] must be positive", i);
+    }
+    // flux data: basis / surface fit and the compatibility condition (zero mean per surface)
+    std::vector<int> basis(n), off(n), nc(n);
+    std::vector<double> coef;
+    for (int i = 0; i < n; ++i) {
+        const woi_flux_desc &f = flux[i];
+        if (f.n_coef < 0 || (f.n_coef > 0 && !f.coef)) return fail(WOI_E_INVALID_ARG, "flux[%d]: bad coefficients", i);
+        std::vector<double> c(f.coef, f.coef + f.n_coef);
+        basis[i] = f.basis;
+        off[i] = (int)coef.size();
+        nc[i] = f.n_coef;
+        const woi_surface_desc &s = g->surf[i];
+        switch (f.basis) {
+        case WOI_FLUX_ZERO:
+            break;
+        case WOI_FLUX_FOURIER: {
+            if (d != 2) return fail(WOI_E_UNSUPPORTED, "flux[%d]: Fourier data need a 2D surface", i);
+            if (f.n_coef < 1 || f.n_coef % 2 == 0) return fail(WOI_E_INVALID_ARG, "flux[%d]: Fourier needs 2K+1 coefficients", i);
+            // int b ds and int |b| ds by the trapezoidal rule in the parameter (spectrally accurate)
+            const int m = 4096;
+            double I = 0.0, I1 = 0.0;
+            for (int j = 0; j < m; ++j) {
+                double t = 2.0 * kPi * j / m;
+                double ds = (s.type == WOI_STAR) ? g->star.speed(t) : s.radius;
+                double b = fourier_eval(c, t);
+                I += b * ds;
+                I1 += std::fabs(b) * ds;
+            }
+            if (std::fabs(I) > 1e-10 * std::max(I1, 1e-300) && std::fabs(I) > 1e-300)
+                return fail(WOI_E_COMPAT, "flux[%d]: int b dA = %.3e is not zero (|b|_1 = %.3e)", i, I, I1);
+            break;
+        }
+        case WOI_FLUX_REAL_SH: {
+            if (d != 3 || s.type != WOI_SPHERE) return fail(WOI_E_UNSUPPORTED, "flux[%d]: spherical harmonics need a 3D sphere", i);
+            int L = (int)std::lround(std::sqrt((double)f.n_coef)) - 1;
+            if (L < 0 || (L + 1) * (L + 1) != f.n_coef || L > 4)
+                return fail(WOI_E_INVALID_ARG, "flux[%d]: need (L+1)^2 coefficients with L <= 4", i);
+            double tot = 0.0;
+            for (double v : c) tot += std::fabs(v);
+            if (std::fabs(c[0]) > 1e-10 * tot) return fail(WOI_E_COMPAT, "flux[%d]: Y_0^0 coefficient must be zero", i);
+            break;
+        }
+        case WOI_FLUX_HARMONIC_POLY: {
+            if (f.n_coef < 2) return fail(WOI_E_INVALID_ARG, "flux[%d]: harmonic polynomial needs [s, T, ...]", i);
+            int T = (int)c[1];
+            if (T < 0 || (double)T != c[1] || f.n_coef != 2 + T * (d + 1))
+                return fail(WOI_E_INVALID_ARG, "flux[%d]: harmonic polynomial layout [s, T, (c, e_1..e_d) x T]", i);
+            for (int t = 0; t < T; ++t)
+                for (int k = 0; k < d; ++k) {
+                    double e = c[2 + t * (d + 1) + 1 + k];
+                    if (e < 0 || e != std::floor(e) || e > 16) return fail(WOI_E_INVALID_ARG, "flux[%d]: bad exponent", i);
+                }
+            double sc;
+            if (!poly_is_harmonic(d, T, c.data() + 2, &sc))
+                return fail(WOI_E_COMPAT, "flux[%d]: the polynomial is not harmonic, its flux is not compatible", i);
+            break;
+        }
+        default:
+            return fail(WOI_E_INVALID_ARG, "flux[%d]: unknown basis %d", i, f.basis);
+        }
+        coef.insert(coef.end(), c.begin(), c.end());
+    }
+    // Sec. 3: alpha_1 = 2, alpha_i = 2 (sigma_i - sigma_p) / (sigma_p + sigma_i);
+    //         beta_1 = (2 / sigma_1) b_1, beta_i = -2 b_i / (sigma_p + sigma_i)
+    std::vector<double> alpha(n), bsc(n);
+    for (int i = 0; i < n; ++i) {
+        if (i == 0) {
+            alpha[i] = 2.0;
+            bsc[i] = 2.0 / sigma[0];
+        } else {
+            const double sp = sigma[g->parent[i]], si = sigma[i];
+            alpha[i] = 2.0 * (si - sp) / (sp + si);
+            bsc[i] = -2.0 / (sp + si);
+        }
+    }
+    // Thm 4.2: P(H = n) = |alpha_n| / A; thresholds T_n = floor(2^32 C_n / A), T_N = 2^32
+    double A = 0.0;
+    for (int i = 0; i < n; ++i) A += std::fabs(alpha[i]);
+    std::vector<uint64_t> th(n);
+    double C = 0.0;
+    for (int i = 0; i < n; ++i) {
+        C += std::fabs(alpha[i]);
+        th[i] = (uint64_t)std::floor(std::ldexp(C / A, 32));
+    }
+    th[n - 1] = 1ull << 32;
+    // Sec. 4.4: arcs of dOmega^+ = {beta >= 0} and dOmega^- = {beta < 0} (2D)
+    bool vr_ok = (d == 2);
+    std::vector<double> at0, at1, alen, plen(2 * n, 0.0);
+    std::vector<int> asg, aoff(n, 0), an(n, 0);
+    for (int i = 0; i < n && vr_ok; ++i) {
+        aoff[i] = (int)at0.size();
+        const woi_surface_desc &s = g->surf[i];
+        auto arc_length = [&](double t0, double t1) {
+            if (s.type == WOI_SPHERE) return s.radius * (t1 - t0);
+            return star_length(g->star, t0, t1, 64);
+        };
+        if (basis[i] == WOI_FLUX_ZERO) {
+            at0.push_back(0.0); at1.push_back(2.0 * kPi); asg.push_back(1);
+            alen.push_back(g->area[i]);
+            plen[2 * i] += g->area[i];
+            an[i] = 1;
+            continue;
+        }
+        if (basis[i] != WOI_FLUX_FOURIER) { vr_ok = false; break; }
+        std::vector<double> c(coef.begin() + off[i], coef.begin() + off[i] + nc[i]);
+        auto beta = [&](double t) { return bsc[i] * fourier_eval(c, t); };
+        const int m = 8192;
+        std::vector<double> cuts{0.0};
+        double tp = 0.0, fp = beta(0.0);
+        for (int j = 1; j <= m; ++j) {
+            double t = 2.0 * kPi * j / m, f = beta(t);
+            if ((fp < 0) != (f < 0)) {
+                double lo = tp, hi = t, flo = fp;
+                for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+                    double mid = 0.5 * (lo + hi), fm = beta(mid);
+                    if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else hi = mid;
+                }
+                cuts.push_back(0.5 * (lo + hi));
+            }
+            tp = t;
+            fp = f;
+        }
+        cuts.push_back(2.0 * kPi);
+        for (size_t j = 0; j + 1 < cuts.size(); ++j) {
+            const double a = cuts[j], b = cuts[j + 1];
+            if (!(b > a)) continue;
+            const int sg = beta(0.5 * (a + b)) >= 0 ? 1 : -1;
+            const double L = arc_length(a, b);
+            at0.push_back(a); at1.push_back(b); asg.push_back(sg); alen.push_back(L);
+            plen[2 * i + (sg > 0 ? 0 : 1)] += L;
+            an[i]++;
+        }
+    }
+    g->sigma.assign(sigma, sigma + n);
+    g->alpha = alpha;
+    g->beta_scale = bsc;
+    g->alpha_l1 = A;
+    g->thresh = th;
+    g->flux_basis = basis;
+    g->flux_off = off;
+    g->flux_n = nc;
+    g->flux_coef = coef;
+    g->vr_ok = vr_ok;
+    g->arc_t0 = at0; g->arc_t1 = at1; g->arc_len = alen; g->arc_sign = asg;
+    g->arc_off = aoff; g->arc_n = an; g->part_len = plen;
+    g->data_ready = true;
+    g->dev_dirty = true;
+    g->blob_M = -1;
+    return WOI_OK;
+}
+
+void woi_destroy_geometry(woi_geometry *g) { delete g; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// device staging and launches
+// ---------------------------------------------------------------------------
+namespace {
+
+woi_status ensure_device(woi_geometry *g)
+{
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(WOI_E_NO_DEVICE, "no CUDA device (%s)", cudaGetErrorString(e));
+    }
+    int dev = 0;
+    WOI_CUDA(cudaGetDevice(&dev));
+    if (g->device >= 0 && g->device != dev) g->release();
+    if (g->device < 0) {
+        g->device = dev;
+        g->dev_dirty = true;
+        WOI_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return WOI_OK;
+}
+
+template <typename T>
+woi_status upload(T **dst, const std::vector<T> &src, cudaStream_t s)
+{
+    cudaFree(*dst);
+    *dst = nullptr;
+    size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    WOI_CUDA(cudaMalloc((void **)dst, bytes));
+    if (!src.empty()) WOI_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return WOI_OK;
+}
+
+// build the blob (and per-M coefficients) and copy it to the device
+woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
+{
+    if (!g->dev_dirty && g->blob_M == M) return WOI_OK;
+    woi_status st;
+    if (g->dev_dirty) {
+        if ((st = upload(&g->d_flux, g->flux_coef, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_arc_t0, g->arc_t0, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_arc_t1, g->arc_t1, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_arc_len, g->arc_len, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_arc_sign, g->arc_sign, s)) != WOI_OK) return st;
+        if (!g->d_blob) WOI_CUDA(cudaMalloc((void **)&g->d_blob, sizeof(DevGeom)));
+    }
+    DevGeom &b = g->blob;
+    std::memset(&b, 0, sizeof(b));
+    b.dim = g->dim;
+    b.n = g->n;
+    b.npad = 1;
+    while (b.npad < g->n) b.npad <<= 1;
+    b.M = M;
+    b.star_idx = g->star_idx;
+    b.star_K = g->star_idx >= 0 ? g->star.K : 0;
+    b.star_lmax = g->star_lmax;
+    for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g->n ? (uint32_t)(g->thresh[i] - 1) : 0xFFFFFFFFu;
+    for (int i = 0; i < g->n; ++i) {
+        for (int k = 0; k < g->dim; ++k) b.center[i][k] = g->surf[i].center[k];
+        b.radius[i] = g->surf[i].radius;
+        b.area[i] = g->area[i];
+        b.alpha_sign[i] = g->alpha[i] > 0 ? 1.0 : (g->alpha[i] < 0 ? -1.0 : 0.0);
+        b.beta_scale[i] = g->beta_scale[i];
+        b.tin[i] = g->tin[i];
+        b.tout[i] = g->tout[i];
+        b.type[i] = g->surf[i].type;
+        b.flux_basis[i] = g->flux_basis[i];
+        b.flux_off[i] = g->flux_off[i];
+        b.flux_n[i] = g->flux_n[i];
+        b.part_len[i][0] = g->part_len.empty() ? 0.0 : g->part_len[2 * i];
+        b.part_len[i][1] = g->part_len.empty() ? 0.0 : g->part_len[2 * i + 1];
+        b.arc_off[i] = g->arc_off.empty() ? 0 : g->arc_off[i];
+        b.arc_n[i] = g->arc_n.empty() ? 0 : g->arc_n[i];
+    }
+    // N w_i ||alpha||_1^i (Eq. woi_estimator with w_i = 1 - delta_iM / 2)
+    double Ai = 1.0;
+    for (int i = 0; i <= M; ++i) {
+        b.coef[i] = (double)g->n * (i == M ? 0.5 : 1.0) * Ai;
+        Ai *= g->alpha_l1;
+    }
+    if (g->star_idx >= 0) {
+        for (int k = 1; k <= g->star.K; ++k) {
+            b.star_a[k] = g->star.a[k];
+            b.star_b[k] = g->star.b[k];
+        }
+        for (int j = 0; j < kStarScan; ++j) {
+            b.star_scan[j][0] = g->star_scan[2 * j];
+            b.star_scan[j][1] = g->star_scan[2 * j + 1];
+        }
+        for (int j = 0; j <= kStarPanels; ++j) b.star_panel_s[j] = g->star_panel_s[j];
+    }
+    b.flux_coef = g->d_flux;
+    b.arc_t0 = g->d_arc_t0;
+    b.arc_t1 = g->d_arc_t1;
+    b.arc_len = g->d_arc_len;
+    b.arc_sign = g->d_arc_sign;
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    WOI_CUDA(cudaMemcpyAsync(g->d_blob, &b, sizeof(DevGeom), cudaMemcpyHostToDevice, s));
+    g->dev_dirty = false;
+    g->blob_M = M;
+    return WOI_OK;
+}
+
+woi_status ensure_scratch(woi_geometry *g, size_t bytes)
+{
+    if (g->scratch_bytes >= bytes) return WOI_OK;
+    cudaFree(g->d_scratch);
+    g->d_scratch = nullptr;
+    g->scratch_bytes = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc(&g->d_scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WOI_E_OOM, "device scratch allocation of %zu bytes failed", want);
+    }
+    g->scratch_bytes = want;
+    return WOI_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+woi_status check_opts(const woi_geometry *g, const woi_opts *o, int64_t n_pts, int64_t walk_begin, int64_t n_walks)
+{
+    if (!g->data_ready) return fail(WOI_E_STATE, "woi_set_sigma_and_data has not been called");
+    if (!o) return fail(WOI_E_INVALID_ARG, "null options");
+    if (o->M < 0 || o->M > WOI_MAX_M) return fail(WOI_E_INVALID_ARG, "M = %d outside [0, %d]", o->M, WOI_MAX_M);
+    if (o->variant != WOI_PLAIN && o->variant != WOI_VR) return fail(WOI_E_INVALID_ARG, "unknown variant %d", o->variant);
+    if (o->precision != WOI_MIXED && o->precision != WOI_FP64_PLAIN)
+        return fail(WOI_E_INVALID_ARG, "unknown precision %d", o->precision);
+    if (o->sched_group != 1 && o->sched_group != 32) return fail(WOI_E_INVALID_ARG, "sched_group must be 1 or 32");
+    if (n_pts < 0 || n_walks < 1 || walk_begin < 0) return fail(WOI_E_INVALID_ARG, "need n_pts >= 0, n_walks >= 1");
+    if (n_walks % o->sched_group || walk_begin % o->sched_group)
+        return fail(WOI_E_INVALID_ARG, "walk range must be a multiple of sched_group");
+    if (o->variant == WOI_VR && !g->vr_ok)
+        return fail(WOI_E_UNSUPPORTED, "variance reduction needs 2D Fourier (or zero) flux on every surface");
+    if (o->block_size != 0 && (o->block_size % 32 || o->block_size < 32 || o->block_size > kMixedMaxBlock))
+        return fail(WOI_E_INVALID_ARG, "block_size must be a multiple of 32 in [32, %d]", kMixedMaxBlock);
+    if (o->walks_per_lane < 0 || o->walks_per_lane > 4096) return fail(WOI_E_INVALID_ARG, "walks_per_lane out of range");
+    return WOI_OK;
+}
+
+// points of the call on the device (staged copy for host input); host input is checked to lie inside
+woi_status stage_points(woi_geometry *g, const double *points, int64_t n_pts, const double **d_points, void *staging,
+                        cudaStream_t s)
+{
+    if (pointer_on_device(points)) {
+        *d_points = points;
+        return WOI_OK;
+    }
+    for (int64_t p = 0; p < n_pts; ++p)
+        if (!inside_surface(*g, 0, points + p * g->dim))
+            return fail(WOI_E_GEOMETRY, "point %lld lies outside the outer surface", (long long)p);
+    WOI_CUDA(cudaMemcpyAsync(staging, points, (size_t)n_pts * g->dim * sizeof(double), cudaMemcpyHostToDevice, s));
+    *d_points = (const double *)staging;
+    return WOI_OK;
+}
+
+struct OutBuf {
+    double *user;
+    bool on_dev;
+    double *dev;
+    size_t count;
+};
+
+woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points, int64_t n_pts, int64_t walk_begin,
+                        int64_t n_walks, uint64_t seed, double *u, double *grad, double *se_u, double *se_grad,
+                        double *moments)
+{
+    woi_status st;
+    if ((st = check_opts(g, o, n_pts, walk_begin, n_walks)) != WOI_OK) return st;
+    if (!points && n_pts > 0) return fail(WOI_E_INVALID_ARG, "null points");
+    if ((st = ensure_device(g)) != WOI_OK) return st;
+    if (n_pts == 0) return WOI_OK;
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    const int d = g->dim, C = d + 1;
+    const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0, fp64 = o->precision == WOI_FP64_PLAIN;
+    if ((st = stage_geometry(g, o->M, s)) != WOI_OK) return st;
+
+    const int block = o->block_size ? o->block_size : 256;
+    const int L = o->walks_per_lane ? o->walks_per_lane : 8;
+    const int64_t unit_walks = (int64_t)block * L;
+    const int64_t chunks = fp64 ? 1 : (n_walks + unit_walks - 1) / unit_walks;
+    const int64_t units = n_pts * chunks;
+
+    // scratch layout: [inst desc][queue][partials][points][outputs]
+    size_t off = 0;
+    const size_t o_desc = off; off = align_up(off + sizeof(InstDesc), 256);
+    const size_t o_queue = off; off = align_up(off + sizeof(unsigned long long), 256);
+    const size_t o_part = off; off = align_up(off + (size_t)units * 2 * C * sizeof(double), 256);
+    const size_t o_pts = off; off = align_up(off + (size_t)n_pts * d * sizeof(double), 256);
+    OutBuf outs[5] = {{u, false, nullptr, (size_t)n_pts}, {grad, false, nullptr, (size_t)n_pts * d},
+                      {se_u, false, nullptr, (size_t)n_pts}, {se_grad, false, nullptr, (size_t)n_pts * d},
+                      {moments, false, nullptr, (size_t)n_pts * 2 * C}};
+    size_t o_out[5];
+    for (int k = 0; k < 5; ++k) {
+        outs[k].on_dev = pointer_on_device(outs[k].user);
+        o_out[k] = off;
+        if (outs[k].user && !outs[k].on_dev) off = align_up(off + outs[k].count * sizeof(double), 256);
+    }
+    if ((st = ensure_scratch(g, off)) != WOI_OK) return st;
+    char *base = (char *)g->d_scratch;
+    for (int k = 0; k < 5; ++k)
+        outs[k].dev = !outs[k].user ? nullptr : (outs[k].on_dev ? outs[k].user : (double *)(base + o_out[k]));
+
+    const double *d_points = nullptr;
+    if ((st = stage_points(g, points, n_pts, &d_points, base + o_pts, s)) != WOI_OK) return st;
+    if (o->timing && !g->ev_start) {
+        WOI_CUDA(cudaEventCreate(&g->ev_start));
+        WOI_CUDA(cudaEventCreate(&g->ev_stop));
+    }
+    g->timed = o->timing != 0;
+
+    FinalizeParams fp{};
+    fp.dim = d;
+    fp.n_pts = n_pts;
+    fp.n_walks = n_walks;
+    fp.sched_group = o->sched_group;
+    fp.unit_begin = 0;
+    fp.chunks_per_point = chunks;
+    fp.partials = (const double *)(base + o_part);
+    fp.u = outs[0].dev;
+    fp.grad = outs[1].dev;
+    fp.se_u = outs[2].dev;
+    fp.se_grad = outs[3].dev;
+    fp.moments = outs[4].dev;
+
+    if (!fp64) {
+        InstDesc desc{};
+        desc.geom = g->d_blob;
+        desc.points = d_points;
+        desc.n_pts = n_pts;
+        desc.n_walks = n_walks;
+        desc.walk_begin = walk_begin;
+        desc.unit_begin = 0;
+        desc.chunks_per_point = chunks;
+        desc.instance_id = 0;
+        desc.sched_group = o->sched_group;
+        WOI_CUDA(cudaMemcpyAsync(base + o_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, s));
+        WOI_CUDA(cudaMemsetAsync(base + o_queue, 0, sizeof(unsigned long long), s));
+        long long key = ((long long)d << 20) | ((long long)vr << 19) | ((long long)star << 18) | block;
+        int per_sm = 0;
+        auto it = g->occ_cache.find(key);
+        if (it == g->occ_cache.end()) {
+            WOI_CUDA(mixed_occupancy(d, vr, star, block, &per_sm));
+            g->occ_cache[key] = per_sm;
+        } else {
+            per_sm = it->second;
+        }
+        if (per_sm < 1) per_sm = 1;
+        const int64_t grid = std::min<int64_t>((int64_t)g->num_sms * per_sm, units);
+        MixedParams mp{};
+        mp.inst = (const InstDesc *)(base + o_desc);
+        mp.n_inst = 1;
+        mp.total_units = units;
+        mp.queue = (unsigned long long *)(base + o_queue);
+        mp.partials = (double *)(base + o_part);
+        mp.walks_per_lane = L;
+        mp.seed = seed;
+        if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_start, s));
+        WOI_CUDA(launch_mixed(d, vr, star, mp, (int)grid, block, s));
+        if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_stop, s));
+        WOI_CUDA(launch_finalize(fp, false, s));
+    } else {
+        // plain FP64 baseline: one launch per evaluation point into [n_pts][2C] accumulators
+        double *acc = (double *)(base + o_part);
+        WOI_CUDA(cudaMemsetAsync(acc, 0, (size_t)n_pts * 2 * C * sizeof(double), s));
+        if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_start, s));
+        for (int64_t p = 0; p < n_pts; ++p) {
+            Fp64PointParams pp{};
+            pp.geom = g->d_blob;
+            pp.x = d_points + p * d;
+            pp.point_id = (uint32_t)p;
+            pp.instance_id = 0;
+            pp.walk_begin = walk_begin;
+            pp.n_walks = n_walks;
+            pp.sched_group = o->sched_group;
+            pp.seed = seed;
+            pp.acc = acc + p * 2 * C;
+            WOI_CUDA(launch_fp64_point(d, vr, star, pp, s));
+        }
+        if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_stop, s));
+        WOI_CUDA(launch_finalize(fp, true, s));
+    }
+    bool any_host = false;
+    for (int k = 0; k < 5; ++k) {
+        if (outs[k].user && !outs[k].on_dev) {
+            WOI_CUDA(cudaMemcpyAsync(outs[k].user, outs[k].dev, outs[k].count * sizeof(double), cudaMemcpyDeviceToHost, s));
+            any_host = true;
+        }
+    }
+    if (any_host || !pointer_on_device(points)) WOI_CUDA(cudaStreamSynchronize(s));
+    return WOI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+woi_status woi_estimate(woi_geometry *g, const woi_opts *opts, const double *points, int64_t n_pts, int64_t n_walks,
+                        uint64_t seed, double *u, double *grad, double *se_u, double *se_grad)
+{
+    g_last_error.clear();
+    if (!g) return fail(WOI_E_INVALID_ARG, "null geometry");
+    return run_estimate(g, opts, points, n_pts, 0, n_walks, seed, u, grad, se_u, se_grad, nullptr);
+}
+
+woi_status woi_estimate_range(woi_geometry *g, const woi_opts *opts, const double *points, int64_t n_pts,
+                              int64_t walk_begin, int64_t n_walks, uint64_t seed, double *moments)
+{
+    g_last_error.clear();
+    if (!g) return fail(WOI_E_INVALID_ARG, "null geometry");
+    if (!moments) return fail(WOI_E_INVALID_ARG, "null moments");
+    return run_estimate(g, opts, points, n_pts, walk_begin, n_walks, seed, nullptr, nullptr, nullptr, nullptr, moments);
+}
+
+woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
+                           const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad)
+{
+    g_last_error.clear();
+    if (!g || !o || !x || (n > 0 && (!walk_ids || !f_u || !f_grad))) return fail(WOI_E_INVALID_ARG, "null argument");
+    woi_status st;
+    if ((st = check_opts(g, o, 1, 0, o->sched_group)) != WOI_OK) return st;
+    if (n < 0) return fail(WOI_E_INVALID_ARG, "n < 0");
+    if ((st = ensure_device(g)) != WOI_OK) return st;
+    if (n == 0) return WOI_OK;
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    const int d = g->dim;
+    if ((st = stage_geometry(g, o->M, s)) != WOI_OK) return st;
+    size_t off = 0;
+    const size_t o_x = off; off = align_up(off + d * sizeof(double), 256);
+    const size_t o_w = off; off = align_up(off + n * sizeof(uint64_t), 256);
+    const size_t o_u = off; off = align_up(off + n * sizeof(double), 256);
+    const size_t o_g = off; off = align_up(off + n * d * sizeof(double), 256);
+    if ((st = ensure_scratch(g, off)) != WOI_OK) return st;
+    char *base = (char *)g->d_scratch;
+    WOI_CUDA(cudaMemcpyAsync(base + o_x, x, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    WOI_CUDA(cudaMemcpyAsync(base + o_w, walk_ids, n * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    WalkValuesParams p{};
+    p.geom = g->d_blob;
+    p.x = (const double *)(base + o_x);
+    p.point_id = point_id;
+    p.instance_id = 0;
+    p.walks = (const uint64_t *)(base + o_w);
+    p.n = n;
+    p.sched_group = o->sched_group;
+    p.seed = seed;
+    p.f_u = (double *)(base + o_u);
+    p.f_grad = (double *)(base + o_g);
+    WOI_CUDA(launch_walk_values(d, o->variant == WOI_VR, g->star_idx >= 0, o->precision == WOI_FP64_PLAIN, p, s));
+    WOI_CUDA(cudaMemcpyAsync(f_u, p.f_u, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    WOI_CUDA(cudaMemcpyAsync(f_grad, p.f_grad, n * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    WOI_CUDA(cudaStreamSynchronize(s));
+    return WOI_OK;
+}
+
+woi_status woi_last_kernel_ms(woi_geometry *g, float *ms)
+{
+    g_last_error.clear();
+    if (!g || !ms) return fail(WOI_E_INVALID_ARG, "null argument");
+    if (!g->timed || !g->ev_stop) return fail(WOI_E_STATE, "no timed estimate on this handle");
+    WOI_CUDA(cudaEventSynchronize(g->ev_stop));
+    WOI_CUDA(cudaEventElapsedTime(ms, g->ev_start, g->ev_stop));
+    return WOI_OK;
+}
+
+woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, const int *m_per_inst,
+                              const double *const *points, const int64_t *n_pts, const int64_t *n_walks, uint64_t seed,
+                              double *const *u, double *const *grad, double *const *se_u, double *const *se_grad)
+{
+    g_last_error.clear();
+    return fail(WOI_E_UNSUPPORTED, "woi_estimate_batch is not available in this build yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,794 @@
+// woi_device.cuh -- device side of the Walk-on-Interfaces walk (sm_103a).
+//
+// One walk per thread.  Everything here is templated on the arithmetic type
+// Real (float for the mixed path, double for the FP64 path) and on the
+// dimension D, so the same source is the FP32 walk and the FP64 baseline.
+//
+// The method (Ding & Stinchcombe, arXiv 2508.16767):
+//   Sec. 3        alpha, beta, truncated Neumann series with w_i = 1 - delta_iM/2
+//   Sec. 4.2      transition densities (Eqs. naive_woi_p0, naive_woi_p) and the
+//                 Q / T factors (Eqs. naive_woi_Q, naive_woi_T)
+//   Sec. 4.3      scheduled interfaces (Thm 4.2), Eq. woi_estimator, Algs. 1-2
+//   Sec. 4.4      variance reduction (Alg. 3)
+//   Sec. 4.5      gradient tally with grad_x Phi
+// Readings: the alpha-sign product runs over m = 1..i (Thm 4.2); in the
+// uniform ("otherwise") transition T is unchanged because Q already carries the
+// signed K*(y_i, y_{i-1}) evaluated with the normal at y_i; "descendant" is a
+// strict descendant at any depth; a line/ray with no admissible intersection
+// ends the walk.
+#pragma once
+
+#include <cstdint>
+
+#include "woi_layout.h"
+
+namespace woi {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+// ---------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                       uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Random-number protocol: key = (seed_lo ^ point, seed_hi ^ instance);
+// counter = (walk_lo, walk_hi, step, (chain << 4) | sub) for the walk's own
+// words and (group_lo, group_hi, step, 0x100) for a shared schedule.
+struct Rng {
+    uint32_t k0, k1;
+    uint32_t w0, w1;
+    __device__ __forceinline__ U4 words(int step, int chain, int sub) const
+    {
+        return philox10(w0, w1, (uint32_t)step, (uint32_t)((chain << 4) | sub), k0, k1);
+    }
+};
+
+// uniform on (0,1): ((w >> 9) + 0.5) / 2^23, exact in FP32 and FP64
+template <typename Real>
+__device__ __forceinline__ Real u01(uint32_t w)
+{
+    return ((Real)(w >> 9) + (Real)0.5) * (Real)(1.0 / 8388608.0);
+}
+
+template <typename Real> struct RealOps;
+template <> struct RealOps<float> {
+    __device__ static __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
+    __device__ static __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+    __device__ static __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
+    __device__ static __forceinline__ float log_(float v) { return logf(v); }
+    __device__ static __forceinline__ void sincos_(float t, float *s, float *c) { sincosf(t, s, c); }
+    __device__ static __forceinline__ float fabs_(float v) { return fabsf(v); }
+    __device__ static __forceinline__ float rcp(float v) { return 1.0f / v; }
+};
+template <> struct RealOps<double> {
+    __device__ static __forceinline__ void sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
+    __device__ static __forceinline__ double sqrt_(double v) { return sqrt(v); }
+    __device__ static __forceinline__ double rsqrt_(double v) { return 1.0 / sqrt(v); }
+    __device__ static __forceinline__ double log_(double v) { return log(v); }
+    __device__ static __forceinline__ void sincos_(double t, double *s, double *c) { sincos(t, s, c); }
+    __device__ static __forceinline__ double fabs_(double v) { return fabs(v); }
+    __device__ static __forceinline__ double rcp(double v) { return 1.0 / v; }
+};
+
+// word k (k >= 1) of a (step, chain) stream: sub-call k / 4, lane k % 4
+struct StepWords {
+    U4 a, b;  // sub 0 and sub 1
+    __device__ __forceinline__ uint32_t get(int k) const
+    {
+        const U4 &v = (k < 4) ? a : b;
+        switch (k & 3) {
+        case 0: return v.x;
+        case 1: return v.y;
+        case 2: return v.z;
+        default: return v.w;
+        }
+    }
+};
+
+// isotropic unit vector from the words 1.. of a step (2D: one angle; 3D:
+// z = 1 - 2u, azimuth 2 pi u'; d >= 4: Box-Muller pairs then normalise)
+template <typename Real, int D>
+__device__ __forceinline__ void direction(const StepWords &w, Real *z)
+{
+    using O = RealOps<Real>;
+    if constexpr (D == 2) {
+        O::sincos2pi(u01<Real>(w.a.y), &z[1], &z[0]);
+    } else if constexpr (D == 3) {
+        const Real u = u01<Real>(w.a.y);
+        Real s, c;
+        O::sincos2pi(u01<Real>(w.a.z), &s, &c);
+        const Real rho = (Real)2 * O::sqrt_(u * ((Real)1 - u));  // sqrt(1 - (1-2u)^2)
+        z[0] = rho * c;
+        z[1] = rho * s;
+        z[2] = (Real)1 - (Real)2 * u;
+    } else {
+        Real g[D + 1];
+#pragma unroll
+        for (int j = 0; 2 * j < D; ++j) {
+            const Real ua = u01<Real>(w.get(1 + 2 * j));
+            const Real ub = u01<Real>(w.get(2 + 2 * j));
+            const Real rho = O::sqrt_((Real)-2 * O::log_(ua));
+            Real s, c;
+            O::sincos2pi(ub, &s, &c);
+            g[2 * j] = rho * c;
+            g[2 * j + 1] = rho * s;
+        }
+        Real n2 = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) n2 += g[k] * g[k];
+        const Real inv = O::rsqrt_(n2);
+#pragma unroll
+        for (int k = 0; k < D; ++k) z[k] = g[k] * inv;
+    }
+}
+
+template <int D> __host__ __device__ constexpr int choice_word() { return D == 2 ? 2 : (D == 3 ? 3 : (D == 4 ? 5 : 7)); }
+template <int D> __host__ __device__ constexpr bool two_calls() { return D >= 4; }
+
+// ---------------------------------------------------------------------------
+// geometry staged in shared memory (one instance)
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct SGeom {
+    int n, npad, M, has_star;
+    uint32_t sched_tm1[kMaxSurfPad];     // T_n - 1 (schedule thresholds), padded with 0xFFFFFFFF
+    Real center[kMaxSurf][kMaxDim];
+    Real radius[kMaxSurf];
+    Real area[kMaxSurf];
+    Real alpha_sign[kMaxSurf];
+    Real beta_scale[kMaxSurf];
+    int tin[kMaxSurf], tout[kMaxSurf];
+    int type[kMaxSurf];
+    Real coef[kMaxM + 1];                // N w_i ||alpha||_1^i
+    // star (at most one star surface per instance: its index, Fourier
+    // coefficients, scan points and arc-length panels)
+    int star_idx, star_K;
+    Real star_a[kMaxStar + 1], star_b[kMaxStar + 1];
+    Real star_lmax;                      // max |gamma'|
+    Real scan[kStarScan][2];             // gamma(t_j) - centre, t_j = 2 pi j / kStarScan
+    Real panel_s[kStarPanels + 1];       // arc length at t_j = 2 pi j / kStarPanels
+};
+
+// Load the device blob of one instance into shared memory (all threads of the block).
+template <typename Real>
+__device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        g.n = src->n;
+        g.npad = src->npad;
+        g.M = src->M;
+        g.has_star = src->star_idx >= 0;
+        g.star_idx = src->star_idx;
+        g.star_K = src->star_K;
+        g.star_lmax = (Real)src->star_lmax;
+    }
+    for (int i = tid; i < kMaxSurfPad; i += nt) g.sched_tm1[i] = src->sched_tm1[i];
+    for (int i = tid; i < src->n; i += nt) {
+        for (int k = 0; k < kMaxDim; ++k) g.center[i][k] = (Real)src->center[i][k];
+        g.radius[i] = (Real)src->radius[i];
+        g.area[i] = (Real)src->area[i];
+        g.alpha_sign[i] = (Real)src->alpha_sign[i];
+        g.beta_scale[i] = (Real)src->beta_scale[i];
+        g.tin[i] = src->tin[i];
+        g.tout[i] = src->tout[i];
+        g.type[i] = src->type[i];
+    }
+    for (int i = tid; i <= kMaxM; i += nt) g.coef[i] = (Real)src->coef[i];
+    if (src->star_idx >= 0) {
+        for (int k = tid; k <= kMaxStar; k += nt) {
+            g.star_a[k] = (Real)src->star_a[k];
+            g.star_b[k] = (Real)src->star_b[k];
+        }
+        for (int j = tid; j < kStarScan; j += nt) {
+            g.scan[j][0] = (Real)src->star_scan[j][0];
+            g.scan[j][1] = (Real)src->star_scan[j][1];
+        }
+        for (int j = tid; j <= kStarPanels; j += nt) g.panel_s[j] = (Real)src->star_panel_s[j];
+    }
+}
+
+// H_i from a 32-bit word: i = 0 uniform over the N surfaces, i >= 1 the first n
+// with w <= T_n - 1 (branch-free binary search over the padded thresholds)
+template <typename Real>
+__device__ __forceinline__ int schedule(const SGeom<Real> &g, int i, uint32_t w)
+{
+    if (i == 0) return (int)(((uint64_t)w * (uint64_t)g.n) >> 32);
+    int lo = 0;
+#pragma unroll 1
+    for (int step = g.npad >> 1; step > 0; step >>= 1)
+        if (g.sched_tm1[lo + step - 1] < w) lo += step;
+    return lo;
+}
+
+// 0: same surface, 1: prev is a strict descendant of cur, 2: otherwise
+template <typename Real>
+__device__ __forceinline__ int relation(const SGeom<Real> &g, int prev, int cur)
+{
+    if (prev == cur) return 0;
+    return (g.tin[cur] < g.tin[prev] && g.tin[prev] < g.tout[cur]) ? 1 : 2;
+}
+
+// ---------------------------------------------------------------------------
+// star curve: r(t) = R (1 + sum a_k cos kt + b_k sin kt) about its centre
+// ---------------------------------------------------------------------------
+template <typename Real>
+__device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr, Real *ddr)
+{
+    const int h = g.star_idx;
+    Real ck = ct, sk = st, s = 1, ds = 0, dds = 0;
+    for (int k = 1; k <= g.star_K; ++k) {
+        const Real a = g.star_a[k], b = g.star_b[k];
+        s += a * ck + b * sk;
+        ds += (Real)k * (b * ck - a * sk);
+        dds -= (Real)(k * k) * (a * ck + b * sk);
+        const Real cn = ck * ct - sk * st;  // cos((k+1)t), sin((k+1)t)
+        sk = sk * ct + ck * st;
+        ck = cn;
+    }
+    *r = g.radius[h] * s;
+    *dr = g.radius[h] * ds;
+    if (ddr) *ddr = g.radius[h] * dds;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real star_speed(const SGeom<Real> &g, Real t)
+{
+    Real st, ct, r, dr;
+    RealOps<Real>::sincos_(t, &st, &ct);
+    star_eval(g, ct, st, &r, &dr, (Real *)nullptr);
+    return RealOps<Real>::sqrt_(r * r + dr * dr);
+}
+
+// point (absolute) and outward unit normal at parameter t
+template <typename Real>
+__device__ __forceinline__ void star_point_normal(const SGeom<Real> &g, Real t, Real *y, Real *n)
+{
+    Real st, ct, r, dr;
+    RealOps<Real>::sincos_(t, &st, &ct);
+    star_eval(g, ct, st, &r, &dr, (Real *)nullptr);
+    const int h = g.star_idx;
+    y[0] = g.center[h][0] + r * ct;
+    y[1] = g.center[h][1] + r * st;
+    const Real tx = dr * ct - r * st, ty = dr * st + r * ct;
+    const Real inv = RealOps<Real>::rsqrt_(tx * tx + ty * ty);
+    n[0] = ty * inv;
+    n[1] = -tx * inv;
+}
+
+// Gauss-Legendre 8-point rule on [-1, 1] (positive half)
+__device__ __forceinline__ double gl8_x(int q)
+{
+    const double x[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    return x[q];
+}
+__device__ __forceinline__ double gl8_w(int q)
+{
+    const double w[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    return w[q];
+}
+
+// arc length from 0 to t (t in [0, 2 pi]): panel table + 8-point Gauss-Legendre on the partial panel
+template <typename Real>
+__device__ Real star_arclen(const SGeom<Real> &g, Real t)
+{
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kStarPanels);
+    int j = (int)(t / H);
+    j = j < 0 ? 0 : (j >= kStarPanels ? kStarPanels - 1 : j);
+    const Real a = (Real)j * H, half = (Real)0.5 * (t - a), mid = a + half;
+    Real s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const Real xq = (Real)gl8_x(q) * half, wq = (Real)gl8_w(q);
+        s += wq * (star_speed(g, mid - xq) + star_speed(g, mid + xq));
+    }
+    return g.panel_s[j] + half * s;
+}
+
+// t in [t_lo, t_hi] with arclen(t) = s (safeguarded Newton)
+template <typename Real>
+__device__ Real star_invert(const SGeom<Real> &g, Real s, Real t_lo, Real t_hi)
+{
+    const Real s_lo = star_arclen(g, t_lo), s_hi = star_arclen(g, t_hi);
+    Real t = t_lo + (t_hi - t_lo) * (s - s_lo) / (s_hi - s_lo);
+    const int iters = sizeof(Real) == 4 ? 12 : 40;
+    for (int it = 0; it < iters; ++it) {
+        const Real f = star_arclen(g, t) - s;
+        if (f > 0) t_hi = t; else t_lo = t;
+        Real tn = t - f / star_speed(g, t);
+        if (!(tn > t_lo && tn < t_hi)) tn = (Real)0.5 * (t_lo + t_hi);
+        const Real step = RealOps<Real>::fabs_(tn - t);
+        t = tn;
+        if (step < (sizeof(Real) == 4 ? (Real)1e-7 : (Real)1e-15)) break;
+    }
+    return t;
+}
+
+// panel containing arc length s (binary search in the table)
+template <typename Real>
+__device__ __forceinline__ Real star_uniform_param(const SGeom<Real> &g, Real s)
+{
+    int lo = 0, hi = kStarPanels;
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (g.panel_s[m] <= s) lo = m; else hi = m;
+    }
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kStarPanels);
+    return star_invert(g, s, (Real)lo * H, (Real)(lo + 1) * H);
+}
+
+// f(t) = (gamma(t) - y) x z and f'(t) for the line y + s z
+template <typename Real>
+__device__ __forceinline__ void star_line_f(const SGeom<Real> &g, Real t, const Real *yc, const Real *z, Real *f,
+                                            Real *df)
+{
+    Real st, ct, r, dr;
+    RealOps<Real>::sincos_(t, &st, &ct);
+    star_eval(g, ct, st, &r, &dr, (Real *)nullptr);
+    const Real px = r * ct - yc[0], py = r * st - yc[1];
+    *f = px * z[1] - py * z[0];
+    const Real tx = dr * ct - r * st, ty = dr * st + r * ct;
+    *df = tx * z[1] - ty * z[0];
+}
+
+template <typename Real>
+__device__ Real star_refine(const SGeom<Real> &g, Real a, Real b, Real fa, const Real *yc, const Real *z)
+{
+    Real t = (Real)0.5 * (a + b);
+    const int iters = sizeof(Real) == 4 ? 30 : 80;
+    for (int it = 0; it < iters; ++it) {
+        Real f, df;
+        star_line_f(g, t, yc, z, &f, &df);
+        if ((f < 0) == (fa < 0)) a = t; else b = t;
+        Real tn = t - f / df;
+        if (!(tn > a && tn < b)) tn = (Real)0.5 * (a + b);
+        const Real step = RealOps<Real>::fabs_(tn - t);
+        t = tn;
+        if (step < (sizeof(Real) == 4 ? (Real)2e-7 : (Real)1e-15) || b - a < (sizeof(Real) == 4 ? (Real)1e-7 : (Real)1e-15))
+            break;
+    }
+    return t;
+}
+
+// Intersections of the line (ray = false) or ray (ray = true) y + s z with the
+// star: roots of f on a kStarScan-sample scan, with hidden root pairs found
+// from the extremum of f in intervals where |f| may reach 0 (|f'| <= lmax).
+// Returns q; tt[] receives the line parameters s, th[] the curve parameters.
+template <typename Real>
+__device__ int star_intersections(const SGeom<Real> &g, const Real *y, const Real *z, bool ray, Real *tt, Real *th)
+{
+    const int h = g.star_idx;
+    const Real yc[2] = {y[0] - g.center[h][0], y[1] - g.center[h][1]};
+    const Real e = yc[0] * z[1] - yc[1] * z[0];
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kStarScan);
+    const Real guard = g.star_lmax * H * (Real)0.5;
+    const Real tiny = sizeof(Real) == 4 ? (Real)2e-5 : (Real)1e-9;
+    int q = 0;
+    Real f0 = g.scan[0][0] * z[1] - g.scan[0][1] * z[0] - e;
+    Real fa = f0;
+    for (int j = 0; j < kStarScan; ++j) {
+        const int jn = (j + 1 == kStarScan) ? 0 : j + 1;
+        const Real fb = (jn == 0) ? f0 : g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
+        const Real a = (Real)j * H, b = (Real)(j + 1) * H;
+        Real cand[2];
+        int nc = 0;
+        if ((fa < 0) != (fb < 0)) {
+            cand[nc++] = star_refine(g, a, b, fa, yc, z);
+        } else if (RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
+            Real f1, d1, f2, d2;
+            star_line_f(g, a, yc, z, &f1, &d1);
+            star_line_f(g, b, yc, z, &f2, &d2);
+            if ((d1 < 0) != (d2 < 0)) {
+                // extremum of f in (a, b): bisection on f'
+                Real lo = a, hi = b, dlo = d1;
+                for (int it = 0; it < (sizeof(Real) == 4 ? 24 : 52); ++it) {
+                    const Real m = (Real)0.5 * (lo + hi);
+                    Real fm, dm;
+                    star_line_f(g, m, yc, z, &fm, &dm);
+                    if ((dm < 0) == (dlo < 0)) { lo = m; dlo = dm; } else hi = m;
+                }
+                const Real te = (Real)0.5 * (lo + hi);
+                Real fe, de;
+                star_line_f(g, te, yc, z, &fe, &de);
+                if ((fe < 0) != (fa < 0)) {
+                    cand[nc++] = star_refine(g, a, te, fa, yc, z);
+                    cand[nc++] = star_refine(g, te, b, fe, yc, z);
+                }
+            }
+        }
+        for (int c = 0; c < nc; ++c) {
+            Real p[2], nn[2];
+            star_point_normal(g, cand[c], p, nn);
+            const Real s = (p[0] - y[0]) * z[0] + (p[1] - y[1]) * z[1];
+            const bool ok = ray ? (s > tiny) : (RealOps<Real>::fabs_(s) > tiny);
+            if (ok && q < kMaxRoots) {
+                tt[q] = s;
+                th[q] = cand[c];
+                ++q;
+            }
+        }
+        fa = fb;
+    }
+    return q;
+}
+
+// ---------------------------------------------------------------------------
+// flux datum b_h(y) at the start point (Sec. 1); u = unit outward direction
+// for spheres / (cos t, sin t) of the parameter for 2D curves; n = normal
+// ---------------------------------------------------------------------------
+template <typename Real, int D>
+__device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *u, const Real *n)
+{
+    const int basis = gd->flux_basis[h];
+    const double *c = gd->flux_coef + gd->flux_off[h];
+    const int nc = gd->flux_n[h];
+    if (basis == kFluxFourier) {
+        Real v = (Real)c[0], ck = u[0], sk = u[1];
+        for (int k = 1; 2 * k <= nc - 1; ++k) {
+            v += (Real)c[2 * k - 1] * ck + (Real)c[2 * k] * sk;
+            const Real cn = ck * u[0] - sk * u[1];
+            sk = sk * u[0] + ck * u[1];
+            ck = cn;
+        }
+        return v;
+    }
+    if (basis == kFluxRealSH) {
+        if constexpr (D == 3) {
+            // associated Legendre P_l^m(x) without the (-1)^m phase, x = cos(polar)
+            const Real x = u[2];
+            const Real sx = RealOps<Real>::sqrt_(fmax((double)0, (double)(1 - x * x)));
+            Real ca = 1, sa = 0;  // cos / sin of the azimuth
+            if (sx > (Real)0) {
+                ca = u[0] / sx;
+                sa = u[1] / sx;
+            }
+            const int L = (int)(RealOps<double>::sqrt_((double)nc) + 1e-9) - 1;
+            Real v = 0;
+            Real pmm = 1, cm = 1, sm = 0;  // P_m^m, cos(m az), sin(m az)
+            for (int m = 0; m <= L; ++m) {
+                if (m > 0) {
+                    pmm *= (Real)(2 * m - 1) * sx;
+                    const Real cn = cm * ca - sm * sa;
+                    sm = sm * ca + cm * sa;
+                    cm = cn;
+                }
+                Real p_prev = 0, p_cur = pmm;
+                for (int l = m; l <= L; ++l) {
+                    if (l > m) {
+                        const Real p_next = (l == m + 1) ? x * (Real)(2 * m + 1) * pmm
+                                                         : ((Real)(2 * l - 1) * x * p_cur - (Real)(l + m - 1) * p_prev) / (Real)(l - m);
+                        p_prev = p_cur;
+                        p_cur = p_next;
+                    }
+                    // normalisation sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)
+                    double ratio = 1.0;
+                    for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+                    const Real nlm = (Real)sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * ratio);
+                    if (m == 0) {
+                        v += (Real)c[l * l + l] * nlm * p_cur;
+                    } else {
+                        const Real base = (Real)1.4142135623730951 * nlm * p_cur;
+                        v += (Real)c[l * l + l + m] * base * cm + (Real)c[l * l + l - m] * base * sm;
+                    }
+                }
+            }
+            return v;
+        }
+        return 0;
+    }
+    if (basis == kFluxHarmonicPoly) {
+        const Real s = (Real)c[0];
+        const int T = (int)c[1];
+        Real grad[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) grad[k] = 0;
+        for (int t = 0; t < T; ++t) {
+            const double *row = c + 2 + t * (D + 1);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int ek = (int)row[1 + k];
+                if (ek == 0) continue;
+                Real term = (Real)row[0] * (Real)ek;
+                for (int j = 0; j < D; ++j) {
+                    const int e = (int)row[1 + j] - (j == k ? 1 : 0);
+                    for (int p = 0; p < e; ++p) term *= y[j];
+                }
+                grad[k] += term;
+            }
+        }
+        Real v = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) v += n[k] * grad[k];
+        return s * v;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation point: (hi, lo) split so that x - y is accurate in FP32
+// ---------------------------------------------------------------------------
+template <typename Real, int D>
+struct XPoint {
+    Real hi[D], lo[D];
+};
+
+template <typename Real, int D>
+__device__ __forceinline__ XPoint<Real, D> make_point(const double *x)
+{
+    XPoint<Real, D> p;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        p.hi[k] = (Real)x[k];
+        p.lo[k] = (Real)(x[k] - (double)p.hi[k]);
+    }
+    return p;
+}
+
+// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D]
+template <typename Real, int D>
+__device__ __forceinline__ void tally(const XPoint<Real, D> &x, const Real *y, Real c, Real *acc)
+{
+    using O = RealOps<Real>;
+    Real dx[D], r2 = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        dx[k] = (x.hi[k] - y[k]) + x.lo[k];
+        r2 += dx[k] * dx[k];
+    }
+    if (r2 <= (Real)0) return;  // x on a walk state exactly: measure zero, contributes nothing
+    constexpr double PI = 3.14159265358979323846;
+    if constexpr (D == 2) {
+        const Real inv_r2 = O::rcp(r2);
+        acc[0] += c * ((Real)(-1.0 / (4.0 * PI)) * O::log_(r2));
+        const Real gc = c * (Real)(-1.0 / (2.0 * PI)) * inv_r2;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[1 + k] += gc * dx[k];
+    } else {
+        // omega_d = 2 pi^{d/2} / Gamma(d/2)
+        constexpr double omega = D == 3 ? 4.0 * PI : (D == 4 ? 2.0 * PI * PI : (D == 5 ? 8.0 * PI * PI / 3.0 : PI * PI * PI));
+        const Real inv_r = O::rsqrt_(r2);
+        Real inv_pow = inv_r;  // r^{-(d-2)}
+#pragma unroll
+        for (int k = 1; k < D - 2; ++k) inv_pow *= inv_r;
+        acc[0] += c * (Real)(1.0 / ((D - 2) * omega)) * inv_pow;
+        const Real gc = c * (Real)(-1.0 / omega) * inv_pow * inv_r * inv_r;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[1 + k] += gc * dx[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one chain's state and its transitions
+// ---------------------------------------------------------------------------
+template <typename Real, int D>
+struct Chain {
+    Real y[D];
+    Real Q, T;
+    bool alive;
+};
+
+// start (i = 0): y_0 uniform on dOmega_h (plain) or on dOmega_h^{+/-} (VR), Q = beta(y_0) |part|
+template <typename Real, int D, bool VR, bool STAR>
+__device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int k, const StepWords &w,
+                            Chain<Real, D> &ch)
+{
+    ch.T = 1;
+    ch.alive = true;
+    Real u[D], nrm[D];
+    Real part_len = g.area[h];
+    if constexpr (VR) {
+        part_len = (Real)gd->part_len[h][k];
+        if (!(part_len > (Real)0) || gd->flux_basis[h] == kFluxZero) {
+            ch.alive = false;
+            ch.Q = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) ch.y[c] = 0;
+            return;
+        }
+    }
+    const bool is_star = STAR && g.type[h] == kStar;
+    if (!VR && !is_star) {
+        direction<Real, D>(w, u);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            ch.y[c] = g.center[h][c] + g.radius[h] * u[c];
+            nrm[c] = u[c];
+        }
+    } else {
+        if constexpr (D == 2) {
+            // a parameter angle: uniform by arc length on the surface, or on the
+            // concatenated arcs of the requested sign (VR)
+            Real t;
+            const Real s_target = u01<Real>(w.a.y) * part_len;
+            if constexpr (VR) {
+                Real s = s_target;
+                const int want = k == 0 ? 1 : -1;
+                int a_sel = -1;
+                for (int a = gd->arc_off[h]; a < gd->arc_off[h] + gd->arc_n[h]; ++a) {
+                    if (gd->arc_sign[a] != want) continue;
+                    a_sel = a;
+                    if (s < (Real)gd->arc_len[a]) break;
+                    s -= (Real)gd->arc_len[a];
+                }
+                if (s > (Real)gd->arc_len[a_sel]) s = (Real)gd->arc_len[a_sel];
+                const Real t0 = (Real)gd->arc_t0[a_sel], t1 = (Real)gd->arc_t1[a_sel];
+                if (is_star) {
+                    t = star_invert(g, star_arclen(g, t0) + s, t0, t1);
+                } else {
+                    t = t0 + s / g.radius[h];
+                }
+            } else {
+                t = star_uniform_param(g, s_target);
+            }
+            if (is_star) {
+                star_point_normal(g, t, ch.y, nrm);
+            } else {
+                Real st, ct;
+                RealOps<Real>::sincos_(t, &st, &ct);
+                nrm[0] = ct;
+                nrm[1] = st;
+                ch.y[0] = g.center[h][0] + g.radius[h] * ct;
+                ch.y[1] = g.center[h][1] + g.radius[h] * st;
+            }
+            RealOps<Real>::sincos_(t, &u[1], &u[0]);
+        }
+    }
+    ch.Q = g.beta_scale[h] * flux_value<Real, D>(gd, h, ch.y, u, nrm) * part_len;
+}
+
+// transition i >= 1 from surface hp to h (relation rel)
+template <typename Real, int D, bool STAR>
+__device__ void chain_step(const SGeom<Real> &g, int hp, int h, int rel, const StepWords &w, Chain<Real, D> &ch)
+{
+    using O = RealOps<Real>;
+    if (STAR && g.type[h] == kStar) {
+        if constexpr (D == 2) {
+            Real ynew[2], nrm[2];
+            if (rel == 2) {
+                // uniform on the star by arc length; Q *= K*(y_i, y_{i-1}) |dOmega_h|
+                const Real t = star_uniform_param(g, u01<Real>(w.a.y) * g.area[h]);
+                star_point_normal(g, t, ynew, nrm);
+                const Real dx = ynew[0] - ch.y[0], dy = ynew[1] - ch.y[1];
+                const Real r2 = dx * dx + dy * dy;
+                ch.Q *= (dx * nrm[0] + dy * nrm[1]) * O::rcp(r2) * (Real)(1.0 / (2.0 * 3.14159265358979323846)) *
+                        g.area[h];
+            } else {
+                Real z[2];
+                direction<Real, 2>(w, z);
+                Real tt[kMaxRoots], th[kMaxRoots];
+                const int q = star_intersections(g, ch.y, z, rel == 1, tt, th);
+                if (q == 0) {
+                    ch.alive = false;
+                    ch.T = 0;
+                    return;
+                }
+                const int j = (int)(((uint64_t)w.get(choice_word<2>()) * (uint64_t)q) >> 32);
+                // the j-th smallest line parameter
+                int sel = 0;
+                for (int a = 0; a < q; ++a) {
+                    int rank = 0;
+                    for (int b = 0; b < q; ++b) rank += (tt[b] < tt[a]) || (tt[b] == tt[a] && b < a);
+                    if (rank == j) sel = a;
+                }
+                star_point_normal(g, th[sel], ynew, nrm);
+                const Real dot = (ynew[0] - ch.y[0]) * nrm[0] + (ynew[1] - ch.y[1]) * nrm[1];
+                if (rel == 0) ch.Q *= (Real)0.5;
+                ch.T *= (Real)q * (dot > 0 ? (Real)1 : (dot < 0 ? (Real)-1 : (Real)0));
+            }
+            ch.y[0] = ynew[0];
+            ch.y[1] = ynew[1];
+            return;
+        }
+    }
+    // circles / d-spheres: one isotropic unit vector z serves the three cases
+    Real z[D], dy[D], b = 0, c0 = 0;
+    direction<Real, D>(w, z);
+    const Real R = g.radius[h];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        dy[c] = ch.y[c] - g.center[h][c];
+        b += z[c] * dy[c];
+        c0 += dy[c] * dy[c];
+    }
+    c0 -= R * R;
+    if (rel == 0) {
+        // line through a point of the sphere: the other intersection, t = -2 b; Q *= 1/2, T *= q sign = +1
+#pragma unroll
+        for (int c = 0; c < D; ++c) ch.y[c] += (Real)-2 * b * z[c];
+        ch.Q *= (Real)0.5;
+    } else if (rel == 1) {
+        // ray from inside: t = -b + sqrt(b^2 - c0) > 0 (stable form); Q *= 1, T *= +1
+        const Real s = O::sqrt_(b * b - c0);
+        const Real t = (b <= 0) ? (s - b) : (-c0) / (b + s);
+#pragma unroll
+        for (int c = 0; c < D; ++c) ch.y[c] += t * z[c];
+    } else {
+        // uniform y' = c + R z (normal z); Q *= K*(y', y) |dOmega_h| = (y'-y).z / (omega_d r^d) |dOmega_h|
+        Real diff[D], r2 = 0, dot = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const Real yn = g.center[h][c] + R * z[c];
+            diff[c] = yn - ch.y[c];
+            r2 += diff[c] * diff[c];
+            dot += diff[c] * z[c];
+            ch.y[c] = yn;
+        }
+        constexpr double PI = 3.14159265358979323846;
+        constexpr double omega = D == 2 ? 2.0 * PI : (D == 3 ? 4.0 * PI : (D == 4 ? 2.0 * PI * PI : (D == 5 ? 8.0 * PI * PI / 3.0 : PI * PI * PI)));
+        Real inv_rd;
+        if constexpr (D == 2) {
+            inv_rd = O::rcp(r2);
+        } else {
+            const Real ir = O::rsqrt_(r2);
+            inv_rd = ir;
+#pragma unroll
+            for (int k = 1; k < D; ++k) inv_rd *= ir;
+        }
+        ch.Q *= dot * inv_rd * (Real)(1.0 / omega) * g.area[h];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one walk: returns the tally f[0] (u) and f[1..D] (grad u) of
+// N sum_i w_i A^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i Phi(x, Y_i), summed
+// over the two chains for VR
+// ---------------------------------------------------------------------------
+template <typename Real, int D, bool VR, bool STAR>
+__device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const XPoint<Real, D> &x, const Rng &rng,
+                     int sched_group, uint64_t group, Real *f)
+{
+#pragma unroll
+    for (int c = 0; c <= D; ++c) f[c] = 0;
+    Chain<Real, D> ch[VR ? 2 : 1];
+    Real S = 1;
+    int hp = 0;
+    for (int i = 0; i <= g.M; ++i) {
+        StepWords w0;
+        w0.a = rng.words(i, 0, 0);
+        if constexpr (two_calls<D>()) w0.b = rng.words(i, 0, 1);
+        uint32_t hw = w0.a.x;
+        if (sched_group > 1) {
+            const U4 gw = philox10((uint32_t)group, (uint32_t)(group >> 32), (uint32_t)i, 0x100u, rng.k0, rng.k1);
+            hw = gw.x;
+        }
+        const int h = schedule(g, i, hw);
+        if (i > 0) S *= g.alpha_sign[h];
+        const int rel = (i > 0) ? relation(g, hp, h) : 0;
+#pragma unroll
+        for (int k = 0; k < (VR ? 2 : 1); ++k) {
+            StepWords w = w0;
+            if (k == 1) {
+                w.a = rng.words(i, 1, 0);
+                if constexpr (two_calls<D>()) w.b = rng.words(i, 1, 1);
+            }
+            if (i == 0) {
+                chain_start<Real, D, VR, STAR>(g, gd, h, k, w, ch[k]);
+            } else if (ch[k].alive) {
+                chain_step<Real, D, STAR>(g, hp, h, rel, w, ch[k]);
+            }
+            if (ch[k].alive) tally<Real, D>(x, ch[k].y, g.coef[i] * S * ch[k].Q * ch[k].T, f);
+        }
+        hp = h;
+    }
+}
+
+}  // namespace woi

@@ -1,0 +1,116 @@
+// woi_kernels.cu -- finalize kernels and the dispatch of the walk kernels
+// over the dimension (the walk kernels are instantiated in woi_k<d>.cu).
+#include <cuda_runtime.h>
+
+#include "woi_kernels.h"
+
+namespace woi {
+
+// ---------------------------------------------------------------------------
+// finalize: ordered sums of the unit partials -> mean, SE, raw moments
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(FinalizeParams p)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int D = p.dim, C = D + 1;
+    if (idx >= p.n_pts * C) return;
+    const int64_t point = idx / C;
+    const int c = (int)(idx - point * C);
+    double S1 = 0.0, S2 = 0.0;
+    const double *src = p.partials + (p.unit_begin + point * p.chunks_per_point) * (2 * C);
+    for (int64_t ch = 0; ch < p.chunks_per_point; ++ch) {
+        S1 += src[ch * 2 * C + c];
+        S2 += src[ch * 2 * C + C + c];
+    }
+    if (p.moments) {
+        p.moments[point * 2 * C + c] = S1;
+        p.moments[point * 2 * C + C + c] = S2;
+    }
+    const double W = (double)p.n_walks;
+    const double G = W / (double)p.sched_group;
+    const double mean = S1 / W;
+    double var = (S2 - G * mean * mean) / (G > 1.0 ? G - 1.0 : 1.0);
+    var = var > 0.0 ? var : 0.0;
+    const double se = sqrt(var / G);
+    if (c == 0) {
+        if (p.u) p.u[point] = mean;
+        if (p.se_u) p.se_u[point] = se;
+    } else {
+        if (p.grad) p.grad[point * D + c - 1] = mean;
+        if (p.se_grad) p.se_grad[point * D + c - 1] = se;
+    }
+}
+
+// the per-point accumulators [n_pts][2(D+1)] -> outputs
+__global__ void k_finalize_acc(FinalizeParams p)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int D = p.dim, C = D + 1;
+    if (idx >= p.n_pts * C) return;
+    const int64_t point = idx / C;
+    const int c = (int)(idx - point * C);
+    const double S1 = p.partials[point * 2 * C + c], S2 = p.partials[point * 2 * C + C + c];
+    if (p.moments) {
+        p.moments[point * 2 * C + c] = S1;
+        p.moments[point * 2 * C + C + c] = S2;
+    }
+    const double W = (double)p.n_walks, G = W / (double)p.sched_group, mean = S1 / W;
+    double var = (S2 - G * mean * mean) / (G > 1.0 ? G - 1.0 : 1.0);
+    var = var > 0.0 ? var : 0.0;
+    const double se = sqrt(var / G);
+    if (c == 0) {
+        if (p.u) p.u[point] = mean;
+        if (p.se_u) p.se_u[point] = se;
+    } else {
+        if (p.grad) p.grad[point * D + c - 1] = mean;
+        if (p.se_grad) p.se_grad[point * D + c - 1] = se;
+    }
+}
+
+template <typename F>
+static cudaError_t by_dim(int dim, bool star, F &&f)
+{
+    switch (dim) {
+    case 2: return star ? f(DimTag<2, true>{}) : f(DimTag<2, false>{});
+    case 3: return f(DimTag<3, false>{});
+    case 4: return f(DimTag<4, false>{});
+    case 5: return f(DimTag<5, false>{});
+    case 6: return f(DimTag<6, false>{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, cudaStream_t s)
+{
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::mixed(vr, p, grid, block, s); });
+}
+
+cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_per_sm)
+{
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy(vr, block, blocks_per_sm); });
+}
+
+cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s)
+{
+    const int64_t n = p.n_pts * (p.dim + 1);
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)((n + 255) / 256);
+    if (from_acc) k_finalize_acc<<<grid, 256, 0, s>>>(p);
+    else k_finalize<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_point(int dim, bool vr, bool star, const Fp64PointParams &p, cudaStream_t s)
+{
+    const int grid = (int)((p.n_walks + 255) / 256);
+    if (grid == 0) return cudaSuccess;
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::fp64_point(vr, p, grid, s); });
+}
+
+cudaError_t launch_walk_values(int dim, bool vr, bool star, bool fp64, const WalkValuesParams &p, cudaStream_t s)
+{
+    if (p.n == 0) return cudaSuccess;
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::values(vr, fp64, p, s); });
+}
+
+}  // namespace woi

@@ -1,0 +1,83 @@
+// woi_kernels.h -- launch parameters and launchers of the libwoi kernels
+// (internal to the library; the public interface is include/woi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "woi_layout.h"
+
+namespace woi {
+
+constexpr int kMixedMaxBlock = 256;
+
+struct MixedParams {
+    const InstDesc *inst;              // device [n_inst], sorted by unit_begin
+    int n_inst;
+    int64_t total_units;
+    unsigned long long *queue;         // device work-queue head, zero before the launch
+    double *partials;                  // device [total_units][2 (dim+1)]
+    int walks_per_lane;
+    uint64_t seed;
+};
+
+struct FinalizeParams {
+    int dim;
+    int64_t n_pts;
+    int64_t n_walks;
+    int sched_group;
+    int64_t unit_begin;
+    int64_t chunks_per_point;
+    const double *partials;            // unit partials, or [n_pts][2 (dim+1)] accumulators
+    double *u, *grad, *se_u, *se_grad; // device, each may be null
+    double *moments;                   // device [n_pts][2][dim+1], may be null
+};
+
+struct Fp64PointParams {
+    const DevGeom *geom;
+    const double *x;                   // device [dim]
+    uint32_t point_id, instance_id;
+    int64_t walk_begin, n_walks;
+    int sched_group;
+    uint64_t seed;
+    double *acc;                       // device [2 (dim+1)]
+};
+
+struct WalkValuesParams {
+    const DevGeom *geom;
+    const double *x;                   // device [dim]
+    uint32_t point_id, instance_id;
+    const uint64_t *walks;             // device [n]
+    int64_t n;
+    int sched_group;
+    uint64_t seed;
+    double *f_u, *f_grad;              // device [n], [n][dim]
+};
+
+// launchers of one dimension / star flag; defined in woi_kernels_impl.cuh and
+// explicitly instantiated in woi_k<d>.cu
+template <int D, bool STAR>
+struct DimLaunchers {
+    static cudaError_t mixed(bool vr, const MixedParams &p, int grid, int block, cudaStream_t s);
+    static cudaError_t occupancy(bool vr, int block, int *blocks_per_sm);
+    static cudaError_t fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s);
+    static cudaError_t values(bool vr, bool fp64, const WalkValuesParams &p, cudaStream_t s);
+};
+template <int D, bool STAR> struct DimTag {
+    using L = DimLaunchers<D, STAR>;
+};
+extern template struct DimLaunchers<2, false>;
+extern template struct DimLaunchers<2, true>;
+extern template struct DimLaunchers<3, false>;
+extern template struct DimLaunchers<4, false>;
+extern template struct DimLaunchers<5, false>;
+extern template struct DimLaunchers<6, false>;
+
+cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, cudaStream_t s);
+cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_per_sm);
+cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s);
+cudaError_t launch_fp64_point(int dim, bool vr, bool star, const Fp64PointParams &p, cudaStream_t s);
+cudaError_t launch_walk_values(int dim, bool vr, bool star, bool fp64, const WalkValuesParams &p, cudaStream_t s);
+
+}  // namespace woi

@@ -1,0 +1,269 @@
+// woi_kernels_impl.cuh -- Walk-on-Interfaces kernel templates for sm_103a
+// (instantiated per dimension in woi_k<d>.cu).
+//
+//   k_walk_mixed      persistent kernel: FP32 walks, one walk per thread; each CTA
+//                     takes (instance, point, walk-chunk) units from a device work
+//                     queue, accumulates compensated FP32 sums per lane and reduces
+//                     them in FP64 to one partial per unit (deterministic order)
+//   k_finalize        per (instance, point, component): ordered sum of the unit
+//                     partials, mean and standard error from the schedule-group
+//                     means (Algorithm 1)
+//   k_walk_fp64_point FP64 walks, one launch per evaluation point, FP64 atomics
+//   k_walk_values     per-walk tallies (pathwise replay), FP32 or FP64
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "woi_device.cuh"
+#include "woi_kernels.h"
+
+namespace woi {
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum_all(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Neumaier (compensated) FP32 accumulation
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v)
+{
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+}
+
+__device__ __forceinline__ int find_instance(const InstDesc *inst, int n_inst, int64_t unit)
+{
+    int lo = 0, hi = n_inst;  // last k with unit_begin <= unit
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (inst[m].unit_begin <= unit) lo = m; else hi = m;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// persistent mixed-precision walk kernel
+// ---------------------------------------------------------------------------
+template <int D, bool VR, bool STAR>
+__global__ void __launch_bounds__(256) k_walk_mixed(MixedParams p)
+{
+    __shared__ SGeom<float> g;
+    __shared__ double red[kMixedMaxBlock / 32][2 * (D + 1)];
+    __shared__ long long unit_sh;
+    __shared__ int inst_sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int B = blockDim.x, L = p.walks_per_lane;
+    int cur_inst = -1;
+
+    for (;;) {
+        if (tid == 0) {
+            const unsigned long long u = atomicAdd(p.queue, 1ull);
+            unit_sh = (long long)u;
+            inst_sh = (u < (unsigned long long)p.total_units) ? find_instance(p.inst, p.n_inst, (int64_t)u) : -1;
+        }
+        __syncthreads();
+        const long long unit = unit_sh;
+        const int k = inst_sh;
+        if (unit >= p.total_units) break;
+        const InstDesc &id = p.inst[k];
+        if (k != cur_inst) {
+            load_geometry(g, id.geom);
+            cur_inst = k;
+            __syncthreads();
+        }
+        const int64_t local = unit - id.unit_begin;
+        const int64_t point = local / id.chunks_per_point;
+        const int64_t chunk = local - point * id.chunks_per_point;
+        const XPoint<float, D> x = make_point<float, D>(id.points + point * D);
+        Rng rng;
+        rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
+        rng.k1 = (uint32_t)(p.seed >> 32) ^ id.instance_id;
+        const int64_t w_end = id.walk_begin + id.n_walks;
+        const int64_t w_base = id.walk_begin + chunk * (int64_t)B * L;
+
+        float s1[D + 1], c1[D + 1], s2[D + 1];
+#pragma unroll
+        for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
+        for (int j = 0; j < L; ++j) {
+            const int64_t w = w_base + (int64_t)j * B + tid;
+            float f[D + 1];
+            const bool valid = w < w_end;
+            if (valid) {
+                rng.w0 = (uint32_t)w;
+                rng.w1 = (uint32_t)((uint64_t)w >> 32);
+                walk<float, D, VR, STAR>(g, id.geom, x, rng, id.sched_group, (uint64_t)w / 32u, f);
+            } else {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) f[c] = 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
+            if (id.sched_group == 1) {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
+            } else {
+                // the 32 lanes of a warp share one schedule (walks w .. w+31 form a group);
+                // a warp's round is entirely valid or entirely past the end
+#pragma unroll
+                for (int c = 0; c <= D; ++c) {
+                    const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
+                    if (lane == 0 && valid) s2[c] += gm * gm;
+                }
+            }
+        }
+        // CTA reduction in FP64, fixed order
+#pragma unroll
+        for (int c = 0; c <= D; ++c) {
+            const double v1 = warp_sum((double)s1[c] + (double)c1[c]);
+            const double v2 = warp_sum((double)s2[c]);
+            if (lane == 0) {
+                red[warp][c] = v1;
+                red[warp][D + 1 + c] = v2;
+            }
+        }
+        __syncthreads();
+        if (tid < 2 * (D + 1)) {
+            double acc = 0.0;
+            for (int wi = 0; wi < nwarp; ++wi) acc += red[wi][tid];
+            p.partials[unit * (2 * (D + 1)) + tid] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 baseline: one launch per point, one walk per thread, FP64 atomics
+// ---------------------------------------------------------------------------
+template <int D, bool VR, bool STAR>
+__global__ void __launch_bounds__(256) k_walk_fp64_point(Fp64PointParams p)
+{
+    __shared__ SGeom<double> g;
+    __shared__ double red[8][2 * (D + 1)];
+    load_geometry(g, p.geom);
+    __syncthreads();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t w = p.walk_begin + (int64_t)blockIdx.x * blockDim.x + tid;
+    const bool valid = w < p.walk_begin + p.n_walks;
+    const XPoint<double, D> x = make_point<double, D>(p.x);
+    double f[D + 1];
+    if (valid) {
+        Rng rng;
+        rng.k0 = (uint32_t)p.seed ^ p.point_id;
+        rng.k1 = (uint32_t)(p.seed >> 32) ^ p.instance_id;
+        rng.w0 = (uint32_t)w;
+        rng.w1 = (uint32_t)((uint64_t)w >> 32);
+        walk<double, D, VR, STAR>(g, p.geom, x, rng, p.sched_group, (uint64_t)w / 32u, f);
+    } else {
+#pragma unroll
+        for (int c = 0; c <= D; ++c) f[c] = 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c <= D; ++c) {
+        const double v1 = warp_sum(f[c]);
+        double v2;
+        if (p.sched_group == 1) {
+            v2 = warp_sum(f[c] * f[c]);
+        } else {
+            const double gm = v1 / 32.0;  // lane 0 holds the group sum
+            v2 = (lane == 0 && valid) ? gm * gm : 0.0;
+        }
+        if (lane == 0) {
+            red[warp][c] = v1;
+            red[warp][D + 1 + c] = v2;
+        }
+    }
+    __syncthreads();
+    if (tid < 2 * (D + 1)) {
+        double acc = 0.0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) acc += red[wi][tid];
+        atomicAdd(p.acc + tid, acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-walk values (pathwise replay)
+// ---------------------------------------------------------------------------
+template <typename Real, int D, bool VR, bool STAR>
+__global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
+{
+    __shared__ SGeom<Real> g;
+    load_geometry(g, p.geom);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const uint64_t w = p.walks[i];
+    const XPoint<Real, D> x = make_point<Real, D>(p.x);
+    Rng rng;
+    rng.k0 = (uint32_t)p.seed ^ p.point_id;
+    rng.k1 = (uint32_t)(p.seed >> 32) ^ p.instance_id;
+    rng.w0 = (uint32_t)w;
+    rng.w1 = (uint32_t)(w >> 32);
+    Real f[D + 1];
+    walk<Real, D, VR, STAR>(g, p.geom, x, rng, p.sched_group, w / 32u, f);
+    p.f_u[i] = (double)f[0];
+#pragma unroll
+    for (int c = 0; c < D; ++c) p.f_grad[i * D + c] = (double)f[1 + c];
+}
+
+// launchers of one dimension / star flag (explicitly instantiated in woi_k<d>.cu)
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::mixed(bool vr, const MixedParams &p, int grid, int block, cudaStream_t s)
+    {
+        if constexpr (D == 2) {
+            if (vr) {
+                k_walk_mixed<2, true, STAR><<<grid, block, 0, s>>>(p);
+                return cudaGetLastError();
+            }
+        }
+        k_walk_mixed<D, false, STAR><<<grid, block, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, int *blocks_per_sm)
+    {
+        if constexpr (D == 2) {
+            if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<2, true, STAR>, block, 0);
+        }
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, false, STAR>, block, 0);
+    }
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s)
+    {
+        if constexpr (D == 2) {
+            if (vr) {
+                k_walk_fp64_point<2, true, STAR><<<grid, 256, 0, s>>>(p);
+                return cudaGetLastError();
+            }
+        }
+        k_walk_fp64_point<D, false, STAR><<<grid, 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::values(bool vr, bool fp64, const WalkValuesParams &p, cudaStream_t s)
+    {
+        const int grid = (int)((p.n + 127) / 128);
+        if constexpr (D == 2) {
+            if (vr) {
+                if (fp64) k_walk_values<double, 2, true, STAR><<<grid, 128, 0, s>>>(p);
+                else k_walk_values<float, 2, true, STAR><<<grid, 128, 0, s>>>(p);
+                return cudaGetLastError();
+            }
+        }
+        if (fp64) k_walk_values<double, D, false, STAR><<<grid, 128, 0, s>>>(p);
+        else k_walk_values<float, D, false, STAR><<<grid, 128, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+
+}  // namespace woi

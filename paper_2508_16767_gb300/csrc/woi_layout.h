@@ -1,0 +1,60 @@
+// woi_layout.h -- the device blob of one geometry instance, written by the
+// host side of libwoi and read (then staged to shared memory) by its kernels.
+#pragma once
+
+#include <cstdint>
+
+namespace woi {
+
+constexpr int kMaxDim = 6;
+constexpr int kMaxSurf = 128;          // surfaces per instance (WOI_MAX_SURF)
+constexpr int kMaxSurfPad = 128;       // schedule thresholds padded to a power of two
+constexpr int kMaxM = 32;              // truncation (WOI_MAX_M)
+constexpr int kMaxStar = 16;           // star Fourier degree (WOI_MAX_STAR_DEGREE)
+constexpr int kStarScan = 256;         // curve samples of the intersection scan
+constexpr int kStarPanels = 256;       // arc-length panels
+constexpr int kMaxRoots = 2 * (kMaxStar + 1) + 2;
+
+enum { kSphere = 0, kStar = 1 };
+enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3 };
+
+struct DevGeom {
+    int dim, n, npad, M;
+    int star_idx, star_K;              // star_idx = -1: no star in this instance
+    double star_lmax;                  // bound on |gamma'| of the star
+    uint32_t sched_tm1[kMaxSurfPad];   // T_n - 1, padded with 0xFFFFFFFF
+    double center[kMaxSurf][kMaxDim];
+    double radius[kMaxSurf];
+    double area[kMaxSurf];
+    double alpha_sign[kMaxSurf];       // sign(alpha_n) in {-1, 0, 1}
+    double beta_scale[kMaxSurf];       // beta_n / b_n (Sec. 3)
+    int tin[kMaxSurf], tout[kMaxSurf]; // Euler-tour interval of each region in the tree
+    int type[kMaxSurf];
+    double coef[kMaxM + 1];            // N w_i ||alpha||_1^i for the current M
+    double star_a[kMaxStar + 1], star_b[kMaxStar + 1];
+    double star_scan[kStarScan][2];    // gamma(t_j) - centre
+    double star_panel_s[kStarPanels + 1];
+    int flux_basis[kMaxSurf], flux_off[kMaxSurf], flux_n[kMaxSurf];
+    const double *flux_coef;           // device array
+    double part_len[kMaxSurf][2];      // |dOmega^+|, |dOmega^-| (2D variance reduction)
+    int arc_off[kMaxSurf], arc_n[kMaxSurf];
+    const double *arc_t0;              // device arrays of the beta-sign arcs
+    const double *arc_t1;
+    const double *arc_len;
+    const int *arc_sign;
+};
+
+// one instance of a (possibly batched) estimate
+struct InstDesc {
+    const DevGeom *geom;
+    const double *points;              // device [n_pts][dim] FP64
+    int64_t n_pts;
+    int64_t n_walks;
+    int64_t walk_begin;
+    int64_t unit_begin;                // first work unit of this instance
+    int64_t chunks_per_point;
+    uint32_t instance_id;              // random-stream instance id
+    int sched_group;
+};
+
+}  // namespace woi

@@ -1,0 +1,110 @@
+"""The C-ABI library loads, exports every entry point that include/woi.h
+declares, and rejects bad input on the host (no GPU needed: no kernel runs)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2508_16767_gb300 import build as B
+from paper_2508_16767_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def woi():
+    B.build()
+    from paper_2508_16767_gb300 import woi as W
+    return W
+
+
+def declared_entry_points():
+    text = open(os.path.join(ROOT, "include", "woi.h")).read()
+    return sorted(set(re.findall(r"WOI_API\s+[\w\s\*]*?\b(woi_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(woi):
+    names = declared_entry_points()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(woi.lib, n), n
+    assert set(names) == set(woi.EXPORTED)
+    assert "sm_103a" in woi.version()
+
+
+def test_geometry_validation(woi):
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(7, [wl._sphere([0] * 6, 1.0)], [-1])
+    assert e.value.status == 1
+    # overlapping inclusions
+    surfs = [wl._sphere([0, 0], 1.0), wl._sphere([0.2, 0], 0.3), wl._sphere([-0.2, 0], 0.3)]
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(2, surfs, [-1, 0, 0])
+    assert e.value.status == 2
+    # inclusion poking out of its parent
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(2, [wl._sphere([0, 0], 1.0), wl._sphere([0.8, 0], 0.3)], [-1, 0])
+    assert e.value.status == 2
+    # parent cycle
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(2, [wl._sphere([0, 0], 1.0), wl._sphere([0, 0], 0.5), wl._sphere([0, 0], 0.2)],
+                                [-1, 2, 1])
+    assert e.value.status == 1
+    # star in 3D
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(3, [wl._star([0, 0, 0], 1.0, [0, 0.1], [0, 0])], [-1])
+    assert e.value.status == 4
+    # circle crossing a star boundary
+    a = [0, 0, 0, 0, 0, 0.15]
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(2, [wl._star([0, 0], 1.0, a, [0] * 6), wl._sphere([1.05, 0], 0.15)], [-1, 0])
+    assert e.value.status == 2
+    # the star workload is valid
+    prob = wl.star_inclusions_problem()
+    h = woi.Geometry(prob)
+    h.close()
+
+
+def test_data_validation(woi):
+    prob = wl.concentric_2d_problem()
+    h = woi.woi_create_geometry(2, prob["surfaces"], prob["parent"])
+    try:
+        bad = [wl.fourier([1.0], [0.0], a0=0.3), prob["flux"][1]]       # non-zero mean on dOmega_1
+        with pytest.raises(woi.WoiError) as e:
+            woi.woi_set_sigma_and_data(h, prob["sigma"], bad)
+        assert e.value.status == 3
+        with pytest.raises(woi.WoiError) as e:
+            woi.woi_set_sigma_and_data(h, [0.0, 2.0], prob["flux"])
+        assert e.value.status == 1
+        nonharm = [wl.harmonic_poly(1.0, [(1.0, (2, 0))], 2), prob["flux"][1]]   # P = x^2 is not harmonic
+        with pytest.raises(woi.WoiError) as e:
+            woi.woi_set_sigma_and_data(h, prob["sigma"], nonharm)
+        assert e.value.status == 3
+        with pytest.raises(woi.WoiError) as e:
+            woi.woi_set_sigma_and_data(h, prob["sigma"], [wl.real_sh({(1, 0): 1.0}, 1), prob["flux"][1]])
+        assert e.value.status == 4
+        woi.woi_set_sigma_and_data(h, prob["sigma"], prob["flux"])
+    finally:
+        woi.lib.woi_destroy_geometry(h)
+
+
+def test_estimate_argument_checks_and_no_device(woi):
+    """Option checks come first; without a GPU the call reports WOI_E_NO_DEVICE."""
+    g = woi.Geometry(wl.nested_3d_problem())
+    pts = wl.ball_points(4, 3, 1)
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_estimate(g, pts, 1000, sched_group=32)           # 1000 is not a multiple of 32
+    assert e.value.status == 1
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_estimate(g, pts, 1024, variant="vr")              # VR needs 2D Fourier data
+    assert e.value.status == 4
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_estimate(g, pts, 1024, M=40)
+    assert e.value.status == 1
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(woi.WoiError) as e:
+            woi.woi_estimate(g, pts, 1024)
+        assert e.value.status == 5
+    g.close()

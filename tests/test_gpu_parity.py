@@ -1,0 +1,215 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+* Pathwise replay: the same Philox streams give the same walks; per-walk
+  tallies agree to 1e-12 (FP64 path) and 1e-5 (FP32 path) relative to the
+  walk's magnitude scale (sum_i |c_i| (|Phi_i| + 1) for u, sum_i |c_i| |grad Phi_i|
+  for grad u), apart from a bounded fraction of FP32 walks whose discrete
+  choices flip at a near-tangency (star curves only).
+* Per-point estimates over the same walks: the FP32 path's mean differs from
+  the oracle's by far less than the Monte Carlo standard error (1e-2 SE), the
+  FP64 path's by rounding only; sizes span several work units and a ragged tail.
+* The full-size 3D workload (4096 points x 1e5 walks, the benchmark's launch
+  configuration) on sampled points.
+* Edge cases: no points, M = 0, the maximum M, shared schedules, resumable walk
+  ranges, device pointers, bit-reproducibility, and host-side errors.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_16767_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-12
+FP32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2508_16767_gb300 import build
+    build.build()
+    from paper_2508_16767_gb300 import woi
+    return woi
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import core
+    core.build()
+    core.set_mutant(0)
+    return core
+
+
+def e3b_problem():
+    return {"name": "e3b", "dim": 3, "surfaces": [wl._sphere([0.0] * 3, 1.0), wl._sphere([0.0] * 3, 0.4)],
+            "parent": [-1, 0], "sigma": [1.0, 0.5],
+            "flux": [wl.real_sh({(1, 1): 5.0 * np.sqrt(4 * np.pi / 3)}, 1), wl.real_sh({(2, 0): 0.7, (2, -2): 0.2}, 2)],
+            "M": 6}
+
+
+def cases():
+    rng = np.random.default_rng(8)
+    yield "2d-concentric", wl.concentric_2d_problem(), wl.concentric_2d_points()[[1, 20, 45, 62]], "plain"
+    yield "2d-concentric-vr", wl.concentric_2d_problem(), wl.concentric_2d_points()[[5, 33]], "vr"
+    yield "3d-nested", wl.nested_3d_problem(), wl.ball_points(4, 3, 12), "plain"
+    yield "e3b", e3b_problem(), wl.ball_points(3, 3, 5), "plain"
+    yield "6d-nested", wl.nested_6d_problem(), wl.ball_points(3, 6, 14), "plain"
+    star3 = wl.star_inclusions_problem(seed=3, n_incl=3)
+    yield "star-3", star3, np.array([[0.1, 0.2], [-0.5, 0.3], [0.6, -0.4]]), "plain"
+    yield "star-3-vr", star3, np.array([[0.1, 0.2], [0.0, -0.7]]), "vr"
+    star = wl.star_inclusions_problem()
+    yield "star-32", star, wl.star_inclusions_points(star, 4, seed=13), "plain"
+    yield "star-32-vr", star, wl.star_inclusions_points(star, 3, seed=14), "vr"
+    for dim in (2, 3):
+        inst = wl.manufactured_instance(dim, rng, k_max=12)
+        yield f"manufactured-{dim}d", inst, wl.ball_points(3, dim, 40 + dim, radius=0.9), "plain"
+
+
+CASES = list(cases())
+IDS = [c[0] for c in CASES]
+
+
+def walk_ids(n=96):
+    ids = np.arange(n, dtype=np.uint64)
+    ids[-8:] = np.uint64(2 ** 33 + 12345) + np.arange(8, dtype=np.uint64)   # high counter word in use
+    return ids
+
+
+def replay(W, O, prob, x, variant, precision, point_id):
+    g = W.Geometry(prob)
+    ids = walk_ids()
+    gv = W.woi_walk_values(g, x, ids, seed=7, point_id=point_id, M=prob["M"], variant=variant, precision=precision)
+    ov = O.walks(prob, x, ids, seed=7, M=prob["M"], variant=variant, point_id=point_id)
+    g.close()
+    sc_u = ov["scale"][:, 0] + ov["scale"][:, 1]
+    sc_g = ov["scale"][:, 2]
+    eu = np.abs(gv["u"] - ov["u"]) / np.maximum(sc_u, 1e-300)
+    eg = np.max(np.abs(gv["grad"] - ov["grad"]), axis=1) / np.maximum(sc_g, 1e-300)
+    return eu, eg
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_replay_fp64_per_walk(W, O, case):
+    name, prob, x, variant = case
+    for p in range(len(x)):
+        eu, eg = replay(W, O, prob, x[p], variant, "fp64", p)
+        assert eu.max() <= FP64_RTOL, (name, p, eu.max())
+        assert eg.max() <= FP64_RTOL, (name, p, eg.max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_replay_fp32_per_walk(W, O, case):
+    name, prob, x, variant = case
+    bad = tot = 0
+    for p in range(len(x)):
+        eu, eg = replay(W, O, prob, x[p], variant, "mixed", p)
+        viol = (eu > FP32_RTOL) | (eg > FP32_RTOL)
+        bad += int(viol.sum())
+        tot += len(eu)
+    allowed = 0 if "star" not in name else max(1, tot // 200)
+    assert bad <= allowed, f"{name}: {bad} of {tot} walks beyond {FP32_RTOL}"
+
+
+def _estimates(W, O, prob, x, n_walks, variant="plain", sched_group=1, seed=3, **kw):
+    g = W.Geometry(prob)
+    gr = W.woi_estimate(g, x, n_walks, seed=seed, M=prob["M"], variant=variant, sched_group=sched_group, **kw)
+    g.close()
+    orr = O.estimate(prob, x, n_walks, seed=seed, M=prob["M"], variant=variant, sched_group=sched_group)
+    return gr, orr
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_estimate_mixed_matches_oracle(W, O, case):
+    name, prob, x, variant = case
+    n_walks = 5000 if "star" not in name else 1200          # several 2048-walk units and a ragged tail
+    gr, orr = _estimates(W, O, prob, x, n_walks, variant)
+    assert np.all(np.abs(gr["u"] - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12), name
+    assert np.all(np.abs(gr["grad"] - orr["grad"]) <= 1e-2 * orr["se_grad"] + 1e-12), name
+    assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-3)
+    assert np.allclose(gr["se_grad"], orr["se_grad"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if "star-32" not in c[0]], ids=[i for i in IDS if "star-32" not in i])
+def test_estimate_fp64_matches_oracle(W, O, case):
+    name, prob, x, variant = case
+    gr, orr = _estimates(W, O, prob, x, 1000, variant, precision="fp64")
+    scale = orr["se_u"] * np.sqrt(1000) + np.abs(orr["u"])
+    assert np.all(np.abs(gr["u"] - orr["u"]) <= 1e-10 * scale), name
+    assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-8)
+
+
+def test_shared_schedules(W, O):
+    prob = wl.nested_3d_problem()
+    x = wl.ball_points(5, 3, 3)
+    for precision in ("mixed", "fp64"):
+        gr, orr = _estimates(W, O, prob, x, 4096 + 32 * 7, sched_group=32, precision=precision)
+        assert np.all(np.abs(gr["u"] - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12)
+        assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-3)
+
+
+def test_full_size_3d_workload_sampled(W, O):
+    """4096 points x 1e5 walks, M = 6, in the benchmark's launch configuration;
+    the oracle recomputes sampled points (their own stream ids) with all walks."""
+    prob = wl.nested_3d_problem()
+    x = wl.ball_points(4096, 3, 12)
+    g = W.Geometry(prob)
+    gr = W.woi_estimate(g, x, 100000, seed=0, M=6)
+    g.close()
+    assert np.all(np.isfinite(gr["u"])) and np.all(gr["se_u"] > 0)
+    prep = O.Prepared(prob)
+    for p in [0, 1, 777, 2048, 4095]:
+        orr = O.estimate(prob, x[p:p + 1], 100000, seed=0, M=6, point_offset=p, prepared=prep)
+        assert abs(gr["u"][p] - orr["u"][0]) <= 1e-2 * orr["se_u"][0], p
+        assert np.all(np.abs(gr["grad"][p] - orr["grad"][0]) <= 1e-2 * orr["se_grad"][0]), p
+        assert abs(gr["se_u"][p] / orr["se_u"][0] - 1) < 1e-3
+
+
+def test_ranges_add_up(W):
+    prob = wl.concentric_2d_problem()
+    x = wl.concentric_2d_points()[:10]
+    g = W.Geometry(prob)
+    a = W.woi_estimate_range(g, x, 0, 6144, seed=5)
+    b1 = W.woi_estimate_range(g, x, 0, 2048, seed=5)
+    b2 = W.woi_estimate_range(g, x, 2048, 4096, seed=5)
+    g.close()
+    assert np.allclose(a, b1 + b2, rtol=1e-12, atol=1e-14)
+    f = W.finalize_moments(a, 6144)
+    assert np.all(np.isfinite(f["u"]))
+
+
+def test_device_pointers_stream_and_reproducibility(W):
+    import torch
+    prob = wl.nested_3d_problem()
+    x = wl.ball_points(300, 3, 9)
+    g = W.Geometry(prob)
+    host = W.woi_estimate(g, x, 3000, seed=1)
+    again = W.woi_estimate(g, x, 3000, seed=1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xd = torch.from_numpy(x).cuda()
+        dev = W.woi_estimate(g, xd, 3000, seed=1)
+    s.synchronize()
+    g.close()
+    for k in ("u", "grad", "se_u", "se_grad"):
+        assert np.array_equal(host[k], again[k])            # deterministic reduction order
+        assert np.array_equal(host[k], dev[k].cpu().numpy())
+
+
+def test_edge_cases(W, O):
+    prob = wl.concentric_2d_problem()
+    g = W.Geometry(prob)
+    empty = W.woi_estimate(g, np.zeros((0, 2)), 1000)
+    assert empty["u"].shape == (0,)
+    with pytest.raises(W.WoiError) as e:
+        W.woi_estimate(g, np.array([[2.0, 0.0]]), 1000)
+    assert e.value.status == 2
+    x = wl.concentric_2d_points()[:3]
+    for M in (0, 1, 32):
+        gr = W.woi_estimate(g, x, 2000, seed=4, M=M)
+        orr = O.estimate(prob, x, 2000, seed=4, M=M)
+        assert np.all(np.abs(gr["u"] - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12), M
+    one = W.woi_estimate(g, x[:1], 1, seed=4)                  # a single walk: SE is 0 by convention
+    assert np.isfinite(one["u"][0])
+    g.close()
