@@ -13,7 +13,7 @@ module prepares its inputs from a problem dictionary with numpy/scipy:
     turned into integer thresholds T_n = floor(2^32 C_n / A), C_n the cumulative
     sum of |alpha| in surface order and A = ||alpha||_1 (T_N = 2^32);
   * Sec. 1: the tree (strict-descendant relation) from the parent array;
-  * |dOmega_i| (circle / d-sphere closed form, star by adaptive quadrature);
+  * |dOmega_i| (circle / d-sphere closed form, star by Gauss-Legendre quadrature);
   * Sec. 4.4: the beta >= 0 / beta < 0 arcs of 2D surfaces for the variance-
     reduced estimator, by a dense sign scan and Brent's method.
 """
@@ -187,13 +187,28 @@ def star_speed(s, t):
     return math.hypot(r, dr)
 
 
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(40)
+
+
+def star_length(s, a, b):
+    """int_a^b |gamma'(t)| dt by 40-point Gauss-Legendre on panels of width <= 2 pi / 256
+    (machine precision for the smooth integrands of star curves)."""
+    n = max(1, int(math.ceil((b - a) / (2 * math.pi / STAR_PANELS))))
+    tot = 0.0
+    for j in range(n):
+        lo = a + (b - a) * j / n
+        hi = a + (b - a) * (j + 1) / n
+        t = 0.5 * (hi - lo) * _GL_X + 0.5 * (hi + lo)
+        tot += 0.5 * (hi - lo) * float(np.sum(_GL_W * np.array([star_speed(s, x) for x in t])))
+    return tot
+
+
 def star_arclen_panels(s):
-    """Arc length at t_j = 2 pi j / STAR_PANELS by adaptive quadrature."""
+    """Arc length at t_j = 2 pi j / STAR_PANELS."""
     out = np.zeros(STAR_PANELS + 1)
     h = 2 * math.pi / STAR_PANELS
     for j in range(STAR_PANELS):
-        v, _ = integrate.quad(lambda t: star_speed(s, t), j * h, (j + 1) * h, epsabs=1e-15, epsrel=1e-14)
-        out[j + 1] = out[j] + v
+        out[j + 1] = out[j] + star_length(s, j * h, (j + 1) * h)
     return out
 
 
@@ -246,7 +261,7 @@ def vr_arcs(dim, s, flux, bscale, n_scan=20000):
         if s["kind"] == "sphere":
             L = s["radius"] * (b - a)
         else:
-            L, _ = integrate.quad(lambda x: star_speed(s, x), a, b, epsabs=1e-14, epsrel=1e-13, limit=200)
+            L = star_length(s, a, b)
         arcs.append((a, b, sign, L))
     return arcs
 

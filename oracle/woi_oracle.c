@@ -379,28 +379,70 @@ static int or_intersections(const or_problem *P, int h, const double *y, const d
         }
         return q;
     }
-    /* star: roots in the parameter angle of cross(gamma(t) - y, z) = 0, by a
-     * dense sign scan and bisection, then the line parameter of each root */
-    double f_prev = 0.0, t_prev = 0.0;
-    double pt[2];
+    /* star: roots in the parameter angle of f(t) = cross(gamma(t) - y, z) = 0,
+     * by a dense sign scan and bisection, then the line parameter of each root.
+     * Ray from an interior point: scan f over [0, 2 pi].
+     * Line through y = gamma(t_y) on the curve: f vanishes at t_y itself; scan
+     * g(t) = f(t) / sin((t - t_y) / 2) over the open range (t_y, t_y + 2 pi),
+     * where sin > 0, g has exactly the other roots of f, and g tends to
+     * 2 f'(t_y) and -2 f'(t_y) at the two ends.  An intersection within one
+     * scan step of y (a near-tangent line) is therefore not lost. */
     const double *scan = P->star_scan + (size_t)h * (OR_STAR_SCAN + 1) * 2;
-    for (int j = 0; j <= OR_STAR_SCAN; ++j) {
-        double th = 2.0 * M_PI * j / OR_STAR_SCAN;
-        double f = (scan[2 * j] - y[0]) * z[1] - (scan[2 * j + 1] - y[1]) * z[0];
-        if (j > 0 && ((f_prev < 0.0) != (f < 0.0))) {
-            double lo = t_prev, hi = th, flo = f_prev;
-            for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
-                double m = 0.5 * (lo + hi);
-                or_star_point(P, h, m, pt);
-                double fm = (pt[0] - y[0]) * z[1] - (pt[1] - y[1]) * z[0];
-                if ((fm < 0.0) == (flo < 0.0)) { lo = m; flo = fm; } else hi = m;
+    double pt[2];
+    const double H = 2.0 * M_PI / OR_STAR_SCAN;
+    if (ray) {
+        double f_prev = 0.0, t_prev = 0.0;
+        for (int j = 0; j <= OR_STAR_SCAN; ++j) {
+            double th = H * j;
+            double f = (scan[2 * j] - y[0]) * z[1] - (scan[2 * j + 1] - y[1]) * z[0];
+            if (j > 0 && ((f_prev < 0.0) != (f < 0.0))) {
+                double lo = t_prev, hi = th, flo = f_prev;
+                for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+                    double m = 0.5 * (lo + hi);
+                    or_star_point(P, h, m, pt);
+                    double fm = (pt[0] - y[0]) * z[1] - (pt[1] - y[1]) * z[0];
+                    if ((fm < 0.0) == (flo < 0.0)) { lo = m; flo = fm; } else hi = m;
+                }
+                or_star_point(P, h, 0.5 * (lo + hi), pt);
+                double t = (pt[0] - y[0]) * z[0] + (pt[1] - y[1]) * z[1];
+                if (t > tiny && q < OR_MAX_ROOTS) ts[q++] = t;
             }
-            double tr = 0.5 * (lo + hi);
-            or_star_point(P, h, tr, pt);
-            double t = (pt[0] - y[0]) * z[0] + (pt[1] - y[1]) * z[1];
-            if ((ray ? (t > tiny) : (fabs(t) > tiny)) && q < OR_MAX_ROOTS) ts[q++] = t;
+            f_prev = f; t_prev = th;
         }
-        f_prev = f; t_prev = th;
+    } else {
+        const double ty = or_param_angle(P, h, y);
+        double r, dr;
+        or_star_r(P, h, ty, &r, &dr);
+        const double gx = dr * cos(ty) - r * sin(ty), gy = dr * sin(ty) + r * cos(ty);
+        const double fpy = gx * z[1] - gy * z[0];      /* f'(t_y) */
+        const int jy = (int)floor(ty / H);
+        double g_prev = 2.0 * fpy, t_prev = ty;
+        for (int k = 1; k <= OR_STAR_SCAN + 1; ++k) {
+            double th, g;
+            if (k <= OR_STAR_SCAN) {
+                th = H * (jy + k);                      /* unwrapped angle in (t_y, t_y + 2 pi] */
+                if (th >= ty + 2.0 * M_PI) continue;
+                int j = (jy + k) % OR_STAR_SCAN;
+                double f = (scan[2 * j] - y[0]) * z[1] - (scan[2 * j + 1] - y[1]) * z[0];
+                g = f / sin(0.5 * (th - ty));
+            } else {
+                th = ty + 2.0 * M_PI;                   /* the limit at the far end */
+                g = -2.0 * fpy;
+            }
+            if ((g_prev < 0.0) != (g < 0.0)) {
+                double lo = t_prev, hi = th, glo = g_prev;
+                for (int it = 0; it < 200 && hi - lo > 1e-16; ++it) {
+                    double m = 0.5 * (lo + hi);
+                    or_star_point(P, h, m, pt);
+                    double gm = ((pt[0] - y[0]) * z[1] - (pt[1] - y[1]) * z[0]) / sin(0.5 * (m - ty));
+                    if ((gm < 0.0) == (glo < 0.0)) { lo = m; glo = gm; } else hi = m;
+                }
+                or_star_point(P, h, 0.5 * (lo + hi), pt);
+                double t = (pt[0] - y[0]) * z[0] + (pt[1] - y[1]) * z[1];
+                if (fabs(t) > tiny && q < OR_MAX_ROOTS) ts[q++] = t;
+            }
+            g_prev = g; t_prev = th;
+        }
     }
     /* insertion sort by t */
     for (int a = 1; a < q; ++a) {

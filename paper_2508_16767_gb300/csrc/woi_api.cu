@@ -119,8 +119,8 @@ struct woi_geometry {
     std::vector<double> area;
     int star_idx = -1;
     StarCurve star;
-    std::vector<double> star_panel_s;          // kStarPanels + 1
-    std::vector<double> star_scan;             // kStarScan * 2
+    std::vector<double> star_panel_s;          // kNodes + 1
+    std::vector<double> star_scan;             // kNodes * 2
     double star_lmax = 0.0;
 
     bool data_ready = false;
@@ -129,7 +129,7 @@ struct woi_geometry {
     double alpha_l1 = 0.0;
     std::vector<int> flux_basis, flux_off, flux_n;
     bool vr_ok = false;
-    std::vector<double> arc_t0, arc_t1, arc_len, part_len;
+    std::vector<double> arc_t0, arc_t1, arc_len, arc_s0, part_len;
     std::vector<int> arc_sign, arc_off, arc_n;
 
     // device side
@@ -137,7 +137,7 @@ struct woi_geometry {
     bool dev_dirty = true;
     DevGeom blob{};
     DevGeom *d_blob = nullptr;
-    double *d_flux = nullptr, *d_arc_t0 = nullptr, *d_arc_t1 = nullptr, *d_arc_len = nullptr;
+    double *d_flux = nullptr, *d_arc_t0 = nullptr, *d_arc_t1 = nullptr, *d_arc_len = nullptr, *d_arc_s0 = nullptr;
     int *d_arc_sign = nullptr;
     int blob_M = -1;
     // grow-only scratch
@@ -160,6 +160,7 @@ struct woi_geometry {
         cudaFree(d_arc_t0);
         cudaFree(d_arc_t1);
         cudaFree(d_arc_len);
+        cudaFree(d_arc_s0);
         cudaFree(d_arc_sign);
         cudaFree(d_scratch);
         if (ev_start) cudaEventDestroy(ev_start);
@@ -168,7 +169,7 @@ struct woi_geometry {
         timed = false;
         if (cur >= 0) cudaSetDevice(cur);
         d_blob = nullptr;
-        d_flux = d_arc_t0 = d_arc_t1 = d_arc_len = nullptr;
+        d_flux = d_arc_t0 = d_arc_t1 = d_arc_len = d_arc_s0 = nullptr;
         d_arc_sign = nullptr;
         d_scratch = nullptr;
         scratch_bytes = 0;
@@ -389,14 +390,14 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
         }
     }
     if (g->star_idx >= 0) {
-        g->star_panel_s.assign(kStarPanels + 1, 0.0);
-        const double H = 2.0 * kPi / kStarPanels;
-        for (int j = 0; j < kStarPanels; ++j)
+        g->star_panel_s.assign(kNodes + 1, 0.0);
+        const double H = 2.0 * kPi / kNodes;
+        for (int j = 0; j < kNodes; ++j)
             g->star_panel_s[j + 1] = g->star_panel_s[j] + star_length(g->star, j * H, (j + 1) * H, 4);
-        g->area[g->star_idx] = g->star_panel_s[kStarPanels];
-        g->star_scan.assign(2 * kStarScan, 0.0);
-        for (int j = 0; j < kStarScan; ++j) {
-            double r, dr, t = 2.0 * kPi * j / kStarScan;
+        g->area[g->star_idx] = g->star_panel_s[kNodes];
+        g->star_scan.assign(2 * kNodes, 0.0);
+        for (int j = 0; j < kNodes; ++j) {
+            double r, dr, t = 2.0 * kPi * j / kNodes;
             g->star.eval(t, &r, &dr);
             g->star_scan[2 * j] = r * std::cos(t);
             g->star_scan[2 * j + 1] = r * std::sin(t);
@@ -506,7 +507,7 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
     th[n - 1] = 1ull << 32;
     // Sec. 4.4: arcs of dOmega^+ = {beta >= 0} and dOmega^- = {beta < 0} (2D)
     bool vr_ok = (d == 2);
-    std::vector<double> at0, at1, alen, plen(2 * n, 0.0);
+    std::vector<double> at0, at1, alen, as0, plen(2 * n, 0.0);
     std::vector<int> asg, aoff(n, 0), an(n, 0);
     for (int i = 0; i < n && vr_ok; ++i) {
         aoff[i] = (int)at0.size();
@@ -515,9 +516,16 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             if (s.type == WOI_SPHERE) return s.radius * (t1 - t0);
             return star_length(g->star, t0, t1, 64);
         };
+        auto arc_start = [&](double t0) {
+            if (s.type == WOI_SPHERE) return s.radius * t0;
+            const double H = 2.0 * kPi / kNodes;
+            int j = std::min(kNodes - 1, std::max(0, (int)(t0 / H)));
+            return g->star_panel_s[j] + star_length(g->star, j * H, t0, 4);
+        };
         if (basis[i] == WOI_FLUX_ZERO) {
             at0.push_back(0.0); at1.push_back(2.0 * kPi); asg.push_back(1);
             alen.push_back(g->area[i]);
+            as0.push_back(0.0);
             plen[2 * i] += g->area[i];
             an[i] = 1;
             continue;
@@ -548,6 +556,7 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             const int sg = beta(0.5 * (a + b)) >= 0 ? 1 : -1;
             const double L = arc_length(a, b);
             at0.push_back(a); at1.push_back(b); asg.push_back(sg); alen.push_back(L);
+            as0.push_back(arc_start(a));
             plen[2 * i + (sg > 0 ? 0 : 1)] += L;
             an[i]++;
         }
@@ -562,7 +571,7 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
     g->flux_n = nc;
     g->flux_coef = coef;
     g->vr_ok = vr_ok;
-    g->arc_t0 = at0; g->arc_t1 = at1; g->arc_len = alen; g->arc_sign = asg;
+    g->arc_t0 = at0; g->arc_t1 = at1; g->arc_len = alen; g->arc_s0 = as0; g->arc_sign = asg;
     g->arc_off = aoff; g->arc_n = an; g->part_len = plen;
     g->data_ready = true;
     g->dev_dirty = true;
@@ -619,6 +628,7 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
         if ((st = upload(&g->d_arc_t0, g->arc_t0, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_t1, g->arc_t1, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_len, g->arc_len, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_arc_s0, g->arc_s0, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_sign, g->arc_sign, s)) != WOI_OK) return st;
         if (!g->d_blob) WOI_CUDA(cudaMalloc((void **)&g->d_blob, sizeof(DevGeom)));
     }
@@ -656,21 +666,26 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
         b.coef[i] = (double)g->n * (i == M ? 0.5 : 1.0) * Ai;
         Ai *= g->alpha_l1;
     }
+    for (int j = 0; j < kNodes; ++j) {
+        b.node_cs[j][0] = std::cos(2.0 * kPi * j / kNodes);
+        b.node_cs[j][1] = std::sin(2.0 * kPi * j / kNodes);
+    }
     if (g->star_idx >= 0) {
         for (int k = 1; k <= g->star.K; ++k) {
             b.star_a[k] = g->star.a[k];
             b.star_b[k] = g->star.b[k];
         }
-        for (int j = 0; j < kStarScan; ++j) {
+        for (int j = 0; j < kNodes; ++j) {
             b.star_scan[j][0] = g->star_scan[2 * j];
             b.star_scan[j][1] = g->star_scan[2 * j + 1];
         }
-        for (int j = 0; j <= kStarPanels; ++j) b.star_panel_s[j] = g->star_panel_s[j];
+        for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g->star_panel_s[j];
     }
     b.flux_coef = g->d_flux;
     b.arc_t0 = g->d_arc_t0;
     b.arc_t1 = g->d_arc_t1;
     b.arc_len = g->d_arc_len;
+    b.arc_s0 = g->d_arc_s0;
     b.arc_sign = g->d_arc_sign;
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     WOI_CUDA(cudaMemcpyAsync(g->d_blob, &b, sizeof(DevGeom), cudaMemcpyHostToDevice, s));

@@ -16,6 +16,12 @@
 // signed K*(y_i, y_{i-1}) evaluated with the normal at y_i; "descendant" is a
 // strict descendant at any depth; a line/ray with no admissible intersection
 // ends the walk.
+//
+// Precision: a walk state is kept as (surface s, offset v = y - c_s) and
+// surface centres as (hi, lo) pairs, so differences between points on nearby
+// surfaces and x - y near a surface are formed without cancellation in FP32.
+// Angles on curves are carried as (node j, small offset delta) with exact node
+// cosines and sines, and arc-length targets are split in FP64 (two operations).
 #pragma once
 
 #include <cstdint>
@@ -89,6 +95,8 @@ template <> struct RealOps<double> {
     __device__ static __forceinline__ double rcp(double v) { return 1.0 / v; }
 };
 
+template <typename Real> __host__ __device__ constexpr Real eps_tol() { return sizeof(Real) == 4 ? (Real)2e-9 : (Real)1e-17; }
+
 // word k (k >= 1) of a (step, chain) stream: sub-call k / 4, lane k % 4
 struct StepWords {
     U4 a, b;  // sub 0 and sub 1
@@ -149,9 +157,10 @@ template <int D> __host__ __device__ constexpr bool two_calls() { return D >= 4;
 // ---------------------------------------------------------------------------
 template <typename Real>
 struct SGeom {
-    int n, npad, M, has_star;
+    int n, npad, M, star_idx, star_K;
     uint32_t sched_tm1[kMaxSurfPad];     // T_n - 1 (schedule thresholds), padded with 0xFFFFFFFF
-    Real center[kMaxSurf][kMaxDim];
+    Real c_hi[kMaxSurf][kMaxDim];        // centres as hi + lo
+    Real c_lo[kMaxSurf][kMaxDim];
     Real radius[kMaxSurf];
     Real area[kMaxSurf];
     Real alpha_sign[kMaxSurf];
@@ -159,16 +168,14 @@ struct SGeom {
     int tin[kMaxSurf], tout[kMaxSurf];
     int type[kMaxSurf];
     Real coef[kMaxM + 1];                // N w_i ||alpha||_1^i
-    // star (at most one star surface per instance: its index, Fourier
-    // coefficients, scan points and arc-length panels)
-    int star_idx, star_K;
+    Real node_cs[kNodes][2];             // cos, sin of t_j = 2 pi j / kNodes
+    // star (at most one per instance)
     Real star_a[kMaxStar + 1], star_b[kMaxStar + 1];
-    Real star_lmax;                      // max |gamma'|
-    Real scan[kStarScan][2];             // gamma(t_j) - centre, t_j = 2 pi j / kStarScan
-    Real panel_s[kStarPanels + 1];       // arc length at t_j = 2 pi j / kStarPanels
+    Real star_lmax;                      // bound on |gamma'|
+    Real scan[kNodes][2];                // gamma(t_j) - centre
+    double panel_s[kNodes + 1];          // arc length at t_j
 };
 
-// Load the device blob of one instance into shared memory (all threads of the block).
 template <typename Real>
 __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
 {
@@ -177,14 +184,18 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.n = src->n;
         g.npad = src->npad;
         g.M = src->M;
-        g.has_star = src->star_idx >= 0;
         g.star_idx = src->star_idx;
         g.star_K = src->star_K;
         g.star_lmax = (Real)src->star_lmax;
     }
     for (int i = tid; i < kMaxSurfPad; i += nt) g.sched_tm1[i] = src->sched_tm1[i];
     for (int i = tid; i < src->n; i += nt) {
-        for (int k = 0; k < kMaxDim; ++k) g.center[i][k] = (Real)src->center[i][k];
+        for (int k = 0; k < kMaxDim; ++k) {
+            const double c = src->center[i][k];
+            const Real hi = (Real)c;
+            g.c_hi[i][k] = hi;
+            g.c_lo[i][k] = (Real)(c - (double)hi);
+        }
         g.radius[i] = (Real)src->radius[i];
         g.area[i] = (Real)src->area[i];
         g.alpha_sign[i] = (Real)src->alpha_sign[i];
@@ -194,21 +205,25 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.type[i] = src->type[i];
     }
     for (int i = tid; i <= kMaxM; i += nt) g.coef[i] = (Real)src->coef[i];
+    for (int j = tid; j < kNodes; j += nt) {
+        g.node_cs[j][0] = (Real)src->node_cs[j][0];
+        g.node_cs[j][1] = (Real)src->node_cs[j][1];
+    }
     if (src->star_idx >= 0) {
         for (int k = tid; k <= kMaxStar; k += nt) {
             g.star_a[k] = (Real)src->star_a[k];
             g.star_b[k] = (Real)src->star_b[k];
         }
-        for (int j = tid; j < kStarScan; j += nt) {
+        for (int j = tid; j < kNodes; j += nt) {
             g.scan[j][0] = (Real)src->star_scan[j][0];
             g.scan[j][1] = (Real)src->star_scan[j][1];
         }
-        for (int j = tid; j <= kStarPanels; j += nt) g.panel_s[j] = (Real)src->star_panel_s[j];
+        for (int j = tid; j <= kNodes; j += nt) g.panel_s[j] = src->star_panel_s[j];
     }
 }
 
 // H_i from a 32-bit word: i = 0 uniform over the N surfaces, i >= 1 the first n
-// with w <= T_n - 1 (branch-free binary search over the padded thresholds)
+// with w <= T_n - 1 (binary search over the padded thresholds)
 template <typename Real>
 __device__ __forceinline__ int schedule(const SGeom<Real> &g, int i, uint32_t w)
 {
@@ -228,51 +243,69 @@ __device__ __forceinline__ int relation(const SGeom<Real> &g, int prev, int cur)
     return (g.tin[cur] < g.tin[prev] && g.tin[prev] < g.tout[cur]) ? 1 : 2;
 }
 
+// c_a - c_b without cancellation
+template <typename Real, int D>
+__device__ __forceinline__ void center_diff(const SGeom<Real> &g, int a, int b, Real *out)
+{
+#pragma unroll
+    for (int k = 0; k < D; ++k) out[k] = (g.c_hi[a][k] - g.c_hi[b][k]) + (g.c_lo[a][k] - g.c_lo[b][k]);
+}
+
 // ---------------------------------------------------------------------------
-// star curve: r(t) = R (1 + sum a_k cos kt + b_k sin kt) about its centre
+// star curve about its centre: r(t) = R (1 + sum a_k cos kt + b_k sin kt).
+// An angle is (node j, offset delta): t = 2 pi j / kNodes + delta.
 // ---------------------------------------------------------------------------
 template <typename Real>
-__device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr, Real *ddr)
+__device__ __forceinline__ void angle_cs(const SGeom<Real> &g, int j, Real delta, Real *ct, Real *st)
 {
-    const int h = g.star_idx;
-    Real ck = ct, sk = st, s = 1, ds = 0, dds = 0;
+    Real sd, cd;
+    RealOps<Real>::sincos_(delta, &sd, &cd);
+    const Real cj = g.node_cs[j][0], sj = g.node_cs[j][1];
+    *ct = cj * cd - sj * sd;
+    *st = sj * cd + cj * sd;
+}
+
+template <typename Real>
+__device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr)
+{
+    Real ck = ct, sk = st, s = 1, ds = 0;
     for (int k = 1; k <= g.star_K; ++k) {
         const Real a = g.star_a[k], b = g.star_b[k];
         s += a * ck + b * sk;
         ds += (Real)k * (b * ck - a * sk);
-        dds -= (Real)(k * k) * (a * ck + b * sk);
         const Real cn = ck * ct - sk * st;  // cos((k+1)t), sin((k+1)t)
         sk = sk * ct + ck * st;
         ck = cn;
     }
-    *r = g.radius[h] * s;
-    *dr = g.radius[h] * ds;
-    if (ddr) *ddr = g.radius[h] * dds;
+    const Real R = g.radius[g.star_idx];
+    *r = R * s;
+    *dr = R * ds;
 }
 
+// local point r (cos t, sin t), outward unit normal and |gamma'| at the angle (ct, st)
 template <typename Real>
-__device__ __forceinline__ Real star_speed(const SGeom<Real> &g, Real t)
+__device__ __forceinline__ Real star_local(const SGeom<Real> &g, Real ct, Real st, Real *v, Real *n)
 {
-    Real st, ct, r, dr;
-    RealOps<Real>::sincos_(t, &st, &ct);
-    star_eval(g, ct, st, &r, &dr, (Real *)nullptr);
-    return RealOps<Real>::sqrt_(r * r + dr * dr);
-}
-
-// point (absolute) and outward unit normal at parameter t
-template <typename Real>
-__device__ __forceinline__ void star_point_normal(const SGeom<Real> &g, Real t, Real *y, Real *n)
-{
-    Real st, ct, r, dr;
-    RealOps<Real>::sincos_(t, &st, &ct);
-    star_eval(g, ct, st, &r, &dr, (Real *)nullptr);
-    const int h = g.star_idx;
-    y[0] = g.center[h][0] + r * ct;
-    y[1] = g.center[h][1] + r * st;
+    Real r, dr;
+    star_eval(g, ct, st, &r, &dr);
+    v[0] = r * ct;
+    v[1] = r * st;
     const Real tx = dr * ct - r * st, ty = dr * st + r * ct;
-    const Real inv = RealOps<Real>::rsqrt_(tx * tx + ty * ty);
-    n[0] = ty * inv;
-    n[1] = -tx * inv;
+    const Real sp = RealOps<Real>::sqrt_(tx * tx + ty * ty);
+    if (n) {
+        n[0] = ty / sp;
+        n[1] = -tx / sp;
+    }
+    return sp;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real star_speed_at(const SGeom<Real> &g, int j, Real delta)
+{
+    Real ct, st, r, dr;
+    angle_cs(g, j, delta, &ct, &st);
+    star_eval(g, ct, st, &r, &dr);
+    return RealOps<Real>::sqrt_(r * r + dr * dr);
 }
 
 // Gauss-Legendre 8-point rule on [-1, 1] (positive half)
@@ -287,142 +320,136 @@ __device__ __forceinline__ double gl8_w(int q)
     return w[q];
 }
 
-// arc length from 0 to t (t in [0, 2 pi]): panel table + 8-point Gauss-Legendre on the partial panel
+// arc length from node j to node j + delta
 template <typename Real>
-__device__ Real star_arclen(const SGeom<Real> &g, Real t)
+__device__ Real star_local_arclen(const SGeom<Real> &g, int j, Real delta)
 {
-    const Real H = (Real)(2.0 * 3.14159265358979323846 / kStarPanels);
-    int j = (int)(t / H);
-    j = j < 0 ? 0 : (j >= kStarPanels ? kStarPanels - 1 : j);
-    const Real a = (Real)j * H, half = (Real)0.5 * (t - a), mid = a + half;
+    const Real half = (Real)0.5 * delta;
     Real s = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const Real xq = (Real)gl8_x(q) * half, wq = (Real)gl8_w(q);
-        s += wq * (star_speed(g, mid - xq) + star_speed(g, mid + xq));
+        const Real xq = (Real)gl8_x(q) * half;
+        s += (Real)gl8_w(q) * (star_speed_at(g, j, half - xq) + star_speed_at(g, j, half + xq));
     }
-    return g.panel_s[j] + half * s;
+    return half * s;
 }
 
-// t in [t_lo, t_hi] with arclen(t) = s (safeguarded Newton)
+// (node, offset) of the point at arc length s_abs (FP64 split of the target)
 template <typename Real>
-__device__ Real star_invert(const SGeom<Real> &g, Real s, Real t_lo, Real t_hi)
+__device__ void star_at_arclen(const SGeom<Real> &g, double s_abs, int *jo, Real *delta_o)
 {
-    const Real s_lo = star_arclen(g, t_lo), s_hi = star_arclen(g, t_hi);
-    Real t = t_lo + (t_hi - t_lo) * (s - s_lo) / (s_hi - s_lo);
-    const int iters = sizeof(Real) == 4 ? 12 : 40;
-    for (int it = 0; it < iters; ++it) {
-        const Real f = star_arclen(g, t) - s;
-        if (f > 0) t_hi = t; else t_lo = t;
-        Real tn = t - f / star_speed(g, t);
-        if (!(tn > t_lo && tn < t_hi)) tn = (Real)0.5 * (t_lo + t_hi);
-        const Real step = RealOps<Real>::fabs_(tn - t);
-        t = tn;
-        if (step < (sizeof(Real) == 4 ? (Real)1e-7 : (Real)1e-15)) break;
-    }
-    return t;
-}
-
-// panel containing arc length s (binary search in the table)
-template <typename Real>
-__device__ __forceinline__ Real star_uniform_param(const SGeom<Real> &g, Real s)
-{
-    int lo = 0, hi = kStarPanels;
+    int lo = 0, hi = kNodes;
     while (hi - lo > 1) {
         const int m = (lo + hi) >> 1;
-        if (g.panel_s[m] <= s) lo = m; else hi = m;
+        if (g.panel_s[m] <= s_abs) lo = m; else hi = m;
     }
-    const Real H = (Real)(2.0 * 3.14159265358979323846 / kStarPanels);
-    return star_invert(g, s, (Real)lo * H, (Real)(lo + 1) * H);
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
+    const Real ds = (Real)(s_abs - g.panel_s[lo]);
+    Real d_lo = 0, d_hi = H;
+    Real delta = ds / star_speed_at(g, lo, (Real)0);
+    if (!(delta > d_lo && delta < d_hi)) delta = (Real)0.5 * H;
+    const int iters = sizeof(Real) == 4 ? 12 : 30;
+    for (int it = 0; it < iters; ++it) {
+        const Real f = star_local_arclen(g, lo, delta) - ds;
+        if (f > 0) d_hi = delta; else d_lo = delta;
+        Real dn = delta - f / star_speed_at(g, lo, delta);
+        if (!(dn > d_lo && dn < d_hi)) dn = (Real)0.5 * (d_lo + d_hi);
+        const Real step = RealOps<Real>::fabs_(dn - delta);
+        delta = dn;
+        if (step <= eps_tol<Real>()) break;
+    }
+    *jo = lo;
+    *delta_o = delta;
 }
 
-// f(t) = (gamma(t) - y) x z and f'(t) for the line y + s z
+// f(delta) = (gamma_loc(t_j + delta) - yc) x z and its derivative
 template <typename Real>
-__device__ __forceinline__ void star_line_f(const SGeom<Real> &g, Real t, const Real *yc, const Real *z, Real *f,
-                                            Real *df)
+__device__ __forceinline__ void star_line_f(const SGeom<Real> &g, int j, Real delta, const Real *yc, const Real *z,
+                                            Real *f, Real *df)
 {
-    Real st, ct, r, dr;
-    RealOps<Real>::sincos_(t, &st, &ct);
-    star_eval(g, ct, st, &r, &dr, (Real *)nullptr);
+    Real ct, st, r, dr;
+    angle_cs(g, j, delta, &ct, &st);
+    star_eval(g, ct, st, &r, &dr);
     const Real px = r * ct - yc[0], py = r * st - yc[1];
     *f = px * z[1] - py * z[0];
     const Real tx = dr * ct - r * st, ty = dr * st + r * ct;
     *df = tx * z[1] - ty * z[0];
 }
 
+// root of f in (a, b) given sign(f(a)) (safeguarded Newton in delta)
 template <typename Real>
-__device__ Real star_refine(const SGeom<Real> &g, Real a, Real b, Real fa, const Real *yc, const Real *z)
+__device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa, const Real *yc, const Real *z)
 {
     Real t = (Real)0.5 * (a + b);
-    const int iters = sizeof(Real) == 4 ? 30 : 80;
+    const int iters = sizeof(Real) == 4 ? 40 : 90;
     for (int it = 0; it < iters; ++it) {
         Real f, df;
-        star_line_f(g, t, yc, z, &f, &df);
+        star_line_f(g, j, t, yc, z, &f, &df);
         if ((f < 0) == (fa < 0)) a = t; else b = t;
         Real tn = t - f / df;
         if (!(tn > a && tn < b)) tn = (Real)0.5 * (a + b);
         const Real step = RealOps<Real>::fabs_(tn - t);
         t = tn;
-        if (step < (sizeof(Real) == 4 ? (Real)2e-7 : (Real)1e-15) || b - a < (sizeof(Real) == 4 ? (Real)1e-7 : (Real)1e-15))
-            break;
+        if (step <= eps_tol<Real>() || b - a <= eps_tol<Real>()) break;
     }
     return t;
 }
 
-// Intersections of the line (ray = false) or ray (ray = true) y + s z with the
-// star: roots of f on a kStarScan-sample scan, with hidden root pairs found
-// from the extremum of f in intervals where |f| may reach 0 (|f'| <= lmax).
-// Returns q; tt[] receives the line parameters s, th[] the curve parameters.
+// Intersections of the line (ray = false) or ray (ray = true) yc + s z (yc
+// relative to the star centre) with the star: roots of f on a kNodes-sample
+// scan, plus root pairs hidden inside a scan interval, found from the
+// extremum of f where |f| may reach 0 (|f'| <= lmax).  The line's own start
+// point (|s| below `tiny`) is excluded.  Returns q; tt[] the line parameters,
+// jj[] / dd[] the roots as (node, offset).
 template <typename Real>
-__device__ int star_intersections(const SGeom<Real> &g, const Real *y, const Real *z, bool ray, Real *tt, Real *th)
+__device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Real *z, bool ray, Real *tt, int *jj,
+                                  Real *dd)
 {
-    const int h = g.star_idx;
-    const Real yc[2] = {y[0] - g.center[h][0], y[1] - g.center[h][1]};
     const Real e = yc[0] * z[1] - yc[1] * z[0];
-    const Real H = (Real)(2.0 * 3.14159265358979323846 / kStarScan);
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
     const Real guard = g.star_lmax * H * (Real)0.5;
-    const Real tiny = sizeof(Real) == 4 ? (Real)2e-5 : (Real)1e-9;
+    const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
     int q = 0;
-    Real f0 = g.scan[0][0] * z[1] - g.scan[0][1] * z[0] - e;
+    const Real f0 = g.scan[0][0] * z[1] - g.scan[0][1] * z[0] - e;
     Real fa = f0;
-    for (int j = 0; j < kStarScan; ++j) {
-        const int jn = (j + 1 == kStarScan) ? 0 : j + 1;
-        const Real fb = (jn == 0) ? f0 : g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
-        const Real a = (Real)j * H, b = (Real)(j + 1) * H;
+    for (int j = 0; j < kNodes; ++j) {
+        const int jn = j + 1;
+        const Real fb = (jn == kNodes) ? f0 : g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
         Real cand[2];
         int nc = 0;
         if ((fa < 0) != (fb < 0)) {
-            cand[nc++] = star_refine(g, a, b, fa, yc, z);
+            cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z);
         } else if (RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
             Real f1, d1, f2, d2;
-            star_line_f(g, a, yc, z, &f1, &d1);
-            star_line_f(g, b, yc, z, &f2, &d2);
+            star_line_f(g, j, (Real)0, yc, z, &f1, &d1);
+            star_line_f(g, j, H, yc, z, &f2, &d2);
             if ((d1 < 0) != (d2 < 0)) {
-                // extremum of f in (a, b): bisection on f'
-                Real lo = a, hi = b, dlo = d1;
-                for (int it = 0; it < (sizeof(Real) == 4 ? 24 : 52); ++it) {
+                Real lo = 0, hi = H, dlo = d1;
+                for (int it = 0; it < (sizeof(Real) == 4 ? 30 : 60); ++it) {
                     const Real m = (Real)0.5 * (lo + hi);
                     Real fm, dm;
-                    star_line_f(g, m, yc, z, &fm, &dm);
+                    star_line_f(g, j, m, yc, z, &fm, &dm);
                     if ((dm < 0) == (dlo < 0)) { lo = m; dlo = dm; } else hi = m;
                 }
                 const Real te = (Real)0.5 * (lo + hi);
                 Real fe, de;
-                star_line_f(g, te, yc, z, &fe, &de);
+                star_line_f(g, j, te, yc, z, &fe, &de);
                 if ((fe < 0) != (fa < 0)) {
-                    cand[nc++] = star_refine(g, a, te, fa, yc, z);
-                    cand[nc++] = star_refine(g, te, b, fe, yc, z);
+                    cand[nc++] = star_refine(g, j, (Real)0, te, fa, yc, z);
+                    cand[nc++] = star_refine(g, j, te, H, fe, yc, z);
                 }
             }
         }
         for (int c = 0; c < nc; ++c) {
-            Real p[2], nn[2];
-            star_point_normal(g, cand[c], p, nn);
-            const Real s = (p[0] - y[0]) * z[0] + (p[1] - y[1]) * z[1];
+            Real ct, st, p[2];
+            angle_cs(g, j, cand[c], &ct, &st);
+            star_local(g, ct, st, p, (Real *)nullptr);
+            const Real s = (p[0] - yc[0]) * z[0] + (p[1] - yc[1]) * z[1];
             const bool ok = ray ? (s > tiny) : (RealOps<Real>::fabs_(s) > tiny);
             if (ok && q < kMaxRoots) {
                 tt[q] = s;
-                th[q] = cand[c];
+                jj[q] = j;
+                dd[q] = cand[c];
                 ++q;
             }
         }
@@ -455,13 +482,13 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
         if constexpr (D == 3) {
             // associated Legendre P_l^m(x) without the (-1)^m phase, x = cos(polar)
             const Real x = u[2];
-            const Real sx = RealOps<Real>::sqrt_(fmax((double)0, (double)(1 - x * x)));
+            const Real sx = RealOps<Real>::sqrt_((Real)fmax(0.0, (double)(1 - x * x)));
             Real ca = 1, sa = 0;  // cos / sin of the azimuth
             if (sx > (Real)0) {
                 ca = u[0] / sx;
                 sa = u[1] / sx;
             }
-            const int L = (int)(RealOps<double>::sqrt_((double)nc) + 1e-9) - 1;
+            const int L = (int)(sqrt((double)nc) + 1e-9) - 1;
             Real v = 0;
             Real pmm = 1, cm = 1, sm = 0;  // P_m^m, cos(m az), sin(m az)
             for (int m = 0; m <= L; ++m) {
@@ -524,7 +551,7 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
 }
 
 // ---------------------------------------------------------------------------
-// evaluation point: (hi, lo) split so that x - y is accurate in FP32
+// evaluation point: (hi, lo) split
 // ---------------------------------------------------------------------------
 template <typename Real, int D>
 struct XPoint {
@@ -543,15 +570,16 @@ __device__ __forceinline__ XPoint<Real, D> make_point(const double *x)
     return p;
 }
 
-// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D]
+// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D], with y = c_s + v
 template <typename Real, int D>
-__device__ __forceinline__ void tally(const XPoint<Real, D> &x, const Real *y, Real c, Real *acc)
+__device__ __forceinline__ void tally(const SGeom<Real> &g, const XPoint<Real, D> &x, int s, const Real *v, Real c,
+                                      Real *acc)
 {
     using O = RealOps<Real>;
     Real dx[D], r2 = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        dx[k] = (x.hi[k] - y[k]) + x.lo[k];
+        dx[k] = ((x.hi[k] - g.c_hi[s][k]) + (x.lo[k] - g.c_lo[s][k])) - v[k];
         r2 += dx[k] * dx[k];
     }
     if (r2 <= (Real)0) return;  // x on a walk state exactly: measure zero, contributes nothing
@@ -577,11 +605,12 @@ __device__ __forceinline__ void tally(const XPoint<Real, D> &x, const Real *y, R
 }
 
 // ---------------------------------------------------------------------------
-// one chain's state and its transitions
+// one chain's state: surface s, offset v = y - c_s
 // ---------------------------------------------------------------------------
 template <typename Real, int D>
 struct Chain {
-    Real y[D];
+    int s;
+    Real v[D];
     Real Q, T;
     bool alive;
 };
@@ -593,15 +622,16 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
 {
     ch.T = 1;
     ch.alive = true;
+    ch.s = h;
     Real u[D], nrm[D];
-    Real part_len = g.area[h];
+    double part_len = g.area[h];
     if constexpr (VR) {
-        part_len = (Real)gd->part_len[h][k];
-        if (!(part_len > (Real)0) || gd->flux_basis[h] == kFluxZero) {
+        part_len = gd->part_len[h][k];
+        if (!(part_len > 0.0) || gd->flux_basis[h] == kFluxZero) {
             ch.alive = false;
             ch.Q = 0;
 #pragma unroll
-            for (int c = 0; c < D; ++c) ch.y[c] = 0;
+            for (int c = 0; c < D; ++c) ch.v[c] = 0;
             return;
         }
     }
@@ -610,129 +640,156 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
         direction<Real, D>(w, u);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            ch.y[c] = g.center[h][c] + g.radius[h] * u[c];
+            ch.v[c] = g.radius[h] * u[c];
             nrm[c] = u[c];
         }
     } else {
         if constexpr (D == 2) {
-            // a parameter angle: uniform by arc length on the surface, or on the
-            // concatenated arcs of the requested sign (VR)
-            Real t;
-            const Real s_target = u01<Real>(w.a.y) * part_len;
+            // target position (FP64) along the surface, or along the concatenated
+            // arcs of the requested sign (VR)
+            const double s_target = (double)u01<Real>(w.a.y) * part_len;
+            Real ct, st;
             if constexpr (VR) {
-                Real s = s_target;
+                double s = s_target;
                 const int want = k == 0 ? 1 : -1;
                 int a_sel = -1;
                 for (int a = gd->arc_off[h]; a < gd->arc_off[h] + gd->arc_n[h]; ++a) {
                     if (gd->arc_sign[a] != want) continue;
                     a_sel = a;
-                    if (s < (Real)gd->arc_len[a]) break;
-                    s -= (Real)gd->arc_len[a];
+                    if (s < gd->arc_len[a]) break;
+                    s -= gd->arc_len[a];
                 }
-                if (s > (Real)gd->arc_len[a_sel]) s = (Real)gd->arc_len[a_sel];
-                const Real t0 = (Real)gd->arc_t0[a_sel], t1 = (Real)gd->arc_t1[a_sel];
+                if (s > gd->arc_len[a_sel]) s = gd->arc_len[a_sel];
                 if (is_star) {
-                    t = star_invert(g, star_arclen(g, t0) + s, t0, t1);
+                    int j;
+                    Real delta;
+                    star_at_arclen(g, gd->arc_s0[a_sel] + s, &j, &delta);
+                    angle_cs(g, j, delta, &ct, &st);
                 } else {
-                    t = t0 + s / g.radius[h];
+                    // t = t0 + s / R, split into a node and an offset in FP64
+                    const double t = gd->arc_t0[a_sel] + s / (double)gd->radius[h];
+                    const double H = 2.0 * 3.14159265358979323846 / kNodes;
+                    int j = (int)(t / H);
+                    j = j < 0 ? 0 : (j >= kNodes ? kNodes - 1 : j);
+                    angle_cs(g, j, (Real)(t - j * H), &ct, &st);
                 }
             } else {
-                t = star_uniform_param(g, s_target);
+                int j;
+                Real delta;
+                star_at_arclen(g, s_target, &j, &delta);
+                angle_cs(g, j, delta, &ct, &st);
             }
             if (is_star) {
-                star_point_normal(g, t, ch.y, nrm);
+                star_local(g, ct, st, ch.v, nrm);
             } else {
-                Real st, ct;
-                RealOps<Real>::sincos_(t, &st, &ct);
                 nrm[0] = ct;
                 nrm[1] = st;
-                ch.y[0] = g.center[h][0] + g.radius[h] * ct;
-                ch.y[1] = g.center[h][1] + g.radius[h] * st;
+                ch.v[0] = g.radius[h] * ct;
+                ch.v[1] = g.radius[h] * st;
             }
-            RealOps<Real>::sincos_(t, &u[1], &u[0]);
+            u[0] = ct;
+            u[1] = st;
         }
     }
-    ch.Q = g.beta_scale[h] * flux_value<Real, D>(gd, h, ch.y, u, nrm) * part_len;
+    Real y[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + ch.v[c];
+    ch.Q = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, u, nrm) * (Real)part_len;
 }
 
-// transition i >= 1 from surface hp to h (relation rel)
+// transition i >= 1 from surface ch.s to h (relation rel)
 template <typename Real, int D, bool STAR>
-__device__ void chain_step(const SGeom<Real> &g, int hp, int h, int rel, const StepWords &w, Chain<Real, D> &ch)
+__device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords &w, Chain<Real, D> &ch)
 {
     using O = RealOps<Real>;
+    constexpr double PI = 3.14159265358979323846;
+    // dy = y - c_h
+    Real dy[D];
+    if (rel == 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) dy[c] = ch.v[c];
+    } else {
+        center_diff<Real, D>(g, ch.s, h, dy);
+#pragma unroll
+        for (int c = 0; c < D; ++c) dy[c] += ch.v[c];
+    }
     if (STAR && g.type[h] == kStar) {
         if constexpr (D == 2) {
-            Real ynew[2], nrm[2];
+            Real vn[2], nrm[2];
             if (rel == 2) {
                 // uniform on the star by arc length; Q *= K*(y_i, y_{i-1}) |dOmega_h|
-                const Real t = star_uniform_param(g, u01<Real>(w.a.y) * g.area[h]);
-                star_point_normal(g, t, ynew, nrm);
-                const Real dx = ynew[0] - ch.y[0], dy = ynew[1] - ch.y[1];
-                const Real r2 = dx * dx + dy * dy;
-                ch.Q *= (dx * nrm[0] + dy * nrm[1]) * O::rcp(r2) * (Real)(1.0 / (2.0 * 3.14159265358979323846)) *
-                        g.area[h];
+                int j;
+                Real delta, ct, st;
+                star_at_arclen(g, (double)u01<Real>(w.a.y) * (double)g.panel_s[kNodes], &j, &delta);
+                angle_cs(g, j, delta, &ct, &st);
+                star_local(g, ct, st, vn, nrm);
+                const Real dx = vn[0] - dy[0], dyy = vn[1] - dy[1];
+                const Real r2 = dx * dx + dyy * dyy;
+                ch.Q *= (dx * nrm[0] + dyy * nrm[1]) * O::rcp(r2) * (Real)(1.0 / (2.0 * PI)) * g.area[h];
             } else {
                 Real z[2];
                 direction<Real, 2>(w, z);
-                Real tt[kMaxRoots], th[kMaxRoots];
-                const int q = star_intersections(g, ch.y, z, rel == 1, tt, th);
+                Real tt[kMaxRoots], dd[kMaxRoots];
+                int jj[kMaxRoots];
+                const int q = star_intersections(g, dy, z, rel == 1, tt, jj, dd);
                 if (q == 0) {
                     ch.alive = false;
                     ch.T = 0;
                     return;
                 }
-                const int j = (int)(((uint64_t)w.get(choice_word<2>()) * (uint64_t)q) >> 32);
-                // the j-th smallest line parameter
+                const int pick = (int)(((uint64_t)w.get(choice_word<2>()) * (uint64_t)q) >> 32);
+                // the pick-th smallest line parameter
                 int sel = 0;
                 for (int a = 0; a < q; ++a) {
                     int rank = 0;
                     for (int b = 0; b < q; ++b) rank += (tt[b] < tt[a]) || (tt[b] == tt[a] && b < a);
-                    if (rank == j) sel = a;
+                    if (rank == pick) sel = a;
                 }
-                star_point_normal(g, th[sel], ynew, nrm);
-                const Real dot = (ynew[0] - ch.y[0]) * nrm[0] + (ynew[1] - ch.y[1]) * nrm[1];
+                Real ct, st;
+                angle_cs(g, jj[sel], dd[sel], &ct, &st);
+                star_local(g, ct, st, vn, nrm);
+                const Real dot = (vn[0] - dy[0]) * nrm[0] + (vn[1] - dy[1]) * nrm[1];
                 if (rel == 0) ch.Q *= (Real)0.5;
                 ch.T *= (Real)q * (dot > 0 ? (Real)1 : (dot < 0 ? (Real)-1 : (Real)0));
             }
-            ch.y[0] = ynew[0];
-            ch.y[1] = ynew[1];
+            ch.s = h;
+            ch.v[0] = vn[0];
+            ch.v[1] = vn[1];
             return;
         }
     }
     // circles / d-spheres: one isotropic unit vector z serves the three cases
-    Real z[D], dy[D], b = 0, c0 = 0;
+    Real z[D];
     direction<Real, D>(w, z);
     const Real R = g.radius[h];
+    Real b = 0;
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-        dy[c] = ch.y[c] - g.center[h][c];
-        b += z[c] * dy[c];
-        c0 += dy[c] * dy[c];
-    }
-    c0 -= R * R;
+    for (int c = 0; c < D; ++c) b += z[c] * dy[c];
     if (rel == 0) {
         // line through a point of the sphere: the other intersection, t = -2 b; Q *= 1/2, T *= q sign = +1
 #pragma unroll
-        for (int c = 0; c < D; ++c) ch.y[c] += (Real)-2 * b * z[c];
+        for (int c = 0; c < D; ++c) ch.v[c] = dy[c] - (Real)2 * b * z[c];
         ch.Q *= (Real)0.5;
     } else if (rel == 1) {
         // ray from inside: t = -b + sqrt(b^2 - c0) > 0 (stable form); Q *= 1, T *= +1
+        Real c0 = -R * R;
+#pragma unroll
+        for (int c = 0; c < D; ++c) c0 += dy[c] * dy[c];
         const Real s = O::sqrt_(b * b - c0);
         const Real t = (b <= 0) ? (s - b) : (-c0) / (b + s);
 #pragma unroll
-        for (int c = 0; c < D; ++c) ch.y[c] += t * z[c];
+        for (int c = 0; c < D; ++c) ch.v[c] = dy[c] + t * z[c];
     } else {
-        // uniform y' = c + R z (normal z); Q *= K*(y', y) |dOmega_h| = (y'-y).z / (omega_d r^d) |dOmega_h|
-        Real diff[D], r2 = 0, dot = 0;
+        // uniform y' = c_h + R z (normal z); Q *= K*(y', y) |dOmega_h| = (y'-y).z / (omega_d r^d) |dOmega_h|
+        Real r2 = 0, dot = 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const Real yn = g.center[h][c] + R * z[c];
-            diff[c] = yn - ch.y[c];
-            r2 += diff[c] * diff[c];
-            dot += diff[c] * z[c];
-            ch.y[c] = yn;
+            const Real vn = R * z[c];
+            const Real diff = vn - dy[c];
+            r2 += diff * diff;
+            dot += diff * z[c];
+            ch.v[c] = vn;
         }
-        constexpr double PI = 3.14159265358979323846;
         constexpr double omega = D == 2 ? 2.0 * PI : (D == 3 ? 4.0 * PI : (D == 4 ? 2.0 * PI * PI : (D == 5 ? 8.0 * PI * PI / 3.0 : PI * PI * PI)));
         Real inv_rd;
         if constexpr (D == 2) {
@@ -745,6 +802,7 @@ __device__ void chain_step(const SGeom<Real> &g, int hp, int h, int rel, const S
         }
         ch.Q *= dot * inv_rd * (Real)(1.0 / omega) * g.area[h];
     }
+    ch.s = h;
 }
 
 // ---------------------------------------------------------------------------
@@ -783,9 +841,9 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const XPoint<Real,
             if (i == 0) {
                 chain_start<Real, D, VR, STAR>(g, gd, h, k, w, ch[k]);
             } else if (ch[k].alive) {
-                chain_step<Real, D, STAR>(g, hp, h, rel, w, ch[k]);
+                chain_step<Real, D, STAR>(g, h, rel, w, ch[k]);
             }
-            if (ch[k].alive) tally<Real, D>(x, ch[k].y, g.coef[i] * S * ch[k].Q * ch[k].T, f);
+            if (ch[k].alive) tally<Real, D>(g, x, ch[k].s, ch[k].v, g.coef[i] * S * ch[k].Q * ch[k].T, f);
         }
         hp = h;
     }

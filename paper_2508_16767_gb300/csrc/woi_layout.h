@@ -11,8 +11,8 @@ constexpr int kMaxSurf = 128;          // surfaces per instance (WOI_MAX_SURF)
 constexpr int kMaxSurfPad = 128;       // schedule thresholds padded to a power of two
 constexpr int kMaxM = 32;              // truncation (WOI_MAX_M)
 constexpr int kMaxStar = 16;           // star Fourier degree (WOI_MAX_STAR_DEGREE)
-constexpr int kStarScan = 256;         // curve samples of the intersection scan
-constexpr int kStarPanels = 256;       // arc-length panels
+constexpr int kNodes = 256;            // angle nodes t_j = 2 pi j / kNodes: star scan samples,
+                                       // arc-length panels and the angle-addition table
 constexpr int kMaxRoots = 2 * (kMaxStar + 1) + 2;
 
 enum { kSphere = 0, kStar = 1 };
@@ -32,8 +32,9 @@ struct DevGeom {
     int type[kMaxSurf];
     double coef[kMaxM + 1];            // N w_i ||alpha||_1^i for the current M
     double star_a[kMaxStar + 1], star_b[kMaxStar + 1];
-    double star_scan[kStarScan][2];    // gamma(t_j) - centre
-    double star_panel_s[kStarPanels + 1];
+    double node_cs[kNodes][2];         // cos t_j, sin t_j
+    double star_scan[kNodes][2];       // gamma(t_j) - centre
+    double star_panel_s[kNodes + 1];   // arc length at t_j
     int flux_basis[kMaxSurf], flux_off[kMaxSurf], flux_n[kMaxSurf];
     const double *flux_coef;           // device array
     double part_len[kMaxSurf][2];      // |dOmega^+|, |dOmega^-| (2D variance reduction)
@@ -41,6 +42,7 @@ struct DevGeom {
     const double *arc_t0;              // device arrays of the beta-sign arcs
     const double *arc_t1;
     const double *arc_len;
+    const double *arc_s0;              // star: arc length at the arc's start angle
     const int *arc_sign;
 };
 

@@ -222,6 +222,16 @@ class Geometry:
 # estimates
 # ---------------------------------------------------------------------------
 
+def _as_input(a):
+    """Contiguous float64 view or copy of an input array (numpy or torch)."""
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64:
+            a = a.to(torch.float64)
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
 def _alloc_like(points, shape):
     if _is_torch(points):
         import torch
@@ -232,6 +242,7 @@ def _alloc_like(points, shape):
 def woi_estimate(geom: Geometry, points, n_walks, seed=0, out=None, stream=None, **opt):
     """u, grad, se_u, se_grad at `points` [P, dim] (numpy or torch, host or CUDA).
     Outputs are allocated like `points` unless `out` = (u, grad, se_u, se_grad)."""
+    points = _as_input(points)
     P = int(points.shape[0])
     if out is None:
         out = (_alloc_like(points, (P,)), _alloc_like(points, (P, geom.dim)), _alloc_like(points, (P,)),
@@ -243,6 +254,7 @@ def woi_estimate(geom: Geometry, points, n_walks, seed=0, out=None, stream=None,
 
 def woi_estimate_range(geom: Geometry, points, walk_begin, n_walks, seed=0, stream=None, **opt):
     """Raw moments [P, 2, dim+1] (sum of f, sum of squared schedule-group means)."""
+    points = _as_input(points)
     P = int(points.shape[0])
     mom = _alloc_like(points, (P, 2, geom.dim + 1))
     o = make_opts(M=opt.pop("M", geom.problem.get("M", 4)), stream=_stream_of([points, mom], stream), **opt)

@@ -72,6 +72,28 @@ def test_star_intersections_match_brute_force(oracle_core):
     assert n_multi > 5   # the star is non-convex: several crossings occur
 
 
+def test_star_near_tangent_lines(oracle_core):
+    """Lines through a curve point at a small angle to the tangent: the second
+    crossing can lie within one scan step of the start point and must be found."""
+    prob = star_problem(amp=0.3)
+    s = prob["surfaces"][0]
+    prep = oracle_core.Prepared(prob)
+    found_close = 0
+    for th in np.linspace(0.05, 2 * np.pi, 37):
+        p0 = star_xy(s, np.array([th]))[:, 0]
+        tan = star_xy(s, np.array([th + 1e-7]))[:, 0] - star_xy(s, np.array([th - 1e-7]))[:, 0]
+        tan /= np.linalg.norm(tan)
+        for ang in (3e-3, 1e-3, -1e-3, 3e-4):
+            c, sn = np.cos(ang), np.sin(ang)
+            z = np.array([c * tan[0] - sn * tan[1], sn * tan[0] + c * tan[1]])
+            ts = oracle_core.intersections(prob, 0, p0, z, False, prepared=prep)
+            ref = brute_star_line(s, p0, z, False)
+            assert len(ts) == len(ref), (th, ang, ts, ref)
+            assert np.allclose(ts, ref, atol=1e-9)
+            found_close += int(np.any(np.abs(ref) < 2 * np.pi / 4096))
+    assert found_close > 0
+
+
 def test_sphere_intersections(oracle_core):
     for d in [2, 3, 6]:
         prob = {"dim": d, "surfaces": [{"kind": "sphere", "center": [0.1] * d, "radius": 0.7}],
