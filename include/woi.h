@@ -177,6 +177,16 @@ WOI_API woi_status woi_walk_values(woi_geometry *geometry, const woi_opts *opts,
                            const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad);
 
 /*
+ * woi_walk_values plus the states of each walk: trace[n][chains][M+1][dim+2]
+ * (host) holds, per step i, the point y_i (dim values), Q_i and T_i (Eqs.
+ * naive_woi_Q / naive_woi_T); chains = 2 for the variance-reduced variant,
+ * else 1.  A chain that ended keeps its last state.
+ */
+WOI_API woi_status woi_walk_trace(woi_geometry *geometry, const woi_opts *opts, const double *x, uint32_t point_id,
+                                  const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad,
+                                  double *trace);
+
+/*
  * Batched heterogeneous estimate: n_inst geometries (each with data set),
  * instance k with n_pts[k] points at points[k] (host or device) and n_walks[k]
  * walks per point.  All instances run in one persistent kernel that takes

@@ -66,7 +66,8 @@ def lib():
         _lib.or_estimate.restype = ctypes.c_int
         _lib.or_walks.argtypes = [P(OrProblem), P(OrOpts), ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
-                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]
         _lib.or_set_mutant.argtypes = [ctypes.c_int]
         _lib.or_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_test_real_sh.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
@@ -393,11 +394,13 @@ def walks(problem, x, walk_ids, seed=0, M=None, variant="plain", sched_group=1, 
     fg = np.zeros((n, d))
     H = np.zeros((n, M + 1), dtype=np.int32)
     Y = np.zeros((n, 2, M + 1, d))
-    sc = np.zeros((n, 3))
+    sc = np.zeros((n, 4))
+    QT = np.zeros((n, 2, M + 1, 2))
     o = _opts(M, variant, sched_group)
     lib().or_walks(ctypes.byref(prep.struct), ctypes.byref(o), x.ctypes.data, point_id, instance, ids.ctypes.data,
-                   n, seed, fu.ctypes.data, fg.ctypes.data, H.ctypes.data, Y.ctypes.data, sc.ctypes.data)
-    return {"u": fu, "grad": fg, "H": H, "Y": Y, "scale": sc}
+                   n, seed, fu.ctypes.data, fg.ctypes.data, H.ctypes.data, Y.ctypes.data, sc.ctypes.data,
+                   QT.ctypes.data)
+    return {"u": fu, "grad": fg, "H": H, "Y": Y, "scale": sc, "Q": QT[..., 0], "T": QT[..., 1]}
 
 
 def flux_at(problem, h, y, prepared=None):

@@ -544,6 +544,54 @@ static double or_flux(const or_problem *P, int h, const double *y)
     }
 }
 
+/* sum of the magnitudes of the terms that make up b_h(y): the scale against
+ * which the rounding error of evaluating b_h is measured in the tests */
+static double or_flux_mag(const or_problem *P, int h, const double *y)
+{
+    int d = P->dim, n = P->flux_n[h];
+    const double *c = P->flux_coef + P->flux_off[h];
+    double m = 0.0;
+    switch (P->flux_basis[h]) {
+    case OR_FLUX_FOURIER:
+        for (int k = 0; k < n; ++k) m += fabs(c[k]);
+        return m;
+    case OR_FLUX_REAL_SH: {
+        double u[3];
+        const double *cc = or_center(P, h);
+        for (int k = 0; k < 3; ++k) u[k] = (y[k] - cc[k]) / P->radius[h];
+        double nn = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        for (int k = 0; k < 3; ++k) u[k] /= nn;
+        for (int idx = 0; idx < n; ++idx) {
+            if (c[idx] == 0.0) continue;
+            int l = (int)floor(sqrt((double)idx) + 1e-9);
+            m += fabs(c[idx] * or_real_sh(l, idx - l * l - l, u));
+        }
+        return m;
+    }
+    case OR_FLUX_HARMONIC_POLY: {
+        int T = (int)c[1];
+        double nrm[OR_MAX_DIM];
+        or_normal(P, h, y, nrm);
+        for (int t = 0; t < T; ++t) {
+            const double *row = c + 2 + t * (d + 1);
+            for (int k = 0; k < d; ++k) {
+                int ek = (int)row[1 + k];
+                if (ek == 0) continue;
+                double term = row[0] * ek;
+                for (int j = 0; j < d; ++j) {
+                    int e = (int)row[1 + j] - (j == k ? 1 : 0);
+                    for (int p = 0; p < e; ++p) term *= fabs(y[j]);
+                }
+                m += fabs(term * nrm[k]);
+            }
+        }
+        return fabs(c[0]) * m;
+    }
+    default:
+        return 0.0;
+    }
+}
+
 static double or_beta(const or_problem *P, int h, const double *y)
 {
     double sc = P->beta_scale[h];
@@ -557,7 +605,9 @@ static double or_beta(const or_problem *P, int h, const double *y)
 typedef struct {
     int *H;          /* [M+1] scheduled interfaces (0-based), or NULL */
     double *Y;       /* [2][M+1][dim] states of each chain, or NULL */
-    double *scale;   /* [3]: sum_i |c_i Phi_i|, sum_i |c_i| and sum_i |c_i| |grad Phi_i| (both chains) */
+    double *scale;   /* [4]: sum_i |c_i Phi_i|, sum_i |c_i|, sum_i |c_i| |grad Phi_i| (both chains), and
+                        max over chains of (term magnitude of beta(y_0)) / |beta(y_0)| (>= 1) */
+    double *QT;      /* [2][M+1][2]: Q_i and T_i of each chain, or NULL */
 } or_trace;
 
 /* H_i: 0-based index; i = 0 uniform over the N surfaces, i >= 1 by |alpha| */
@@ -586,6 +636,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0}, sc_phi = 0.0, sc_c = 0.0, sc_g = 0.0;
 
     double y[2][OR_MAX_DIM], Q[2], T[2];
+    double cond0 = 1.0;
     int alive[2] = {1, 1};
     double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m})  (reading R1) */
     double Ai = 1.0;         /* ||alpha||_1^i */
@@ -616,6 +667,8 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                 if (o->variant == 0) {
                     or_uniform_point(P, h, &rng, 0, k, y[k]);
                     Q[k] = or_beta(P, h, y[k]) * P->area[h];
+                    double b0 = fabs(or_flux(P, h, y[k])), bm = or_flux_mag(P, h, y[k]);
+                    if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
                 } else {
                     double L = P->part_len[2 * h + k];
                     if (L <= 0.0 || P->flux_basis[h] == OR_FLUX_ZERO) {
@@ -625,6 +678,8 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     } else {
                         or_uniform_part_point(P, h, k, &rng, 0, k, y[k]);
                         Q[k] = or_beta(P, h, y[k]) * L;
+                        double b0 = fabs(or_flux(P, h, y[k])), bm = or_flux_mag(P, h, y[k]);
+                        if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
                     }
                 }
             } else if (alive[k]) {
@@ -668,6 +723,10 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
             }
             if (tr && tr->Y)
                 for (int c = 0; c < d; ++c) tr->Y[((size_t)k * (M + 1) + i) * d + c] = y[k][c];
+            if (tr && tr->QT) {
+                tr->QT[((size_t)k * (M + 1) + i) * 2] = Q[k];
+                tr->QT[((size_t)k * (M + 1) + i) * 2 + 1] = T[k];
+            }
             if (!alive[k]) continue;
             /* tally: N w_i ||alpha||^i prod sign(alpha) Q T Phi(x, y_i), and grad_x Phi */
             double coef = (or_mutant == 4 ? 1.0 : (double)N) * weight * Ai * S * Q[k] * T[k];
@@ -685,7 +744,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     }
     *out_u = acc_u;
     for (int c = 0; c < d; ++c) out_g[c] = acc_g[c];
-    if (tr && tr->scale) { tr->scale[0] = sc_phi; tr->scale[1] = sc_c; tr->scale[2] = sc_g; }
+    if (tr && tr->scale) { tr->scale[0] = sc_phi; tr->scale[1] = sc_c; tr->scale[2] = sc_g; tr->scale[3] = cond0; }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -731,12 +790,12 @@ int or_estimate(const or_problem *P, const or_opts *o, const double *points, int
 /* per-walk values for pathwise replay: walks[w] for one point */
 void or_walks(const or_problem *P, const or_opts *o, const double *x, uint32_t point_id, uint32_t instance,
               const uint64_t *walks, int64_t n_walks, uint64_t seed, double *out_u, double *out_g, int *out_H,
-              double *out_Y, double *out_scale)
+              double *out_Y, double *out_scale, double *out_QT)
 {
     const int d = P->dim, M = o->M;
     for (int64_t w = 0; w < n_walks; ++w) {
         or_trace tr = {out_H ? out_H + w * (M + 1) : NULL, out_Y ? out_Y + (size_t)w * 2 * (M + 1) * d : NULL,
-                       out_scale ? out_scale + 3 * w : NULL};
+                       out_scale ? out_scale + 4 * w : NULL, out_QT ? out_QT + (size_t)w * 2 * (M + 1) * 2 : NULL};
         or_walk(P, o, x, point_id, instance, walks[w], seed, out_u + w, out_g + w * d, &tr);
     }
 }

@@ -905,8 +905,9 @@ woi_status woi_estimate_range(woi_geometry *g, const woi_opts *opts, const doubl
     return run_estimate(g, opts, points, n_pts, walk_begin, n_walks, seed, nullptr, nullptr, nullptr, nullptr, moments);
 }
 
-woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
-                           const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad)
+static woi_status walk_values_impl(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
+                                   const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad,
+                                   double *trace)
 {
     g_last_error.clear();
     if (!g || !o || !x || (n > 0 && (!walk_ids || !f_u || !f_grad))) return fail(WOI_E_INVALID_ARG, "null argument");
@@ -917,12 +918,15 @@ woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, 
     if (n == 0) return WOI_OK;
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     const int d = g->dim;
+    const int chains = o->variant == WOI_VR ? 2 : 1;
+    const size_t trace_count = (size_t)n * chains * (o->M + 1) * (d + 2);
     if ((st = stage_geometry(g, o->M, s)) != WOI_OK) return st;
     size_t off = 0;
     const size_t o_x = off; off = align_up(off + d * sizeof(double), 256);
     const size_t o_w = off; off = align_up(off + n * sizeof(uint64_t), 256);
     const size_t o_u = off; off = align_up(off + n * sizeof(double), 256);
     const size_t o_g = off; off = align_up(off + n * d * sizeof(double), 256);
+    const size_t o_t = off; off = align_up(off + (trace ? trace_count : 0) * sizeof(double), 256);
     if ((st = ensure_scratch(g, off)) != WOI_OK) return st;
     char *base = (char *)g->d_scratch;
     WOI_CUDA(cudaMemcpyAsync(base + o_x, x, d * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -938,11 +942,31 @@ woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, 
     p.seed = seed;
     p.f_u = (double *)(base + o_u);
     p.f_grad = (double *)(base + o_g);
+    p.trace = trace ? (double *)(base + o_t) : nullptr;
+    if (trace) WOI_CUDA(cudaMemsetAsync(p.trace, 0, trace_count * sizeof(double), s));
     WOI_CUDA(launch_walk_values(d, o->variant == WOI_VR, g->star_idx >= 0, o->precision == WOI_FP64_PLAIN, p, s));
     WOI_CUDA(cudaMemcpyAsync(f_u, p.f_u, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     WOI_CUDA(cudaMemcpyAsync(f_grad, p.f_grad, n * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (trace) WOI_CUDA(cudaMemcpyAsync(trace, p.trace, trace_count * sizeof(double), cudaMemcpyDeviceToHost, s));
     WOI_CUDA(cudaStreamSynchronize(s));
     return WOI_OK;
+}
+
+woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
+                           const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad)
+{
+    return walk_values_impl(g, o, x, point_id, walk_ids, n, seed, f_u, f_grad, nullptr);
+}
+
+woi_status woi_walk_trace(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
+                          const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad,
+                          double *trace)
+{
+    if (!trace) {
+        g_last_error = "null trace";
+        return WOI_E_INVALID_ARG;
+    }
+    return walk_values_impl(g, o, x, point_id, walk_ids, n, seed, f_u, f_grad, trace);
 }
 
 woi_status woi_last_kernel_ms(woi_geometry *g, float *ms)

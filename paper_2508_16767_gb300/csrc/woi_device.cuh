@@ -95,7 +95,11 @@ template <> struct RealOps<double> {
     __device__ static __forceinline__ double rcp(double v) { return 1.0 / v; }
 };
 
-template <typename Real> __host__ __device__ constexpr Real eps_tol() { return sizeof(Real) == 4 ? (Real)2e-9 : (Real)1e-17; }
+// Newton step below which the iteration has converged (the last step is then taken:
+// with quadratic convergence the result is accurate to the rounding noise of f)
+template <typename Real> __host__ __device__ constexpr Real eps_tol() { return sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-10; }
+// bracket width below which a bisection-safeguarded search stops
+template <typename Real> __host__ __device__ constexpr Real bracket_tol() { return sizeof(Real) == 4 ? (Real)1e-9 : (Real)1e-17; }
 
 // word k (k >= 1) of a (step, chain) stream: sub-call k / 4, lane k % 4
 struct StepWords {
@@ -351,12 +355,16 @@ __device__ void star_at_arclen(const SGeom<Real> &g, double s_abs, int *jo, Real
     const int iters = sizeof(Real) == 4 ? 12 : 30;
     for (int it = 0; it < iters; ++it) {
         const Real f = star_local_arclen(g, lo, delta) - ds;
+        if (f == (Real)0) break;
         if (f > 0) d_hi = delta; else d_lo = delta;
-        Real dn = delta - f / star_speed_at(g, lo, delta);
+        const Real step = f / star_speed_at(g, lo, delta);
+        if (RealOps<Real>::fabs_(step) <= eps_tol<Real>()) {   // converged: take the last Newton step
+            delta -= step;
+            break;
+        }
+        Real dn = delta - step;
         if (!(dn > d_lo && dn < d_hi)) dn = (Real)0.5 * (d_lo + d_hi);
-        const Real step = RealOps<Real>::fabs_(dn - delta);
         delta = dn;
-        if (step <= eps_tol<Real>()) break;
     }
     *jo = lo;
     *delta_o = delta;
@@ -385,12 +393,17 @@ __device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa
     for (int it = 0; it < iters; ++it) {
         Real f, df;
         star_line_f(g, j, t, yc, z, &f, &df);
+        if (f == (Real)0) break;
         if ((f < 0) == (fa < 0)) a = t; else b = t;
-        Real tn = t - f / df;
+        const Real step = f / df;
+        if (RealOps<Real>::fabs_(step) <= eps_tol<Real>()) {   // converged: take the last Newton step
+            t -= step;
+            break;
+        }
+        Real tn = t - step;
         if (!(tn > a && tn < b)) tn = (Real)0.5 * (a + b);
-        const Real step = RealOps<Real>::fabs_(tn - t);
         t = tn;
-        if (step <= eps_tol<Real>() || b - a <= eps_tol<Real>()) break;
+        if (b - a <= bracket_tol<Real>()) break;
     }
     return t;
 }
@@ -398,18 +411,20 @@ __device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa
 // Intersections of the line (ray = false) or ray (ray = true) yc + s z (yc
 // relative to the star centre) with the star: roots of f on a kNodes-sample
 // scan, plus root pairs hidden inside a scan interval, found from the
-// extremum of f where |f| may reach 0 (|f'| <= lmax).  The line's own start
-// point (|s| below `tiny`) is excluded.  Returns q; tt[] the line parameters,
-// jj[] / dd[] the roots as (node, offset).
+// extremum of f where |f| may reach 0 (|f'| <= lmax).  For a line, the start
+// point is itself on the curve at angle (sj, sd): exactly one root, the one
+// nearest to that angle, is the start point and is dropped.  Returns q; tt[]
+// the line parameters, jj[] / dd[] the roots as (node, offset).
 template <typename Real>
-__device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Real *z, bool ray, Real *tt, int *jj,
-                                  Real *dd)
+__device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Real *z, bool ray, int sj, Real sd,
+                                  Real *tt, int *jj, Real *dd)
 {
     const Real e = yc[0] * z[1] - yc[1] * z[0];
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
     const Real guard = g.star_lmax * H * (Real)0.5;
     const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
-    int q = 0;
+    int q = 0, self = -1;
+    Real self_dist = (Real)1e30;
     const Real f0 = g.scan[0][0] * z[1] - g.scan[0][1] * z[0] - e;
     Real fa = f0;
     for (int j = 0; j < kNodes; ++j) {
@@ -445,15 +460,33 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
             angle_cs(g, j, cand[c], &ct, &st);
             star_local(g, ct, st, p, (Real *)nullptr);
             const Real s = (p[0] - yc[0]) * z[0] + (p[1] - yc[1]) * z[1];
-            const bool ok = ray ? (s > tiny) : (RealOps<Real>::fabs_(s) > tiny);
+            const bool ok = ray ? (s > tiny) : true;
             if (ok && q < kMaxRoots) {
                 tt[q] = s;
                 jj[q] = j;
                 dd[q] = cand[c];
+                if (!ray) {
+                    int dj = j - sj;  // cyclic angular distance to the start point
+                    if (dj > kNodes / 2) dj -= kNodes;
+                    if (dj < -kNodes / 2) dj += kNodes;
+                    const Real dist = RealOps<Real>::fabs_((Real)dj * H + (cand[c] - sd));
+                    if (dist < self_dist) {
+                        self_dist = dist;
+                        self = q;
+                    }
+                }
                 ++q;
             }
         }
         fa = fb;
+    }
+    if (!ray && self >= 0) {  // drop the start point
+        for (int a = self; a + 1 < q; ++a) {
+            tt[a] = tt[a + 1];
+            jj[a] = jj[a + 1];
+            dd[a] = dd[a + 1];
+        }
+        --q;
     }
     return q;
 }
@@ -613,6 +646,8 @@ struct Chain {
     Real v[D];
     Real Q, T;
     bool alive;
+    int aj;       // on a star: the state's angle as node aj + offset ad
+    Real ad;
 };
 
 // start (i = 0): y_0 uniform on dOmega_h (plain) or on dOmega_h^{+/-} (VR), Q = beta(y_0) |part|
@@ -623,6 +658,8 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
     ch.T = 1;
     ch.alive = true;
     ch.s = h;
+    ch.aj = 0;
+    ch.ad = 0;
     Real u[D], nrm[D];
     double part_len = g.area[h];
     if constexpr (VR) {
@@ -649,6 +686,8 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
             // arcs of the requested sign (VR)
             const double s_target = (double)u01<Real>(w.a.y) * part_len;
             Real ct, st;
+            int j_sel = 0;
+            Real d_sel = 0;
             if constexpr (VR) {
                 double s = s_target;
                 const int want = k == 0 ? 1 : -1;
@@ -661,10 +700,8 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
                 }
                 if (s > gd->arc_len[a_sel]) s = gd->arc_len[a_sel];
                 if (is_star) {
-                    int j;
-                    Real delta;
-                    star_at_arclen(g, gd->arc_s0[a_sel] + s, &j, &delta);
-                    angle_cs(g, j, delta, &ct, &st);
+                    star_at_arclen(g, gd->arc_s0[a_sel] + s, &j_sel, &d_sel);
+                    angle_cs(g, j_sel, d_sel, &ct, &st);
                 } else {
                     // t = t0 + s / R, split into a node and an offset in FP64
                     const double t = gd->arc_t0[a_sel] + s / (double)gd->radius[h];
@@ -674,13 +711,13 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
                     angle_cs(g, j, (Real)(t - j * H), &ct, &st);
                 }
             } else {
-                int j;
-                Real delta;
-                star_at_arclen(g, s_target, &j, &delta);
-                angle_cs(g, j, delta, &ct, &st);
+                star_at_arclen(g, s_target, &j_sel, &d_sel);
+                angle_cs(g, j_sel, d_sel, &ct, &st);
             }
             if (is_star) {
                 star_local(g, ct, st, ch.v, nrm);
+                ch.aj = j_sel;
+                ch.ad = d_sel;
             } else {
                 nrm[0] = ct;
                 nrm[1] = st;
@@ -723,6 +760,8 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
                 star_at_arclen(g, (double)u01<Real>(w.a.y) * (double)g.panel_s[kNodes], &j, &delta);
                 angle_cs(g, j, delta, &ct, &st);
                 star_local(g, ct, st, vn, nrm);
+                ch.aj = j;
+                ch.ad = delta;
                 const Real dx = vn[0] - dy[0], dyy = vn[1] - dy[1];
                 const Real r2 = dx * dx + dyy * dyy;
                 ch.Q *= (dx * nrm[0] + dyy * nrm[1]) * O::rcp(r2) * (Real)(1.0 / (2.0 * PI)) * g.area[h];
@@ -731,7 +770,7 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
                 direction<Real, 2>(w, z);
                 Real tt[kMaxRoots], dd[kMaxRoots];
                 int jj[kMaxRoots];
-                const int q = star_intersections(g, dy, z, rel == 1, tt, jj, dd);
+                const int q = star_intersections(g, dy, z, rel == 1, ch.aj, ch.ad, tt, jj, dd);
                 if (q == 0) {
                     ch.alive = false;
                     ch.T = 0;
@@ -748,6 +787,8 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
                 Real ct, st;
                 angle_cs(g, jj[sel], dd[sel], &ct, &st);
                 star_local(g, ct, st, vn, nrm);
+                ch.aj = jj[sel];
+                ch.ad = dd[sel];
                 const Real dot = (vn[0] - dy[0]) * nrm[0] + (vn[1] - dy[1]) * nrm[1];
                 if (rel == 0) ch.Q *= (Real)0.5;
                 ch.T *= (Real)q * (dot > 0 ? (Real)1 : (dot < 0 ? (Real)-1 : (Real)0));
@@ -810,9 +851,9 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
 // N sum_i w_i A^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i Phi(x, Y_i), summed
 // over the two chains for VR
 // ---------------------------------------------------------------------------
-template <typename Real, int D, bool VR, bool STAR>
+template <typename Real, int D, bool VR, bool STAR, bool TRACE = false>
 __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const XPoint<Real, D> &x, const Rng &rng,
-                     int sched_group, uint64_t group, Real *f)
+                     int sched_group, uint64_t group, Real *f, double *trace = nullptr)
 {
 #pragma unroll
     for (int c = 0; c <= D; ++c) f[c] = 0;
@@ -844,6 +885,15 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const XPoint<Real,
                 chain_step<Real, D, STAR>(g, h, rel, w, ch[k]);
             }
             if (ch[k].alive) tally<Real, D>(g, x, ch[k].s, ch[k].v, g.coef[i] * S * ch[k].Q * ch[k].T, f);
+            if constexpr (TRACE) {
+                if (trace) {
+                    double *t = trace + ((size_t)k * (g.M + 1) + i) * (D + 2);
+                    for (int c = 0; c < D; ++c)
+                        t[c] = ((double)g.c_hi[ch[k].s][c] + (double)g.c_lo[ch[k].s][c]) + (double)ch[k].v[c];
+                    t[D] = (double)ch[k].Q;
+                    t[D + 1] = (double)ch[k].T;
+                }
+            }
         }
         hp = h;
     }

@@ -53,6 +53,7 @@ struct WalkValuesParams {
     int sched_group;
     uint64_t seed;
     double *f_u, *f_grad;              // device [n], [n][dim]
+    double *trace;                     // device [n][chains][M+1][dim+2] (y, Q, T per step) or null
 };
 
 // launchers of one dimension / star flag; defined in woi_kernels_impl.cuh and

@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
     rng.w0 = (uint32_t)w;
     rng.w1 = (uint32_t)(w >> 32);
     Real f[D + 1];
-    walk<Real, D, VR, STAR>(g, p.geom, x, rng, p.sched_group, w / 32u, f);
+    walk<Real, D, VR, STAR, true>(g, p.geom, x, rng, p.sched_group, w / 32u, f,
+                                  p.trace ? p.trace + (size_t)i * (VR ? 2 : 1) * (g.M + 1) * (D + 2) : nullptr);
     p.f_u[i] = (double)f[0];
 #pragma unroll
     for (int c = 0; c < D; ++c) p.f_grad[i * D + c] = (double)f[1 + c];

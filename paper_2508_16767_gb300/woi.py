@@ -28,7 +28,7 @@ WOI_MIXED, WOI_FP64_PLAIN = 0, 1
 STATUS = {0: "WOI_OK", 1: "WOI_E_INVALID_ARG", 2: "WOI_E_GEOMETRY", 3: "WOI_E_COMPAT", 4: "WOI_E_UNSUPPORTED",
           5: "WOI_E_NO_DEVICE", 6: "WOI_E_CUDA", 7: "WOI_E_OOM", 8: "WOI_E_TIMEOUT", 9: "WOI_E_STATE"}
 EXPORTED = ["woi_default_opts", "woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate",
-            "woi_estimate_range", "woi_walk_values", "woi_estimate_batch", "woi_last_kernel_ms",
+            "woi_estimate_range", "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
             "woi_destroy_geometry", "woi_last_error", "woi_version"]
 
 
@@ -71,6 +71,7 @@ def _load():
     lib.woi_estimate.argtypes = [vp, P(Opts), dp, i64, i64, u64, dp, dp, dp, dp]
     lib.woi_estimate_range.argtypes = [vp, P(Opts), dp, i64, i64, i64, u64, dp]
     lib.woi_walk_values.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, dp, i64, u64, dp, dp]
+    lib.woi_walk_trace.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, dp, i64, u64, dp, dp, dp]
     lib.woi_estimate_batch.argtypes = [ctypes.c_int, P(vp), P(Opts), P(ctypes.c_int), P(dp), P(i64), P(i64), u64,
                                        P(dp), P(dp), P(dp), P(dp)]
     lib.woi_last_kernel_ms.argtypes = [vp, P(ctypes.c_float)]
@@ -79,7 +80,7 @@ def _load():
     lib.woi_last_error.restype = ctypes.c_char_p
     lib.woi_version.restype = ctypes.c_char_p
     for name in ["woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate", "woi_estimate_range",
-                 "woi_walk_values", "woi_estimate_batch", "woi_last_kernel_ms"]:
+                 "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms"]:
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -274,6 +275,22 @@ def woi_walk_values(geom: Geometry, x, walk_ids, seed=0, point_id=0, **opt):
     _check(lib.woi_walk_values(geom.handle, ctypes.byref(o), x.ctypes.data, int(point_id), ids.ctypes.data, n,
                                int(seed), fu.ctypes.data, fg.ctypes.data))
     return {"u": fu, "grad": fg}
+
+
+def woi_walk_trace(geom: Geometry, x, walk_ids, seed=0, point_id=0, **opt):
+    """Per-walk tallies and per-step states (y, Q, T) of every chain."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    ids = np.ascontiguousarray(walk_ids, dtype=np.uint64)
+    n = len(ids)
+    M = opt.pop("M", geom.problem.get("M", 4))
+    chains = 2 if opt.get("variant", "plain") == "vr" else 1
+    fu = np.zeros(n)
+    fg = np.zeros((n, geom.dim))
+    tr = np.zeros((n, chains, M + 1, geom.dim + 2))
+    o = make_opts(M=M, **opt)
+    _check(lib.woi_walk_trace(geom.handle, ctypes.byref(o), x.ctypes.data, int(point_id), ids.ctypes.data, n,
+                              int(seed), fu.ctypes.data, fg.ctypes.data, tr.ctypes.data))
+    return {"u": fu, "grad": fg, "Y": tr[..., :geom.dim], "Q": tr[..., geom.dim], "T": tr[..., geom.dim + 1]}
 
 
 def finalize_moments(mom, n_walks, sched_group=1):

@@ -3,8 +3,9 @@
 * Pathwise replay: the same Philox streams give the same walks; per-walk
   tallies agree to 1e-12 (FP64 path) and 1e-5 (FP32 path) relative to the
   walk's magnitude scale (sum_i |c_i| (|Phi_i| + 1) for u, sum_i |c_i| |grad Phi_i|
-  for grad u), apart from a bounded fraction of FP32 walks whose discrete
-  choices flip at a near-tangency (star curves only).
+  for grad u, each times the conditioning of the start flux: the sum of the
+  magnitudes of its terms over its value), apart from a bounded fraction of
+  FP32 walks whose discrete choices flip at a near-tangency (star curves only).
 * Per-point estimates over the same walks: the FP32 path's mean differs from
   the oracle's by far less than the Monte Carlo standard error (1e-2 SE), the
   FP64 path's by rounding only; sizes span several work units and a ragged tail.
@@ -83,8 +84,11 @@ def replay(W, O, prob, x, variant, precision, point_id):
     gv = W.woi_walk_values(g, x, ids, seed=7, point_id=point_id, M=prob["M"], variant=variant, precision=precision)
     ov = O.walks(prob, x, ids, seed=7, M=prob["M"], variant=variant, point_id=point_id)
     g.close()
-    sc_u = ov["scale"][:, 0] + ov["scale"][:, 1]
-    sc_g = ov["scale"][:, 2]
+    # magnitude scales: sum_i |c_i| (|Phi_i| + 1) and sum_i |c_i| |grad Phi_i|, times the
+    # conditioning of the start flux beta(y_0) (the sum of |terms| over |value|)
+    cond = ov["scale"][:, 3]
+    sc_u = (ov["scale"][:, 0] + ov["scale"][:, 1]) * cond
+    sc_g = ov["scale"][:, 2] * cond
     eu = np.abs(gv["u"] - ov["u"]) / np.maximum(sc_u, 1e-300)
     eg = np.max(np.abs(gv["grad"] - ov["grad"]), axis=1) / np.maximum(sc_g, 1e-300)
     return eu, eg
