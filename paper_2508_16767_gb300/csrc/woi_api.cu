@@ -125,6 +125,8 @@ struct woi_geometry {
 
     bool data_ready = false;
     std::vector<double> sigma, alpha, beta_scale, flux_coef;
+    std::vector<double> flux_dev;              // device format of flux_coef
+    std::vector<float> flux_dev_f;
     std::vector<uint64_t> thresh;
     double alpha_l1 = 0.0;
     std::vector<int> flux_basis, flux_off, flux_n;
@@ -137,6 +139,7 @@ struct woi_geometry {
     bool dev_dirty = true;
     DevGeom blob{};
     DevGeom *d_blob = nullptr;
+    float *d_flux_f = nullptr;
     double *d_flux = nullptr, *d_arc_t0 = nullptr, *d_arc_t1 = nullptr, *d_arc_len = nullptr, *d_arc_s0 = nullptr;
     int *d_arc_sign = nullptr;
     int blob_M = -1;
@@ -157,6 +160,7 @@ struct woi_geometry {
         cudaSetDevice(device);
         cudaFree(d_blob);
         cudaFree(d_flux);
+        cudaFree(d_flux_f);
         cudaFree(d_arc_t0);
         cudaFree(d_arc_t1);
         cudaFree(d_arc_len);
@@ -170,6 +174,7 @@ struct woi_geometry {
         if (cur >= 0) cudaSetDevice(cur);
         d_blob = nullptr;
         d_flux = d_arc_t0 = d_arc_t1 = d_arc_len = d_arc_s0 = nullptr;
+        d_flux_f = nullptr;
         d_arc_sign = nullptr;
         d_scratch = nullptr;
         scratch_bytes = 0;
@@ -570,6 +575,22 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
     g->flux_off = off;
     g->flux_n = nc;
     g->flux_coef = coef;
+    // device format: real spherical harmonics carry N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!)
+    // and the sqrt(2) of m != 0, so that the kernels evaluate only the Legendre recursion
+    g->flux_dev = coef;
+    for (int i = 0; i < n; ++i) {
+        if (basis[i] != WOI_FLUX_REAL_SH) continue;
+        for (int idx = 0; idx < nc[i]; ++idx) {
+            int l = 0;
+            while ((l + 1) * (l + 1) <= idx) ++l;
+            const int m = idx - l * l - l, am = m < 0 ? -m : m;
+            double ratio = 1.0;
+            for (int k = l - am + 1; k <= l + am; ++k) ratio /= k;
+            const double nlm = std::sqrt((2.0 * l + 1.0) / (4.0 * kPi) * ratio) * (m == 0 ? 1.0 : std::sqrt(2.0));
+            g->flux_dev[off[i] + idx] *= nlm;
+        }
+    }
+    g->flux_dev_f.assign(g->flux_dev.begin(), g->flux_dev.end());
     g->vr_ok = vr_ok;
     g->arc_t0 = at0; g->arc_t1 = at1; g->arc_len = alen; g->arc_s0 = as0; g->arc_sign = asg;
     g->arc_off = aoff; g->arc_n = an; g->part_len = plen;
@@ -624,7 +645,8 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
     if (!g->dev_dirty && g->blob_M == M) return WOI_OK;
     woi_status st;
     if (g->dev_dirty) {
-        if ((st = upload(&g->d_flux, g->flux_coef, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_flux, g->flux_dev, s)) != WOI_OK) return st;
+        if ((st = upload(&g->d_flux_f, g->flux_dev_f, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_t0, g->arc_t0, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_t1, g->arc_t1, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_len, g->arc_len, s)) != WOI_OK) return st;
@@ -682,6 +704,7 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
         for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g->star_panel_s[j];
     }
     b.flux_coef = g->d_flux;
+    b.flux_coef_f = g->d_flux_f;
     b.arc_t0 = g->d_arc_t0;
     b.arc_t1 = g->d_arc_t1;
     b.arc_len = g->d_arc_len;

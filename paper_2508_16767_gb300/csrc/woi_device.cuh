@@ -81,6 +81,7 @@ template <> struct RealOps<float> {
     __device__ static __forceinline__ float sqrt_(float v) { return sqrtf(v); }
     __device__ static __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
     __device__ static __forceinline__ float log_(float v) { return logf(v); }
+    __device__ static __forceinline__ float fast_log(float v) { return __logf(v); }
     __device__ static __forceinline__ void sincos_(float t, float *s, float *c) { sincosf(t, s, c); }
     __device__ static __forceinline__ float fabs_(float v) { return fabsf(v); }
     __device__ static __forceinline__ float rcp(float v) { return 1.0f / v; }
@@ -90,6 +91,7 @@ template <> struct RealOps<double> {
     __device__ static __forceinline__ double sqrt_(double v) { return sqrt(v); }
     __device__ static __forceinline__ double rsqrt_(double v) { return 1.0 / sqrt(v); }
     __device__ static __forceinline__ double log_(double v) { return log(v); }
+    __device__ static __forceinline__ double fast_log(double v) { return log(v); }
     __device__ static __forceinline__ void sincos_(double t, double *s, double *c) { sincos(t, s, c); }
     __device__ static __forceinline__ double fabs_(double v) { return fabs(v); }
     __device__ static __forceinline__ double rcp(double v) { return 1.0 / v; }
@@ -495,16 +497,20 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
 // flux datum b_h(y) at the start point (Sec. 1); u = unit outward direction
 // for spheres / (cos t, sin t) of the parameter for 2D curves; n = normal
 // ---------------------------------------------------------------------------
+template <typename Real> __device__ __forceinline__ const Real *flux_coefs(const DevGeom *gd);
+template <> __device__ __forceinline__ const float *flux_coefs<float>(const DevGeom *gd) { return gd->flux_coef_f; }
+template <> __device__ __forceinline__ const double *flux_coefs<double>(const DevGeom *gd) { return gd->flux_coef; }
+
 template <typename Real, int D>
 __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *u, const Real *n)
 {
     const int basis = gd->flux_basis[h];
-    const double *c = gd->flux_coef + gd->flux_off[h];
+    const Real *c = flux_coefs<Real>(gd) + gd->flux_off[h];
     const int nc = gd->flux_n[h];
     if (basis == kFluxFourier) {
-        Real v = (Real)c[0], ck = u[0], sk = u[1];
+        Real v = c[0], ck = u[0], sk = u[1];
         for (int k = 1; 2 * k <= nc - 1; ++k) {
-            v += (Real)c[2 * k - 1] * ck + (Real)c[2 * k] * sk;
+            v += c[2 * k - 1] * ck + c[2 * k] * sk;
             const Real cn = ck * u[0] - sk * u[1];
             sk = sk * u[0] + ck * u[1];
             ck = cn;
@@ -513,15 +519,20 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
     }
     if (basis == kFluxRealSH) {
         if constexpr (D == 3) {
-            // associated Legendre P_l^m(x) without the (-1)^m phase, x = cos(polar)
+            // associated Legendre P_l^m(x) without the (-1)^m phase, x = cos(polar); the
+            // coefficients already carry the normalisation of the real harmonics
             const Real x = u[2];
-            const Real sx = RealOps<Real>::sqrt_((Real)fmax(0.0, (double)(1 - x * x)));
+            Real sx2 = (Real)1 - x * x;
+            sx2 = sx2 > (Real)0 ? sx2 : (Real)0;
+            const Real sx = RealOps<Real>::sqrt_(sx2);
             Real ca = 1, sa = 0;  // cos / sin of the azimuth
             if (sx > (Real)0) {
-                ca = u[0] / sx;
-                sa = u[1] / sx;
+                const Real inv = (Real)1 / sx;
+                ca = u[0] * inv;
+                sa = u[1] * inv;
             }
-            const int L = (int)(sqrt((double)nc) + 1e-9) - 1;
+            int L = 0;
+            while ((L + 2) * (L + 2) <= nc) ++L;
             Real v = 0;
             Real pmm = 1, cm = 1, sm = 0;  // P_m^m, cos(m az), sin(m az)
             for (int m = 0; m <= L; ++m) {
@@ -539,16 +550,8 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
                         p_prev = p_cur;
                         p_cur = p_next;
                     }
-                    // normalisation sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)
-                    double ratio = 1.0;
-                    for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
-                    const Real nlm = (Real)sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * ratio);
-                    if (m == 0) {
-                        v += (Real)c[l * l + l] * nlm * p_cur;
-                    } else {
-                        const Real base = (Real)1.4142135623730951 * nlm * p_cur;
-                        v += (Real)c[l * l + l + m] * base * cm + (Real)c[l * l + l - m] * base * sm;
-                    }
+                    if (m == 0) v += c[l * l + l] * p_cur;
+                    else v += (c[l * l + l + m] * cm + c[l * l + l - m] * sm) * p_cur;
                 }
             }
             return v;
@@ -556,18 +559,18 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
         return 0;
     }
     if (basis == kFluxHarmonicPoly) {
-        const Real s = (Real)c[0];
+        const Real s = c[0];
         const int T = (int)c[1];
         Real grad[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) grad[k] = 0;
         for (int t = 0; t < T; ++t) {
-            const double *row = c + 2 + t * (D + 1);
+            const Real *row = c + 2 + t * (D + 1);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const int ek = (int)row[1 + k];
                 if (ek == 0) continue;
-                Real term = (Real)row[0] * (Real)ek;
+                Real term = row[0] * (Real)ek;
                 for (int j = 0; j < D; ++j) {
                     const int e = (int)row[1 + j] - (j == k ? 1 : 0);
                     for (int p = 0; p < e; ++p) term *= y[j];
@@ -619,7 +622,7 @@ __device__ __forceinline__ void tally(const SGeom<Real> &g, const XPoint<Real, D
     constexpr double PI = 3.14159265358979323846;
     if constexpr (D == 2) {
         const Real inv_r2 = O::rcp(r2);
-        acc[0] += c * ((Real)(-1.0 / (4.0 * PI)) * O::log_(r2));
+        acc[0] += c * ((Real)(-1.0 / (4.0 * PI)) * O::fast_log(r2));
         const Real gc = c * (Real)(-1.0 / (2.0 * PI)) * inv_r2;
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[1 + k] += gc * dx[k];

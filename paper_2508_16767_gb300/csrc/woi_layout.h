@@ -36,7 +36,9 @@ struct DevGeom {
     double star_scan[kNodes][2];       // gamma(t_j) - centre
     double star_panel_s[kNodes + 1];   // arc length at t_j
     int flux_basis[kMaxSurf], flux_off[kMaxSurf], flux_n[kMaxSurf];
-    const double *flux_coef;           // device array
+    const double *flux_coef;           // device array, device format (real-SH entries carry their
+                                       // normalisation); FP32 copy in flux_coef_f
+    const float *flux_coef_f;
     double part_len[kMaxSurf][2];      // |dOmega^+|, |dOmega^-| (2D variance reduction)
     int arc_off[kMaxSurf], arc_n[kMaxSurf];
     const double *arc_t0;              // device arrays of the beta-sign arcs

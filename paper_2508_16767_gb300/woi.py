@@ -29,6 +29,7 @@ STATUS = {0: "WOI_OK", 1: "WOI_E_INVALID_ARG", 2: "WOI_E_GEOMETRY", 3: "WOI_E_CO
           5: "WOI_E_NO_DEVICE", 6: "WOI_E_CUDA", 7: "WOI_E_OOM", 8: "WOI_E_TIMEOUT", 9: "WOI_E_STATE"}
 EXPORTED = ["woi_default_opts", "woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate",
             "woi_estimate_range", "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
+
             "woi_destroy_geometry", "woi_last_error", "woi_version"]
 
 
@@ -303,3 +304,4 @@ def finalize_moments(mom, n_walks, sched_group=1):
     var = np.maximum(S2 - G * mean * mean, 0.0) / max(G - 1, 1)
     se = np.sqrt(var / G)
     return {"u": mean[:, 0], "grad": mean[:, 1:], "se_u": se[:, 0], "se_grad": se[:, 1:]}
+
