@@ -207,6 +207,38 @@ WOI_API woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geometrie
  */
 WOI_API woi_status woi_last_kernel_ms(woi_geometry *geometry, float *ms);
 
+/*
+ * Allocation-free variant of woi_estimate (mixed precision only).  The paper
+ * has no counterpart: this entry point exists for callers that must not
+ * allocate device memory while they run -- e.g. code inside a region where a
+ * host framework owns the whole device heap through its own pool, real-time or
+ * embedded hosts that fix their memory budget at start-up, or plug-ins that
+ * are only allowed to launch work on memory handed to them.
+ *
+ * Every byte of scratch it needs (the instance's geometry tables, the work
+ * queue head and the per-work-unit partial sums) lives in one fixed array of
+ * WOI_NOALLOC_SCRATCH_BYTES (16 MiB) compiled into the library; each GPU that
+ * loads the library holds that array until the process exits.  The call makes
+ * no cudaMalloc / cudaFree and uses no allocating library routine.
+ *
+ * points [n_pts][dim] and the outputs u[n_pts], grad[n_pts][dim], se_u[n_pts],
+ * se_grad[n_pts][dim] must be device pointers (outputs may be NULL).  The
+ * call is asynchronous on opts->cuda_stream.  Sizes whose scratch would exceed
+ * the array are rejected with WOI_E_INVALID_ARG (about 16 MiB / (16 (dim+1))
+ * work units of 2048 walks each, e.g. 4096 points x 1e5 walks in 3D fits).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the contents of the
+ * last call, so calls that may overlap on the GPU (different streams, or
+ * different host threads) race with each other and must be serialised by the
+ * caller.
+ */
+#define WOI_NOALLOC_SCRATCH_BYTES (16u << 20)
+WOI_API woi_status woi_estimate_noalloc(woi_geometry *geometry, const woi_opts *opts, const double *points,
+                                        int64_t n_pts, int64_t n_walks, uint64_t seed, double *u, double *grad,
+                                        double *se_u, double *se_grad);
+
 /* Release a geometry and its device buffers. NULL is accepted. */
 WOI_API void woi_destroy_geometry(woi_geometry *geometry);
 

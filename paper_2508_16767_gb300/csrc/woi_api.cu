@@ -1011,3 +1011,202 @@ woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geoms, const woi_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free estimate (no counterpart in the paper).
+//
+// For callers that may not allocate device memory while they run.  All scratch
+// -- the geometry blob, flux and arc tables, the instance descriptor, the work
+// queue head and the per-unit partials -- is carved out of one file-scope
+// device array.  In host code the array's name is only a host-side stand-in,
+// so its device address is looked up once per device with
+// cudaGetSymbolAddress (that device current) and passed to the kernels.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WOI_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+void *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+thread_local DevGeom g_noalloc_blob;   // host image of the blob (no heap allocation)
+
+woi_status noalloc_scratch_address(int dev, char **out)
+{
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(WOI_E_UNSUPPORTED, "device ordinal %d too large", dev);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(WOI_E_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (char *)g_noalloc_addr[dev];
+    return WOI_OK;
+}
+
+}  // namespace
+
+extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, const double *points, int64_t n_pts,
+                                           int64_t n_walks, uint64_t seed, double *u, double *grad, double *se_u,
+                                           double *se_grad)
+{
+    g_last_error.clear();
+    if (!g) return fail(WOI_E_INVALID_ARG, "null geometry");
+    woi_status st;
+    if ((st = check_opts(g, o, n_pts, 0, n_walks)) != WOI_OK) return st;
+    if (o->precision != WOI_MIXED) return fail(WOI_E_UNSUPPORTED, "the allocation-free estimate runs the mixed path only");
+    if (n_pts > 0 && !pointer_on_device(points)) return fail(WOI_E_INVALID_ARG, "points must be device memory");
+    double *outs[4] = {u, grad, se_u, se_grad};
+    for (double *p : outs)
+        if (p && !pointer_on_device(p)) return fail(WOI_E_INVALID_ARG, "outputs must be device memory");
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(WOI_E_NO_DEVICE, "no CUDA device");
+    }
+    if (n_pts == 0) return WOI_OK;
+    int dev = 0, num_sms = 0;
+    WOI_CUDA(cudaGetDevice(&dev));
+    WOI_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    char *base = nullptr;
+    if ((st = noalloc_scratch_address(dev, &base)) != WOI_OK) return st;
+
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    const int d = g->dim, C = d + 1, M = o->M;
+    const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0;
+    const int block = o->block_size ? o->block_size : 256;
+    const int L = o->walks_per_lane ? o->walks_per_lane : 8;
+    const int64_t unit_walks = (int64_t)block * L;
+    const int64_t chunks = (n_walks + unit_walks - 1) / unit_walks;
+    const int64_t units = n_pts * chunks;
+
+    // layout inside the fixed array; reject what does not fit
+    size_t off = 0;
+    const size_t o_blob = off; off = align_up(off + sizeof(DevGeom), 256);
+    const size_t o_flux = off; off = align_up(off + g->flux_dev.size() * sizeof(double), 256);
+    const size_t o_flux_f = off; off = align_up(off + g->flux_dev_f.size() * sizeof(float), 256);
+    const size_t o_t0 = off; off = align_up(off + g->arc_t0.size() * sizeof(double), 256);
+    const size_t o_t1 = off; off = align_up(off + g->arc_t1.size() * sizeof(double), 256);
+    const size_t o_len = off; off = align_up(off + g->arc_len.size() * sizeof(double), 256);
+    const size_t o_s0 = off; off = align_up(off + g->arc_s0.size() * sizeof(double), 256);
+    const size_t o_sign = off; off = align_up(off + g->arc_sign.size() * sizeof(int), 256);
+    const size_t o_desc = off; off = align_up(off + sizeof(InstDesc), 256);
+    const size_t o_queue = off; off = align_up(off + sizeof(unsigned long long), 256);
+    const size_t o_part = off; off = align_up(off + (size_t)units * 2 * C * sizeof(double), 256);
+    if (off > (size_t)WOI_NOALLOC_SCRATCH_BYTES)
+        return fail(WOI_E_INVALID_ARG,
+                    "%lld points x %lld walks need %zu bytes of scratch; the allocation-free estimate has %u",
+                    (long long)n_pts, (long long)n_walks, off, (unsigned)WOI_NOALLOC_SCRATCH_BYTES);
+
+    // tables of this geometry (pageable sources: staged before cudaMemcpyAsync returns)
+    auto put = [&](size_t at, const void *src, size_t bytes) -> cudaError_t {
+        return bytes ? cudaMemcpyAsync(base + at, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    WOI_CUDA(put(o_flux, g->flux_dev.data(), g->flux_dev.size() * sizeof(double)));
+    WOI_CUDA(put(o_flux_f, g->flux_dev_f.data(), g->flux_dev_f.size() * sizeof(float)));
+    WOI_CUDA(put(o_t0, g->arc_t0.data(), g->arc_t0.size() * sizeof(double)));
+    WOI_CUDA(put(o_t1, g->arc_t1.data(), g->arc_t1.size() * sizeof(double)));
+    WOI_CUDA(put(o_len, g->arc_len.data(), g->arc_len.size() * sizeof(double)));
+    WOI_CUDA(put(o_s0, g->arc_s0.data(), g->arc_s0.size() * sizeof(double)));
+    WOI_CUDA(put(o_sign, g->arc_sign.data(), g->arc_sign.size() * sizeof(int)));
+
+    DevGeom &b = g_noalloc_blob;
+    std::memset(&b, 0, sizeof(b));
+    b.dim = d;
+    b.n = g->n;
+    b.npad = 1;
+    while (b.npad < g->n) b.npad <<= 1;
+    b.M = M;
+    b.star_idx = g->star_idx;
+    b.star_K = star ? g->star.K : 0;
+    b.star_lmax = g->star_lmax;
+    for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g->n ? (uint32_t)(g->thresh[i] - 1) : 0xFFFFFFFFu;
+    for (int i = 0; i < g->n; ++i) {
+        for (int k = 0; k < d; ++k) b.center[i][k] = g->surf[i].center[k];
+        b.radius[i] = g->surf[i].radius;
+        b.area[i] = g->area[i];
+        b.alpha_sign[i] = g->alpha[i] > 0 ? 1.0 : (g->alpha[i] < 0 ? -1.0 : 0.0);
+        b.beta_scale[i] = g->beta_scale[i];
+        b.tin[i] = g->tin[i];
+        b.tout[i] = g->tout[i];
+        b.type[i] = g->surf[i].type;
+        b.flux_basis[i] = g->flux_basis[i];
+        b.flux_off[i] = g->flux_off[i];
+        b.flux_n[i] = g->flux_n[i];
+        b.part_len[i][0] = g->part_len.empty() ? 0.0 : g->part_len[2 * i];
+        b.part_len[i][1] = g->part_len.empty() ? 0.0 : g->part_len[2 * i + 1];
+        b.arc_off[i] = g->arc_off.empty() ? 0 : g->arc_off[i];
+        b.arc_n[i] = g->arc_n.empty() ? 0 : g->arc_n[i];
+    }
+    double Ai = 1.0;   // N w_i ||alpha||_1^i
+    for (int i = 0; i <= M; ++i) {
+        b.coef[i] = (double)g->n * (i == M ? 0.5 : 1.0) * Ai;
+        Ai *= g->alpha_l1;
+    }
+    for (int j = 0; j < kNodes; ++j) {
+        b.node_cs[j][0] = std::cos(2.0 * kPi * j / kNodes);
+        b.node_cs[j][1] = std::sin(2.0 * kPi * j / kNodes);
+    }
+    if (star) {
+        for (int k = 1; k <= g->star.K; ++k) {
+            b.star_a[k] = g->star.a[k];
+            b.star_b[k] = g->star.b[k];
+        }
+        for (int j = 0; j < kNodes; ++j) {
+            b.star_scan[j][0] = g->star_scan[2 * j];
+            b.star_scan[j][1] = g->star_scan[2 * j + 1];
+        }
+        for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g->star_panel_s[j];
+    }
+    b.flux_coef = (const double *)(base + o_flux);
+    b.flux_coef_f = (const float *)(base + o_flux_f);
+    b.arc_t0 = (const double *)(base + o_t0);
+    b.arc_t1 = (const double *)(base + o_t1);
+    b.arc_len = (const double *)(base + o_len);
+    b.arc_s0 = (const double *)(base + o_s0);
+    b.arc_sign = (const int *)(base + o_sign);
+    WOI_CUDA(put(o_blob, &b, sizeof(DevGeom)));
+
+    InstDesc desc{};
+    desc.geom = (const DevGeom *)(base + o_blob);
+    desc.points = points;
+    desc.n_pts = n_pts;
+    desc.n_walks = n_walks;
+    desc.walk_begin = 0;
+    desc.unit_begin = 0;
+    desc.chunks_per_point = chunks;
+    desc.instance_id = 0;
+    desc.sched_group = o->sched_group;
+    WOI_CUDA(put(o_desc, &desc, sizeof(desc)));
+    // the previous call's queue head is still in the array: restart it at zero
+    WOI_CUDA(cudaMemsetAsync(base + o_queue, 0, sizeof(unsigned long long), s));
+
+    int per_sm = 0;
+    WOI_CUDA(mixed_occupancy(d, vr, star, block, &per_sm));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, units);
+    MixedParams mp{};
+    mp.inst = (const InstDesc *)(base + o_desc);
+    mp.n_inst = 1;
+    mp.total_units = units;
+    mp.queue = (unsigned long long *)(base + o_queue);
+    mp.partials = (double *)(base + o_part);   // every unit's row is written before it is read
+    mp.walks_per_lane = L;
+    mp.seed = seed;
+    WOI_CUDA(launch_mixed(d, vr, star, mp, (int)grid, block, s));
+    FinalizeParams fp{};
+    fp.dim = d;
+    fp.n_pts = n_pts;
+    fp.n_walks = n_walks;
+    fp.sched_group = o->sched_group;
+    fp.unit_begin = 0;
+    fp.chunks_per_point = chunks;
+    fp.partials = (const double *)(base + o_part);
+    fp.u = u;
+    fp.grad = grad;
+    fp.se_u = se_u;
+    fp.se_grad = se_grad;
+    fp.moments = nullptr;
+    WOI_CUDA(launch_finalize(fp, false, s));
+    return WOI_OK;
+}

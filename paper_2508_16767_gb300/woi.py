@@ -29,7 +29,7 @@ STATUS = {0: "WOI_OK", 1: "WOI_E_INVALID_ARG", 2: "WOI_E_GEOMETRY", 3: "WOI_E_CO
           5: "WOI_E_NO_DEVICE", 6: "WOI_E_CUDA", 7: "WOI_E_OOM", 8: "WOI_E_TIMEOUT", 9: "WOI_E_STATE"}
 EXPORTED = ["woi_default_opts", "woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate",
             "woi_estimate_range", "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
-
+            "woi_estimate_noalloc",
             "woi_destroy_geometry", "woi_last_error", "woi_version"]
 
 
@@ -76,12 +76,14 @@ def _load():
     lib.woi_estimate_batch.argtypes = [ctypes.c_int, P(vp), P(Opts), P(ctypes.c_int), P(dp), P(i64), P(i64), u64,
                                        P(dp), P(dp), P(dp), P(dp)]
     lib.woi_last_kernel_ms.argtypes = [vp, P(ctypes.c_float)]
+    lib.woi_estimate_noalloc.argtypes = [vp, P(Opts), dp, i64, i64, u64, dp, dp, dp, dp]
     lib.woi_destroy_geometry.argtypes = [vp]
     lib.woi_destroy_geometry.restype = None
     lib.woi_last_error.restype = ctypes.c_char_p
     lib.woi_version.restype = ctypes.c_char_p
     for name in ["woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate", "woi_estimate_range",
-                 "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms"]:
+                 "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
+                 "woi_estimate_noalloc"]:
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -305,3 +307,18 @@ def finalize_moments(mom, n_walks, sched_group=1):
     se = np.sqrt(var / G)
     return {"u": mean[:, 0], "grad": mean[:, 1:], "se_u": se[:, 0], "se_grad": se[:, 1:]}
 
+
+def woi_estimate_noalloc(geom: Geometry, points, n_walks, seed=0, out=None, stream=None, **opt):
+    """The allocation-free estimate: points and outputs must be CUDA tensors
+    (outputs are allocated here by torch when `out` is None -- callers that may
+    not allocate pass their own).  Scratch comes from the library's fixed
+    device array; see include/woi.h."""
+    points = _as_input(points)
+    P = int(points.shape[0])
+    if out is None:
+        out = (_alloc_like(points, (P,)), _alloc_like(points, (P, geom.dim)), _alloc_like(points, (P,)),
+               _alloc_like(points, (P, geom.dim)))
+    o = make_opts(M=opt.pop("M", geom.problem.get("M", 4)), stream=_stream_of([points, *out], stream), **opt)
+    _check(lib.woi_estimate_noalloc(geom.handle, ctypes.byref(o), _ptr(points), P, int(n_walks), int(seed),
+                                    *[_ptr(a) for a in out]))
+    return {"u": out[0], "grad": out[1], "se_u": out[2], "se_grad": out[3]}
