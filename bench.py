@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--walks-per-lane", type=int, default=0)
     ap.add_argument("--sched-group", type=int, default=1)
+    ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -211,6 +212,8 @@ def main():
 
     cfg = WORKLOADS[args.workload]
     problem, points = make_workload(args.workload)
+    if args.points:
+        points = np.ascontiguousarray(points[:args.points])
     P, d, Wk, M = len(points), problem["dim"], cfg["walks"], cfg["M"]
     geom = woi.Geometry(problem)
     stream = torch.cuda.Stream()
