@@ -586,36 +586,16 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
     return 0;
 }
 
-// ---------------------------------------------------------------------------
-// evaluation point: (hi, lo) split
-// ---------------------------------------------------------------------------
+// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D], with y = c_s + v and
+// xc[s] = x - c_s formed in FP64 once per evaluation point (no cancellation near a surface)
 template <typename Real, int D>
-struct XPoint {
-    Real hi[D], lo[D];
-};
-
-template <typename Real, int D>
-__device__ __forceinline__ XPoint<Real, D> make_point(const double *x)
-{
-    XPoint<Real, D> p;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        p.hi[k] = (Real)x[k];
-        p.lo[k] = (Real)(x[k] - (double)p.hi[k]);
-    }
-    return p;
-}
-
-// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D], with y = c_s + v
-template <typename Real, int D>
-__device__ __forceinline__ void tally(const SGeom<Real> &g, const XPoint<Real, D> &x, int s, const Real *v, Real c,
-                                      Real *acc)
+__device__ __forceinline__ void tally(const Real (*xc)[kMaxDim], int s, const Real *v, Real c, Real *acc)
 {
     using O = RealOps<Real>;
     Real dx[D], r2 = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        dx[k] = ((x.hi[k] - g.c_hi[s][k]) + (x.lo[k] - g.c_lo[s][k])) - v[k];
+        dx[k] = xc[s][k] - v[k];
         r2 += dx[k] * dx[k];
     }
     if (r2 <= (Real)0) return;  // x on a walk state exactly: measure zero, contributes nothing
@@ -637,6 +617,16 @@ __device__ __forceinline__ void tally(const SGeom<Real> &g, const XPoint<Real, D
         const Real gc = c * (Real)(-1.0 / omega) * inv_pow * inv_r * inv_r;
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[1 + k] += gc * dx[k];
+    }
+}
+
+// x - c_s for every surface of the staged instance (all threads of the block)
+template <typename Real>
+__device__ __forceinline__ void fill_xc(Real (*xc)[kMaxDim], const DevGeom *gd, int n, int dim, const double *x)
+{
+    for (int i = threadIdx.x; i < n * dim; i += blockDim.x) {
+        const int s = i / dim, k = i - s * dim;
+        xc[s][k] = (Real)(x[k] - gd->center[s][k]);
     }
 }
 
@@ -855,7 +845,7 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
 // over the two chains for VR
 // ---------------------------------------------------------------------------
 template <typename Real, int D, bool VR, bool STAR, bool TRACE = false>
-__device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const XPoint<Real, D> &x, const Rng &rng,
+__device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[kMaxDim], const Rng &rng,
                      int sched_group, uint64_t group, Real *f, double *trace = nullptr)
 {
 #pragma unroll
@@ -887,7 +877,7 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const XPoint<Real,
             } else if (ch[k].alive) {
                 chain_step<Real, D, STAR>(g, h, rel, w, ch[k]);
             }
-            if (ch[k].alive) tally<Real, D>(g, x, ch[k].s, ch[k].v, g.coef[i] * S * ch[k].Q * ch[k].T, f);
+            if (ch[k].alive) tally<Real, D>(xc, ch[k].s, ch[k].v, g.coef[i] * S * ch[k].Q * ch[k].T, f);
             if constexpr (TRACE) {
                 if (trace) {
                     double *t = trace + ((size_t)k * (g.M + 1) + i) * (D + 2);

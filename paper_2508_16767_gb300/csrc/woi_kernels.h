@@ -11,6 +11,7 @@
 namespace woi {
 
 constexpr int kMixedMaxBlock = 256;
+constexpr int kMixedMinBlocks = 3;    // resident blocks per SM the walk kernel is compiled for
 
 struct MixedParams {
     const InstDesc *inst;              // device [n_inst], sorted by unit_begin

@@ -35,6 +35,20 @@ __device__ __forceinline__ float warp_sum_all(float v)
     return v;
 }
 
+// warp sum of (hi, lo) FP32 pairs with error-free additions (Knuth's TwoSum): the
+// result in lane 0 keeps about twice the FP32 precision; no FP64 instruction
+__device__ __forceinline__ void warp_sum_pair(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(0xFFFFFFFFu, hi, o), bl = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+        const float s = hi + bh, bb = s - hi;
+        const float e = (hi - (s - bb)) + (bh - bb);
+        hi = s;
+        lo = lo + bl + e;
+    }
+}
+
 // Neumaier (compensated) FP32 accumulation
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 {
@@ -57,9 +71,10 @@ __device__ __forceinline__ int find_instance(const InstDesc *inst, int n_inst, i
 // persistent mixed-precision walk kernel
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
-__global__ void __launch_bounds__(256) k_walk_mixed(MixedParams p)
+__global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams p)
 {
     __shared__ SGeom<float> g;
+    __shared__ float xc[kMaxSurf][kMaxDim];
     __shared__ double red[kMixedMaxBlock / 32][2 * (D + 1)];
     __shared__ long long unit_sh;
     __shared__ int inst_sh;
@@ -86,7 +101,8 @@ __global__ void __launch_bounds__(256) k_walk_mixed(MixedParams p)
         const int64_t local = unit - id.unit_begin;
         const int64_t point = local / id.chunks_per_point;
         const int64_t chunk = local - point * id.chunks_per_point;
-        const XPoint<float, D> x = make_point<float, D>(id.points + point * D);
+        fill_xc<float>(xc, id.geom, g.n, D, id.points + point * D);
+        __syncthreads();
         Rng rng;
         rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
         rng.k1 = (uint32_t)(p.seed >> 32) ^ id.instance_id;
@@ -103,7 +119,7 @@ __global__ void __launch_bounds__(256) k_walk_mixed(MixedParams p)
             if (valid) {
                 rng.w0 = (uint32_t)w;
                 rng.w1 = (uint32_t)((uint64_t)w >> 32);
-                walk<float, D, VR, STAR>(g, id.geom, x, rng, id.sched_group, (uint64_t)w / 32u, f);
+                walk<float, D, VR, STAR>(g, id.geom, xc, rng, id.sched_group, (uint64_t)w / 32u, f);
             } else {
 #pragma unroll
                 for (int c = 0; c <= D; ++c) f[c] = 0.f;
@@ -123,14 +139,15 @@ __global__ void __launch_bounds__(256) k_walk_mixed(MixedParams p)
                 }
             }
         }
-        // CTA reduction in FP64, fixed order
+        // warp sums as FP32 (hi, lo) pairs, FP64 only in lane 0; CTA sum in FP64, fixed order
 #pragma unroll
         for (int c = 0; c <= D; ++c) {
-            const double v1 = warp_sum((double)s1[c] + (double)c1[c]);
-            const double v2 = warp_sum((double)s2[c]);
+            float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
+            warp_sum_pair(h1, l1);
+            warp_sum_pair(h2, l2);
             if (lane == 0) {
-                red[warp][c] = v1;
-                red[warp][D + 1 + c] = v2;
+                red[warp][c] = (double)h1 + (double)l1;
+                red[warp][D + 1 + c] = (double)h2 + (double)l2;
             }
         }
         __syncthreads();
@@ -150,13 +167,14 @@ template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(256) k_walk_fp64_point(Fp64PointParams p)
 {
     __shared__ SGeom<double> g;
+    __shared__ double xc[kMaxSurf][kMaxDim];
     __shared__ double red[8][2 * (D + 1)];
     load_geometry(g, p.geom);
+    fill_xc<double>(xc, p.geom, p.geom->n, D, p.x);
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t w = p.walk_begin + (int64_t)blockIdx.x * blockDim.x + tid;
     const bool valid = w < p.walk_begin + p.n_walks;
-    const XPoint<double, D> x = make_point<double, D>(p.x);
     double f[D + 1];
     if (valid) {
         Rng rng;
@@ -164,7 +182,7 @@ __global__ void __launch_bounds__(256) k_walk_fp64_point(Fp64PointParams p)
         rng.k1 = (uint32_t)(p.seed >> 32) ^ p.instance_id;
         rng.w0 = (uint32_t)w;
         rng.w1 = (uint32_t)((uint64_t)w >> 32);
-        walk<double, D, VR, STAR>(g, p.geom, x, rng, p.sched_group, (uint64_t)w / 32u, f);
+        walk<double, D, VR, STAR>(g, p.geom, xc, rng, p.sched_group, (uint64_t)w / 32u, f);
     } else {
 #pragma unroll
         for (int c = 0; c <= D; ++c) f[c] = 0.0;
@@ -199,19 +217,20 @@ template <typename Real, int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
 {
     __shared__ SGeom<Real> g;
+    __shared__ Real xc[kMaxSurf][kMaxDim];
     load_geometry(g, p.geom);
+    fill_xc<Real>(xc, p.geom, p.geom->n, D, p.x);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n) return;
     const uint64_t w = p.walks[i];
-    const XPoint<Real, D> x = make_point<Real, D>(p.x);
     Rng rng;
     rng.k0 = (uint32_t)p.seed ^ p.point_id;
     rng.k1 = (uint32_t)(p.seed >> 32) ^ p.instance_id;
     rng.w0 = (uint32_t)w;
     rng.w1 = (uint32_t)(w >> 32);
     Real f[D + 1];
-    walk<Real, D, VR, STAR, true>(g, p.geom, x, rng, p.sched_group, w / 32u, f,
+    walk<Real, D, VR, STAR, true>(g, p.geom, xc, rng, p.sched_group, w / 32u, f,
                                   p.trace ? p.trace + (size_t)i * (VR ? 2 : 1) * (g.M + 1) * (D + 2) : nullptr);
     p.f_u[i] = (double)f[0];
 #pragma unroll
