@@ -169,12 +169,13 @@ WOI_API woi_status woi_estimate_range(woi_geometry *geometry, const woi_opts *op
 
 /*
  * Per-walk values for pathwise replay: for one point x[dim] (host) with
- * stream id point_id, the walks walk_ids[n] (host) give f_u[n] and
+ * stream ids point_id and instance_id (the instance index of a batch, 0 otherwise), the walks walk_ids[n] (host) give f_u[n] and
  * f_grad[n][dim] (host), each the full walk tally N sum_i c_i Phi(x, y_i)
  * (resp. grad_x Phi), in the precision opts->precision selects.
  */
 WOI_API woi_status woi_walk_values(woi_geometry *geometry, const woi_opts *opts, const double *x, uint32_t point_id,
-                           const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad);
+                                   uint32_t instance_id, const uint64_t *walk_ids, int64_t n, uint64_t seed,
+                                   double *f_u, double *f_grad);
 
 /*
  * woi_walk_values plus the states of each walk: trace[n][chains][M+1][dim+2]
@@ -183,8 +184,8 @@ WOI_API woi_status woi_walk_values(woi_geometry *geometry, const woi_opts *opts,
  * else 1.  A chain that ended keeps its last state.
  */
 WOI_API woi_status woi_walk_trace(woi_geometry *geometry, const woi_opts *opts, const double *x, uint32_t point_id,
-                                  const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad,
-                                  double *trace);
+                                  uint32_t instance_id, const uint64_t *walk_ids, int64_t n, uint64_t seed,
+                                  double *f_u, double *f_grad, double *trace);
 
 /*
  * Batched heterogeneous estimate: n_inst geometries (each with data set),
@@ -194,6 +195,12 @@ WOI_API woi_status woi_walk_trace(woi_geometry *geometry, const woi_opts *opts, 
  * instance as for woi_estimate (u[k], grad[k], se_u[k], se_grad[k], each may
  * be NULL).  Random streams use instance id k.  opts applies to all instances
  * except M, which comes from m_per_inst[k] when m_per_inst is not NULL.
+ * Instances are grouped by (dimension, star surface): one persistent launch per
+ * group, then one finalize; the sequence is captured as a CUDA graph and
+ * replayed while the same batch (handles, sizes, pointers, seed, options) is
+ * run again.  With WOI_FP64_PLAIN the instances run one after another, one
+ * launch per point (the FP64 baseline).  The call returns when the results are
+ * written; batch calls share one library scratch area and must not overlap.
  */
 WOI_API woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geometries, const woi_opts *opts, const int *m_per_inst,
                               const double *const *points, const int64_t *n_pts, const int64_t *n_walks,
@@ -238,6 +245,20 @@ WOI_API woi_status woi_last_kernel_ms(woi_geometry *geometry, float *ms);
 WOI_API woi_status woi_estimate_noalloc(woi_geometry *geometry, const woi_opts *opts, const double *points,
                                         int64_t n_pts, int64_t n_walks, uint64_t seed, double *u, double *grad,
                                         double *se_u, double *se_grad);
+
+/*
+ * Autotuner of the FP32 walk kernel's launch shape.  Times the persistent
+ * kernel on a probe of the given workload (the first few waves of work units)
+ * for block sizes {128, 256} x walks per lane {4, 8, 16, 32}, and keeps the
+ * fastest pair for this (dimension, star surface, variant, schedule group, M)
+ * in a process-wide table that later calls with block_size = walks_per_lane = 0
+ * use.  If the environment variable WOI_TUNE_CACHE names a file, the table is
+ * read from it at the first call and written back after each tuning.  points
+ * as for woi_estimate; *block_size / *walks_per_lane receive the choice (may be
+ * NULL).  Synchronous.
+ */
+WOI_API woi_status woi_autotune(woi_geometry *geometry, const woi_opts *opts, const double *points, int64_t n_pts,
+                                int64_t n_walks, uint64_t seed, int *block_size, int *walks_per_lane);
 
 /* Release a geometry and its device buffers. NULL is accepted. */
 WOI_API void woi_destroy_geometry(woi_geometry *geometry);

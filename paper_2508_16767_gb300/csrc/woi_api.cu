@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <vector>
@@ -122,6 +123,7 @@ struct woi_geometry {
     std::vector<double> star_panel_s;          // kNodes + 1
     std::vector<double> star_scan;             // kNodes * 2
     double star_lmax = 0.0;
+    double star_rmin = 0.0, star_rmax = 0.0;
 
     bool data_ready = false;
     std::vector<double> sigma, alpha, beta_scale, flux_coef;
@@ -407,9 +409,22 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
             g->star_scan[2 * j] = r * std::cos(t);
             g->star_scan[2 * j + 1] = r * std::sin(t);
         }
-        double lm = 0.0;
-        for (int j = 0; j < 16384; ++j) lm = std::max(lm, g->star.speed(2.0 * kPi * j / 16384));
+        double lm = 0.0, rmin = 1e300, rmax = 0.0, b2 = 0.0;
+        for (int k = 1; k <= g->star.K; ++k) b2 += (double)k * k * (std::fabs(g->star.a[k]) + std::fabs(g->star.b[k]));
+        b2 *= g->star.R;                                   // bound on |r''|
+        const int ms = 16384;
+        for (int j = 0; j < ms; ++j) {
+            const double t = 2.0 * kPi * j / ms;
+            double r, dr;
+            g->star.eval(t, &r, &dr);
+            lm = std::max(lm, std::sqrt(r * r + dr * dr));
+            rmin = std::min(rmin, r);
+            rmax = std::max(rmax, r);
+        }
+        const double h = 2.0 * kPi / ms, margin = b2 * h * h / 8.0 + 1e-9 * g->star.R;
         g->star_lmax = lm * 1.02 + 1e-12;
+        g->star_rmin = std::max(0.0, rmin - margin);
+        g->star_rmax = rmax + margin;
     }
     *out = g;
     return WOI_OK;
@@ -609,6 +624,63 @@ void woi_destroy_geometry(woi_geometry *g) { delete g; }
 // ---------------------------------------------------------------------------
 namespace {
 
+// ---------------------------------------------------------------------------
+// autotuned launch shapes: (dim, star, variant, sched_group, M) -> (block, walks per lane)
+// ---------------------------------------------------------------------------
+std::map<uint64_t, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+uint64_t tune_key(int dim, bool star, int variant, int sched_group, int M)
+{
+    return ((uint64_t)dim << 40) | ((uint64_t)star << 32) | ((uint64_t)variant << 24) | ((uint64_t)sched_group << 8) |
+           (uint64_t)M;
+}
+
+void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("WOI_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    unsigned long long k;
+    int b, l;
+    // one entry per line: {"key": K, "block": B, "walks_per_lane": L}
+    while (std::fscanf(f, " {\"key\": %llu, \"block\": %d, \"walks_per_lane\": %d}", &k, &b, &l) == 3)
+        g_tune[(uint64_t)k] = {b, l};
+    std::fclose(f);
+}
+
+void tune_save()
+{
+    const char *path = std::getenv("WOI_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : g_tune)
+        std::fprintf(f, "{\"key\": %llu, \"block\": %d, \"walks_per_lane\": %d}\n", (unsigned long long)kv.first,
+                     kv.second.first, kv.second.second);
+    std::fclose(f);
+}
+
+// launch shape of the FP32 walk kernel: explicit options, else the tuned table, else 256 x 8
+void launch_shape(const woi_opts *o, int dim, bool star, int *block, int *L)
+{
+    *block = o->block_size;
+    *L = o->walks_per_lane;
+    if (*block == 0 && *L == 0) {
+        tune_load();
+        auto it = g_tune.find(tune_key(dim, star, o->variant, o->sched_group, o->M));
+        if (it != g_tune.end()) {
+            *block = it->second.first;
+            *L = it->second.second;
+        }
+    }
+    if (*block == 0) *block = 256;
+    if (*L == 0) *L = 8;
+}
+
 woi_status ensure_device(woi_geometry *g)
 {
     int count = 0;
@@ -664,6 +736,8 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
     b.star_idx = g->star_idx;
     b.star_K = g->star_idx >= 0 ? g->star.K : 0;
     b.star_lmax = g->star_lmax;
+    b.star_rmin = g->star_rmin;
+    b.star_rmax = g->star_rmax;
     for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g->n ? (uint32_t)(g->thresh[i] - 1) : 0xFFFFFFFFu;
     for (int i = 0; i < g->n; ++i) {
         for (int k = 0; k < g->dim; ++k) b.center[i][k] = g->surf[i].center[k];
@@ -779,7 +853,7 @@ struct OutBuf {
 
 woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points, int64_t n_pts, int64_t walk_begin,
                         int64_t n_walks, uint64_t seed, double *u, double *grad, double *se_u, double *se_grad,
-                        double *moments)
+                        double *moments, uint32_t instance_id = 0)
 {
     woi_status st;
     if ((st = check_opts(g, o, n_pts, walk_begin, n_walks)) != WOI_OK) return st;
@@ -791,8 +865,8 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
     const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0, fp64 = o->precision == WOI_FP64_PLAIN;
     if ((st = stage_geometry(g, o->M, s)) != WOI_OK) return st;
 
-    const int block = o->block_size ? o->block_size : 256;
-    const int L = o->walks_per_lane ? o->walks_per_lane : 8;
+    int block, L;
+    launch_shape(o, d, star, &block, &L);
     const int64_t unit_walks = (int64_t)block * L;
     const int64_t chunks = fp64 ? 1 : (n_walks + unit_walks - 1) / unit_walks;
     const int64_t units = n_pts * chunks;
@@ -848,7 +922,7 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
         desc.walk_begin = walk_begin;
         desc.unit_begin = 0;
         desc.chunks_per_point = chunks;
-        desc.instance_id = 0;
+        desc.instance_id = instance_id;
         desc.sched_group = o->sched_group;
         WOI_CUDA(cudaMemcpyAsync(base + o_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, s));
         WOI_CUDA(cudaMemsetAsync(base + o_queue, 0, sizeof(unsigned long long), s));
@@ -885,7 +959,7 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
             pp.geom = g->d_blob;
             pp.x = d_points + p * d;
             pp.point_id = (uint32_t)p;
-            pp.instance_id = 0;
+            pp.instance_id = instance_id;
             pp.walk_begin = walk_begin;
             pp.n_walks = n_walks;
             pp.sched_group = o->sched_group;
@@ -904,6 +978,259 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
         }
     }
     if (any_host || !pointer_on_device(points)) WOI_CUDA(cudaStreamSynchronize(s));
+    return WOI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched estimate: one persistent launch per (dimension, star) group over the
+// (instance, point, chunk) units of all its instances, a batched finalize, and
+// the launch sequence kept as a CUDA graph that is replayed for a repeated batch
+// ---------------------------------------------------------------------------
+struct BatchState {
+    int device = -1;
+    void *scratch = nullptr;
+    size_t bytes = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> key;                 // signature of the captured batch
+};
+BatchState g_batch;
+
+woi_status batch_scratch(size_t bytes)
+{
+    int dev = 0;
+    WOI_CUDA(cudaGetDevice(&dev));
+    if (g_batch.device != dev) {
+        if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+        g_batch = BatchState{};
+        g_batch.device = dev;
+    }
+    if (g_batch.bytes >= bytes) return WOI_OK;
+    cudaFree(g_batch.scratch);
+    g_batch.scratch = nullptr;
+    g_batch.bytes = 0;
+    if (g_batch.exec) {
+        cudaGraphExecDestroy(g_batch.exec);
+        g_batch.exec = nullptr;
+        g_batch.key.clear();
+    }
+    const size_t want = std::max(bytes, (size_t)1 << 22);
+    if (cudaMalloc(&g_batch.scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WOI_E_OOM, "batch scratch allocation of %zu bytes failed", want);
+    }
+    g_batch.bytes = want;
+    return WOI_OK;
+}
+
+woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, const int *m_per_inst,
+                     const double *const *points, const int64_t *n_pts, const int64_t *n_walks, uint64_t seed,
+                     double *const *u, double *const *grad, double *const *se_u, double *const *se_grad)
+{
+    if (n_inst < 1 || !geoms || !o || !points || !n_pts || !n_walks) return fail(WOI_E_INVALID_ARG, "null argument");
+    woi_status st;
+    // validation with each instance's truncation
+    std::vector<woi_opts> oi(n_inst, *o);
+    for (int k = 0; k < n_inst; ++k) {
+        if (!geoms[k]) return fail(WOI_E_INVALID_ARG, "null geometry %d", k);
+        if (m_per_inst) oi[k].M = m_per_inst[k];
+        if ((st = check_opts(geoms[k], &oi[k], n_pts[k], 0, n_walks[k])) != WOI_OK) return st;
+        if (n_pts[k] > 0 && !points[k]) return fail(WOI_E_INVALID_ARG, "null points of instance %d", k);
+    }
+    if (o->precision == WOI_FP64_PLAIN) {
+        // the FP64 baseline: instance by instance, one launch per point
+        for (int k = 0; k < n_inst; ++k)
+            if ((st = run_estimate(geoms[k], &oi[k], points[k], n_pts[k], 0, n_walks[k], seed, u ? u[k] : nullptr,
+                                   grad ? grad[k] : nullptr, se_u ? se_u[k] : nullptr, se_grad ? se_grad[k] : nullptr,
+                                   nullptr, (uint32_t)k)) != WOI_OK)
+                return st;
+        return WOI_OK;
+    }
+    for (int k = 0; k < n_inst; ++k)
+        if ((st = ensure_device(geoms[k])) != WOI_OK) return st;
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    if (!s) {
+        if (!g_batch.own_stream) WOI_CUDA(cudaStreamCreateWithFlags(&g_batch.own_stream, cudaStreamNonBlocking));
+        s = g_batch.own_stream;
+    }
+    for (int k = 0; k < n_inst; ++k)
+        if ((st = stage_geometry(geoms[k], oi[k].M, s)) != WOI_OK) return st;
+    const bool vr = o->variant == WOI_VR;
+    const int block = o->block_size ? o->block_size : 256;
+    const int L = o->walks_per_lane ? o->walks_per_lane : 8;
+    const int64_t unit_walks = (int64_t)block * L;
+
+    // groups of instances that share a kernel: (dimension, star)
+    std::map<int, std::vector<int>> groups;
+    for (int k = 0; k < n_inst; ++k)
+        if (n_pts[k] > 0) groups[geoms[k]->dim * 2 + (geoms[k]->star_idx >= 0)].push_back(k);
+
+    // scratch layout: per group [InstDesc x n][queue][partials]; then staged points and outputs
+    struct Group {
+        int dim;
+        bool star;
+        std::vector<int> members;
+        std::vector<InstDesc> desc;
+        size_t o_desc, o_queue, o_part;
+        int64_t units, points;
+    };
+    std::vector<Group> gs;
+    size_t off = 0;
+    for (auto &kv : groups) {
+        Group gr;
+        gr.dim = kv.first / 2;
+        gr.star = kv.first % 2;
+        gr.members = kv.second;
+        gr.units = gr.points = 0;
+        for (int k : gr.members) {
+            const int64_t chunks = (n_walks[k] + unit_walks - 1) / unit_walks;
+            InstDesc d{};
+            d.geom = geoms[k]->d_blob;
+            d.n_pts = n_pts[k];
+            d.n_walks = n_walks[k];
+            d.walk_begin = 0;
+            d.unit_begin = gr.units;
+            d.chunks_per_point = chunks;
+            d.instance_id = (uint32_t)k;
+            d.sched_group = o->sched_group;
+            d.point_begin = gr.points;
+            gr.units += n_pts[k] * chunks;
+            gr.points += n_pts[k];
+            gr.desc.push_back(d);
+        }
+        gr.o_desc = off; off = align_up(off + gr.desc.size() * sizeof(InstDesc), 256);
+        gr.o_queue = off; off = align_up(off + sizeof(unsigned long long), 256);
+        gr.o_part = off; off = align_up(off + (size_t)gr.units * 2 * (gr.dim + 1) * sizeof(double), 256);
+        gs.push_back(std::move(gr));
+    }
+    // staged host inputs / outputs
+    std::vector<size_t> o_pts(n_inst, 0), o_out(4 * (size_t)n_inst, 0);
+    std::vector<char> pts_host(n_inst, 0), out_host(4 * (size_t)n_inst, 0);
+    double *const *outs[4] = {u, grad, se_u, se_grad};
+    for (int k = 0; k < n_inst; ++k) {
+        const int d = geoms[k]->dim;
+        if (n_pts[k] > 0 && !pointer_on_device(points[k])) {
+            pts_host[k] = 1;
+            o_pts[k] = off;
+            off = align_up(off + (size_t)n_pts[k] * d * sizeof(double), 256);
+        }
+        const size_t cnt[4] = {(size_t)n_pts[k], (size_t)n_pts[k] * d, (size_t)n_pts[k], (size_t)n_pts[k] * d};
+        for (int j = 0; j < 4; ++j) {
+            double *p = outs[j] ? outs[j][k] : nullptr;
+            if (p && !pointer_on_device(p)) {
+                out_host[4 * k + j] = 1;
+                o_out[4 * k + j] = off;
+                off = align_up(off + cnt[j] * sizeof(double), 256);
+            }
+        }
+    }
+    if ((st = batch_scratch(off)) != WOI_OK) return st;
+    char *base = (char *)g_batch.scratch;
+    for (int k = 0; k < n_inst; ++k) {
+        if (!pts_host[k]) continue;
+        for (int64_t q = 0; q < n_pts[k]; ++q)
+            if (!inside_surface(*geoms[k], 0, points[k] + q * geoms[k]->dim))
+                return fail(WOI_E_GEOMETRY, "instance %d: point %lld lies outside the outer surface", k, (long long)q);
+        WOI_CUDA(cudaMemcpyAsync(base + o_pts[k], points[k], (size_t)n_pts[k] * geoms[k]->dim * sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    // descriptors (host copies are staged before cudaMemcpyAsync returns)
+    std::vector<uint64_t> key{(uint64_t)n_inst, seed, (uint64_t)o->variant, (uint64_t)o->sched_group, (uint64_t)block,
+                              (uint64_t)L, (uint64_t)(uintptr_t)base};
+    for (auto &gr : gs) {
+        for (size_t i = 0; i < gr.members.size(); ++i) {
+            const int k = gr.members[i];
+            InstDesc &d = gr.desc[i];
+            d.points = pts_host[k] ? (const double *)(base + o_pts[k]) : points[k];
+            double *dv[4];
+            for (int j = 0; j < 4; ++j) {
+                double *p = outs[j] ? outs[j][k] : nullptr;
+                dv[j] = !p ? nullptr : (out_host[4 * k + j] ? (double *)(base + o_out[4 * k + j]) : p);
+            }
+            d.u = dv[0];
+            d.grad = dv[1];
+            d.se_u = dv[2];
+            d.se_grad = dv[3];
+            key.insert(key.end(), {(uint64_t)(uintptr_t)d.geom, (uint64_t)(uintptr_t)d.points, (uint64_t)d.n_pts,
+                                   (uint64_t)d.n_walks, (uint64_t)oi[k].M, (uint64_t)(uintptr_t)dv[0],
+                                   (uint64_t)(uintptr_t)dv[1], (uint64_t)(uintptr_t)dv[2], (uint64_t)(uintptr_t)dv[3]});
+        }
+        WOI_CUDA(cudaMemcpyAsync(base + gr.o_desc, gr.desc.data(), gr.desc.size() * sizeof(InstDesc),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    // the launch sequence, captured once per batch signature and replayed
+    if (!(g_batch.exec && g_batch.key == key)) {
+        if (g_batch.exec) {
+            cudaGraphExecDestroy(g_batch.exec);
+            g_batch.exec = nullptr;
+        }
+        std::vector<int> grid(gs.size());
+        int num_sms = geoms[0]->num_sms;
+        for (size_t i = 0; i < gs.size(); ++i) {
+            int per_sm = 0;
+            WOI_CUDA(mixed_occupancy(gs[i].dim, vr, gs[i].star, block, &per_sm));
+            grid[i] = (int)std::min<int64_t>((int64_t)num_sms * std::max(per_sm, 1), gs[i].units);
+        }
+        cudaGraph_t graph = nullptr;
+        WOI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        for (size_t i = 0; i < gs.size() && ce == cudaSuccess; ++i) {
+            Group &gr = gs[i];
+            ce = cudaMemsetAsync(base + gr.o_queue, 0, sizeof(unsigned long long), s);
+            if (ce != cudaSuccess) break;
+            MixedParams mp{};
+            mp.inst = (const InstDesc *)(base + gr.o_desc);
+            mp.n_inst = (int)gr.desc.size();
+            mp.total_units = gr.units;
+            mp.queue = (unsigned long long *)(base + gr.o_queue);
+            mp.partials = (double *)(base + gr.o_part);
+            mp.walks_per_lane = L;
+            mp.seed = seed;
+            ce = launch_mixed(gr.dim, vr, gr.star, mp, grid[i], block, s);
+            if (ce != cudaSuccess) break;
+            BatchFinalizeParams bp{};
+            bp.inst = (const InstDesc *)(base + gr.o_desc);
+            bp.n_inst = (int)gr.desc.size();
+            bp.dim = gr.dim;
+            bp.total_points = gr.points;
+            bp.partials = (const double *)(base + gr.o_part);
+            ce = launch_finalize_batch(bp, s);
+        }
+        cudaError_t ee = cudaStreamEndCapture(s, &graph);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(WOI_E_CUDA, "batch capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        }
+        ce = cudaGraphInstantiate(&g_batch.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            g_batch.exec = nullptr;
+            return fail(WOI_E_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(ce));
+        }
+        g_batch.key = key;
+    }
+    if (o->timing) {
+        // events of the first geometry time the whole batch launch
+        woi_geometry *g0 = geoms[0];
+        if (!g0->ev_start) {
+            WOI_CUDA(cudaEventCreate(&g0->ev_start));
+            WOI_CUDA(cudaEventCreate(&g0->ev_stop));
+        }
+        g0->timed = true;
+        WOI_CUDA(cudaEventRecord(g0->ev_start, s));
+    }
+    WOI_CUDA(cudaGraphLaunch(g_batch.exec, s));
+    if (o->timing) WOI_CUDA(cudaEventRecord(geoms[0]->ev_stop, s));
+    for (int k = 0; k < n_inst; ++k) {
+        const size_t cnt[4] = {(size_t)n_pts[k], (size_t)n_pts[k] * geoms[k]->dim, (size_t)n_pts[k],
+                               (size_t)n_pts[k] * geoms[k]->dim};
+        for (int j = 0; j < 4; ++j)
+            if (out_host[4 * k + j])
+                WOI_CUDA(cudaMemcpyAsync(outs[j][k], base + o_out[4 * k + j], cnt[j] * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+    }
+    // the batch scratch and the captured graph are shared by batch calls: finish before returning
+    WOI_CUDA(cudaStreamSynchronize(s));
     return WOI_OK;
 }
 
@@ -929,8 +1256,8 @@ woi_status woi_estimate_range(woi_geometry *g, const woi_opts *opts, const doubl
 }
 
 static woi_status walk_values_impl(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
-                                   const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad,
-                                   double *trace)
+                                   uint32_t instance_id, const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u,
+                                   double *f_grad, double *trace)
 {
     g_last_error.clear();
     if (!g || !o || !x || (n > 0 && (!walk_ids || !f_u || !f_grad))) return fail(WOI_E_INVALID_ARG, "null argument");
@@ -958,7 +1285,7 @@ static woi_status walk_values_impl(woi_geometry *g, const woi_opts *o, const dou
     p.geom = g->d_blob;
     p.x = (const double *)(base + o_x);
     p.point_id = point_id;
-    p.instance_id = 0;
+    p.instance_id = instance_id;
     p.walks = (const uint64_t *)(base + o_w);
     p.n = n;
     p.sched_group = o->sched_group;
@@ -976,20 +1303,76 @@ static woi_status walk_values_impl(woi_geometry *g, const woi_opts *o, const dou
 }
 
 woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
-                           const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad)
+                           uint32_t instance_id, const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u,
+                           double *f_grad)
 {
-    return walk_values_impl(g, o, x, point_id, walk_ids, n, seed, f_u, f_grad, nullptr);
+    return walk_values_impl(g, o, x, point_id, instance_id, walk_ids, n, seed, f_u, f_grad, nullptr);
 }
 
 woi_status woi_walk_trace(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
-                          const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u, double *f_grad,
-                          double *trace)
+                          uint32_t instance_id, const uint64_t *walk_ids, int64_t n, uint64_t seed, double *f_u,
+                          double *f_grad, double *trace)
 {
     if (!trace) {
         g_last_error = "null trace";
         return WOI_E_INVALID_ARG;
     }
-    return walk_values_impl(g, o, x, point_id, walk_ids, n, seed, f_u, f_grad, trace);
+    return walk_values_impl(g, o, x, point_id, instance_id, walk_ids, n, seed, f_u, f_grad, trace);
+}
+
+woi_status woi_autotune(woi_geometry *g, const woi_opts *o, const double *points, int64_t n_pts, int64_t n_walks,
+                        uint64_t seed, int *block_out, int *lpl_out)
+{
+    g_last_error.clear();
+    if (!g) return fail(WOI_E_INVALID_ARG, "null geometry");
+    woi_status st;
+    if ((st = check_opts(g, o, n_pts, 0, n_walks)) != WOI_OK) return st;
+    if (o->precision != WOI_MIXED) return fail(WOI_E_UNSUPPORTED, "the autotuner tunes the FP32 walk kernel");
+    if (n_pts < 1) return fail(WOI_E_INVALID_ARG, "need at least one point");
+    if ((st = ensure_device(g)) != WOI_OK) return st;
+    tune_load();
+    const int d = g->dim;
+    const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0;
+    const int blocks[2] = {128, 256}, lanes[4] = {4, 8, 16, 32};
+    float best = 1e30f;
+    int bb = 256, bl = 8;
+    woi_opts t = *o;
+    t.timing = 1;
+    for (int bi = 0; bi < 2; ++bi)
+        for (int li = 0; li < 4; ++li) {
+            t.block_size = blocks[bi];
+            t.walks_per_lane = lanes[li];
+            // probe: enough points for about four waves of units of this shape
+            int per_sm = 1;
+            if (mixed_occupancy(d, vr, star, blocks[bi], &per_sm) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            const int64_t unit_walks = (int64_t)blocks[bi] * lanes[li];
+            const int64_t chunks = (n_walks + unit_walks - 1) / unit_walks;
+            const int64_t want_units = 4LL * g->num_sms * std::max(per_sm, 1);
+            const int64_t probe_pts = std::max<int64_t>(1, std::min<int64_t>(n_pts, (want_units + chunks - 1) / chunks));
+            // one untimed run (caches the geometry and scratch), one timed run
+            if ((st = run_estimate(g, &t, points, probe_pts, 0, n_walks, seed, nullptr, nullptr, nullptr, nullptr,
+                                   nullptr)) != WOI_OK)
+                return st;
+            if ((st = run_estimate(g, &t, points, probe_pts, 0, n_walks, seed, nullptr, nullptr, nullptr, nullptr,
+                                   nullptr)) != WOI_OK)
+                return st;
+            float ms = 0.f;
+            if ((st = woi_last_kernel_ms(g, &ms)) != WOI_OK) return st;
+            const float per_walk = ms / (float)(probe_pts * n_walks);
+            if (per_walk < best) {
+                best = per_walk;
+                bb = blocks[bi];
+                bl = lanes[li];
+            }
+        }
+    g_tune[tune_key(d, star, o->variant, o->sched_group, o->M)] = {bb, bl};
+    tune_save();
+    if (block_out) *block_out = bb;
+    if (lpl_out) *lpl_out = bl;
+    return WOI_OK;
 }
 
 woi_status woi_last_kernel_ms(woi_geometry *g, float *ms)
@@ -1007,7 +1390,7 @@ woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geoms, const woi_
                               double *const *u, double *const *grad, double *const *se_u, double *const *se_grad)
 {
     g_last_error.clear();
-    return fail(WOI_E_UNSUPPORTED, "woi_estimate_batch is not available in this build yet");
+    return run_batch(n_inst, geoms, o, m_per_inst, points, n_pts, n_walks, seed, u, grad, se_u, se_grad);
 }
 
 }  // extern "C"
@@ -1120,6 +1503,8 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     b.star_idx = g->star_idx;
     b.star_K = star ? g->star.K : 0;
     b.star_lmax = g->star_lmax;
+    b.star_rmin = g->star_rmin;
+    b.star_rmax = g->star_rmax;
     for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g->n ? (uint32_t)(g->thresh[i] - 1) : 0xFFFFFFFFu;
     for (int i = 0; i < g->n; ++i) {
         for (int k = 0; k < d; ++k) b.center[i][k] = g->surf[i].center[k];

@@ -85,6 +85,7 @@ template <> struct RealOps<float> {
     __device__ static __forceinline__ void sincos_(float t, float *s, float *c) { sincosf(t, s, c); }
     __device__ static __forceinline__ float fabs_(float v) { return fabsf(v); }
     __device__ static __forceinline__ float rcp(float v) { return 1.0f / v; }
+    __device__ static __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
 };
 template <> struct RealOps<double> {
     __device__ static __forceinline__ void sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
@@ -95,6 +96,7 @@ template <> struct RealOps<double> {
     __device__ static __forceinline__ void sincos_(double t, double *s, double *c) { sincos(t, s, c); }
     __device__ static __forceinline__ double fabs_(double v) { return fabs(v); }
     __device__ static __forceinline__ double rcp(double v) { return 1.0 / v; }
+    __device__ static __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
 };
 
 // Newton step below which the iteration has converged (the last step is then taken:
@@ -178,6 +180,7 @@ struct SGeom {
     // star (at most one per instance)
     Real star_a[kMaxStar + 1], star_b[kMaxStar + 1];
     Real star_lmax;                      // bound on |gamma'|
+    Real star_rmin, star_rmax;           // annulus that contains the star
     Real scan[kNodes][2];                // gamma(t_j) - centre
     double panel_s[kNodes + 1];          // arc length at t_j
 };
@@ -193,6 +196,8 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.star_idx = src->star_idx;
         g.star_K = src->star_K;
         g.star_lmax = (Real)src->star_lmax;
+        g.star_rmin = (Real)src->star_rmin;
+        g.star_rmax = (Real)src->star_rmax;
     }
     for (int i = tid; i < kMaxSurfPad; i += nt) g.sched_tm1[i] = src->sched_tm1[i];
     for (int i = tid; i < src->n; i += nt) {
@@ -410,77 +415,134 @@ __device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa
     return t;
 }
 
+// Roots of f in the scan interval [t_j, t_j+1] (j in [0, kNodes)) appended as candidates:
+// a sign change gives one root; otherwise, where |f| may reach 0 (|f'| <= lmax) and f'
+// changes sign, the extremum decides whether a pair of roots hides in the interval.
+template <typename Real>
+__device__ __forceinline__ int star_interval_roots(const SGeom<Real> &g, int j, Real fa, Real fb, const Real *yc,
+                                                   const Real *z, Real *cand)
+{
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
+    const Real guard = g.star_lmax * H * (Real)0.5;
+    int nc = 0;
+    if ((fa < 0) != (fb < 0)) {
+        cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z);
+    } else if (RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
+        Real f1, d1, f2, d2;
+        star_line_f(g, j, (Real)0, yc, z, &f1, &d1);
+        star_line_f(g, j, H, yc, z, &f2, &d2);
+        if ((d1 < 0) != (d2 < 0)) {
+            Real lo = 0, hi = H, dlo = d1;
+            for (int it = 0; it < (sizeof(Real) == 4 ? 30 : 60); ++it) {
+                const Real m = (Real)0.5 * (lo + hi);
+                Real fm, dm;
+                star_line_f(g, j, m, yc, z, &fm, &dm);
+                if ((dm < 0) == (dlo < 0)) { lo = m; dlo = dm; } else hi = m;
+            }
+            const Real te = (Real)0.5 * (lo + hi);
+            Real fe, de;
+            star_line_f(g, j, te, yc, z, &fe, &de);
+            if ((fe < 0) != (fa < 0)) {
+                cand[nc++] = star_refine(g, j, (Real)0, te, fa, yc, z);
+                cand[nc++] = star_refine(g, j, te, H, fe, yc, z);
+            }
+        }
+    }
+    return nc;
+}
+
+// mark the scan intervals of the nodes whose angles lie between the polar angles of
+// the points yc + sa z and yc + sb z (the angle is monotone along a line that misses
+// the centre; it increases when e = yc x z > 0), padded by one node on each side
+template <typename Real>
+__device__ __forceinline__ void star_mark_window(const Real *yc, const Real *z, Real e, Real sa, Real sb,
+                                                 uint32_t *mask)
+{
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes), TWO_PI = (Real)(2.0 * 3.14159265358979323846);
+    Real pa = RealOps<Real>::atan2_(yc[1] + sa * z[1], yc[0] + sa * z[0]);
+    Real pb = RealOps<Real>::atan2_(yc[1] + sb * z[1], yc[0] + sb * z[0]);
+    if (e < 0) {  // sweep from pb to pa instead
+        const Real t = pa;
+        pa = pb;
+        pb = t;
+    }
+    if (pa < 0) pa += TWO_PI;
+    if (pb < 0) pb += TWO_PI;
+    Real span = pb - pa;
+    if (span < 0) span += TWO_PI;
+    int j0 = (int)(pa / H) - 1;
+    const int count = (int)(span / H) + 3;
+    for (int c = 0; c < count && c < kNodes; ++c) {
+        int j = j0 + c;
+        j = (j % kNodes + kNodes) % kNodes;
+        mask[j >> 5] |= 1u << (j & 31);
+    }
+}
+
 // Intersections of the line (ray = false) or ray (ray = true) yc + s z (yc
-// relative to the star centre) with the star: roots of f on a kNodes-sample
-// scan, plus root pairs hidden inside a scan interval, found from the
-// extremum of f where |f| may reach 0 (|f'| <= lmax).  For a line, the start
-// point is itself on the curve at angle (sj, sd): exactly one root, the one
-// nearest to that angle, is the start point and is dropped.  Returns q; tt[]
-// the line parameters, jj[] / dd[] the roots as (node, offset).
+// relative to the star centre) with the star.  A root is a point of the curve on
+// the line, so it lies where the line is inside the annulus rmin <= |p| <= rmax:
+// at most two windows of polar angle, scanned node by node (roots as in
+// star_interval_roots).  For a line, the start point is itself on the curve at
+// angle (sj, sd): exactly one root, the one nearest to that angle, is the start
+// point and is dropped.  Returns q; tt[] the line parameters, jj[] / dd[] the
+// roots as (node, offset).
 template <typename Real>
 __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Real *z, bool ray, int sj, Real sd,
                                   Real *tt, int *jj, Real *dd)
 {
     const Real e = yc[0] * z[1] - yc[1] * z[0];
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
-    const Real guard = g.star_lmax * H * (Real)0.5;
     const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
+    const Real ae = RealOps<Real>::fabs_(e);
+    if (ae >= g.star_rmax) return 0;
+    uint32_t mask[kNodes / 32];
+#pragma unroll
+    for (int w = 0; w < kNodes / 32; ++w) mask[w] = 0u;
+    {
+        const Real sf = -(yc[0] * z[0] + yc[1] * z[1]);          // foot of the perpendicular from the centre
+        const Real outer = RealOps<Real>::sqrt_(g.star_rmax * g.star_rmax - e * e);
+        const Real in2 = g.star_rmin * g.star_rmin - e * e;
+        const Real inner = in2 > (Real)0 ? RealOps<Real>::sqrt_(in2) : (Real)0;
+        star_mark_window(yc, z, e, sf - outer, sf - inner, mask);
+        star_mark_window(yc, z, e, sf + inner, sf + outer, mask);
+    }
     int q = 0, self = -1;
     Real self_dist = (Real)1e30;
-    const Real f0 = g.scan[0][0] * z[1] - g.scan[0][1] * z[0] - e;
-    Real fa = f0;
-    for (int j = 0; j < kNodes; ++j) {
-        const int jn = j + 1;
-        const Real fb = (jn == kNodes) ? f0 : g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
-        Real cand[2];
-        int nc = 0;
-        if ((fa < 0) != (fb < 0)) {
-            cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z);
-        } else if (RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
-            Real f1, d1, f2, d2;
-            star_line_f(g, j, (Real)0, yc, z, &f1, &d1);
-            star_line_f(g, j, H, yc, z, &f2, &d2);
-            if ((d1 < 0) != (d2 < 0)) {
-                Real lo = 0, hi = H, dlo = d1;
-                for (int it = 0; it < (sizeof(Real) == 4 ? 30 : 60); ++it) {
-                    const Real m = (Real)0.5 * (lo + hi);
-                    Real fm, dm;
-                    star_line_f(g, j, m, yc, z, &fm, &dm);
-                    if ((dm < 0) == (dlo < 0)) { lo = m; dlo = dm; } else hi = m;
-                }
-                const Real te = (Real)0.5 * (lo + hi);
-                Real fe, de;
-                star_line_f(g, j, te, yc, z, &fe, &de);
-                if ((fe < 0) != (fa < 0)) {
-                    cand[nc++] = star_refine(g, j, (Real)0, te, fa, yc, z);
-                    cand[nc++] = star_refine(g, j, te, H, fe, yc, z);
-                }
-            }
-        }
-        for (int c = 0; c < nc; ++c) {
-            Real ct, st, p[2];
-            angle_cs(g, j, cand[c], &ct, &st);
-            star_local(g, ct, st, p, (Real *)nullptr);
-            const Real s = (p[0] - yc[0]) * z[0] + (p[1] - yc[1]) * z[1];
-            const bool ok = ray ? (s > tiny) : true;
-            if (ok && q < kMaxRoots) {
-                tt[q] = s;
-                jj[q] = j;
-                dd[q] = cand[c];
-                if (!ray) {
-                    int dj = j - sj;  // cyclic angular distance to the start point
-                    if (dj > kNodes / 2) dj -= kNodes;
-                    if (dj < -kNodes / 2) dj += kNodes;
-                    const Real dist = RealOps<Real>::fabs_((Real)dj * H + (cand[c] - sd));
-                    if (dist < self_dist) {
-                        self_dist = dist;
-                        self = q;
+    for (int w = 0; w < kNodes / 32; ++w) {
+        uint32_t bits = mask[w];
+        while (bits) {
+            const int j = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int jn = (j + 1 == kNodes) ? 0 : j + 1;
+            const Real fa = g.scan[j][0] * z[1] - g.scan[j][1] * z[0] - e;
+            const Real fb = g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
+            Real cand[2];
+            const int nc = star_interval_roots(g, j, fa, fb, yc, z, cand);
+            for (int c = 0; c < nc; ++c) {
+                Real ct, st, p[2];
+                angle_cs(g, j, cand[c], &ct, &st);
+                star_local(g, ct, st, p, (Real *)nullptr);
+                const Real s = (p[0] - yc[0]) * z[0] + (p[1] - yc[1]) * z[1];
+                const bool ok = ray ? (s > tiny) : true;
+                if (ok && q < kMaxRoots) {
+                    tt[q] = s;
+                    jj[q] = j;
+                    dd[q] = cand[c];
+                    if (!ray) {
+                        int dj = j - sj;  // cyclic angular distance to the start point
+                        if (dj > kNodes / 2) dj -= kNodes;
+                        if (dj < -kNodes / 2) dj += kNodes;
+                        const Real dist = RealOps<Real>::fabs_((Real)dj * H + (cand[c] - sd));
+                        if (dist < self_dist) {
+                            self_dist = dist;
+                            self = q;
+                        }
                     }
+                    ++q;
                 }
-                ++q;
             }
         }
-        fa = fb;
     }
     if (!ray && self >= 0) {  // drop the start point
         for (int a = self; a + 1 < q; ++a) {
@@ -800,7 +862,14 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
 #pragma unroll
     for (int c = 0; c < D; ++c) b += z[c] * dy[c];
     if (rel == 0) {
-        // line through a point of the sphere: the other intersection, t = -2 b; Q *= 1/2, T *= q sign = +1
+        // line through a point of the sphere: the other intersection, t = -2 b; Q *= 1/2, T *= q sign = +1.
+        // A tangent line (|t| at rounding level) meets the sphere only at y: q = 0 ends the walk.
+        const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
+        if (RealOps<Real>::fabs_((Real)2 * b) <= tiny * R) {
+            ch.alive = false;
+            ch.T = 0;
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < D; ++c) ch.v[c] = dy[c] - (Real)2 * b * z[c];
         ch.Q *= (Real)0.5;

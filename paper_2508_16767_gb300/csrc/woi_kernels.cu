@@ -67,6 +67,48 @@ __global__ void k_finalize_acc(FinalizeParams p)
     }
 }
 
+// batched finalize: one thread per (instance point, component)
+__global__ void k_finalize_batch(BatchFinalizeParams p)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int D = p.dim, C = D + 1;
+    if (idx >= p.total_points * C) return;
+    const int64_t gp = idx / C;
+    const int c = (int)(idx - gp * C);
+    int lo = 0, hi = p.n_inst;  // last instance with point_begin <= gp
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (p.inst[m].point_begin <= gp) lo = m; else hi = m;
+    }
+    const InstDesc &id = p.inst[lo];
+    const int64_t point = gp - id.point_begin;
+    const double *src = p.partials + (id.unit_begin + point * id.chunks_per_point) * (2 * C);
+    double S1 = 0.0, S2 = 0.0;
+    for (int64_t ch = 0; ch < id.chunks_per_point; ++ch) {
+        S1 += src[ch * 2 * C + c];
+        S2 += src[ch * 2 * C + C + c];
+    }
+    const double W = (double)id.n_walks, G = W / (double)id.sched_group, mean = S1 / W;
+    double var = (S2 - G * mean * mean) / (G > 1.0 ? G - 1.0 : 1.0);
+    var = var > 0.0 ? var : 0.0;
+    const double se = sqrt(var / G);
+    if (c == 0) {
+        if (id.u) id.u[point] = mean;
+        if (id.se_u) id.se_u[point] = se;
+    } else {
+        if (id.grad) id.grad[point * D + c - 1] = mean;
+        if (id.se_grad) id.se_grad[point * D + c - 1] = se;
+    }
+}
+
+cudaError_t launch_finalize_batch(const BatchFinalizeParams &p, cudaStream_t s)
+{
+    const int64_t n = p.total_points * (p.dim + 1);
+    if (n == 0) return cudaSuccess;
+    k_finalize_batch<<<(int)((n + 255) / 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename F>
 static cudaError_t by_dim(int dim, bool star, F &&f)
 {

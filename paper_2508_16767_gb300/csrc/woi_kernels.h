@@ -76,7 +76,16 @@ extern template struct DimLaunchers<4, false>;
 extern template struct DimLaunchers<5, false>;
 extern template struct DimLaunchers<6, false>;
 
+struct BatchFinalizeParams {
+    const InstDesc *inst;              // device [n_inst], sorted by point_begin
+    int n_inst;
+    int dim;
+    int64_t total_points;
+    const double *partials;            // unit partials of all instances
+};
+
 cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, cudaStream_t s);
+cudaError_t launch_finalize_batch(const BatchFinalizeParams &p, cudaStream_t s);
 cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_per_sm);
 cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s);
 cudaError_t launch_fp64_point(int dim, bool vr, bool star, const Fp64PointParams &p, cudaStream_t s);

@@ -22,6 +22,7 @@ struct DevGeom {
     int dim, n, npad, M;
     int star_idx, star_K;              // star_idx = -1: no star in this instance
     double star_lmax;                  // bound on |gamma'| of the star
+    double star_rmin, star_rmax;       // bounds on r(t): every point of the star lies in this annulus
     uint32_t sched_tm1[kMaxSurfPad];   // T_n - 1, padded with 0xFFFFFFFF
     double center[kMaxSurf][kMaxDim];
     double radius[kMaxSurf];
@@ -59,6 +60,8 @@ struct InstDesc {
     int64_t chunks_per_point;
     uint32_t instance_id;              // random-stream instance id
     int sched_group;
+    int64_t point_begin;               // first point of this instance in a batch
+    double *u, *grad, *se_u, *se_grad; // device outputs of a batch (each may be null)
 };
 
 }  // namespace woi

@@ -29,7 +29,7 @@ STATUS = {0: "WOI_OK", 1: "WOI_E_INVALID_ARG", 2: "WOI_E_GEOMETRY", 3: "WOI_E_CO
           5: "WOI_E_NO_DEVICE", 6: "WOI_E_CUDA", 7: "WOI_E_OOM", 8: "WOI_E_TIMEOUT", 9: "WOI_E_STATE"}
 EXPORTED = ["woi_default_opts", "woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate",
             "woi_estimate_range", "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
-            "woi_estimate_noalloc",
+            "woi_estimate_noalloc", "woi_autotune",
             "woi_destroy_geometry", "woi_last_error", "woi_version"]
 
 
@@ -71,19 +71,20 @@ def _load():
     lib.woi_set_sigma_and_data.argtypes = [vp, P(ctypes.c_double), P(FluxDesc)]
     lib.woi_estimate.argtypes = [vp, P(Opts), dp, i64, i64, u64, dp, dp, dp, dp]
     lib.woi_estimate_range.argtypes = [vp, P(Opts), dp, i64, i64, i64, u64, dp]
-    lib.woi_walk_values.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, dp, i64, u64, dp, dp]
-    lib.woi_walk_trace.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, dp, i64, u64, dp, dp, dp]
-    lib.woi_estimate_batch.argtypes = [ctypes.c_int, P(vp), P(Opts), P(ctypes.c_int), P(dp), P(i64), P(i64), u64,
-                                       P(dp), P(dp), P(dp), P(dp)]
+    lib.woi_walk_values.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, ctypes.c_uint32, dp, i64, u64, dp, dp]
+    lib.woi_walk_trace.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, ctypes.c_uint32, dp, i64, u64, dp, dp, dp]
+    lib.woi_estimate_batch.argtypes = [ctypes.c_int, P(vp), P(Opts), P(ctypes.c_int), P(vp), P(i64), P(i64), u64,
+                                       P(vp), P(vp), P(vp), P(vp)]
     lib.woi_last_kernel_ms.argtypes = [vp, P(ctypes.c_float)]
     lib.woi_estimate_noalloc.argtypes = [vp, P(Opts), dp, i64, i64, u64, dp, dp, dp, dp]
+    lib.woi_autotune.argtypes = [vp, P(Opts), dp, i64, i64, u64, P(ctypes.c_int), P(ctypes.c_int)]
     lib.woi_destroy_geometry.argtypes = [vp]
     lib.woi_destroy_geometry.restype = None
     lib.woi_last_error.restype = ctypes.c_char_p
     lib.woi_version.restype = ctypes.c_char_p
     for name in ["woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate", "woi_estimate_range",
                  "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
-                 "woi_estimate_noalloc"]:
+                 "woi_estimate_noalloc", "woi_autotune"]:
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -267,7 +268,7 @@ def woi_estimate_range(geom: Geometry, points, walk_begin, n_walks, seed=0, stre
     return mom
 
 
-def woi_walk_values(geom: Geometry, x, walk_ids, seed=0, point_id=0, **opt):
+def woi_walk_values(geom: Geometry, x, walk_ids, seed=0, point_id=0, instance_id=0, **opt):
     """Per-walk tallies (host arrays) of one point for pathwise replay."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     ids = np.ascontiguousarray(walk_ids, dtype=np.uint64)
@@ -275,12 +276,12 @@ def woi_walk_values(geom: Geometry, x, walk_ids, seed=0, point_id=0, **opt):
     fu = np.zeros(n)
     fg = np.zeros((n, geom.dim))
     o = make_opts(M=opt.pop("M", geom.problem.get("M", 4)), **opt)
-    _check(lib.woi_walk_values(geom.handle, ctypes.byref(o), x.ctypes.data, int(point_id), ids.ctypes.data, n,
-                               int(seed), fu.ctypes.data, fg.ctypes.data))
+    _check(lib.woi_walk_values(geom.handle, ctypes.byref(o), x.ctypes.data, int(point_id), int(instance_id),
+                               ids.ctypes.data, n, int(seed), fu.ctypes.data, fg.ctypes.data))
     return {"u": fu, "grad": fg}
 
 
-def woi_walk_trace(geom: Geometry, x, walk_ids, seed=0, point_id=0, **opt):
+def woi_walk_trace(geom: Geometry, x, walk_ids, seed=0, point_id=0, instance_id=0, **opt):
     """Per-walk tallies and per-step states (y, Q, T) of every chain."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     ids = np.ascontiguousarray(walk_ids, dtype=np.uint64)
@@ -291,9 +292,51 @@ def woi_walk_trace(geom: Geometry, x, walk_ids, seed=0, point_id=0, **opt):
     fg = np.zeros((n, geom.dim))
     tr = np.zeros((n, chains, M + 1, geom.dim + 2))
     o = make_opts(M=M, **opt)
-    _check(lib.woi_walk_trace(geom.handle, ctypes.byref(o), x.ctypes.data, int(point_id), ids.ctypes.data, n,
-                              int(seed), fu.ctypes.data, fg.ctypes.data, tr.ctypes.data))
+    _check(lib.woi_walk_trace(geom.handle, ctypes.byref(o), x.ctypes.data, int(point_id), int(instance_id),
+                              ids.ctypes.data, n, int(seed), fu.ctypes.data, fg.ctypes.data, tr.ctypes.data))
     return {"u": fu, "grad": fg, "Y": tr[..., :geom.dim], "Q": tr[..., geom.dim], "T": tr[..., geom.dim + 1]}
+
+
+def woi_autotune(geom: Geometry, points, n_walks, seed=0, stream=None, **opt):
+    """Tune (block size, walks per lane) of the FP32 walk kernel on this workload;
+    later calls with block_size = walks_per_lane = 0 use the choice."""
+    points = _as_input(points)
+    b, l = ctypes.c_int(), ctypes.c_int()
+    o = make_opts(M=opt.pop("M", geom.problem.get("M", 4)), stream=_stream_of([points], stream), **opt)
+    _check(lib.woi_autotune(geom.handle, ctypes.byref(o), _ptr(points), int(points.shape[0]), int(n_walks), int(seed),
+                            ctypes.byref(b), ctypes.byref(l)))
+    return b.value, l.value
+
+
+def woi_estimate_batch(instances, seed=0, stream=None, **opt):
+    """Batched estimate.  instances: list of (Geometry, points, n_walks[, M]);
+    points numpy (host) or torch CUDA tensors.  Instance k uses random-stream
+    instance id k.  Returns a list of dicts like woi_estimate, with outputs
+    allocated like each instance's points."""
+    n = len(instances)
+    P = ctypes.POINTER
+    geoms = (ctypes.c_void_p * n)()
+    pts = (ctypes.c_void_p * n)()
+    npts = (ctypes.c_int64 * n)()
+    nw = (ctypes.c_int64 * n)()
+    ms = (ctypes.c_int * n)()
+    outs = [(ctypes.c_void_p * n)() for _ in range(4)]
+    keep, results = [], []
+    for k, inst in enumerate(instances):
+        geom, points, n_walks = inst[0], _as_input(inst[1]), inst[2]
+        M = inst[3] if len(inst) > 3 else geom.problem.get("M", 4)
+        Pk = int(points.shape[0])
+        out = (_alloc_like(points, (Pk,)), _alloc_like(points, (Pk, geom.dim)), _alloc_like(points, (Pk,)),
+               _alloc_like(points, (Pk, geom.dim)))
+        keep += [points, *out]
+        geoms[k], pts[k], npts[k], nw[k], ms[k] = geom.handle, _ptr(points), Pk, int(n_walks), int(M)
+        for j in range(4):
+            outs[j][k] = _ptr(out[j])
+        results.append({"u": out[0], "grad": out[1], "se_u": out[2], "se_grad": out[3]})
+    arrays = [inst[1] for inst in instances]
+    o = make_opts(M=4, stream=_stream_of(arrays, stream), **opt)
+    _check(lib.woi_estimate_batch(n, geoms, ctypes.byref(o), ms, pts, npts, nw, int(seed), *outs))
+    return results
 
 
 def finalize_moments(mom, n_walks, sched_group=1):

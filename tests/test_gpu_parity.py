@@ -217,3 +217,32 @@ def test_edge_cases(W, O):
     one = W.woi_estimate(g, x[:1], 1, seed=4)                  # a single walk: SE is 0 by convention
     assert np.isfinite(one["u"][0])
     g.close()
+
+
+def test_batch_matches_oracle_and_fp64_path(W, O):
+    """woi_estimate_batch over mixed 2D / 3D manufactured instances (one
+    persistent launch per dimension, graph replayed on the second call) against
+    the oracle with the instance's random-stream id, and the FP64 batch path."""
+    import torch
+    rng = np.random.default_rng(21)
+    insts = []
+    for k in range(6):
+        dim = 2 if k % 2 == 0 else 3
+        prob = wl.manufactured_instance(dim, rng, k_max=20)
+        x = wl.ball_points(5 + 3 * k, dim, 100 + k, radius=0.9)
+        insts.append((prob, x, 2048 + 1024 * (k % 3)))
+    geoms = [W.Geometry(p) for p, _, _ in insts]
+    args = [(g, torch.from_numpy(x).cuda() if k % 3 else x, n) for k, (g, (p, x, n)) in enumerate(zip(geoms, insts))]
+    first = W.woi_estimate_batch(args, seed=5)
+    second = W.woi_estimate_batch(args, seed=5)                 # replays the captured graph
+    fp64 = W.woi_estimate_batch([(g, x, n) for g, (p, x, n) in zip(geoms, insts)], seed=5, precision="fp64")
+    torch.cuda.synchronize()
+    for k, (prob, x, n) in enumerate(insts):
+        orr = O.estimate(prob, x, n, seed=5, M=prob["M"], instance=k)
+        for res in (first[k], second[k]):
+            u = res["u"].cpu().numpy() if hasattr(res["u"], "cpu") else res["u"]
+            assert np.all(np.abs(u - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12), k
+        scale = orr["se_u"] * np.sqrt(n) + np.abs(orr["u"])
+        assert np.all(np.abs(fp64[k]["u"] - orr["u"]) <= 1e-10 * scale), k
+    for g in geoms:
+        g.close()
