@@ -112,7 +112,8 @@ typedef struct {
     int sched_group;                  /* walkers per interface schedule (Algorithm 1): 1 or 32 */
     void *cuda_stream;                /* cudaStream_t to launch on; NULL = the legacy default stream */
     int block_size;                   /* 0 = autotuned / default */
-    int walks_per_lane;               /* walks each lane runs per work unit; 0 = default */
+    int walks_per_lane;               /* walks each lane runs per work unit (a unit is one warp's, or for a
+                                         batch one block's, share of a point's walks); 0 = default */
     int timing;                       /* 1: record CUDA events around the walk kernel(s) on the launch
                                          stream (read back with woi_last_kernel_ms) */
 } woi_opts;
@@ -232,7 +233,8 @@ WOI_API woi_status woi_last_kernel_ms(woi_geometry *geometry, float *ms);
  * se_grad[n_pts][dim] must be device pointers (outputs may be NULL).  The
  * call is asynchronous on opts->cuda_stream.  Sizes whose scratch would exceed
  * the array are rejected with WOI_E_INVALID_ARG (about 16 MiB / (16 (dim+1))
- * work units of 2048 walks each, e.g. 4096 points x 1e5 walks in 3D fits).
+ * work units of 32 x walks_per_lane walks each -- 2048 by default -- e.g.
+ * 4096 points x 1e5 walks in 3D fits).
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
@@ -249,7 +251,7 @@ WOI_API woi_status woi_estimate_noalloc(woi_geometry *geometry, const woi_opts *
 /*
  * Autotuner of the FP32 walk kernel's launch shape.  Times the persistent
  * kernel on a probe of the given workload (the first few waves of work units)
- * for block sizes {128, 256} x walks per lane {4, 8, 16, 32}, and keeps the
+ * for block sizes {128, 256} x walks per lane {8, 16, 32, 64}, and keeps the
  * fastest pair for this (dimension, star surface, variant, schedule group, M)
  * in a process-wide table that later calls with block_size = walks_per_lane = 0
  * use.  If the environment variable WOI_TUNE_CACHE names a file, the table is

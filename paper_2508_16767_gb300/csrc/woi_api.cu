@@ -664,8 +664,9 @@ void tune_save()
     std::fclose(f);
 }
 
-// launch shape of the FP32 walk kernel: explicit options, else the tuned table, else 256 x 8
-void launch_shape(const woi_opts *o, int dim, bool star, int *block, int *L)
+// launch shape of the FP32 walk kernel: explicit options, else the tuned table, else 256
+// threads x default_L walks per lane
+void launch_shape(const woi_opts *o, int dim, bool star, int *block, int *L, int default_L = 32)
 {
     *block = o->block_size;
     *L = o->walks_per_lane;
@@ -678,7 +679,7 @@ void launch_shape(const woi_opts *o, int dim, bool star, int *block, int *L)
         }
     }
     if (*block == 0) *block = 256;
-    if (*L == 0) *L = 8;
+    if (*L == 0) *L = default_L;
 }
 
 woi_status ensure_device(woi_geometry *g)
@@ -867,7 +868,7 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
 
     int block, L;
     launch_shape(o, d, star, &block, &L);
-    const int64_t unit_walks = (int64_t)block * L;
+    const int64_t unit_walks = 32LL * L;       // warp-level work units
     const int64_t chunks = fp64 ? 1 : (n_walks + unit_walks - 1) / unit_walks;
     const int64_t units = n_pts * chunks;
 
@@ -926,17 +927,20 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
         desc.sched_group = o->sched_group;
         WOI_CUDA(cudaMemcpyAsync(base + o_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, s));
         WOI_CUDA(cudaMemsetAsync(base + o_queue, 0, sizeof(unsigned long long), s));
-        long long key = ((long long)d << 20) | ((long long)vr << 19) | ((long long)star << 18) | block;
+        const size_t smem = (size_t)(block / 32) * g->n * kMaxDim * sizeof(float);
+        long long key = ((long long)d << 20) | ((long long)vr << 19) | ((long long)star << 18) | ((long long)g->n << 10) |
+                        block;
         int per_sm = 0;
         auto it = g->occ_cache.find(key);
         if (it == g->occ_cache.end()) {
-            WOI_CUDA(mixed_occupancy(d, vr, star, block, &per_sm));
+            WOI_CUDA(mixed_warp_occupancy(d, vr, star, block, smem, &per_sm));
             g->occ_cache[key] = per_sm;
         } else {
             per_sm = it->second;
         }
         if (per_sm < 1) per_sm = 1;
-        const int64_t grid = std::min<int64_t>((int64_t)g->num_sms * per_sm, units);
+        const int64_t warps = units;
+        const int64_t grid = std::min<int64_t>((int64_t)g->num_sms * per_sm, (warps + block / 32 - 1) / (block / 32));
         MixedParams mp{};
         mp.inst = (const InstDesc *)(base + o_desc);
         mp.n_inst = 1;
@@ -946,7 +950,7 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
         mp.walks_per_lane = L;
         mp.seed = seed;
         if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_start, s));
-        WOI_CUDA(launch_mixed(d, vr, star, mp, (int)grid, block, s));
+        WOI_CUDA(launch_mixed_warp(d, vr, star, mp, (int)grid, block, smem, s));
         if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_stop, s));
         WOI_CUDA(launch_finalize(fp, false, s));
     } else {
@@ -1333,7 +1337,7 @@ woi_status woi_autotune(woi_geometry *g, const woi_opts *o, const double *points
     tune_load();
     const int d = g->dim;
     const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0;
-    const int blocks[2] = {128, 256}, lanes[4] = {4, 8, 16, 32};
+    const int blocks[2] = {128, 256}, lanes[4] = {8, 16, 32, 64};
     float best = 1e30f;
     int bb = 256, bl = 8;
     woi_opts t = *o;
@@ -1344,13 +1348,14 @@ woi_status woi_autotune(woi_geometry *g, const woi_opts *o, const double *points
             t.walks_per_lane = lanes[li];
             // probe: enough points for about four waves of units of this shape
             int per_sm = 1;
-            if (mixed_occupancy(d, vr, star, blocks[bi], &per_sm) != cudaSuccess) {
+            const size_t smem = (size_t)(blocks[bi] / 32) * g->n * kMaxDim * sizeof(float);
+            if (mixed_warp_occupancy(d, vr, star, blocks[bi], smem, &per_sm) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
-            const int64_t unit_walks = (int64_t)blocks[bi] * lanes[li];
+            const int64_t unit_walks = 32LL * lanes[li];
             const int64_t chunks = (n_walks + unit_walks - 1) / unit_walks;
-            const int64_t want_units = 4LL * g->num_sms * std::max(per_sm, 1);
+            const int64_t want_units = 4LL * g->num_sms * std::max(per_sm, 1) * (blocks[bi] / 32);
             const int64_t probe_pts = std::max<int64_t>(1, std::min<int64_t>(n_pts, (want_units + chunks - 1) / chunks));
             // one untimed run (caches the geometry and scratch), one timed run
             if ((st = run_estimate(g, &t, points, probe_pts, 0, n_walks, seed, nullptr, nullptr, nullptr, nullptr,
@@ -1458,8 +1463,8 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     const int d = g->dim, C = d + 1, M = o->M;
     const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0;
     const int block = o->block_size ? o->block_size : 256;
-    const int L = o->walks_per_lane ? o->walks_per_lane : 8;
-    const int64_t unit_walks = (int64_t)block * L;
+    const int L = o->walks_per_lane ? o->walks_per_lane : 64;
+    const int64_t unit_walks = 32LL * L;       // warp-level work units
     const int64_t chunks = (n_walks + unit_walks - 1) / unit_walks;
     const int64_t units = n_pts * chunks;
 
@@ -1567,9 +1572,10 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     WOI_CUDA(cudaMemsetAsync(base + o_queue, 0, sizeof(unsigned long long), s));
 
     int per_sm = 0;
-    WOI_CUDA(mixed_occupancy(d, vr, star, block, &per_sm));
+    const size_t smem = (size_t)(block / 32) * g->n * kMaxDim * sizeof(float);
+    WOI_CUDA(mixed_warp_occupancy(d, vr, star, block, smem, &per_sm));
     if (per_sm < 1) per_sm = 1;
-    const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, units);
+    const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, (units + block / 32 - 1) / (block / 32));
     MixedParams mp{};
     mp.inst = (const InstDesc *)(base + o_desc);
     mp.n_inst = 1;
@@ -1578,7 +1584,7 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     mp.partials = (double *)(base + o_part);   // every unit's row is written before it is read
     mp.walks_per_lane = L;
     mp.seed = seed;
-    WOI_CUDA(launch_mixed(d, vr, star, mp, (int)grid, block, s));
+    WOI_CUDA(launch_mixed_warp(d, vr, star, mp, (int)grid, block, smem, s));
     FinalizeParams fp{};
     fp.dim = d;
     fp.n_pts = n_pts;

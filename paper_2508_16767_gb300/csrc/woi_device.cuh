@@ -293,6 +293,27 @@ __device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st
     *dr = R * ds;
 }
 
+// r, r' and r'' at the angle (ct, st)
+template <typename Real>
+__device__ __forceinline__ void star_eval2(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr, Real *ddr)
+{
+    Real ck = ct, sk = st, s = 1, ds = 0, dds = 0;
+    for (int k = 1; k <= g.star_K; ++k) {
+        const Real a = g.star_a[k], b = g.star_b[k];
+        const Real ca = a * ck + b * sk;
+        s += ca;
+        ds += (Real)k * (b * ck - a * sk);
+        dds -= (Real)(k * k) * ca;
+        const Real cn = ck * ct - sk * st;
+        sk = sk * ct + ck * st;
+        ck = cn;
+    }
+    const Real R = g.radius[g.star_idx];
+    *r = R * s;
+    *dr = R * ds;
+    *ddr = R * dds;
+}
+
 // local point r (cos t, sin t), outward unit normal and |gamma'| at the angle (ct, st)
 template <typename Real>
 __device__ __forceinline__ Real star_local(const SGeom<Real> &g, Real ct, Real st, Real *v, Real *n)
@@ -391,11 +412,26 @@ __device__ __forceinline__ void star_line_f(const SGeom<Real> &g, int j, Real de
     *df = tx * z[1] - ty * z[0];
 }
 
+// f'(delta) = gamma' x z and f''(delta) = gamma'' x z
+template <typename Real>
+__device__ __forceinline__ void star_line_df(const SGeom<Real> &g, int j, Real delta, const Real *z, Real *df,
+                                             Real *ddf)
+{
+    Real ct, st, r, dr, ddr;
+    angle_cs(g, j, delta, &ct, &st);
+    star_eval2(g, ct, st, &r, &dr, &ddr);
+    const Real tx = dr * ct - r * st, ty = dr * st + r * ct;
+    const Real ax = (ddr - r) * ct - (Real)2 * dr * st, ay = (ddr - r) * st + (Real)2 * dr * ct;
+    *df = tx * z[1] - ty * z[0];
+    *ddf = ax * z[1] - ay * z[0];
+}
+
 // root of f in (a, b) given sign(f(a)) (safeguarded Newton in delta)
 template <typename Real>
-__device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa, const Real *yc, const Real *z)
+__device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa, const Real *yc, const Real *z,
+                           Real t0 = (Real)-1)
 {
-    Real t = (Real)0.5 * (a + b);
+    Real t = (t0 > a && t0 < b) ? t0 : (Real)0.5 * (a + b);
     const int iters = sizeof(Real) == 4 ? 40 : 90;
     for (int it = 0; it < iters; ++it) {
         Real f, df;
@@ -426,20 +462,31 @@ __device__ __forceinline__ int star_interval_roots(const SGeom<Real> &g, int j, 
     const Real guard = g.star_lmax * H * (Real)0.5;
     int nc = 0;
     if ((fa < 0) != (fb < 0)) {
-        cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z);
+        cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z, H * fa / (fa - fb));   // secant start
     } else if (RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
-        Real f1, d1, f2, d2;
-        star_line_f(g, j, (Real)0, yc, z, &f1, &d1);
-        star_line_f(g, j, H, yc, z, &f2, &d2);
+        Real d1, dd1, d2, dd2;
+        star_line_df(g, j, (Real)0, z, &d1, &dd1);
+        star_line_df(g, j, H, z, &d2, &dd2);
         if ((d1 < 0) != (d2 < 0)) {
+            // extremum of f in (0, H): safeguarded Newton on f' = 0
             Real lo = 0, hi = H, dlo = d1;
+            Real te = H * d1 / (d1 - d2);
             for (int it = 0; it < (sizeof(Real) == 4 ? 30 : 60); ++it) {
-                const Real m = (Real)0.5 * (lo + hi);
-                Real fm, dm;
-                star_line_f(g, j, m, yc, z, &fm, &dm);
-                if ((dm < 0) == (dlo < 0)) { lo = m; dlo = dm; } else hi = m;
+                Real dm, ddm;
+                star_line_df(g, j, te, z, &dm, &ddm);
+                if (dm == (Real)0) break;
+                if ((dm < 0) == (dlo < 0)) { lo = te; dlo = dm; } else hi = te;
+                const Real step = dm / ddm;
+                if (RealOps<Real>::fabs_(step) <= eps_tol<Real>()) {
+                    te -= step;
+                    break;
+                }
+                Real tn = te - step;
+                if (!(tn > lo && tn < hi)) tn = (Real)0.5 * (lo + hi);
+                te = tn;
+                if (hi - lo <= bracket_tol<Real>()) break;
             }
-            const Real te = (Real)0.5 * (lo + hi);
+            if (!(te > (Real)0 && te < H)) te = (Real)0.5 * H;
             Real fe, de;
             star_line_f(g, j, te, yc, z, &fe, &de);
             if ((fe < 0) != (fa < 0)) {

@@ -132,6 +132,17 @@ cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_
     return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy(vr, block, blocks_per_sm); });
 }
 
+cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,
+                              cudaStream_t s)
+{
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::mixed_warp(vr, p, grid, block, smem, s); });
+}
+
+cudaError_t mixed_warp_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm)
+{
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy_warp(vr, block, smem, blocks_per_sm); });
+}
+
 cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s)
 {
     const int64_t n = p.n_pts * (p.dim + 1);

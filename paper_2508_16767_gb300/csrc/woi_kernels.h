@@ -63,6 +63,8 @@ template <int D, bool STAR>
 struct DimLaunchers {
     static cudaError_t mixed(bool vr, const MixedParams &p, int grid, int block, cudaStream_t s);
     static cudaError_t occupancy(bool vr, int block, int *blocks_per_sm);
+    static cudaError_t mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s);
+    static cudaError_t occupancy_warp(bool vr, int block, size_t smem, int *blocks_per_sm);
     static cudaError_t fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s);
     static cudaError_t values(bool vr, bool fp64, const WalkValuesParams &p, cudaStream_t s);
 };
@@ -87,6 +89,11 @@ struct BatchFinalizeParams {
 cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, cudaStream_t s);
 cudaError_t launch_finalize_batch(const BatchFinalizeParams &p, cudaStream_t s);
 cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_per_sm);
+// single-instance kernel with warp-level work units of 32 x walks_per_lane walks;
+// dynamic shared memory: (block / 32) * n_surf * kMaxDim floats
+cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,
+                              cudaStream_t s);
+cudaError_t mixed_warp_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm);
 cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s);
 cudaError_t launch_fp64_point(int dim, bool vr, bool star, const Fp64PointParams &p, cudaStream_t s);
 cudaError_t launch_walk_values(int dim, bool vr, bool star, bool fp64, const WalkValuesParams &p, cudaStream_t s);

@@ -161,6 +161,82 @@ __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams
 }
 
 // ---------------------------------------------------------------------------
+// single-instance variant: warp-level work units (32 lanes x L walks of one
+// point), each warp with its own x - c_s table, no block barrier per unit
+// ---------------------------------------------------------------------------
+template <int D, bool VR, bool STAR>
+__global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed_warp(MixedParams p)
+{
+    __shared__ SGeom<float> g;
+    extern __shared__ float xc_all[];   // [warps][n][kMaxDim]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const InstDesc &id = p.inst[0];
+    load_geometry(g, id.geom);
+    __syncthreads();
+    float(*xc)[kMaxDim] = reinterpret_cast<float(*)[kMaxDim]>(xc_all + (size_t)warp * g.n * kMaxDim);
+    const int L = p.walks_per_lane;
+    const int64_t w_end = id.walk_begin + id.n_walks;
+    Rng rng;
+    rng.k1 = (uint32_t)(p.seed >> 32) ^ id.instance_id;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(p.queue, 1ull);
+        u = __shfl_sync(0xFFFFFFFFu, u, 0);
+        if (u >= (unsigned long long)p.total_units) break;
+        const int64_t unit = (int64_t)u;
+        const int64_t point = unit / id.chunks_per_point;
+        const int64_t chunk = unit - point * id.chunks_per_point;
+        const double *x = id.points + point * D;
+        for (int i = lane; i < g.n * D; i += 32) {
+            const int sidx = i / D, k = i - sidx * D;
+            xc[sidx][k] = (float)(x[k] - id.geom->center[sidx][k]);
+        }
+        __syncwarp();
+        rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
+        const int64_t w_base = id.walk_begin + chunk * 32LL * L;
+        float s1[D + 1], c1[D + 1], s2[D + 1];
+#pragma unroll
+        for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
+        for (int j = 0; j < L; ++j) {
+            const int64_t w = w_base + (int64_t)j * 32 + lane;
+            float f[D + 1];
+            const bool valid = w < w_end;
+            if (valid) {
+                rng.w0 = (uint32_t)w;
+                rng.w1 = (uint32_t)((uint64_t)w >> 32);
+                walk<float, D, VR, STAR>(g, id.geom, xc, rng, id.sched_group, (uint64_t)w / 32u, f);
+            } else {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) f[c] = 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
+            if (id.sched_group == 1) {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) {
+                    const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
+                    if (lane == 0 && valid) s2[c] += gm * gm;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c <= D; ++c) {
+            float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
+            warp_sum_pair(h1, l1);
+            warp_sum_pair(h2, l2);
+            if (lane == 0) {
+                p.partials[unit * (2 * (D + 1)) + c] = (double)h1 + (double)l1;
+                p.partials[unit * (2 * (D + 1)) + D + 1 + c] = (double)h2 + (double)l2;
+            }
+        }
+        __syncwarp();   // the table is rewritten for the next unit
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 baseline: one launch per point, one walk per thread, FP64 atomics
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
@@ -250,6 +326,29 @@ cudaError_t DimLaunchers<D, STAR>::mixed(bool vr, const MixedParams &p, int grid
         k_walk_mixed<D, false, STAR><<<grid, block, 0, s>>>(p);
         return cudaGetLastError();
     }
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem,
+                                             cudaStream_t s)
+{
+    if constexpr (D == 2) {
+        if (vr) {
+            k_walk_mixed_warp<2, true, STAR><<<grid, block, smem, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
+    k_walk_mixed_warp<D, false, STAR><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t smem, int *blocks_per_sm)
+{
+    if constexpr (D == 2) {
+        if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<2, true, STAR>, block, smem);
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, false, STAR>, block, smem);
+}
+
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, int *blocks_per_sm)
     {
