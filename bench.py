@@ -42,6 +42,11 @@ def alg_flops_per_walk_step(dim: int) -> float:
     return 30.0 if dim == 2 else 11.0 * dim + 15.0
 
 
+# of which the Phi / grad Phi tally at one point: 2D 14, d-spheres 5 d + 8
+def alg_tally_flops(dim: int) -> float:
+    return 14.0 if dim == 2 else 5.0 * dim + 8.0
+
+
 # DRAM bytes per launch of the walk kernel from the ncu capture of the
 # workload named as key, scaled to one full launch (None once the kernel has
 # changed since the counters were taken).
@@ -193,11 +198,14 @@ def main():
     ap.add_argument("--workload", default="3d-nested", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--walks-per-lane", type=int, default=0)
     ap.add_argument("--sched-group", type=int, default=1)
     ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling)")
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
+    ap.add_argument("--tile-points", type=int, default=0, choices=[0, 32],
+                    help="32: tiles of 32 points share their walks (Sec. 4.6)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -226,7 +234,7 @@ def main():
             torch.empty(P, dtype=torch.float64, device="cuda"), torch.empty(P, d, dtype=torch.float64, device="cuda"))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     opt = dict(M=M, precision=args.precision, sched_group=args.sched_group, block_size=args.block,
-               walks_per_lane=args.walks_per_lane)
+               walks_per_lane=args.walks_per_lane, tile_points=args.tile_points)
 
     def step(timing):
         # each rank runs its own walk range: rank r takes walks [r W, (r + 1) W)
@@ -268,7 +276,12 @@ def main():
     props = torch.cuda.get_device_properties(local)
     peak_tflops = props.multi_processor_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     k_ms = float(np.mean(kernel_ms))
-    flops = P * Wk * (M + 1) * alg_flops_per_walk_step(d)
+    if args.tile_points:
+        # one walk per tile of 32 points, tallied at each of them
+        n_tiles = -(-P // args.tile_points)
+        flops = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d) - alg_tally_flops(d)) + P * alg_tally_flops(d))
+    else:
+        flops = P * Wk * (M + 1) * alg_flops_per_walk_step(d)
     achieved = flops / (k_ms / 1000.0) / 1e12
     rms_se = float(torch.sqrt(torch.mean(outs[2] ** 2)).item()) if ws == 1 else None
 
@@ -287,6 +300,23 @@ def main():
         e2e = {"value": P / te, "unit": "estimates/s", "h2d_bytes_per_step": P * d * 8,
                "d2h_bytes_per_step": P * (2 + 2 * d) * 8}
 
+    # the plain FP64 one-launch-per-point GPU path on a sample of the points
+    # (same estimator, same walks per point, so the same RMS error), for comparison
+    fp64 = None
+    if rank == 0 and ws == 1 and args.precision == "mixed" and not args.no_fp64_baseline:
+        n_s = min(P, 64)
+        xs = xd[:n_s].contiguous()
+        woi.woi_estimate(geom, xs, Wk, seed=0, stream=stream.cuda_stream, M=M, precision="fp64")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        woi.woi_estimate(geom, xs, Wk, seed=0, stream=stream.cuda_stream, M=M, precision="fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1000.0
+        fp64 = {"value": n_s / t64, "unit": "estimates/s", "points_sampled": n_s,
+                "speedup_of_mixed": value / (n_s / t64)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(problem, points, M, Wk)
@@ -301,6 +331,7 @@ def main():
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "points": P, "walks_per_point": Wk, "M": M, "dim": d,
                        "precision": args.precision, "sched_group": args.sched_group,
+                       "tile_points": args.tile_points,
                        "l2": "flushed between steps (512 MiB write outside the step events)",
                        "parallelism": f"replicas x{ws}, disjoint walk ranges"},
             "walk_steps_per_s": wsps, "rms_se_u": rms_se,
@@ -308,7 +339,7 @@ def main():
                          "frac": achieved / peak_tflops, "traffic": TRAFFIC.get(args.workload),
                          "peak_source": f"FP32: SMs x 128 lanes x 2 x sm_max_mhz ({src})",
                          "kernel_ms": k_ms, "alg_flops_per_walk_step": alg_flops_per_walk_step(d)},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "cpu_baseline": cpu, "fp64_plain_gpu_path": fp64, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (2 if args.precision == "mixed" else P + 1),
         }
         print(json.dumps(line))

@@ -116,6 +116,11 @@ typedef struct {
                                          batch one block's, share of a point's walks); 0 = default */
     int timing;                       /* 1: record CUDA events around the walk kernel(s) on the launch
                                          stream (read back with woi_last_kernel_ms) */
+    int tile_points;                  /* 0: every point has its own walks (streams keyed by point).
+                                         32: shared trajectories (Sec. 4.6): the points
+                                         [32 t, 32 t + 32) of the call all use the walks of stream id t,
+                                         each tallied against all 32 points; errors of points in a tile
+                                         are correlated.  Mixed precision, woi_estimate / _range only. */
 } woi_opts;
 
 /* Fills `o` with the defaults: M = 4, WOI_PLAIN, WOI_MIXED, sched_group 1, NULL stream. */

@@ -348,12 +348,21 @@ def _opts(M, variant, sched_group):
 
 
 def estimate(problem, points, n_walks, seed=0, M=None, variant="plain", sched_group=1, walk_begin=0,
-             instance=0, prepared=None, point_offset=0):
+             instance=0, prepared=None, point_offset=0, tile=0):
     """Algorithm 1 over every point: mean of N * (walk sum), and the standard
     error from the schedule-group means (groups of `sched_group` walkers).
-    Point p uses the random stream of point id point_offset + p.
+    Point p uses the random stream of point id point_offset + p; with tile > 0
+    (trajectories shared by a batch of points, Sec. 4.6) it uses the stream of
+    id (point_offset + p) // tile, so the points of one tile see the same walks.
     Returns a dict with u [P], grad [P, d], se_u, se_grad and raw sums."""
     prep = prepared or Prepared(problem, variant)
+    if tile > 0:
+        parts = [estimate(problem, points[p:p + 1], n_walks, seed, M, variant, sched_group, walk_begin, instance,
+                          prep, (point_offset + p) // tile) for p in range(len(points))]
+        cat = {k: np.concatenate([r[k] for r in parts]) for k in ("u", "grad", "se_u", "se_grad", "sum_f",
+                                                                 "sum_gm", "sum_gm2")}
+        cat.update(n_walks=n_walks, n_groups=parts[0]["n_groups"] if parts else 0)
+        return cat
     M = problem["M"] if M is None else M
     pts = np.ascontiguousarray(points, dtype=np.float64)
     P, d = pts.shape

@@ -826,6 +826,10 @@ woi_status check_opts(const woi_geometry *g, const woi_opts *o, int64_t n_pts, i
     if (o->block_size != 0 && (o->block_size % 32 || o->block_size < 32 || o->block_size > kMixedMaxBlock))
         return fail(WOI_E_INVALID_ARG, "block_size must be a multiple of 32 in [32, %d]", kMixedMaxBlock);
     if (o->walks_per_lane < 0 || o->walks_per_lane > 4096) return fail(WOI_E_INVALID_ARG, "walks_per_lane out of range");
+    if (o->tile_points != 0 && o->tile_points != kTile)
+        return fail(WOI_E_INVALID_ARG, "tile_points must be 0 or %d", kTile);
+    if (o->tile_points && o->precision != WOI_MIXED)
+        return fail(WOI_E_UNSUPPORTED, "shared trajectories run in mixed precision only");
     return WOI_OK;
 }
 
@@ -868,15 +872,23 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
 
     int block, L;
     launch_shape(o, d, star, &block, &L);
+    const bool tiled = o->tile_points != 0;
+    if (tiled) {
+        // per round a lane runs one walk and tallies 32: fewer walks per unit keep the queue balanced
+        block = kSharedBlock;
+        L = o->walks_per_lane > 0 ? o->walks_per_lane : 8;
+    }
     const int64_t unit_walks = 32LL * L;       // warp-level work units
     const int64_t chunks = fp64 ? 1 : (n_walks + unit_walks - 1) / unit_walks;
-    const int64_t units = n_pts * chunks;
+    const int64_t n_tiles = (n_pts + kTile - 1) / kTile;
+    const int64_t units = tiled ? n_tiles * chunks : n_pts * chunks;
+    const int64_t rows = tiled ? units * kTile : units;
 
     // scratch layout: [inst desc][queue][partials][points][outputs]
     size_t off = 0;
     const size_t o_desc = off; off = align_up(off + sizeof(InstDesc), 256);
     const size_t o_queue = off; off = align_up(off + sizeof(unsigned long long), 256);
-    const size_t o_part = off; off = align_up(off + (size_t)units * 2 * C * sizeof(double), 256);
+    const size_t o_part = off; off = align_up(off + (size_t)rows * 2 * C * sizeof(double), 256);
     const size_t o_pts = off; off = align_up(off + (size_t)n_pts * d * sizeof(double), 256);
     OutBuf outs[5] = {{u, false, nullptr, (size_t)n_pts}, {grad, false, nullptr, (size_t)n_pts * d},
                       {se_u, false, nullptr, (size_t)n_pts}, {se_grad, false, nullptr, (size_t)n_pts * d},
@@ -908,6 +920,7 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
     fp.unit_begin = 0;
     fp.chunks_per_point = chunks;
     fp.partials = (const double *)(base + o_part);
+    fp.tile = tiled ? kTile : 0;
     fp.u = outs[0].dev;
     fp.grad = outs[1].dev;
     fp.se_u = outs[2].dev;
@@ -927,18 +940,21 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
         desc.sched_group = o->sched_group;
         WOI_CUDA(cudaMemcpyAsync(base + o_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, s));
         WOI_CUDA(cudaMemsetAsync(base + o_queue, 0, sizeof(unsigned long long), s));
-        const size_t smem = (size_t)(block / 32) * g->n * kMaxDim * sizeof(float);
-        long long key = ((long long)d << 20) | ((long long)vr << 19) | ((long long)star << 18) | ((long long)g->n << 10) |
-                        block;
+        const size_t smem = tiled ? (size_t)(kSharedBlock / 32) * (vr ? 2 : 1) * (o->M + 1) * 32 * shared_record_floats(d) *
+                                        sizeof(float)
+                                  : (size_t)(block / 32) * g->n * kMaxDim * sizeof(float);
+        long long key = ((long long)tiled << 40) | ((long long)o->M << 32) | ((long long)d << 20) | ((long long)vr << 19) |
+                        ((long long)star << 18) | ((long long)g->n << 10) | block;
         int per_sm = 0;
         auto it = g->occ_cache.find(key);
         if (it == g->occ_cache.end()) {
-            WOI_CUDA(mixed_warp_occupancy(d, vr, star, block, smem, &per_sm));
+            if (tiled) WOI_CUDA(shared_occupancy(d, vr, star, smem, &per_sm));
+            else WOI_CUDA(mixed_warp_occupancy(d, vr, star, block, smem, &per_sm));
             g->occ_cache[key] = per_sm;
         } else {
             per_sm = it->second;
         }
-        if (per_sm < 1) per_sm = 1;
+        if (per_sm < 1) return fail(WOI_E_UNSUPPORTED, "walk kernel does not fit on an SM (M = %d)", o->M);
         const int64_t warps = units;
         const int64_t grid = std::min<int64_t>((int64_t)g->num_sms * per_sm, (warps + block / 32 - 1) / (block / 32));
         MixedParams mp{};
@@ -950,7 +966,8 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
         mp.walks_per_lane = L;
         mp.seed = seed;
         if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_start, s));
-        WOI_CUDA(launch_mixed_warp(d, vr, star, mp, (int)grid, block, smem, s));
+        if (tiled) WOI_CUDA(launch_shared(d, vr, star, mp, (int)grid, smem, s));
+        else WOI_CUDA(launch_mixed_warp(d, vr, star, mp, (int)grid, block, smem, s));
         if (o->timing) WOI_CUDA(cudaEventRecord(g->ev_stop, s));
         WOI_CUDA(launch_finalize(fp, false, s));
     } else {
@@ -1342,6 +1359,7 @@ woi_status woi_autotune(woi_geometry *g, const woi_opts *o, const double *points
     int bb = 256, bl = 8;
     woi_opts t = *o;
     t.timing = 1;
+    t.tile_points = 0;                 // the table holds shapes of the per-point kernel
     for (int bi = 0; bi < 2; ++bi)
         for (int li = 0; li < 4; ++li) {
             t.block_size = blocks[bi];
@@ -1395,6 +1413,7 @@ woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geoms, const woi_
                               double *const *u, double *const *grad, double *const *se_u, double *const *se_grad)
 {
     g_last_error.clear();
+    if (o && o->tile_points) return fail(WOI_E_UNSUPPORTED, "shared trajectories are not supported in a batch");
     return run_batch(n_inst, geoms, o, m_per_inst, points, n_pts, n_walks, seed, u, grad, se_u, se_grad);
 }
 
@@ -1443,6 +1462,7 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     woi_status st;
     if ((st = check_opts(g, o, n_pts, 0, n_walks)) != WOI_OK) return st;
     if (o->precision != WOI_MIXED) return fail(WOI_E_UNSUPPORTED, "the allocation-free estimate runs the mixed path only");
+    if (o->tile_points) return fail(WOI_E_UNSUPPORTED, "the allocation-free estimate has no shared-trajectory mode");
     if (n_pts > 0 && !pointer_on_device(points)) return fail(WOI_E_INVALID_ARG, "points must be device memory");
     double *outs[4] = {u, grad, se_u, se_grad};
     for (double *p : outs)

@@ -695,18 +695,14 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
     return 0;
 }
 
-// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D], with y = c_s + v and
-// xc[s] = x - c_s formed in FP64 once per evaluation point (no cancellation near a surface)
+// c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D], given dx = x - y
 template <typename Real, int D>
-__device__ __forceinline__ void tally(const Real (*xc)[kMaxDim], int s, const Real *v, Real c, Real *acc)
+__device__ __forceinline__ void tally_dx(const Real *dx, Real c, Real *acc)
 {
     using O = RealOps<Real>;
-    Real dx[D], r2 = 0;
+    Real r2 = 0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        dx[k] = xc[s][k] - v[k];
-        r2 += dx[k] * dx[k];
-    }
+    for (int k = 0; k < D; ++k) r2 += dx[k] * dx[k];
     if (r2 <= (Real)0) return;  // x on a walk state exactly: measure zero, contributes nothing
     constexpr double PI = 3.14159265358979323846;
     if constexpr (D == 2) {
@@ -727,6 +723,17 @@ __device__ __forceinline__ void tally(const Real (*xc)[kMaxDim], int s, const Re
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[1 + k] += gc * dx[k];
     }
+}
+
+// the same with y = c_s + v and xc[s] = x - c_s formed in FP64 once per evaluation
+// point (no cancellation near a surface)
+template <typename Real, int D>
+__device__ __forceinline__ void tally(const Real (*xc)[kMaxDim], int s, const Real *v, Real c, Real *acc)
+{
+    Real dx[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) dx[k] = xc[s][k] - v[k];
+    tally_dx<Real, D>(dx, c, acc);
 }
 
 // x - c_s for every surface of the staged instance (all threads of the block)
@@ -960,12 +967,13 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
 // N sum_i w_i A^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i Phi(x, Y_i), summed
 // over the two chains for VR
 // ---------------------------------------------------------------------------
-template <typename Real, int D, bool VR, bool STAR, bool TRACE = false>
-__device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[kMaxDim], const Rng &rng,
-                     int sched_group, uint64_t group, Real *f, double *trace = nullptr)
+// The steps of one walk (Algorithms 2-3), handing each state to `sink`:
+// sink(i, k, chain, c) with c = N w_i ||alpha||_1^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i
+// the coefficient of Phi(x, y_i) (0 for a chain that has ended).
+template <typename Real, int D, bool VR, bool STAR, typename Sink>
+__device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *gd, const Rng &rng, int sched_group,
+                                           uint64_t group, Sink &sink)
 {
-#pragma unroll
-    for (int c = 0; c <= D; ++c) f[c] = 0;
     Chain<Real, D> ch[VR ? 2 : 1];
     Real S = 1;
     int hp = 0;
@@ -993,19 +1001,56 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[k
             } else if (ch[k].alive) {
                 chain_step<Real, D, STAR>(g, h, rel, w, ch[k]);
             }
-            if (ch[k].alive) tally<Real, D>(xc, ch[k].s, ch[k].v, g.coef[i] * S * ch[k].Q * ch[k].T, f);
-            if constexpr (TRACE) {
-                if (trace) {
-                    double *t = trace + ((size_t)k * (g.M + 1) + i) * (D + 2);
-                    for (int c = 0; c < D; ++c)
-                        t[c] = ((double)g.c_hi[ch[k].s][c] + (double)g.c_lo[ch[k].s][c]) + (double)ch[k].v[c];
-                    t[D] = (double)ch[k].Q;
-                    t[D + 1] = (double)ch[k].T;
-                }
-            }
+            sink(i, k, ch[k], ch[k].alive ? g.coef[i] * S * ch[k].Q * ch[k].T : (Real)0);
         }
         hp = h;
     }
+}
+
+// sink that tallies Phi and grad Phi at one point (and optionally records the states)
+template <typename Real, int D, bool TRACE>
+struct TallySink {
+    const SGeom<Real> &g;
+    const Real (*xc)[kMaxDim];
+    Real *f;
+    double *trace;
+    __device__ __forceinline__ void operator()(int i, int k, const Chain<Real, D> &ch, Real c)
+    {
+        if (ch.alive) tally<Real, D>(xc, ch.s, ch.v, c, f);
+        if constexpr (TRACE) {
+            if (trace) {
+                double *t = trace + ((size_t)k * (g.M + 1) + i) * (D + 2);
+                for (int q = 0; q < D; ++q)
+                    t[q] = ((double)g.c_hi[ch.s][q] + (double)g.c_lo[ch.s][q]) + (double)ch.v[q];
+                t[D] = (double)ch.Q;
+                t[D + 1] = (double)ch.T;
+            }
+        }
+    }
+};
+
+// one walk: returns the tally f[0] (u) and f[1..D] (grad u) of
+// N sum_i w_i A^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i Phi(x, Y_i), summed
+// over the two chains for VR
+template <typename Real, int D, bool VR, bool STAR, bool TRACE = false>
+__device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[kMaxDim], const Rng &rng,
+                     int sched_group, uint64_t group, Real *f, double *trace = nullptr)
+{
+#pragma unroll
+    for (int c = 0; c <= D; ++c) f[c] = 0;
+    TallySink<Real, D, TRACE> sink{g, xc, f, trace};
+    walk_steps<Real, D, VR, STAR>(g, gd, rng, sched_group, group, sink);
+}
+
+// c Phi(x, y) and c grad_x Phi(x, y) for y = c_s + v with x as an FP32 (hi, lo) pair
+template <int D>
+__device__ __forceinline__ void tally_hl(const SGeom<float> &g, const float *xhi, const float *xlo, int s,
+                                         const float *v, float c, float *acc)
+{
+    float dx[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) dx[k] = ((xhi[k] - g.c_hi[s][k]) + (xlo[k] - g.c_lo[s][k])) - v[k];
+    tally_dx<float, D>(dx, c, acc);
 }
 
 }  // namespace woi

@@ -17,10 +17,19 @@ __global__ void k_finalize(FinalizeParams p)
     const int64_t point = idx / C;
     const int c = (int)(idx - point * C);
     double S1 = 0.0, S2 = 0.0;
-    const double *src = p.partials + (p.unit_begin + point * p.chunks_per_point) * (2 * C);
-    for (int64_t ch = 0; ch < p.chunks_per_point; ++ch) {
-        S1 += src[ch * 2 * C + c];
-        S2 += src[ch * 2 * C + C + c];
+    if (p.tile > 0) {
+        const int64_t t = point / p.tile, q = point - t * p.tile;
+        for (int64_t ch = 0; ch < p.chunks_per_point; ++ch) {
+            const double *row = p.partials + ((t * p.chunks_per_point + ch) * p.tile + q) * (2 * C);
+            S1 += row[c];
+            S2 += row[C + c];
+        }
+    } else {
+        const double *src = p.partials + (p.unit_begin + point * p.chunks_per_point) * (2 * C);
+        for (int64_t ch = 0; ch < p.chunks_per_point; ++ch) {
+            S1 += src[ch * 2 * C + c];
+            S2 += src[ch * 2 * C + C + c];
+        }
     }
     if (p.moments) {
         p.moments[point * 2 * C + c] = S1;
@@ -141,6 +150,16 @@ cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p,
 cudaError_t mixed_warp_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm)
 {
     return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy_warp(vr, block, smem, blocks_per_sm); });
+}
+
+cudaError_t launch_shared(int dim, bool vr, bool star, const MixedParams &p, int grid, size_t smem, cudaStream_t s)
+{
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::shared(vr, p, grid, smem, s); });
+}
+
+cudaError_t shared_occupancy(int dim, bool vr, bool star, size_t smem, int *blocks_per_sm)
+{
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy_shared(vr, smem, blocks_per_sm); });
 }
 
 cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s)

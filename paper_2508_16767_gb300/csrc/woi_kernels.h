@@ -12,6 +12,8 @@ namespace woi {
 
 constexpr int kMixedMaxBlock = 256;
 constexpr int kMixedMinBlocks = 3;    // resident blocks per SM the walk kernel is compiled for
+constexpr int kSharedBlock = 128;     // threads per block of the shared-trajectory kernel
+constexpr int kTile = 32;             // points per shared-trajectory tile
 
 struct MixedParams {
     const InstDesc *inst;              // device [n_inst], sorted by unit_begin
@@ -31,6 +33,7 @@ struct FinalizeParams {
     int64_t unit_begin;
     int64_t chunks_per_point;
     const double *partials;            // unit partials, or [n_pts][2 (dim+1)] accumulators
+    int tile;                          // > 0: shared-trajectory rows [(tile, chunk)][tile points]
     double *u, *grad, *se_u, *se_grad; // device, each may be null
     double *moments;                   // device [n_pts][2][dim+1], may be null
 };
@@ -65,6 +68,8 @@ struct DimLaunchers {
     static cudaError_t occupancy(bool vr, int block, int *blocks_per_sm);
     static cudaError_t mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s);
     static cudaError_t occupancy_warp(bool vr, int block, size_t smem, int *blocks_per_sm);
+    static cudaError_t shared(bool vr, const MixedParams &p, int grid, size_t smem, cudaStream_t s);
+    static cudaError_t occupancy_shared(bool vr, size_t smem, int *blocks_per_sm);
     static cudaError_t fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s);
     static cudaError_t values(bool vr, bool fp64, const WalkValuesParams &p, cudaStream_t s);
 };
@@ -94,6 +99,11 @@ cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_
 cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,
                               cudaStream_t s);
 cudaError_t mixed_warp_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm);
+// shared-trajectory kernel (tiles of kTile points share walks); dynamic shared memory:
+// (kSharedBlock / 32) * chains * (M + 1) * 32 * shared_record_floats(dim) * 4 bytes
+constexpr int shared_record_floats(int dim) { return ((2 * dim + 1) + 3) / 4 * 4; }
+cudaError_t launch_shared(int dim, bool vr, bool star, const MixedParams &p, int grid, size_t smem, cudaStream_t s);
+cudaError_t shared_occupancy(int dim, bool vr, bool star, size_t smem, int *blocks_per_sm);
 cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s);
 cudaError_t launch_fp64_point(int dim, bool vr, bool star, const Fp64PointParams &p, cudaStream_t s);
 cudaError_t launch_walk_values(int dim, bool vr, bool star, bool fp64, const WalkValuesParams &p, cudaStream_t s);

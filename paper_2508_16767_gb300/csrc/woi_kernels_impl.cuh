@@ -237,6 +237,145 @@ __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed_warp(MixedP
 }
 
 // ---------------------------------------------------------------------------
+// shared trajectories (Sec. 4.6): the 32 points of a tile share their walks.
+// A warp unit is (tile, walk chunk): per round each lane runs one walk and
+// records its states (surface, offset, coefficient) in shared memory, then each
+// lane tallies its point against the 32 recorded walks (broadcast reads).
+// ---------------------------------------------------------------------------
+// record of one walk state for the tile: y = c_s + v as an unevaluated FP32 sum
+// yhi + ylo (TwoSum, then c_lo), and the coefficient c; kRec<D> floats, 16-byte
+// aligned so that the 32 lanes read a record with kRec<D> / 4 broadcast vector loads
+template <int D>
+constexpr int kRec = ((2 * D + 1) + 3) / 4 * 4;
+
+template <int D>
+struct RecordSink {
+    const SGeom<float> &g;
+    float *rec;    // [chains][M+1][32 walks][kRec<D>]
+    int M1, lane;
+    __device__ __forceinline__ void operator()(int i, int k, const Chain<float, D> &ch, float c)
+    {
+        float *r = rec + ((size_t)(k * M1 + i) * 32 + lane) * kRec<D>;
+        float out[kRec<D>];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            const float a = g.c_hi[ch.s][q], b = ch.v[q];
+            const float sum = a + b, bb = sum - a;
+            out[q] = sum;
+            out[D + q] = ((a - (sum - bb)) + (b - bb)) + g.c_lo[ch.s][q];
+        }
+        out[2 * D] = c;
+#pragma unroll
+        for (int q = 2 * D + 1; q < kRec<D>; ++q) out[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kRec<D>; q += 4)
+            *reinterpret_cast<float4 *>(r + q) = make_float4(out[q], out[q + 1], out[q + 2], out[q + 3]);
+    }
+};
+
+template <int D, bool VR, bool STAR>
+__global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
+{
+    __shared__ SGeom<float> g;
+    extern __shared__ float4 rec_all4[];
+    float *rec_all = reinterpret_cast<float *>(rec_all4);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const InstDesc &id = p.inst[0];
+    load_geometry(g, id.geom);
+    __syncthreads();
+    constexpr int chains = VR ? 2 : 1;
+    constexpr int R = kRec<D>;
+    const int M1 = g.M + 1;
+    const int n_rec = chains * M1;
+    float *rec = rec_all + (size_t)warp * n_rec * 32 * R;
+    RecordSink<D> sink{g, rec, M1, lane};
+    const int L = p.walks_per_lane;
+    const int64_t w_end = id.walk_begin + id.n_walks;
+    Rng rng;
+    rng.k1 = (uint32_t)(p.seed >> 32) ^ id.instance_id;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(p.queue, 1ull);
+        u = __shfl_sync(0xFFFFFFFFu, u, 0);
+        if (u >= (unsigned long long)p.total_units) break;
+        const int64_t unit = (int64_t)u;
+        const int64_t tile = unit / id.chunks_per_point;
+        const int64_t chunk = unit - tile * id.chunks_per_point;
+        const int64_t point = tile * 32 + lane;
+        const bool has_point = point < id.n_pts;
+        float xhi[D], xlo[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double xv = has_point ? id.points[point * D + k] : 0.0;
+            xhi[k] = (float)xv;
+            xlo[k] = (float)(xv - (double)xhi[k]);
+        }
+        rng.k0 = (uint32_t)p.seed ^ (uint32_t)tile;
+        const int64_t w_base = id.walk_begin + chunk * 32LL * L;
+        float s1[D + 1], c1[D + 1], s2[D + 1];
+#pragma unroll
+        for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
+        for (int j = 0; j < L; ++j) {
+            const int64_t w0 = w_base + (int64_t)j * 32;
+            if (w0 >= w_end) break;
+            const int64_t w = w0 + lane;
+            if (w < w_end) {
+                rng.w0 = (uint32_t)w;
+                rng.w1 = (uint32_t)((uint64_t)w >> 32);
+                walk_steps<float, D, VR, STAR>(g, id.geom, rng, id.sched_group, (uint64_t)w / 32u, sink);
+            }
+            __syncwarp();
+            const int n_valid = (int)min((int64_t)32, w_end - w0);
+            float gs[D + 1];
+#pragma unroll
+            for (int c = 0; c <= D; ++c) gs[c] = 0.f;
+            for (int ww = 0; ww < n_valid; ++ww) {
+                float f[D + 1];
+#pragma unroll
+                for (int c = 0; c <= D; ++c) f[c] = 0.f;
+                for (int e = 0; e < n_rec; ++e) {
+                    const float *r = rec + ((size_t)e * 32 + ww) * R;
+                    float y[R];
+#pragma unroll
+                    for (int q = 0; q < R; q += 4) {
+                        const float4 t = *reinterpret_cast<const float4 *>(r + q);
+                        y[q] = t.x; y[q + 1] = t.y; y[q + 2] = t.z; y[q + 3] = t.w;
+                    }
+                    const float cc = y[2 * D];
+                    if (cc == 0.f) continue;
+                    float dx[D];
+#pragma unroll
+                    for (int q = 0; q < D; ++q) dx[q] = (xhi[q] - y[q]) + (xlo[q] - y[D + q]);
+                    tally_dx<float, D>(dx, cc, f);
+                }
+#pragma unroll
+                for (int c = 0; c <= D; ++c) {
+                    kahan_add(s1[c], c1[c], f[c]);
+                    if (id.sched_group == 1) s2[c] += f[c] * f[c];
+                    else gs[c] += f[c];
+                }
+            }
+            if (id.sched_group != 1) {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) {
+                    const float gm = gs[c] * (1.0f / 32.0f);
+                    s2[c] += gm * gm;
+                }
+            }
+            __syncwarp();
+        }
+        if (has_point) {
+            double *row = p.partials + (unit * 32 + lane) * (2 * (D + 1));
+#pragma unroll
+            for (int c = 0; c <= D; ++c) {
+                row[c] = (double)s1[c] + (double)c1[c];
+                row[D + 1 + c] = (double)s2[c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 baseline: one launch per point, one walk per thread, FP64 atomics
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
@@ -347,6 +486,38 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t sme
         if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<2, true, STAR>, block, smem);
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, false, STAR>, block, smem);
+}
+
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::shared(bool vr, const MixedParams &p, int grid, size_t smem, cudaStream_t s)
+{
+    if constexpr (D == 2) {
+        if (vr) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(k_walk_shared<2, true, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_walk_shared<2, true, STAR><<<grid, kSharedBlock, smem, s>>>(p);
+            return cudaGetLastError();
+        }
+    }
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_walk_shared<D, false, STAR><<<grid, kSharedBlock, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int D, bool STAR>
+cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *blocks_per_sm)
+{
+    if constexpr (D == 2) {
+        if (vr) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(k_walk_shared<2, true, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_shared<2, true, STAR>, kSharedBlock, smem);
+        }
+    }
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_shared<D, false, STAR>, kSharedBlock, smem);
 }
 
 template <int D, bool STAR>

@@ -52,7 +52,7 @@ class FluxDesc(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("variant", ctypes.c_int), ("precision", ctypes.c_int),
                 ("sched_group", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("block_size", ctypes.c_int),
-                ("walks_per_lane", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("walks_per_lane", ctypes.c_int), ("timing", ctypes.c_int), ("tile_points", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -131,7 +131,7 @@ def _stream_of(arrays, stream):
 
 
 def make_opts(M=4, variant="plain", precision="mixed", sched_group=1, stream=None, block_size=0,
-              walks_per_lane=0, timing=False) -> Opts:
+              walks_per_lane=0, timing=False, tile_points=0) -> Opts:
     o = Opts()
     lib.woi_default_opts(ctypes.byref(o))
     o.M = int(M)
@@ -142,6 +142,7 @@ def make_opts(M=4, variant="plain", precision="mixed", sched_group=1, stream=Non
     o.block_size = int(block_size)
     o.walks_per_lane = int(walks_per_lane)
     o.timing = int(bool(timing))
+    o.tile_points = int(tile_points)
     return o
 
 

@@ -153,6 +153,30 @@ def test_shared_schedules(W, O):
         assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-3)
 
 
+@pytest.mark.parametrize("name,variant,sched_group", [("3d-nested", "plain", 1), ("3d-nested", "plain", 32),
+                                                      ("2d-concentric-vr", "vr", 1), ("star-3", "plain", 1),
+                                                      ("6d-nested", "plain", 1)])
+def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
+    """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
+    estimate is still the mean over the same walks the oracle draws for that
+    stream.  70 points = two full tiles and a ragged one; 2048 + 160 walks =
+    several walk chunks and a ragged chunk."""
+    prob = dict((c[0], c[1]) for c in CASES)[name]
+    if name.startswith("star"):
+        x = wl.star_inclusions_points(prob, 70, seed=22)
+    else:
+        x = wl.ball_points(70, prob["dim"], 23, radius=0.9)
+    n_walks = 2048 + 160
+    g = W.Geometry(prob)
+    gr = W.woi_estimate(g, x, n_walks, seed=4, M=prob["M"], variant=variant, sched_group=sched_group, tile_points=32)
+    g.close()
+    orr = O.estimate(prob, x, n_walks, seed=4, M=prob["M"], variant=variant, sched_group=sched_group, tile=32)
+    assert np.all(np.abs(gr["u"] - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12), name
+    assert np.all(np.abs(gr["grad"] - orr["grad"]) <= 1e-2 * orr["se_grad"] + 1e-12), name
+    assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-3)
+    assert np.allclose(gr["se_grad"], orr["se_grad"], rtol=1e-3)
+
+
 def test_full_size_3d_workload_sampled(W, O):
     """4096 points x 1e5 walks, M = 6, in the benchmark's launch configuration;
     the oracle recomputes sampled points (their own stream ids) with all walks."""
