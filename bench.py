@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
     ap.add_argument("--tile-points", type=int, default=0, choices=[0, 32],
                     help="32: tiles of 32 points share their walks (Sec. 4.6)")
+    ap.add_argument("--no-shared", action="store_true", help="skip the shared-trajectory comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -317,6 +318,34 @@ def main():
         fp64 = {"value": n_s / t64, "unit": "estimates/s", "points_sampled": n_s,
                 "speedup_of_mixed": value / (n_s / t64)}
 
+    # the same workload with shared trajectories (Sec. 4.6: tiles of 32 points share
+    # their walks), timed like the main steps, for comparison
+    shared = None
+    if rank == 0 and ws == 1 and args.precision == "mixed" and not args.tile_points and not args.no_shared:
+        so = dict(opt, tile_points=32)
+        so.pop("walks_per_lane", None)
+        so.pop("block_size", None)
+        for _ in range(args.warmup):
+            woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, **so)
+        sms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, timing=True, **so)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sms.append((e0.elapsed_time(e1), woi.woi_last_kernel_ms(geom)))
+        t_s = float(np.mean([a for a, _ in sms])) / 1000.0
+        k_s = float(np.mean([b for _, b in sms]))
+        n_tiles = -(-P // 32)
+        fl = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d) - alg_tally_flops(d)) + P * alg_tally_flops(d))
+        shared = {"value": P / t_s, "unit": "estimates/s", "ms_per_step": 1000.0 * t_s, "tile_points": 32,
+                  "walk_steps_per_s": P * Wk * (M + 1) / t_s, "kernel_ms": k_s,
+                  "rms_se_u": float(torch.sqrt(torch.mean(outs[2] ** 2)).item()),
+                  "roofline_frac": fl / (k_s / 1000.0) / 1e12 / peak_tflops, "speedup_of_per_point": (P / t_s) / value}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(problem, points, M, Wk)
@@ -339,7 +368,8 @@ def main():
                          "frac": achieved / peak_tflops, "traffic": TRAFFIC.get(args.workload),
                          "peak_source": f"FP32: SMs x 128 lanes x 2 x sm_max_mhz ({src})",
                          "kernel_ms": k_ms, "alg_flops_per_walk_step": alg_flops_per_walk_step(d)},
-            "cpu_baseline": cpu, "fp64_plain_gpu_path": fp64, "e2e": e2e, "clocks": clocks,
+            "cpu_baseline": cpu, "fp64_plain_gpu_path": fp64, "shared_trajectories": shared, "e2e": e2e,
+            "clocks": clocks,
             "gpu_launches": args.steps * (2 if args.precision == "mixed" else P + 1),
         }
         print(json.dumps(line))

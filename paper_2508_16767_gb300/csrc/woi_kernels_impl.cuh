@@ -488,19 +488,23 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t sme
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, false, STAR>, block, smem);
 }
 
+// the static SGeom and the dynamic records together exceed the default 48 KB per
+// block, so the dynamic limit is raised for every launch of the shared kernels
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::shared(bool vr, const MixedParams &p, int grid, size_t smem, cudaStream_t s)
 {
     if constexpr (D == 2) {
         if (vr) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k_walk_shared<2, true, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(k_walk_shared<2, true, STAR>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
             k_walk_shared<2, true, STAR><<<grid, kSharedBlock, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     k_walk_shared<D, false, STAR><<<grid, kSharedBlock, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -510,13 +514,15 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *b
 {
     if constexpr (D == 2) {
         if (vr) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k_walk_shared<2, true, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(k_walk_shared<2, true, STAR>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_shared<2, true, STAR>, kSharedBlock, smem);
         }
     }
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_shared<D, false, STAR>, kSharedBlock, smem);
 }
 
