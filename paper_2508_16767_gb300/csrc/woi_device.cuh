@@ -74,22 +74,57 @@ __device__ __forceinline__ Real u01(uint32_t w)
 {
     return ((Real)(w >> 9) + (Real)0.5) * (Real)(1.0 / 8388608.0);
 }
+// FP32: the same value without an int-to-float conversion: 1.m - (1 - 2^-24) = (2m + 1) / 2^24,
+// exact (Sterbenz) since both operands lie in [1 - 2^-24, 2)
+template <>
+__device__ __forceinline__ float u01<float>(uint32_t w)
+{
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522f;
+}
 
 template <typename Real> struct RealOps;
 template <> struct RealOps<float> {
-    __device__ static __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
+    // sin and cos of 2 pi u for a uniform u in (0, 1) (24-bit, exact in FP32): an exact
+    // reduction to a quarter turn q and a remainder r = u - q/4 in [-1/8, 1/8], the Taylor
+    // series of sin and cos at theta = 2 pi r (|theta| <= pi/4; the first omitted terms,
+    // theta^11/11! and theta^12/12!, are below 2e-9), then the rotation by q quarter turns
+    __device__ static __forceinline__ void sincos2pi(float u, float *s, float *c)
+    {
+        const float q = rintf(4.0f * u);
+        const float r = fmaf(q, -0.25f, u);                    // exact
+        const float t = r * 6.28318530717958648f;
+        const float t2 = t * t;
+        float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+        ps = fmaf(t2, ps, 1.0f / 120.0f);
+        ps = fmaf(t2, ps, -1.0f / 6.0f);
+        const float sn = fmaf(t * t2, ps, t);
+        float pc = fmaf(t2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+        pc = fmaf(t2, pc, -1.0f / 720.0f);
+        pc = fmaf(t2, pc, 1.0f / 24.0f);
+        pc = fmaf(t2, pc, -0.5f);
+        const float cs = fmaf(t2, pc, 1.0f);
+        const int k = (int)q & 3;
+        const float a = (k & 1) ? cs : sn, b = (k & 1) ? sn : cs;
+        *s = (k & 2) ? -a : a;
+        *c = ((k + 1) & 2) ? -b : b;
+    }
     __device__ static __forceinline__ float sqrt_(float v) { return sqrtf(v); }
+    // sqrt of a strictly positive argument through the reciprocal square root
+    __device__ static __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(v); }
+    __device__ static __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
     __device__ static __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
     __device__ static __forceinline__ float log_(float v) { return logf(v); }
     __device__ static __forceinline__ float fast_log(float v) { return __logf(v); }
     __device__ static __forceinline__ void sincos_(float t, float *s, float *c) { sincosf(t, s, c); }
     __device__ static __forceinline__ float fabs_(float v) { return fabsf(v); }
-    __device__ static __forceinline__ float rcp(float v) { return 1.0f / v; }
+    __device__ static __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
     __device__ static __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
 };
 template <> struct RealOps<double> {
     __device__ static __forceinline__ void sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
     __device__ static __forceinline__ double sqrt_(double v) { return sqrt(v); }
+    __device__ static __forceinline__ double sqrt_pos(double v) { return sqrt(v); }
+    __device__ static __forceinline__ double div_(double a, double b) { return a / b; }
     __device__ static __forceinline__ double rsqrt_(double v) { return 1.0 / sqrt(v); }
     __device__ static __forceinline__ double log_(double v) { return log(v); }
     __device__ static __forceinline__ double fast_log(double v) { return log(v); }
@@ -132,7 +167,7 @@ __device__ __forceinline__ void direction(const StepWords &w, Real *z)
         const Real u = u01<Real>(w.a.y);
         Real s, c;
         O::sincos2pi(u01<Real>(w.a.z), &s, &c);
-        const Real rho = (Real)2 * O::sqrt_(u * ((Real)1 - u));  // sqrt(1 - (1-2u)^2)
+        const Real rho = (Real)2 * O::sqrt_pos(u * ((Real)1 - u));  // sqrt(1 - (1-2u)^2); u in (0, 1)
         z[0] = rho * c;
         z[1] = rho * s;
         z[2] = (Real)1 - (Real)2 * u;
@@ -142,7 +177,7 @@ __device__ __forceinline__ void direction(const StepWords &w, Real *z)
         for (int j = 0; 2 * j < D; ++j) {
             const Real ua = u01<Real>(w.get(1 + 2 * j));
             const Real ub = u01<Real>(w.get(2 + 2 * j));
-            const Real rho = O::sqrt_((Real)-2 * O::log_(ua));
+            const Real rho = O::sqrt_pos((Real)-2 * O::log_(ua));   // ua < 1: log < 0
             Real s, c;
             O::sincos2pi(ub, &s, &c);
             g[2 * j] = rho * c;
@@ -908,57 +943,47 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
             return;
         }
     }
-    // circles / d-spheres: one isotropic unit vector z serves the three cases
+    // circles / d-spheres: one isotropic unit vector z serves the three cases, evaluated
+    // without branches (the lanes of a warp take different cases) and selected at the end
     Real z[D];
     direction<Real, D>(w, z);
     const Real R = g.radius[h];
-    Real b = 0;
+    Real b = 0, c0 = -R * R, r2 = 0, dot = 0;
 #pragma unroll
-    for (int c = 0; c < D; ++c) b += z[c] * dy[c];
-    if (rel == 0) {
-        // line through a point of the sphere: the other intersection, t = -2 b; Q *= 1/2, T *= q sign = +1.
-        // A tangent line (|t| at rounding level) meets the sphere only at y: q = 0 ends the walk.
-        const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
-        if (RealOps<Real>::fabs_((Real)2 * b) <= tiny * R) {
-            ch.alive = false;
-            ch.T = 0;
-            return;
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) ch.v[c] = dy[c] - (Real)2 * b * z[c];
-        ch.Q *= (Real)0.5;
-    } else if (rel == 1) {
-        // ray from inside: t = -b + sqrt(b^2 - c0) > 0 (stable form); Q *= 1, T *= +1
-        Real c0 = -R * R;
-#pragma unroll
-        for (int c = 0; c < D; ++c) c0 += dy[c] * dy[c];
-        const Real s = O::sqrt_(b * b - c0);
-        const Real t = (b <= 0) ? (s - b) : (-c0) / (b + s);
-#pragma unroll
-        for (int c = 0; c < D; ++c) ch.v[c] = dy[c] + t * z[c];
-    } else {
-        // uniform y' = c_h + R z (normal z); Q *= K*(y', y) |dOmega_h| = (y'-y).z / (omega_d r^d) |dOmega_h|
-        Real r2 = 0, dot = 0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const Real vn = R * z[c];
-            const Real diff = vn - dy[c];
-            r2 += diff * diff;
-            dot += diff * z[c];
-            ch.v[c] = vn;
-        }
-        constexpr double omega = D == 2 ? 2.0 * PI : (D == 3 ? 4.0 * PI : (D == 4 ? 2.0 * PI * PI : (D == 5 ? 8.0 * PI * PI / 3.0 : PI * PI * PI)));
-        Real inv_rd;
-        if constexpr (D == 2) {
-            inv_rd = O::rcp(r2);
-        } else {
-            const Real ir = O::rsqrt_(r2);
-            inv_rd = ir;
-#pragma unroll
-            for (int k = 1; k < D; ++k) inv_rd *= ir;
-        }
-        ch.Q *= dot * inv_rd * (Real)(1.0 / omega) * g.area[h];
+    for (int c = 0; c < D; ++c) {
+        b += z[c] * dy[c];
+        c0 += dy[c] * dy[c];
+        const Real diff = R * z[c] - dy[c];
+        r2 += diff * diff;
+        dot += diff * z[c];
     }
+    // same surface: line through a point of the sphere, the other intersection at t = -2 b;
+    // Q *= 1/2, T *= q sign = +1.  A tangent line (|t| at rounding level) meets the sphere
+    // only at y: q = 0 ends the walk.
+    const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
+    if (rel == 0 && O::fabs_((Real)2 * b) <= tiny * R) {
+        ch.alive = false;
+        ch.T = 0;
+        return;
+    }
+    // descendant: ray from inside, t = -b + sqrt(b^2 - c0) > 0 in the stable form; Q, T unchanged
+    const Real sq = O::sqrt_(b * b - c0 > 0 ? b * b - c0 : (Real)0);
+    const Real t_ray = (b <= 0) ? (sq - b) : O::div_(-c0, b + sq);
+    // otherwise: uniform y' = c_h + R z (normal z); Q *= K*(y', y) |dOmega_h| = (y'-y).z / (omega_d r^d) |dOmega_h|
+    constexpr double omega = D == 2 ? 2.0 * PI : (D == 3 ? 4.0 * PI : (D == 4 ? 2.0 * PI * PI : (D == 5 ? 8.0 * PI * PI / 3.0 : PI * PI * PI)));
+    Real inv_rd;
+    if constexpr (D == 2) {
+        inv_rd = O::rcp(r2);
+    } else {
+        const Real ir = O::rsqrt_(r2);
+        inv_rd = ir;
+#pragma unroll
+        for (int k = 1; k < D; ++k) inv_rd *= ir;
+    }
+    const Real t = rel == 0 ? (Real)-2 * b : t_ray;
+#pragma unroll
+    for (int c = 0; c < D; ++c) ch.v[c] = rel == 2 ? R * z[c] : dy[c] + t * z[c];
+    ch.Q *= rel == 0 ? (Real)0.5 : (rel == 1 ? (Real)1 : dot * inv_rd * (Real)(1.0 / omega) * g.area[h]);
     ch.s = h;
 }
 
