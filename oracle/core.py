@@ -13,7 +13,11 @@ module prepares its inputs from a problem dictionary with numpy/scipy:
     turned into integer thresholds T_n = floor(2^32 C_n / A), C_n the cumulative
     sum of |alpha| in surface order and A = ||alpha||_1 (T_N = 2^32);
   * Sec. 1: the tree (strict-descendant relation) from the parent array;
-  * |dOmega_i| (circle / d-sphere closed form, star by Gauss-Legendre quadrature);
+  * |dOmega_i| (circle / d-sphere closed form, star by Gauss-Legendre quadrature,
+    ellipsoid by a one-dimensional integral for the mean area ratio, see
+    ellipsoid_area);
+  * ellipsoids (Sec. 5, Example 2): the eigen-decomposition A = R diag(1/a^2) R^T
+    that maps the unit sphere onto the surface;
   * Sec. 4.4: the beta >= 0 / beta < 0 arcs of 2D surfaces for the variance-
     reduced estimator, by a dense sign scan and Brent's method.
 """
@@ -36,8 +40,9 @@ MAX_DIM = 6
 MAX_STAR = 16
 STAR_PANELS = 256
 STAR_SCAN = 4096
-SPHERE, STAR = 0, 1
-FLUX = {"zero": 0, "fourier": 1, "real_sh": 2, "harmonic_poly": 3}
+SPHERE, STAR, ELLIPSOID = 0, 1, 2
+KIND = {"sphere": SPHERE, "star": STAR, "ellipsoid": ELLIPSOID}
+FLUX = {"zero": 0, "fourier": 1, "real_sh": 2, "harmonic_poly": 3, "point_charge": 4}
 
 
 def build(force: bool = False) -> str:
@@ -96,7 +101,7 @@ class OrProblem(ctypes.Structure):
          "beta_scale", "thresh"]] + [("alpha_l1", ctypes.c_double)] + [
         (n, ctypes.c_void_p) for n in
         ["flux_basis", "flux_off", "flux_n", "flux_coef", "arc_off", "arc_n", "arc_t0", "arc_t1", "arc_sign",
-         "arc_len", "part_len"]]
+         "arc_len", "part_len", "ell_A", "ell_map", "ell_inva", "ell_jmax"]]
 
 
 class OrOpts(ctypes.Structure):
@@ -213,9 +218,47 @@ def star_arclen_panels(s):
     return out
 
 
+def ellipsoid_axes(s):
+    """Eigen-decomposition of the ellipsoid matrix: A = R diag(lam) R^T, semi-axes
+    a = lam^{-1/2}; y = c + R diag(a) u maps the unit sphere onto the surface."""
+    A = np.asarray(s["matrix"], dtype=np.float64)
+    lam, R = np.linalg.eigh(0.5 * (A + A.T))
+    if np.any(lam <= 0):
+        raise ValueError("ellipsoid matrix must be positive definite")
+    return lam, R
+
+
+def ellipsoid_area(dim, lam):
+    """|dE| for E = {y : y^T A y <= 1} with eigenvalues lam of A.
+
+    The map u -> diag(a) u (a = lam^{-1/2}) takes the unit sphere onto dE and
+    scales area by J(u) prod(a), J(u) = |diag(sqrt(lam)) u|, so |dE| =
+    |S^{d-1}| prod(a) E_u[J].  With a standard normal g = |g| u (|g| and u
+    independent), E_u[J] = E sqrt(S) / E|g| for S = sum lam_k g_k^2, and
+    sqrt(S) = (1 / (2 sqrt(pi))) int_0^inf (1 - exp(-s S)) s^{-3/2} ds gives
+    E sqrt(S) = (1 / sqrt(pi)) int_0^inf (1 - prod_k (1 + 2 lam_k t^2)^{-1/2}) t^{-2} dt
+    (s = t^2, E exp(-s lam g^2) = (1 + 2 s lam)^{-1/2}); E|g| = sqrt(2) Gamma((d+1)/2) / Gamma(d/2)."""
+    lam = np.asarray(lam, dtype=np.float64)
+
+    def f(t):
+        if t == 0.0:
+            return float(np.sum(lam))
+        # 1 - prod (1 + x_k)^{-1/2} without cancellation at small t
+        return -math.expm1(-0.5 * float(np.sum(np.log1p(2.0 * lam * t * t)))) / (t * t)
+
+    scale = 1.0 / math.sqrt(float(np.max(lam)))
+    I1, _ = integrate.quad(f, 0.0, 50.0 * scale, epsabs=0, epsrel=1e-13, limit=500)
+    I2, _ = integrate.quad(f, 50.0 * scale, np.inf, epsabs=0, epsrel=1e-13, limit=500)
+    e_sqrt_s = (I1 + I2) / math.sqrt(math.pi)
+    e_norm = math.sqrt(2.0) * math.exp(math.lgamma((dim + 1) / 2) - math.lgamma(dim / 2))
+    return omega(dim) * float(np.prod(lam ** -0.5)) * e_sqrt_s / e_norm
+
+
 def surface_area(dim, s):
     if s["kind"] == "sphere":
         return omega(dim) * s["radius"] ** (dim - 1)
+    if s["kind"] == "ellipsoid":
+        return ellipsoid_area(dim, ellipsoid_axes(s)[0])
     return float(star_arclen_panels(s)[-1])
 
 
@@ -281,9 +324,13 @@ class Prepared:
         parent = [int(p) for p in problem["parent"]]
         sigma = [float(s) for s in problem["sigma"]]
         self.dim, self.n = d, n
-        self.type = np.array([SPHERE if s["kind"] == "sphere" else STAR for s in surfs], dtype=np.int32)
+        self.type = np.array([KIND[s["kind"]] for s in surfs], dtype=np.int32)
         self.center = np.zeros((n, MAX_DIM))
-        self.radius = np.array([s["radius"] for s in surfs], dtype=np.float64)
+        self.radius = np.array([s.get("radius", 0.0) for s in surfs], dtype=np.float64)
+        self.ell_A = np.zeros((n, MAX_DIM, MAX_DIM))
+        self.ell_map = np.zeros((n, MAX_DIM, MAX_DIM))
+        self.ell_inva = np.zeros((n, MAX_DIM))
+        self.ell_jmax = np.zeros(n)
         self.star_K = np.zeros(n, dtype=np.int32)
         self.star_a = np.zeros((n, MAX_STAR + 1))
         self.star_b = np.zeros((n, MAX_STAR + 1))
@@ -291,6 +338,12 @@ class Prepared:
         self.star_scan = np.zeros((n, STAR_SCAN + 1, 2))
         for i, s in enumerate(surfs):
             self.center[i, :d] = s["center"]
+            if s["kind"] == "ellipsoid":
+                lam, R = ellipsoid_axes(s)
+                self.ell_A[i, :d, :d] = np.asarray(s["matrix"], dtype=np.float64)
+                self.ell_map[i, :d, :d] = R * (lam ** -0.5)[None, :]
+                self.ell_inva[i, :d] = np.sqrt(lam)
+                self.ell_jmax[i] = math.sqrt(float(np.max(lam)))
             if s["kind"] == "star":
                 K = len(s["star_a"]) - 1
                 self.star_K[i] = K
@@ -337,7 +390,8 @@ class Prepared:
             self.thresh.ctypes.data, float(self.alpha_l1), self.flux_basis.ctypes.data, self.flux_off.ctypes.data,
             self.flux_n.ctypes.data, self.flux_coef.ctypes.data, self.arc_off.ctypes.data,
             self.arc_n.ctypes.data, self.arc_t0.ctypes.data, self.arc_t1.ctypes.data, self.arc_sign.ctypes.data,
-            self.arc_len.ctypes.data, self.part_len.ctypes.data)
+            self.arc_len.ctypes.data, self.part_len.ctypes.data, self.ell_A.ctypes.data, self.ell_map.ctypes.data,
+            self.ell_inva.ctypes.data, self.ell_jmax.ctypes.data)
 
 
 VARIANTS = {"plain": 0, "vr": 1}

@@ -26,6 +26,12 @@
  *     beta < 0 parts of the first interface).
  *   - Sec. 4.5, Eq. naive_woi_grad_estimator: the gradient tally uses
  *     grad_x Phi on the same trajectory.
+ *   - Sec. 5, Example 2: ellipsoids (y - c)^T A (y - c) = 1 as surfaces, with
+ *     the point-charge potential |x - x0|^{2-d} as manufactured solution.
+ *     Uniform points by surface measure come from a uniform point u of the
+ *     unit sphere mapped to y = c + R diag(a) u (A = R diag(1/a^2) R^T),
+ *     accepted with probability J(u) / max J, J(u) = |diag(1/a) u| the area
+ *     ratio of the map (von Neumann rejection).
  *
  * Readings of the paper taken here (each one is listed with its reason in
  * the design notes of the repository):
@@ -48,8 +54,11 @@
 #define OR_STAR_SCAN 4096
 #define OR_STAR_PANELS 256
 
-enum { OR_SPHERE = 0, OR_STAR = 1 };
-enum { OR_FLUX_ZERO = 0, OR_FLUX_FOURIER = 1, OR_FLUX_REAL_SH = 2, OR_FLUX_HARMONIC_POLY = 3 };
+#define OR_ELL_ATTEMPTS 64   /* rejection attempts for a uniform point on an ellipsoid; the last one is kept */
+
+enum { OR_SPHERE = 0, OR_STAR = 1, OR_ELLIPSOID = 2 };
+enum { OR_FLUX_ZERO = 0, OR_FLUX_FOURIER = 1, OR_FLUX_REAL_SH = 2, OR_FLUX_HARMONIC_POLY = 3,
+       OR_FLUX_POINT_CHARGE = 4 };
 enum { OR_REL_SAME = 0, OR_REL_DESC = 1, OR_REL_OTHER = 2 };
 
 /* Planted-mistake switch.  Only the tests that show that the pins detect
@@ -91,6 +100,10 @@ typedef struct {
     const int *arc_sign;      /* +1: part of dOmega^+ (beta >= 0), -1: dOmega^- */
     const double *arc_len;
     const double *part_len;   /* [n_surf][2] |dOmega^+|, |dOmega^-| */
+    const double *ell_A;      /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] ellipsoid matrix A (row-major) */
+    const double *ell_map;    /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] R diag(a): unit sphere -> ellipsoid */
+    const double *ell_inva;   /* [n_surf][OR_MAX_DIM] 1 / a_k (the columns of ell_map in order) */
+    const double *ell_jmax;   /* [n_surf] max_k 1 / a_k */
 } or_problem;
 
 typedef struct {
@@ -136,17 +149,22 @@ typedef struct {
     uint32_t words[4];
 } or_rng;
 
-static uint32_t or_word(or_rng *r, int step, int chain, int k)
+/* word k of attempt `attempt` of a (step, chain) stream: counter word 3 is
+ * (attempt << 9) | (chain << 4) | sub; attempt 0 is the stream itself, later
+ * attempts serve rejection sampling */
+static uint32_t or_word_at(or_rng *r, int step, int chain, int attempt, int k)
 {
-    int sub = k >> 2;
+    int sub = (attempt << 5) | (k >> 2);
     if (r->cached_step != step || r->cached_chain != chain || r->cached_sub != sub) {
         uint32_t ctr[4] = {(uint32_t)r->walk, (uint32_t)(r->walk >> 32), (uint32_t)step,
-                           (uint32_t)((chain << 4) | sub)};
+                           ((uint32_t)attempt << 9) | (uint32_t)((chain << 4) | (k >> 2))};
         or_philox4x32_10(ctr, r->key, r->words);
         r->cached_step = step; r->cached_chain = chain; r->cached_sub = sub;
     }
     return r->words[k & 3];
 }
+
+static uint32_t or_word(or_rng *r, int step, int chain, int k) { return or_word_at(r, step, chain, 0, k); }
 
 /* uniform on (0,1) from the top 23 bits: (2k+1) / 2^24 with k < 2^23, a value
  * that FP32 and FP64 both represent exactly */
@@ -270,22 +288,37 @@ static void or_normal(const or_problem *P, int h, const double *y, double *n)
     if (P->type[h] == OR_SPHERE) {
         const double *c = or_center(P, h);
         for (int k = 0; k < d; ++k) n[k] = (y[k] - c[k]) / P->radius[h];
+    } else if (P->type[h] == OR_ELLIPSOID) {
+        /* grad of (y - c)^T A (y - c) is 2 A (y - c) */
+        const double *c = or_center(P, h), *A = P->ell_A + (size_t)h * OR_MAX_DIM * OR_MAX_DIM;
+        double nn = 0.0;
+        for (int k = 0; k < d; ++k) {
+            n[k] = 0.0;
+            for (int j = 0; j < d; ++j) n[k] += A[k * OR_MAX_DIM + j] * (y[j] - c[j]);
+            nn += n[k] * n[k];
+        }
+        nn = sqrt(nn);
+        for (int k = 0; k < d; ++k) n[k] /= nn;
     } else {
         or_star_speed_normal(P, h, or_param_angle(P, h, y), n);
     }
 }
 
-/* isotropic unit direction from the words 1.. of a (step, chain) stream */
-static void or_direction(or_rng *r, int d, int step, int chain, double *z)
+/* index of the word that picks one of q intersections (and, on an ellipsoid,
+ * decides a rejection attempt: a uniform transition makes no pick) */
+static int or_choice_word(int d) { return d == 2 ? 2 : (d == 3 ? 3 : (d == 4 ? 5 : 7)); }
+
+/* isotropic unit direction from the words 1.. of attempt `a` of a (step, chain) stream */
+static void or_direction_at(or_rng *r, int d, int step, int chain, int a, double *z)
 {
     if (d == 2) {
-        double phi = 2.0 * M_PI * or_u01(or_word(r, step, chain, 1));
+        double phi = 2.0 * M_PI * or_u01(or_word_at(r, step, chain, a, 1));
         z[0] = cos(phi); z[1] = sin(phi);
         return;
     }
     if (d == 3) {
-        double zz = 1.0 - 2.0 * or_u01(or_word(r, step, chain, 1));
-        double phi = 2.0 * M_PI * or_u01(or_word(r, step, chain, 2));
+        double zz = 1.0 - 2.0 * or_u01(or_word_at(r, step, chain, a, 1));
+        double phi = 2.0 * M_PI * or_u01(or_word_at(r, step, chain, a, 2));
         double rho = sqrt(1.0 - zz * zz);
         z[0] = rho * cos(phi); z[1] = rho * sin(phi); z[2] = zz;
         return;
@@ -293,8 +326,8 @@ static void or_direction(or_rng *r, int d, int step, int chain, double *z)
     /* d >= 4: Box-Muller on pairs of words (1,2), (3,4), (5,6), then normalise */
     double g[OR_MAX_DIM + 1], nrm = 0.0;
     for (int j = 0; 2 * j < d; ++j) {
-        double ua = or_u01(or_word(r, step, chain, 1 + 2 * j));
-        double ub = or_u01(or_word(r, step, chain, 2 + 2 * j));
+        double ua = or_u01(or_word_at(r, step, chain, a, 1 + 2 * j));
+        double ub = or_u01(or_word_at(r, step, chain, a, 2 + 2 * j));
         double rho = sqrt(-2.0 * log(ua));
         g[2 * j] = rho * cos(2.0 * M_PI * ub);
         g[2 * j + 1] = rho * sin(2.0 * M_PI * ub);
@@ -304,8 +337,8 @@ static void or_direction(or_rng *r, int d, int step, int chain, double *z)
     for (int k = 0; k < d; ++k) z[k] = g[k] / nrm;
 }
 
-/* index of the word that picks one of q intersections */
-static int or_choice_word(int d) { return d == 2 ? 2 : (d == 3 ? 3 : (d == 4 ? 5 : 7)); }
+static void or_direction(or_rng *r, int d, int step, int chain, double *z) { or_direction_at(r, d, step, chain, 0, z); }
+
 
 /* uniform point on dOmega_h (Eq. naive_woi_p0; by surface measure) */
 static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, int chain, double *y)
@@ -316,6 +349,23 @@ static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, in
         or_direction(r, d, step, chain, z);
         const double *c = or_center(P, h);
         for (int k = 0; k < d; ++k) y[k] = c[k] + P->radius[h] * z[k];
+    } else if (P->type[h] == OR_ELLIPSOID) {
+        /* u uniform on the unit sphere, accepted when v^2 max J^2 <= J(u)^2 with v the
+         * attempt's choice word and J(u)^2 = sum_k u_k^2 / a_k^2 */
+        const double *c = or_center(P, h), *Mp = P->ell_map + (size_t)h * OR_MAX_DIM * OR_MAX_DIM;
+        const double *ia = P->ell_inva + (size_t)h * OR_MAX_DIM, jm = P->ell_jmax[h];
+        double z[OR_MAX_DIM];
+        for (int a = 0; a < OR_ELL_ATTEMPTS; ++a) {
+            or_direction_at(r, d, step, chain, a, z);
+            double J2 = 0.0;
+            for (int k = 0; k < d; ++k) J2 += z[k] * z[k] * ia[k] * ia[k];
+            double v = or_u01(or_word_at(r, step, chain, a, or_choice_word(d)));
+            if (v * v * jm * jm <= J2) break;
+        }
+        for (int k = 0; k < d; ++k) {
+            y[k] = c[k];
+            for (int j = 0; j < d; ++j) y[k] += Mp[k * OR_MAX_DIM + j] * z[j];
+        }
     } else {
         double s = or_u01(or_word(r, step, chain, 1)) * P->area[h];
         double t = or_star_invert(P, h, s, 0.0, 2.0 * M_PI);
@@ -376,6 +426,31 @@ static int or_intersections(const or_problem *P, int h, const double *y, const d
         for (int j = 0; j < 2; ++j) {
             double t = cand[j];
             if (ray ? (t > tiny * R) : (fabs(t) > tiny * R)) ts[q++] = t;
+        }
+        return q;
+    }
+    if (P->type[h] == OR_ELLIPSOID) {
+        /* (dy + t z)^T A (dy + t z) = 1: a2 t^2 + 2 b1 t + c0 = 0 */
+        const double *c = or_center(P, h), *A = P->ell_A + (size_t)h * OR_MAX_DIM * OR_MAX_DIM;
+        double dy[OR_MAX_DIM], a2 = 0.0, b1 = 0.0, c0 = -1.0;
+        for (int k = 0; k < d; ++k) dy[k] = y[k] - c[k];
+        for (int k = 0; k < d; ++k)
+            for (int j = 0; j < d; ++j) {
+                double Akj = A[k * OR_MAX_DIM + j];
+                a2 += z[k] * Akj * z[j];
+                b1 += z[k] * Akj * dy[j];
+                c0 += dy[k] * Akj * dy[j];
+            }
+        double disc = b1 * b1 - a2 * c0;
+        if (disc < 0.0) return 0;
+        double sq = sqrt(disc);
+        double qq = -(b1 + (b1 >= 0 ? sq : -sq));
+        double r1 = qq / a2, r2 = (qq != 0.0) ? c0 / qq : 0.0;
+        double cand[2] = {r1 < r2 ? r1 : r2, r1 < r2 ? r2 : r1};
+        double scale = 1.0 / P->ell_jmax[h];      /* smallest semi-axis */
+        for (int j = 0; j < 2; ++j) {
+            double t = cand[j];
+            if (ray ? (t > tiny * scale) : (fabs(t) > tiny * scale)) ts[q++] = t;
         }
         return q;
     }
@@ -539,6 +614,16 @@ static double or_flux(const or_problem *P, int h, const double *y)
         for (int k = 0; k < d; ++k) v += nrm[k] * grad[k];
         return s * v;
     }
+    case OR_FLUX_POINT_CHARGE: { /* [s, x0_1..x0_d]: b = s n . grad_y |y - x0|^{2-d} (d >= 3) */
+        double nrm[OR_MAX_DIM], r2 = 0.0, dot = 0.0;
+        or_normal(P, h, y, nrm);
+        for (int k = 0; k < d; ++k) {
+            double e = y[k] - c[1 + k];
+            r2 += e * e;
+            dot += e * nrm[k];
+        }
+        return c[0] * (2.0 - d) * pow(r2, -0.5 * d) * dot;
+    }
     default:
         return 0.0;
     }
@@ -586,6 +671,13 @@ static double or_flux_mag(const or_problem *P, int h, const double *y)
             }
         }
         return fabs(c[0]) * m;
+    }
+    case OR_FLUX_POINT_CHARGE: {
+        double nrm[OR_MAX_DIM], r2 = 0.0;
+        or_normal(P, h, y, nrm);
+        for (int k = 0; k < d; ++k) r2 += (y[k] - c[1 + k]) * (y[k] - c[1 + k]);
+        for (int k = 0; k < d; ++k) m += fabs((y[k] - c[1 + k]) * nrm[k]);
+        return fabs(c[0] * (2.0 - d)) * pow(r2, -0.5 * d) * m;
     }
     default:
         return 0.0;

@@ -9,9 +9,11 @@ it with its own code.
 Problem dictionary (JSON-compatible):
 
     dim       int, 2..6
-    surfaces  list of {"kind": "sphere" | "star", "center": [dim], "radius": R,
-              "star_a": [K+1], "star_b": [K+1]}  (star: 2D only,
-              r(t) = R (1 + sum_k a_k cos kt + b_k sin kt), index 0 unused)
+    surfaces  list of {"kind": "sphere" | "star" | "ellipsoid", "center": [dim],
+              "radius": R, "star_a": [K+1], "star_b": [K+1], "matrix": [dim][dim]}
+              (star: 2D only, r(t) = R (1 + sum_k a_k cos kt + b_k sin kt), index 0
+              unused; ellipsoid: d >= 3, (y - c)^T A (y - c) = 1 with A = matrix
+              symmetric positive definite)
     parent    list of int, parent[0] = -1 (the outer boundary dOmega_1),
               parent[i] = index of the region that contains region i
     sigma     list of float, conductivity inside each region (sigma_1 > 0)
@@ -23,6 +25,8 @@ Problem dictionary (JSON-compatible):
                                harmonics of the unit direction from the centre (3D)
               "harmonic_poly"  [s, T, (c, e_1..e_dim) x T]: b(y) = s n(y).grad P(y)
                                with P(y) = sum c prod y_k^e_k harmonic
+              "point_charge"   [s, x0_1..x0_dim]: b(y) = s n(y).grad |y - x0|^{2-dim}
+                               (dim >= 3)
     M         default truncation for this workload
 
 The recipes follow the synthetic workloads used to measure the estimator:
@@ -38,6 +42,11 @@ import numpy as np
 
 def _sphere(center, radius):
     return {"kind": "sphere", "center": [float(c) for c in center], "radius": float(radius)}
+
+
+def _ellipsoid(center, matrix):
+    return {"kind": "ellipsoid", "center": [float(c) for c in center],
+            "matrix": [[float(v) for v in row] for row in np.asarray(matrix, dtype=np.float64)]}
 
 
 def _star(center, radius, a, b):
@@ -348,10 +357,82 @@ def batch_instances(n_inst=256, seed=5, k_max=64, p_range=(16, 4096), w_range=(1
     return out
 
 
+# ---------------------------------------------------------------------------
+# nested ellipsoids with the point-charge potential (the paper's Example 2)
+# ---------------------------------------------------------------------------
+
+def ellipsoids_problem(dim, M=None):
+    """Three nested ellipsoids (Example 2, Table of ellipsoid parameters):
+    Omega_1 centre (1.3, 0, ...), diag(A) = [1, 0.9, 1.2, ...], sigma 1.1;
+    Omega_2 centre (1.4, 0, ...), diag(A) = [1.5, 3.2, 2, ...], A_12 = A_21 = -1, sigma 1.3;
+    Omega_3 centre (1.6, 0, ...), diag(A) = [8, 6, 4, ...], A_12 = A_21 = -2, sigma 0.9.
+    Data of the manufactured solution u = |x|^{2-dim} (a point charge at the
+    origin, outside every region): Neumann flux sigma_1 d_n u on the outer
+    surface and jumps (sigma_p - sigma_i) d_n u across the interfaces.
+    M as in the paper's table: 5, 6, 7, 8 for dim 3..6.
+
+    As printed, Omega_2 (centre 1.4) reaches outside Omega_1 (the quadratic form
+    of Omega_1 reaches 1.14 on it); its centre is taken at (1.3, 0, ...), the
+    centre of Omega_1, which nests the three ellipsoids (forms <= 0.95 on the
+    inner surfaces) and changes nothing else."""
+    if dim < 3:
+        raise ValueError("the point-charge workload needs dim >= 3")
+
+    def mat(diag, off):
+        A = np.diag(np.asarray(diag, dtype=np.float64))
+        A[0, 1] = A[1, 0] = off
+        return A
+
+    e1 = [0.0] * dim
+    A1 = mat([1.0, 0.9] + [1.2] * (dim - 2), 0.0)
+    A2 = mat([1.5, 3.2] + [2.0] * (dim - 2), -1.0)
+    A3 = mat([8.0, 6.0] + [4.0] * (dim - 2), -2.0)
+    c1, c2, c3 = ([x] + e1[1:] for x in (1.3, 1.3, 1.6))
+    sigma = [1.1, 1.3, 0.9]
+    parent = [-1, 0, 1]
+    zero = [0.0] * dim
+    flux = [{"basis": "point_charge", "coef": [sigma[0]] + zero},
+            {"basis": "point_charge", "coef": [sigma[0] - sigma[1]] + zero},
+            {"basis": "point_charge", "coef": [sigma[1] - sigma[2]] + zero}]
+    return {"name": f"{dim}d-ellipsoids", "dim": dim,
+            "surfaces": [_ellipsoid(c1, A1), _ellipsoid(c2, A2), _ellipsoid(c3, A3)],
+            "parent": parent, "sigma": sigma, "flux": flux, "M": {3: 5, 4: 6, 5: 7, 6: 8}[dim] if M is None else M}
+
+
+def inside_ellipsoid(s, p):
+    c = np.asarray(s["center"], dtype=np.float64)
+    A = np.asarray(s["matrix"], dtype=np.float64)
+    e = np.atleast_2d(p) - c
+    return np.einsum("ni,ij,nj->n", e, A, e) < 1.0
+
+
+def ellipsoid_points(problem, n, seed=16):
+    """n points uniform in the outer ellipsoid (rejection from its bounding box)."""
+    s = problem["surfaces"][0]
+    A = np.asarray(s["matrix"], dtype=np.float64)
+    c = np.asarray(s["center"], dtype=np.float64)
+    half = np.sqrt(np.diag(np.linalg.inv(A)))          # half-widths of the bounding box
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        p = c + rng.uniform(-1.0, 1.0, size=(4 * n, len(c))) * half
+        out += list(p[inside_ellipsoid(s, p)])
+    return np.ascontiguousarray(np.asarray(out[:n], dtype=np.float64))
+
+
+def point_charge(x):
+    """u = |x|^{2-d} and grad u = (2 - d) |x|^{-d} x (the manufactured solution)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    d = x.shape[1]
+    r = np.linalg.norm(x, axis=1)
+    return r ** (2 - d), (2 - d) * (r ** -d)[:, None] * x
+
+
 CONFIGS = {
     "2d-concentric": "unit disk + r=0.5 inclusion, 64 polar-grid points, W=1e4, M=4",
     "3d-nested": "spheres 1/0.8/0.5, sigma 1/5/0.2, 4096 ball points, W=1e5, M=6",
     "2d-star-inclusions": "star + 32 circles, 16384 points (30% near surfaces), W=1e5, M=4",
     "6d-nested": "hyperspheres 1/0.6, sigma 1/4, 1024 ball points, W=1e6, M=8",
     "batch": "256 manufactured 2D/3D instances, 1-64 inclusions, P 16..4096, W 1e4..1e5",
+    "ellipsoids": "3 nested ellipsoids (Example 2), point charge at the origin, 3D-6D, M = d + 2",
 }
