@@ -38,8 +38,10 @@ sys.path.insert(0, ROOT)
 # Algorithmic FP32 flops per walk-step (FMA = 2) of the walk on circles /
 # d-spheres: 11 d + 15 (direction sampling, one transition and the Phi /
 # grad Phi tally); 2D circles 30.  Derivation in the design notes.
-def alg_flops_per_walk_step(dim: int) -> float:
-    return 30.0 if dim == 2 else 11.0 * dim + 15.0
+def alg_flops_per_walk_step(dim: int, ellipsoid: bool = False) -> float:
+    # ellipsoids add the two matrix-vector products A z and A (y - c) of the line / ray
+    # quadratic: 4 d^2
+    return 30.0 if dim == 2 else 11.0 * dim + 15.0 + (4.0 * dim * dim if ellipsoid else 0.0)
 
 
 # of which the Phi / grad Phi tally at one point: 2D 14, d-spheres 5 d + 8
@@ -57,6 +59,8 @@ WORKLOADS = {
     "2d-concentric": dict(points=64, walks=10_000, M=4),
     "2d-star-inclusions": dict(points=16384, walks=100_000, M=4),
     "6d-nested": dict(points=1024, walks=1_000_000, M=8),
+    "3d-ellipsoids": dict(points=4096, walks=100_000, M=5),
+    "6d-ellipsoids": dict(points=1024, walks=1_000_000, M=8),
     "batch": dict(points=None, walks=None, M=None),
 }
 
@@ -72,6 +76,10 @@ def make_workload(name):
         return p, wl.star_inclusions_points(p, 16384)
     if name == "6d-nested":
         return wl.nested_6d_problem(), wl.ball_points(1024, 6, 14)
+    if name in ("3d-ellipsoids", "6d-ellipsoids"):
+        d = int(name[0])
+        p = wl.ellipsoids_problem(d)
+        return p, wl.ellipsoid_points(p, WORKLOADS[name]["points"], seed=16)
     raise ValueError(name)
 
 
@@ -228,6 +236,7 @@ def main():
     if args.points:
         points = np.ascontiguousarray(points[:args.points])
     P, d, Wk, M = len(points), problem["dim"], cfg["walks"], cfg["M"]
+    ell = any(srf["kind"] == "ellipsoid" for srf in problem["surfaces"])
     geom = woi.Geometry(problem)
     stream = torch.cuda.Stream()
     xd = torch.from_numpy(points).cuda()
@@ -280,9 +289,9 @@ def main():
     if args.tile_points:
         # one walk per tile of 32 points, tallied at each of them
         n_tiles = -(-P // args.tile_points)
-        flops = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d) - alg_tally_flops(d)) + P * alg_tally_flops(d))
+        flops = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d, ell) - alg_tally_flops(d)) + P * alg_tally_flops(d))
     else:
-        flops = P * Wk * (M + 1) * alg_flops_per_walk_step(d)
+        flops = P * Wk * (M + 1) * alg_flops_per_walk_step(d, ell)
     achieved = flops / (k_ms / 1000.0) / 1e12
     rms_se = float(torch.sqrt(torch.mean(outs[2] ** 2)).item()) if ws == 1 else None
 
@@ -340,7 +349,7 @@ def main():
         t_s = float(np.mean([a for a, _ in sms])) / 1000.0
         k_s = float(np.mean([b for _, b in sms]))
         n_tiles = -(-P // 32)
-        fl = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d) - alg_tally_flops(d)) + P * alg_tally_flops(d))
+        fl = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d, ell) - alg_tally_flops(d)) + P * alg_tally_flops(d))
         shared = {"value": P / t_s, "unit": "estimates/s", "ms_per_step": 1000.0 * t_s, "tile_points": 32,
                   "walk_steps_per_s": P * Wk * (M + 1) / t_s, "kernel_ms": k_s,
                   "rms_se_u": float(torch.sqrt(torch.mean(outs[2] ** 2)).item()),
@@ -367,7 +376,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved / peak_tflops, "traffic": TRAFFIC.get(args.workload),
                          "peak_source": f"FP32: SMs x 128 lanes x 2 x sm_max_mhz ({src})",
-                         "kernel_ms": k_ms, "alg_flops_per_walk_step": alg_flops_per_walk_step(d)},
+                         "kernel_ms": k_ms, "alg_flops_per_walk_step": alg_flops_per_walk_step(d, ell)},
             "cpu_baseline": cpu, "fp64_plain_gpu_path": fp64, "shared_trajectories": shared, "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": args.steps * (2 if args.precision == "mixed" else P + 1),

@@ -68,18 +68,24 @@ typedef enum {
     WOI_E_STATE = 9          /* call order violated (e.g. estimate before set_sigma_and_data) */
 } woi_status;
 
+#define WOI_MAX_ELLIPSOIDS 8
+
 /* surface kinds */
-enum { WOI_SPHERE = 0,  /* circle (2D) or (d-1)-sphere: centre, radius */
-       WOI_STAR = 1 };  /* 2D star-shaped curve about `center`:
-                           r(t) = radius (1 + sum_{k=1..K} a_k cos kt + b_k sin kt) */
+enum { WOI_SPHERE = 0,     /* circle (2D) or (d-1)-sphere: centre, radius */
+       WOI_STAR = 1,       /* 2D star-shaped curve about `center`:
+                              r(t) = radius (1 + sum_{k=1..K} a_k cos kt + b_k sin kt) */
+       WOI_ELLIPSOID = 2 }; /* d >= 3: (y - center)^T A (y - center) = 1, A = matrix symmetric
+                              positive definite (Sec. 5, Example 2); at most WOI_MAX_ELLIPSOIDS
+                              per geometry */
 
 typedef struct {
-    int type;                         /* WOI_SPHERE or WOI_STAR */
+    int type;                         /* WOI_SPHERE, WOI_STAR or WOI_ELLIPSOID */
     double center[WOI_MAX_DIM];       /* first `dim` entries used */
-    double radius;                    /* sphere radius, or the star's base radius */
+    double radius;                    /* sphere radius, or the star's base radius (unused for ellipsoids) */
     int star_degree;                  /* K (star only), 0..WOI_MAX_STAR_DEGREE */
     const double *star_a;             /* [K+1], index 0 ignored (star only) */
     const double *star_b;             /* [K+1], index 0 ignored (star only) */
+    const double *matrix;             /* [dim][dim] row-major A (ellipsoid only) */
 } woi_surface_desc;
 
 /* flux bases (the data b_i of Sec. 1 on each surface) */
@@ -90,8 +96,11 @@ enum {
     WOI_FLUX_REAL_SH = 2,       /* 3D spheres: coef[l*l + l + m], l <= 4, orthonormal real
                                    spherical harmonics of the unit vector from the centre, no
                                    Condon-Shortley phase: sin(phi) cos(theta) = sqrt(4pi/3) Y_1^1 */
-    WOI_FLUX_HARMONIC_POLY = 3  /* any d: coef = [s, T, (c, e_1..e_d) x T];
+    WOI_FLUX_HARMONIC_POLY = 3, /* any d: coef = [s, T, (c, e_1..e_d) x T];
                                    b(y) = s n(y) . grad P(y), P = sum c prod y_k^{e_k} harmonic */
+    WOI_FLUX_POINT_CHARGE = 4   /* d >= 3: coef = [s, x0_1..x0_d]; b(y) = s n(y) . grad |y - x0|^{2-d}
+                                   (the point-charge potential of Sec. 5, Example 2); x0 must lie
+                                   outside the region the surface bounds (compatibility) */
 };
 
 typedef struct {
@@ -137,6 +146,14 @@ WOI_API void woi_default_opts(woi_opts *o);
  */
 WOI_API woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surfaces, const int *parent,
                                woi_geometry **out);
+
+/*
+ * |dOmega_i| of surface i as the estimator uses it (Eq. naive_woi_p0): closed
+ * form for circles / d-spheres, Gauss-Legendre arc length for the star, and for
+ * an ellipsoid |S^{d-1}| prod(a_k) E_u |diag(1/a) u| (u uniform on the unit
+ * sphere, a_k the semi-axes) by a one-dimensional quadrature.  Host only.
+ */
+WOI_API woi_status woi_surface_area(const woi_geometry *geometry, int i, double *area);
 
 /*
  * Set conductivities and flux data.  sigma[n_surf] (sigma_i >= 0, sigma_0 > 0,

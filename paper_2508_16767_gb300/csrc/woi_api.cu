@@ -124,6 +124,14 @@ struct woi_geometry {
     std::vector<double> star_scan;             // kNodes * 2
     double star_lmax = 0.0;
     double star_rmin = 0.0, star_rmax = 0.0;
+    struct Ellipsoid {
+        double A[kMaxDim][kMaxDim];            // (y - c)^T A (y - c) = 1
+        double map[kMaxDim][kMaxDim];          // R diag(a): unit sphere -> surface (about c)
+        double inva[kMaxDim];                  // 1 / a_k
+        double jmax;                           // max_k 1 / a_k
+    };
+    std::vector<Ellipsoid> ell;
+    std::vector<int> ell_slot;                 // per surface, -1 if not an ellipsoid
 
     bool data_ready = false;
     std::vector<double> sigma, alpha, beta_scale, flux_coef;
@@ -149,7 +157,10 @@ struct woi_geometry {
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int num_sms = 0;
-    std::map<long long, int> occ_cache;        // (dim, vr, star, block) -> blocks per SM
+    std::map<long long, int> occ_cache;        // (dim, vr, general surfaces, block) -> blocks per SM
+
+    // kernels with non-sphere surfaces: the star (2D) or ellipsoids (d >= 3)
+    bool general() const { return star_idx >= 0 || !ell.empty(); }
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     bool timed = false;
 
@@ -196,6 +207,138 @@ double dist(int d, const double *a, const double *b)
     return std::sqrt(s);
 }
 
+// symmetric eigen-decomposition A = V diag(lam) V^T by cyclic Jacobi rotations
+// (each rotation in the (p, q) plane zeroes A_pq; converges quadratically)
+void jacobi_eigen(int d, const double (*A_in)[kMaxDim], double *lam, double (*V)[kMaxDim])
+{
+    double A[kMaxDim][kMaxDim];
+    double norm2 = 0.0;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            A[i][j] = A_in[i][j];
+            V[i][j] = i == j ? 1.0 : 0.0;
+            norm2 += A[i][j] * A[i][j];
+        }
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) off += A[p][q] * A[p][q];
+        if (off <= 1e-32 * norm2) break;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                // A <- J^T A J, V <- V J with J the rotation by (c, sn) in the (p, q) plane
+                for (int k = 0; k < d; ++k) {
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < d; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int k = 0; k < d; ++k) lam[k] = A[k][k];
+}
+
+// |dE| of {y : y^T A y = 1} from the eigenvalues lam of A.  The map u -> diag(a) u
+// (a = lam^{-1/2}) takes the unit sphere onto the surface and scales area by
+// prod(a) |diag(sqrt(lam)) u|, so |dE| = |S^{d-1}| prod(a) E_u |diag(sqrt(lam)) u|.
+// For a standard normal g = |g| u, E_u[.] = E sqrt(S) / E|g| with S = sum lam_k g_k^2;
+// sqrt(S) = pi^{-1/2} int_0^inf (1 - exp(-t^2 S)) t^{-2} dt turns E sqrt(S) into
+// pi^{-1/2} int_0^inf (1 - prod_k (1 + 2 lam_k t^2)^{-1/2}) t^{-2} dt, integrated here
+// over theta = atan(t / s) in [0, pi/2) by composite 8-point Gauss-Legendre.
+double ellipsoid_area(int d, const double *lam)
+{
+    static const double x[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    static const double w[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    double lg = 0.0, prod_a = 1.0;
+    for (int k = 0; k < d; ++k) {
+        lg += std::log(lam[k]);
+        prod_a /= std::sqrt(lam[k]);
+    }
+    const double sc = std::exp(-0.5 * lg / d);               // t = sc tan(theta)
+    auto integrand = [&](double th) {
+        const double t = sc * std::tan(th), t2 = t * t;
+        double ls = 0.0;
+        for (int k = 0; k < d; ++k) ls += std::log1p(2.0 * lam[k] * t2);
+        const double sec = 1.0 / std::cos(th);
+        return -std::expm1(-0.5 * ls) / t2 * sc * sec * sec;   // f(t) dt / dtheta
+    };
+    const int panels = 256;
+    const double h = 0.5 * kPi / panels;
+    double I = 0.0;
+    for (int j = 0; j < panels; ++j) {
+        const double mid = (j + 0.5) * h, half = 0.5 * h;
+        double acc = 0.0;
+        for (int q = 0; q < 4; ++q) acc += w[q] * (integrand(mid - half * x[q]) + integrand(mid + half * x[q]));
+        I += half * acc;
+    }
+    const double e_sqrt_s = I / std::sqrt(kPi);
+    const double e_norm = std::sqrt(2.0) * std::exp(std::lgamma(0.5 * (d + 1)) - std::lgamma(0.5 * d));
+    return omega_d(d) * prod_a * e_sqrt_s / e_norm;
+}
+
+// deterministic points on surface i of a d >= 3 geometry (sphere or ellipsoid):
+// unit vectors from SplitMix64 words by Box-Muller, mapped onto the surface
+std::vector<double> sample_surface(const woi_geometry &g, int i, int m)
+{
+    const int d = g.dim;
+    std::vector<double> p((size_t)m * d);
+    uint64_t st = 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    auto next = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    const woi_surface_desc &s = g.surf[i];
+    for (int j = 0; j < m; ++j) {
+        double u[kMaxDim + 1], nn = 0.0;
+        for (int k = 0; k < d; k += 2) {
+            const double r = std::sqrt(-2.0 * std::log(next())), a = 2.0 * kPi * next();
+            u[k] = r * std::cos(a);
+            u[k + 1] = r * std::sin(a);
+        }
+        for (int k = 0; k < d; ++k) nn += u[k] * u[k];
+        nn = std::sqrt(nn);
+        for (int k = 0; k < d; ++k) u[k] /= nn;
+        for (int k = 0; k < d; ++k) {
+            double v = s.center[k];
+            if (s.type == WOI_ELLIPSOID) {
+                const auto &e = g.ell[g.ell_slot[i]];
+                for (int q = 0; q < d; ++q) v += e.map[k][q] * u[q];
+            } else {
+                v += s.radius * u[k];
+            }
+            p[(size_t)j * d + k] = v;
+        }
+    }
+    return p;
+}
+
+// (x - c)^T A (x - c) of ellipsoid surface i
+double ellipsoid_form(const woi_geometry &g, int i, const double *x)
+{
+    const auto &e = g.ell[g.ell_slot[i]];
+    const double *c = g.surf[i].center;
+    double q = 0.0;
+    for (int a = 0; a < g.dim; ++a)
+        for (int b = 0; b < g.dim; ++b) q += (x[a] - c[a]) * e.A[a][b] * (x[b] - c[b]);
+    return q;
+}
+
 // a dense sample of surface i (2D only: circles and stars), used for star checks
 std::vector<double> sample_curve(const woi_geometry &g, int i, int m)
 {
@@ -217,6 +360,7 @@ bool inside_surface(const woi_geometry &g, int i, const double *x)
 {
     const woi_surface_desc &s = g.surf[i];
     if (s.type == WOI_SPHERE) return dist(g.dim, x, s.center) < s.radius;
+    if (s.type == WOI_ELLIPSOID) return ellipsoid_form(g, i, x) < 1.0;
     double t = std::atan2(x[1] - s.center[1], x[0] - s.center[0]);
     double r, dr;
     g.star.eval(t, &r, &dr);
@@ -234,6 +378,12 @@ woi_status check_nesting(const woi_geometry &g)
         if (si.type == WOI_SPHERE && sp.type == WOI_SPHERE) {
             if (!(dist(d, si.center, sp.center) + si.radius < sp.radius))
                 return fail(WOI_E_GEOMETRY, "surface %d is not strictly inside its parent %d", i, p);
+        } else if (d >= 3) {
+            // convex surfaces: every point of surface i inside the parent (a dense sample)
+            std::vector<double> pts = sample_surface(g, i, M * 4);
+            for (int j = 0; j < M * 4; ++j)
+                if (!inside_surface(g, p, &pts[(size_t)j * d]))
+                    return fail(WOI_E_GEOMETRY, "surface %d is not strictly inside its parent %d", i, p);
         } else {
             std::vector<double> pts = sample_curve(g, i, M);
             for (int j = 0; j < M; ++j)
@@ -253,6 +403,11 @@ woi_status check_nesting(const woi_geometry &g)
             if (si.type == WOI_SPHERE && sj.type == WOI_SPHERE) {
                 if (!(dist(d, si.center, sj.center) > si.radius + sj.radius))
                     return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
+            } else if (d >= 3) {
+                std::vector<double> a = sample_surface(g, i, M * 4), b = sample_surface(g, j, M * 4);
+                for (int k = 0; k < M * 4; ++k)
+                    if (inside_surface(g, j, &a[(size_t)k * d]) || inside_surface(g, i, &b[(size_t)k * d]))
+                        return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
             } else {
                 std::vector<double> a = sample_curve(g, i, M), b = sample_curve(g, j, M);
                 for (int k = 0; k < M; ++k)
@@ -330,9 +485,11 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
     g->n = n_surf;
     g->surf.assign(surfaces, surfaces + n_surf);
     g->parent.assign(parent, parent + n_surf);
+    g->ell_slot.assign(n_surf, -1);
     for (int i = 0; i < n_surf; ++i) {
         woi_surface_desc &s = g->surf[i];
         s.star_a = s.star_b = nullptr;         // deep copy below; no pointer retained
+        s.matrix = nullptr;
         if (s.type == WOI_SPHERE) {
             if (!(s.radius > 0.0) || !std::isfinite(s.radius)) {
                 delete g;
@@ -361,6 +518,43 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
                 g->star.eval(2.0 * kPi * j / 8192, &r, &dr);
                 if (!(r > 0.0)) { delete g; return fail(WOI_E_GEOMETRY, "surface %d: star radius not positive", i); }
             }
+        } else if (s.type == WOI_ELLIPSOID) {
+            if (dim < 3) { delete g; return fail(WOI_E_UNSUPPORTED, "ellipsoid surfaces need dim >= 3"); }
+            if ((int)g->ell.size() >= kMaxEll) {
+                delete g;
+                return fail(WOI_E_UNSUPPORTED, "at most %d ellipsoids per geometry", kMaxEll);
+            }
+            const double *A = surfaces[i].matrix;
+            if (!A) { delete g; return fail(WOI_E_INVALID_ARG, "surface %d: null ellipsoid matrix", i); }
+            woi_geometry::Ellipsoid e{};
+            double amax = 0.0;
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) {
+                    e.A[a][b] = A[a * dim + b];
+                    amax = std::max(amax, std::fabs(A[a * dim + b]));
+                    if (!std::isfinite(A[a * dim + b])) { delete g; return fail(WOI_E_INVALID_ARG, "surface %d: matrix not finite", i); }
+                }
+            for (int a = 0; a < dim; ++a)
+                for (int b = a + 1; b < dim; ++b)
+                    if (std::fabs(e.A[a][b] - e.A[b][a]) > 1e-12 * amax) {
+                        delete g;
+                        return fail(WOI_E_INVALID_ARG, "surface %d: ellipsoid matrix is not symmetric", i);
+                    }
+            double lam[kMaxDim], V[kMaxDim][kMaxDim];
+            jacobi_eigen(dim, e.A, lam, V);
+            for (int k = 0; k < dim; ++k)
+                if (!(lam[k] > 0.0)) {
+                    delete g;
+                    return fail(WOI_E_INVALID_ARG, "surface %d: ellipsoid matrix is not positive definite", i);
+                }
+            e.jmax = 0.0;
+            for (int k = 0; k < dim; ++k) {
+                e.inva[k] = std::sqrt(lam[k]);
+                e.jmax = std::max(e.jmax, e.inva[k]);
+                for (int a = 0; a < dim; ++a) e.map[a][k] = V[a][k] / e.inva[k];
+            }
+            g->ell_slot[i] = (int)g->ell.size();
+            g->ell.push_back(e);
         } else {
             delete g;
             return fail(WOI_E_INVALID_ARG, "surface %d: unknown type %d", i, s.type);
@@ -394,6 +588,11 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
     for (int i = 0; i < n_surf; ++i) {
         if (g->surf[i].type == WOI_SPHERE) {
             g->area[i] = omega_d(dim) * std::pow(g->surf[i].radius, dim - 1);
+        } else if (g->surf[i].type == WOI_ELLIPSOID) {
+            const auto &e = g->ell[g->ell_slot[i]];
+            double lam[kMaxDim];
+            for (int k = 0; k < dim; ++k) lam[k] = e.inva[k] * e.inva[k];
+            g->area[i] = ellipsoid_area(dim, lam);
         }
     }
     if (g->star_idx >= 0) {
@@ -427,6 +626,15 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
         g->star_rmax = rmax + margin;
     }
     *out = g;
+    return WOI_OK;
+}
+
+woi_status woi_surface_area(const woi_geometry *g, int i, double *area)
+{
+    g_last_error.clear();
+    if (!g || !area) return fail(WOI_E_INVALID_ARG, "null argument");
+    if (i < 0 || i >= g->n) return fail(WOI_E_INVALID_ARG, "surface %d out of range", i);
+    *area = g->area[i];
     return WOI_OK;
 }
 
@@ -495,6 +703,17 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             double sc;
             if (!poly_is_harmonic(d, T, c.data() + 2, &sc))
                 return fail(WOI_E_COMPAT, "flux[%d]: the polynomial is not harmonic, its flux is not compatible", i);
+            break;
+        }
+        case WOI_FLUX_POINT_CHARGE: {
+            if (d < 3) return fail(WOI_E_UNSUPPORTED, "flux[%d]: the point-charge datum needs dim >= 3", i);
+            if (f.n_coef != 1 + d) return fail(WOI_E_INVALID_ARG, "flux[%d]: point charge needs [s, x0_1..x0_d]", i);
+            // the charge must lie outside the region the surface bounds: then d_n |y - x0|^{2-d}
+            // integrates to zero over the surface (the potential is harmonic inside)
+            const double *x0 = c.data() + 1;
+            const bool outside = s.type == WOI_ELLIPSOID ? ellipsoid_form(*g, i, x0) > 1.0 + 1e-12
+                                                         : dist(d, x0, s.center) > s.radius * (1.0 + 1e-12);
+            if (!outside) return fail(WOI_E_COMPAT, "flux[%d]: the charge lies inside the surface, int b dA != 0", i);
             break;
         }
         default:
@@ -712,6 +931,72 @@ woi_status upload(T **dst, const std::vector<T> &src, cudaStream_t s)
     return WOI_OK;
 }
 
+// the host image of the blob for truncation M (device pointers are set by the caller)
+void fill_blob(const woi_geometry &g, int M, DevGeom &b)
+{
+    std::memset(&b, 0, sizeof(b));
+    b.dim = g.dim;
+    b.n = g.n;
+    b.npad = 1;
+    while (b.npad < g.n) b.npad <<= 1;
+    b.M = M;
+    b.star_idx = g.star_idx;
+    b.star_K = g.star_idx >= 0 ? g.star.K : 0;
+    b.star_lmax = g.star_lmax;
+    b.star_rmin = g.star_rmin;
+    b.star_rmax = g.star_rmax;
+    for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g.n ? (uint32_t)(g.thresh[i] - 1) : 0xFFFFFFFFu;
+    for (int i = 0; i < g.n; ++i) {
+        for (int k = 0; k < g.dim; ++k) b.center[i][k] = g.surf[i].center[k];
+        b.radius[i] = g.surf[i].radius;
+        b.area[i] = g.area[i];
+        b.alpha_sign[i] = g.alpha[i] > 0 ? 1.0 : (g.alpha[i] < 0 ? -1.0 : 0.0);
+        b.beta_scale[i] = g.beta_scale[i];
+        b.tin[i] = g.tin[i];
+        b.tout[i] = g.tout[i];
+        b.type[i] = g.surf[i].type;
+        b.flux_basis[i] = g.flux_basis[i];
+        b.flux_off[i] = g.flux_off[i];
+        b.flux_n[i] = g.flux_n[i];
+        b.part_len[i][0] = g.part_len.empty() ? 0.0 : g.part_len[2 * i];
+        b.part_len[i][1] = g.part_len.empty() ? 0.0 : g.part_len[2 * i + 1];
+        b.arc_off[i] = g.arc_off.empty() ? 0 : g.arc_off[i];
+        b.arc_n[i] = g.arc_n.empty() ? 0 : g.arc_n[i];
+        b.ell_slot[i] = g.ell_slot[i];
+    }
+    // N w_i ||alpha||_1^i (Eq. woi_estimator with w_i = 1 - delta_iM / 2)
+    double Ai = 1.0;
+    for (int i = 0; i <= M; ++i) {
+        b.coef[i] = (double)g.n * (i == M ? 0.5 : 1.0) * Ai;
+        Ai *= g.alpha_l1;
+    }
+    for (int j = 0; j < kNodes; ++j) {
+        b.node_cs[j][0] = std::cos(2.0 * kPi * j / kNodes);
+        b.node_cs[j][1] = std::sin(2.0 * kPi * j / kNodes);
+    }
+    if (g.star_idx >= 0) {
+        for (int k = 1; k <= g.star.K; ++k) {
+            b.star_a[k] = g.star.a[k];
+            b.star_b[k] = g.star.b[k];
+        }
+        for (int j = 0; j < kNodes; ++j) {
+            b.star_scan[j][0] = g.star_scan[2 * j];
+            b.star_scan[j][1] = g.star_scan[2 * j + 1];
+        }
+        for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g.star_panel_s[j];
+    }
+    b.n_ell = (int)g.ell.size();
+    for (int e = 0; e < b.n_ell; ++e) {
+        for (int a = 0; a < kMaxDim; ++a)
+            for (int c = 0; c < kMaxDim; ++c) {
+                b.ell_A[e][a][c] = g.ell[e].A[a][c];
+                b.ell_map[e][a][c] = g.ell[e].map[a][c];
+            }
+        for (int k = 0; k < kMaxDim; ++k) b.ell_inva[e][k] = g.ell[e].inva[k];
+        b.ell_jmax[e] = g.ell[e].jmax;
+    }
+}
+
 // build the blob (and per-M coefficients) and copy it to the device
 woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
 {
@@ -728,56 +1013,7 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
         if (!g->d_blob) WOI_CUDA(cudaMalloc((void **)&g->d_blob, sizeof(DevGeom)));
     }
     DevGeom &b = g->blob;
-    std::memset(&b, 0, sizeof(b));
-    b.dim = g->dim;
-    b.n = g->n;
-    b.npad = 1;
-    while (b.npad < g->n) b.npad <<= 1;
-    b.M = M;
-    b.star_idx = g->star_idx;
-    b.star_K = g->star_idx >= 0 ? g->star.K : 0;
-    b.star_lmax = g->star_lmax;
-    b.star_rmin = g->star_rmin;
-    b.star_rmax = g->star_rmax;
-    for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g->n ? (uint32_t)(g->thresh[i] - 1) : 0xFFFFFFFFu;
-    for (int i = 0; i < g->n; ++i) {
-        for (int k = 0; k < g->dim; ++k) b.center[i][k] = g->surf[i].center[k];
-        b.radius[i] = g->surf[i].radius;
-        b.area[i] = g->area[i];
-        b.alpha_sign[i] = g->alpha[i] > 0 ? 1.0 : (g->alpha[i] < 0 ? -1.0 : 0.0);
-        b.beta_scale[i] = g->beta_scale[i];
-        b.tin[i] = g->tin[i];
-        b.tout[i] = g->tout[i];
-        b.type[i] = g->surf[i].type;
-        b.flux_basis[i] = g->flux_basis[i];
-        b.flux_off[i] = g->flux_off[i];
-        b.flux_n[i] = g->flux_n[i];
-        b.part_len[i][0] = g->part_len.empty() ? 0.0 : g->part_len[2 * i];
-        b.part_len[i][1] = g->part_len.empty() ? 0.0 : g->part_len[2 * i + 1];
-        b.arc_off[i] = g->arc_off.empty() ? 0 : g->arc_off[i];
-        b.arc_n[i] = g->arc_n.empty() ? 0 : g->arc_n[i];
-    }
-    // N w_i ||alpha||_1^i (Eq. woi_estimator with w_i = 1 - delta_iM / 2)
-    double Ai = 1.0;
-    for (int i = 0; i <= M; ++i) {
-        b.coef[i] = (double)g->n * (i == M ? 0.5 : 1.0) * Ai;
-        Ai *= g->alpha_l1;
-    }
-    for (int j = 0; j < kNodes; ++j) {
-        b.node_cs[j][0] = std::cos(2.0 * kPi * j / kNodes);
-        b.node_cs[j][1] = std::sin(2.0 * kPi * j / kNodes);
-    }
-    if (g->star_idx >= 0) {
-        for (int k = 1; k <= g->star.K; ++k) {
-            b.star_a[k] = g->star.a[k];
-            b.star_b[k] = g->star.b[k];
-        }
-        for (int j = 0; j < kNodes; ++j) {
-            b.star_scan[j][0] = g->star_scan[2 * j];
-            b.star_scan[j][1] = g->star_scan[2 * j + 1];
-        }
-        for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g->star_panel_s[j];
-    }
+    fill_blob(*g, M, b);
     b.flux_coef = g->d_flux;
     b.flux_coef_f = g->d_flux_f;
     b.arc_t0 = g->d_arc_t0;
@@ -867,7 +1103,7 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
     if (n_pts == 0) return WOI_OK;
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     const int d = g->dim, C = d + 1;
-    const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0, fp64 = o->precision == WOI_FP64_PLAIN;
+    const bool vr = o->variant == WOI_VR, star = g->general(), fp64 = o->precision == WOI_FP64_PLAIN;
     if ((st = stage_geometry(g, o->M, s)) != WOI_OK) return st;
 
     int block, L;
@@ -1084,7 +1320,7 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
     // groups of instances that share a kernel: (dimension, star)
     std::map<int, std::vector<int>> groups;
     for (int k = 0; k < n_inst; ++k)
-        if (n_pts[k] > 0) groups[geoms[k]->dim * 2 + (geoms[k]->star_idx >= 0)].push_back(k);
+        if (n_pts[k] > 0) groups[geoms[k]->dim * 2 + (int)geoms[k]->general()].push_back(k);
 
     // scratch layout: per group [InstDesc x n][queue][partials]; then staged points and outputs
     struct Group {
@@ -1315,7 +1551,7 @@ static woi_status walk_values_impl(woi_geometry *g, const woi_opts *o, const dou
     p.f_grad = (double *)(base + o_g);
     p.trace = trace ? (double *)(base + o_t) : nullptr;
     if (trace) WOI_CUDA(cudaMemsetAsync(p.trace, 0, trace_count * sizeof(double), s));
-    WOI_CUDA(launch_walk_values(d, o->variant == WOI_VR, g->star_idx >= 0, o->precision == WOI_FP64_PLAIN, p, s));
+    WOI_CUDA(launch_walk_values(d, o->variant == WOI_VR, g->general(), o->precision == WOI_FP64_PLAIN, p, s));
     WOI_CUDA(cudaMemcpyAsync(f_u, p.f_u, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     WOI_CUDA(cudaMemcpyAsync(f_grad, p.f_grad, n * d * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (trace) WOI_CUDA(cudaMemcpyAsync(trace, p.trace, trace_count * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1353,7 +1589,7 @@ woi_status woi_autotune(woi_geometry *g, const woi_opts *o, const double *points
     if ((st = ensure_device(g)) != WOI_OK) return st;
     tune_load();
     const int d = g->dim;
-    const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0;
+    const bool vr = o->variant == WOI_VR, star = g->general();
     const int blocks[2] = {128, 256}, lanes[4] = {8, 16, 32, 64};
     float best = 1e30f;
     int bb = 256, bl = 8;
@@ -1481,7 +1717,7 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
 
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     const int d = g->dim, C = d + 1, M = o->M;
-    const bool vr = o->variant == WOI_VR, star = g->star_idx >= 0;
+    const bool vr = o->variant == WOI_VR, star = g->general();
     const int block = o->block_size ? o->block_size : 256;
     const int L = o->walks_per_lane ? o->walks_per_lane : 64;
     const int64_t unit_walks = 32LL * L;       // warp-level work units
@@ -1519,55 +1755,7 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     WOI_CUDA(put(o_sign, g->arc_sign.data(), g->arc_sign.size() * sizeof(int)));
 
     DevGeom &b = g_noalloc_blob;
-    std::memset(&b, 0, sizeof(b));
-    b.dim = d;
-    b.n = g->n;
-    b.npad = 1;
-    while (b.npad < g->n) b.npad <<= 1;
-    b.M = M;
-    b.star_idx = g->star_idx;
-    b.star_K = star ? g->star.K : 0;
-    b.star_lmax = g->star_lmax;
-    b.star_rmin = g->star_rmin;
-    b.star_rmax = g->star_rmax;
-    for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g->n ? (uint32_t)(g->thresh[i] - 1) : 0xFFFFFFFFu;
-    for (int i = 0; i < g->n; ++i) {
-        for (int k = 0; k < d; ++k) b.center[i][k] = g->surf[i].center[k];
-        b.radius[i] = g->surf[i].radius;
-        b.area[i] = g->area[i];
-        b.alpha_sign[i] = g->alpha[i] > 0 ? 1.0 : (g->alpha[i] < 0 ? -1.0 : 0.0);
-        b.beta_scale[i] = g->beta_scale[i];
-        b.tin[i] = g->tin[i];
-        b.tout[i] = g->tout[i];
-        b.type[i] = g->surf[i].type;
-        b.flux_basis[i] = g->flux_basis[i];
-        b.flux_off[i] = g->flux_off[i];
-        b.flux_n[i] = g->flux_n[i];
-        b.part_len[i][0] = g->part_len.empty() ? 0.0 : g->part_len[2 * i];
-        b.part_len[i][1] = g->part_len.empty() ? 0.0 : g->part_len[2 * i + 1];
-        b.arc_off[i] = g->arc_off.empty() ? 0 : g->arc_off[i];
-        b.arc_n[i] = g->arc_n.empty() ? 0 : g->arc_n[i];
-    }
-    double Ai = 1.0;   // N w_i ||alpha||_1^i
-    for (int i = 0; i <= M; ++i) {
-        b.coef[i] = (double)g->n * (i == M ? 0.5 : 1.0) * Ai;
-        Ai *= g->alpha_l1;
-    }
-    for (int j = 0; j < kNodes; ++j) {
-        b.node_cs[j][0] = std::cos(2.0 * kPi * j / kNodes);
-        b.node_cs[j][1] = std::sin(2.0 * kPi * j / kNodes);
-    }
-    if (star) {
-        for (int k = 1; k <= g->star.K; ++k) {
-            b.star_a[k] = g->star.a[k];
-            b.star_b[k] = g->star.b[k];
-        }
-        for (int j = 0; j < kNodes; ++j) {
-            b.star_scan[j][0] = g->star_scan[2 * j];
-            b.star_scan[j][1] = g->star_scan[2 * j + 1];
-        }
-        for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g->star_panel_s[j];
-    }
+    fill_blob(*g, M, b);
     b.flux_coef = (const double *)(base + o_flux);
     b.flux_coef_f = (const float *)(base + o_flux_f);
     b.arc_t0 = (const double *)(base + o_t0);

@@ -24,6 +24,8 @@
 // cosines and sines, and arc-length targets are split in FP64 (two operations).
 #pragma once
 
+#include <type_traits>
+
 #include <cstdint>
 
 #include "woi_layout.h"
@@ -65,6 +67,11 @@ struct Rng {
     __device__ __forceinline__ U4 words(int step, int chain, int sub) const
     {
         return philox10(w0, w1, (uint32_t)step, (uint32_t)((chain << 4) | sub), k0, k1);
+    }
+    // the words of rejection attempt a >= 1 of a (step, chain) stream: (a << 9) in counter word 3
+    __device__ __forceinline__ U4 words_at(int step, int chain, int attempt, int sub) const
+    {
+        return philox10(w0, w1, (uint32_t)step, ((uint32_t)attempt << 9) | (uint32_t)((chain << 4) | sub), k0, k1);
     }
 };
 
@@ -266,6 +273,41 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         }
         for (int j = tid; j <= kNodes; j += nt) g.panel_s[j] = src->star_panel_s[j];
     }
+}
+
+// ellipsoids of an instance (d >= 3), staged only by kernels compiled for them
+template <typename Real>
+struct SEll {
+    int slot[kMaxSurf];                  // slot of surface i, -1 if not an ellipsoid
+    Real A[kMaxEll][kMaxDim][kMaxDim];   // (y - c)^T A (y - c) = 1
+    Real map[kMaxEll][kMaxDim][kMaxDim]; // R diag(a): unit sphere -> surface
+    Real inva[kMaxEll][kMaxDim];         // 1 / a_k: area ratio of the map |diag(inva) u|
+    Real jmax[kMaxEll];                  // max_k 1 / a_k
+};
+
+template <typename Real>
+struct SGeomE : SGeom<Real> {
+    SEll<Real> ell;
+};
+
+// the staged geometry of a kernel: with the ellipsoid tables when it serves general
+// surfaces in d >= 3 (STAR is the kernels' flag for "not only spheres")
+template <typename Real, int D, bool STAR>
+using SGeomFor = typename std::conditional<(STAR && D >= 3), SGeomE<Real>, SGeom<Real>>::type;
+
+template <typename Real>
+__device__ void load_geometry(SGeomE<Real> &g, const DevGeom *src)
+{
+    load_geometry(static_cast<SGeom<Real> &>(g), src);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < kMaxSurf; i += nt) g.ell.slot[i] = i < src->n ? src->ell_slot[i] : -1;
+    for (int i = tid; i < src->n_ell * kMaxDim * kMaxDim; i += nt) {
+        const int e = i / (kMaxDim * kMaxDim), r = (i / kMaxDim) % kMaxDim, c = i % kMaxDim;
+        g.ell.A[e][r][c] = (Real)src->ell_A[e][r][c];
+        g.ell.map[e][r][c] = (Real)src->ell_map[e][r][c];
+    }
+    for (int i = tid; i < src->n_ell * kMaxDim; i += nt) g.ell.inva[i / kMaxDim][i % kMaxDim] = (Real)src->ell_inva[i / kMaxDim][i % kMaxDim];
+    for (int i = tid; i < src->n_ell; i += nt) g.ell.jmax[i] = (Real)src->ell_jmax[i];
 }
 
 // H_i from a 32-bit word: i = 0 uniform over the N surfaces, i >= 1 the first n
@@ -727,7 +769,70 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
         for (int k = 0; k < D; ++k) v += n[k] * grad[k];
         return s * v;
     }
+    if (basis == kFluxPointCharge) {
+        // s n . grad_y |y - x0|^{2-d} = s (2 - d) |y - x0|^{-d} (y - x0) . n
+        Real r2 = 0, dot = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const Real e = y[k] - c[1 + k];
+            r2 += e * e;
+            dot += e * n[k];
+        }
+        const Real ir = RealOps<Real>::rsqrt_(r2);
+        Real ird = ir;
+#pragma unroll
+        for (int k = 1; k < D; ++k) ird *= ir;
+        return c[0] * (Real)(2 - D) * ird * dot;
+    }
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// ellipsoids (Sec. 5, Example 2)
+// ---------------------------------------------------------------------------
+// uniform point by surface measure on ellipsoid slot e (Eq. naive_woi_p0): u uniform on
+// the unit sphere from the words of attempt a of the (step, chain) stream, accepted when
+// v^2 jmax^2 <= |diag(inva) u|^2 (v the attempt's choice word); y - c = map u and the
+// outward normal A (y - c) / |A (y - c)|.  After kEllAttempts rejections the last
+// attempt is kept (probability below (1 - 1/jmax a_max)^64 for every ellipsoid).
+template <typename Real, int D>
+__device__ void ell_uniform(const SEll<Real> &E, int e, const Rng &rng, int step, int chain, const StepWords &w0,
+                            Real *v, Real *nrm)
+{
+    Real u[D];
+    StepWords w = w0;
+    const Real jm = E.jmax[e];
+    for (int a = 0; a < kEllAttempts; ++a) {
+        if (a > 0) {
+            w.a = rng.words_at(step, chain, a, 0);
+            if constexpr (two_calls<D>()) w.b = rng.words_at(step, chain, a, 1);
+        }
+        direction<Real, D>(w, u);
+        Real J2 = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) J2 += u[k] * u[k] * E.inva[e][k] * E.inva[e][k];
+        const Real acc = u01<Real>(w.get(choice_word<D>()));
+        if (acc * acc * jm * jm <= J2) break;
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        Real t = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += E.map[e][r][c] * u[c];
+        v[r] = t;
+    }
+    Real nn = 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        Real t = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += E.A[e][r][c] * v[c];
+        nrm[r] = t;
+        nn += t * t;
+    }
+    const Real inv = RealOps<Real>::rsqrt_(nn);
+#pragma unroll
+    for (int r = 0; r < D; ++r) nrm[r] *= inv;
 }
 
 // c Phi(x, y) and c grad_x Phi(x, y) added to acc[0], acc[1..D], given dx = x - y
@@ -797,7 +902,7 @@ struct Chain {
 // start (i = 0): y_0 uniform on dOmega_h (plain) or on dOmega_h^{+/-} (VR), Q = beta(y_0) |part|
 template <typename Real, int D, bool VR, bool STAR>
 __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int k, const StepWords &w,
-                            Chain<Real, D> &ch)
+                            const Rng &rng, Chain<Real, D> &ch)
 {
     ch.T = 1;
     ch.alive = true;
@@ -817,7 +922,16 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
         }
     }
     const bool is_star = STAR && g.type[h] == kStar;
-    if (!VR && !is_star) {
+    bool is_ell = false;
+    if constexpr (STAR && D >= 3) is_ell = g.type[h] == kEllipsoid;
+    if (is_ell) {
+        if constexpr (STAR && D >= 3) {
+            const SEll<Real> &E = static_cast<const SGeomE<Real> &>(g).ell;
+            ell_uniform<Real, D>(E, E.slot[h], rng, 0, k, w, ch.v, nrm);
+#pragma unroll
+            for (int c = 0; c < D; ++c) u[c] = nrm[c];
+        }
+    } else if (!VR && !is_star) {
         direction<Real, D>(w, u);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -878,9 +992,76 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
     ch.Q = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, u, nrm) * (Real)part_len;
 }
 
+// transition i >= 1 from an ellipsoid-bound state to ellipsoid h (relation rel); dy = y - c_h.
+// Line (same surface): the other root t = -2 b / a of a t^2 + 2 b t + c = 0, Q *= 1/2, T *= q sign
+// = +1 (a chord of a convex surface leaves it outward).  Ray (from a descendant): the positive
+// root, Q and T unchanged.  Otherwise: uniform y' with Q *= K*(y', y) |dOmega_h|.
+template <typename Real, int D>
+__device__ void ell_step(const SGeomE<Real> &g, int h, int rel, const StepWords &w, const Rng &rng, int step,
+                         int chain, const Real *dy, Chain<Real, D> &ch)
+{
+    using O = RealOps<Real>;
+    constexpr double PI = 3.14159265358979323846;
+    const SEll<Real> &E = g.ell;
+    const int e = E.slot[h];
+    if (rel == 2) {
+        Real vn[D], nrm[D];
+        ell_uniform<Real, D>(E, e, rng, step, chain, w, vn, nrm);
+        Real r2 = 0, dot = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const Real diff = vn[c] - dy[c];
+            r2 += diff * diff;
+            dot += diff * nrm[c];
+            ch.v[c] = vn[c];
+        }
+        constexpr double omega = D == 3 ? 4.0 * PI : (D == 4 ? 2.0 * PI * PI : (D == 5 ? 8.0 * PI * PI / 3.0 : PI * PI * PI));
+        const Real ir = O::rsqrt_(r2);
+        Real inv_rd = ir;
+#pragma unroll
+        for (int k = 1; k < D; ++k) inv_rd *= ir;
+        ch.Q *= dot * inv_rd * (Real)(1.0 / omega) * g.area[h];
+    } else {
+        Real z[D];
+        direction<Real, D>(w, z);
+        Real a2 = 0, b1 = 0, c0 = -1;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            Real az = 0, ady = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                az += E.A[e][r][c] * z[c];
+                ady += E.A[e][r][c] * dy[c];
+            }
+            a2 += z[r] * az;
+            b1 += dy[r] * az;
+            c0 += dy[r] * ady;
+        }
+        Real t;
+        if (rel == 0) {
+            t = (Real)-2 * b1 / a2;
+            const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
+            if (O::fabs_(t) * E.jmax[e] <= tiny) {   // tangent: only y itself (reading R5)
+                ch.alive = false;
+                ch.T = 0;
+                return;
+            }
+            ch.Q *= (Real)0.5;
+        } else {
+            const Real disc = b1 * b1 - a2 * c0;
+            const Real sq = O::sqrt_(disc > 0 ? disc : (Real)0);
+            t = (b1 <= 0) ? (sq - b1) / a2 : -c0 / (b1 + sq);
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) ch.v[c] = dy[c] + t * z[c];
+    }
+    ch.s = h;
+}
+
 // transition i >= 1 from surface ch.s to h (relation rel)
 template <typename Real, int D, bool STAR>
-__device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords &w, Chain<Real, D> &ch)
+__device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords &w, const Rng &rng, int step,
+                           int chain, Chain<Real, D> &ch)
 {
     using O = RealOps<Real>;
     constexpr double PI = 3.14159265358979323846;
@@ -893,6 +1074,12 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
         center_diff<Real, D>(g, ch.s, h, dy);
 #pragma unroll
         for (int c = 0; c < D; ++c) dy[c] += ch.v[c];
+    }
+    if constexpr (STAR && D >= 3) {
+        if (g.type[h] == kEllipsoid) {
+            ell_step<Real, D>(static_cast<const SGeomE<Real> &>(g), h, rel, w, rng, step, chain, dy, ch);
+            return;
+        }
     }
     if (STAR && g.type[h] == kStar) {
         if constexpr (D == 2) {
@@ -1022,9 +1209,9 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
                 if constexpr (two_calls<D>()) w.b = rng.words(i, 1, 1);
             }
             if (i == 0) {
-                chain_start<Real, D, VR, STAR>(g, gd, h, k, w, ch[k]);
+                chain_start<Real, D, VR, STAR>(g, gd, h, k, w, rng, ch[k]);
             } else if (ch[k].alive) {
-                chain_step<Real, D, STAR>(g, h, rel, w, ch[k]);
+                chain_step<Real, D, STAR>(g, h, rel, w, rng, i, k, ch[k]);
             }
             sink(i, k, ch[k], ch[k].alive ? g.coef[i] * S * ch[k].Q * ch[k].T : (Real)0);
         }

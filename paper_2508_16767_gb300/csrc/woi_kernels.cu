@@ -123,10 +123,10 @@ static cudaError_t by_dim(int dim, bool star, F &&f)
 {
     switch (dim) {
     case 2: return star ? f(DimTag<2, true>{}) : f(DimTag<2, false>{});
-    case 3: return f(DimTag<3, false>{});
-    case 4: return f(DimTag<4, false>{});
-    case 5: return f(DimTag<5, false>{});
-    case 6: return f(DimTag<6, false>{});
+    case 3: return star ? f(DimTag<3, true>{}) : f(DimTag<3, false>{});
+    case 4: return star ? f(DimTag<4, true>{}) : f(DimTag<4, false>{});
+    case 5: return star ? f(DimTag<5, true>{}) : f(DimTag<5, false>{});
+    case 6: return star ? f(DimTag<6, true>{}) : f(DimTag<6, false>{});
     default: return cudaErrorInvalidValue;
     }
 }

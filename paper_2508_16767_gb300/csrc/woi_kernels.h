@@ -82,6 +82,10 @@ extern template struct DimLaunchers<3, false>;
 extern template struct DimLaunchers<4, false>;
 extern template struct DimLaunchers<5, false>;
 extern template struct DimLaunchers<6, false>;
+extern template struct DimLaunchers<3, true>;
+extern template struct DimLaunchers<4, true>;
+extern template struct DimLaunchers<5, true>;
+extern template struct DimLaunchers<6, true>;
 
 struct BatchFinalizeParams {
     const InstDesc *inst;              // device [n_inst], sorted by point_begin

@@ -73,7 +73,7 @@ __device__ __forceinline__ int find_instance(const InstDesc *inst, int n_inst, i
 template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams p)
 {
-    __shared__ SGeom<float> g;
+    __shared__ SGeomFor<float, D, STAR> g;
     __shared__ float xc[kMaxSurf][kMaxDim];
     __shared__ double red[kMixedMaxBlock / 32][2 * (D + 1)];
     __shared__ long long unit_sh;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams
 template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed_warp(MixedParams p)
 {
-    __shared__ SGeom<float> g;
+    __shared__ SGeomFor<float, D, STAR> g;
     extern __shared__ float xc_all[];   // [warps][n][kMaxDim]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const InstDesc &id = p.inst[0];
@@ -276,7 +276,7 @@ struct RecordSink {
 template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
 {
-    __shared__ SGeom<float> g;
+    __shared__ SGeomFor<float, D, STAR> g;
     extern __shared__ float4 rec_all4[];
     float *rec_all = reinterpret_cast<float *>(rec_all4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
 template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(256) k_walk_fp64_point(Fp64PointParams p)
 {
-    __shared__ SGeom<double> g;
+    __shared__ SGeomFor<double, D, STAR> g;
     __shared__ double xc[kMaxSurf][kMaxDim];
     __shared__ double red[8][2 * (D + 1)];
     load_geometry(g, p.geom);
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_walk_fp64_point(Fp64PointParams p)
 template <typename Real, int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
 {
-    __shared__ SGeom<Real> g;
+    __shared__ SGeomFor<Real, D, STAR> g;
     __shared__ Real xc[kMaxSurf][kMaxDim];
     load_geometry(g, p.geom);
     fill_xc<Real>(xc, p.geom, p.geom->n, D, p.x);

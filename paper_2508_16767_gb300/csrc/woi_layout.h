@@ -14,9 +14,11 @@ constexpr int kMaxStar = 16;           // star Fourier degree (WOI_MAX_STAR_DEGR
 constexpr int kNodes = 256;            // angle nodes t_j = 2 pi j / kNodes: star scan samples,
                                        // arc-length panels and the angle-addition table
 constexpr int kMaxRoots = 2 * (kMaxStar + 1) + 2;
+constexpr int kMaxEll = 8;             // ellipsoids per instance (WOI_MAX_ELLIPSOIDS)
+constexpr int kEllAttempts = 64;       // rejection attempts for a uniform point on an ellipsoid
 
-enum { kSphere = 0, kStar = 1 };
-enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3 };
+enum { kSphere = 0, kStar = 1, kEllipsoid = 2 };
+enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4 };
 
 struct DevGeom {
     int dim, n, npad, M;
@@ -47,6 +49,14 @@ struct DevGeom {
     const double *arc_len;
     const double *arc_s0;              // star: arc length at the arc's start angle
     const int *arc_sign;
+    // ellipsoids (d >= 3): A = R diag(1/a^2) R^T; map = R diag(a) takes the unit sphere onto
+    // the surface; inva = 1/a (the area ratio of the map is |diag(inva) u|), jmax = max inva
+    int n_ell;
+    int ell_slot[kMaxSurf];            // slot of surface i, -1 if it is not an ellipsoid
+    double ell_A[kMaxEll][kMaxDim][kMaxDim];
+    double ell_map[kMaxEll][kMaxDim][kMaxDim];
+    double ell_inva[kMaxEll][kMaxDim];
+    double ell_jmax[kMaxEll];
 };
 
 // one instance of a (possibly batched) estimate

@@ -21,15 +21,16 @@ import numpy as np
 from . import build as _build
 
 WOI_MAX_DIM = 6
-WOI_SPHERE, WOI_STAR = 0, 1
-FLUX = {"zero": 0, "fourier": 1, "real_sh": 2, "harmonic_poly": 3}
+WOI_SPHERE, WOI_STAR, WOI_ELLIPSOID = 0, 1, 2
+KIND = {"sphere": WOI_SPHERE, "star": WOI_STAR, "ellipsoid": WOI_ELLIPSOID}
+FLUX = {"zero": 0, "fourier": 1, "real_sh": 2, "harmonic_poly": 3, "point_charge": 4}
 WOI_PLAIN, WOI_VR = 0, 1
 WOI_MIXED, WOI_FP64_PLAIN = 0, 1
 STATUS = {0: "WOI_OK", 1: "WOI_E_INVALID_ARG", 2: "WOI_E_GEOMETRY", 3: "WOI_E_COMPAT", 4: "WOI_E_UNSUPPORTED",
           5: "WOI_E_NO_DEVICE", 6: "WOI_E_CUDA", 7: "WOI_E_OOM", 8: "WOI_E_TIMEOUT", 9: "WOI_E_STATE"}
 EXPORTED = ["woi_default_opts", "woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate",
             "woi_estimate_range", "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
-            "woi_estimate_noalloc", "woi_autotune",
+            "woi_estimate_noalloc", "woi_autotune", "woi_surface_area",
             "woi_destroy_geometry", "woi_last_error", "woi_version"]
 
 
@@ -42,7 +43,7 @@ class WoiError(RuntimeError):
 class SurfaceDesc(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("center", ctypes.c_double * WOI_MAX_DIM), ("radius", ctypes.c_double),
                 ("star_degree", ctypes.c_int), ("star_a", ctypes.POINTER(ctypes.c_double)),
-                ("star_b", ctypes.POINTER(ctypes.c_double))]
+                ("star_b", ctypes.POINTER(ctypes.c_double)), ("matrix", ctypes.POINTER(ctypes.c_double))]
 
 
 class FluxDesc(ctypes.Structure):
@@ -78,6 +79,7 @@ def _load():
     lib.woi_last_kernel_ms.argtypes = [vp, P(ctypes.c_float)]
     lib.woi_estimate_noalloc.argtypes = [vp, P(Opts), dp, i64, i64, u64, dp, dp, dp, dp]
     lib.woi_autotune.argtypes = [vp, P(Opts), dp, i64, i64, u64, P(ctypes.c_int), P(ctypes.c_int)]
+    lib.woi_surface_area.argtypes = [vp, ctypes.c_int, P(ctypes.c_double)]
     lib.woi_destroy_geometry.argtypes = [vp]
     lib.woi_destroy_geometry.restype = None
     lib.woi_last_error.restype = ctypes.c_char_p
@@ -158,15 +160,19 @@ def woi_last_kernel_ms(geom) -> float:
 # ---------------------------------------------------------------------------
 
 def woi_create_geometry(dim, surfaces, parent):
-    """surfaces: list of dicts {"kind", "center", "radius", "star_a", "star_b"}."""
+    """surfaces: list of dicts {"kind", "center", "radius", "star_a", "star_b", "matrix"}."""
     n = len(surfaces)
     arr = (SurfaceDesc * n)()
     keep = []
     for i, s in enumerate(surfaces):
-        arr[i].type = WOI_SPHERE if s["kind"] == "sphere" else WOI_STAR
+        arr[i].type = KIND[s["kind"]]
         for k, v in enumerate(s["center"]):
             arr[i].center[k] = float(v)
-        arr[i].radius = float(s["radius"])
+        arr[i].radius = float(s.get("radius", 0.0))
+        if s["kind"] == "ellipsoid":
+            m = np.ascontiguousarray(s["matrix"], dtype=np.float64)
+            keep.append(m)
+            arr[i].matrix = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         if s["kind"] == "star":
             a = np.ascontiguousarray(s["star_a"], dtype=np.float64)
             b = np.ascontiguousarray(s["star_b"], dtype=np.float64)
@@ -208,6 +214,12 @@ class Geometry:
             lib.woi_destroy_geometry(self.handle)
             self.handle = None
             raise
+
+    def surface_area(self, i):
+        """|dOmega_i| as the estimator uses it."""
+        a = ctypes.c_double()
+        _check(lib.woi_surface_area(self.handle, int(i), ctypes.byref(a)))
+        return a.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -108,3 +108,45 @@ def test_estimate_argument_checks_and_no_device(woi):
             woi.woi_estimate(g, pts, 1024)
         assert e.value.status == 5
     g.close()
+
+
+def test_ellipsoid_host_geometry(woi):
+    """Ellipsoids (Example 2) on the host side of the library: the area the
+    estimator uses equals the oracle's (an independent quadrature of the same
+    formula, scipy instead of Gauss-Legendre; eigenvectors from numpy instead of
+    Jacobi), the printed Example 2 geometry is rejected as not nested, and bad
+    matrices and charges inside a surface are rejected."""
+    from oracle import core
+    for d in (3, 4, 5, 6):
+        prob = wl.ellipsoids_problem(d)
+        prep = core.Prepared(prob)
+        with woi.Geometry(prob) as g:
+            for i in range(3):
+                assert g.surface_area(i) == pytest.approx(prep.area[i], rel=1e-11)
+    # a strongly eccentric rotated ellipsoid
+    Q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((4, 4)))
+    A = Q @ np.diag([0.5, 2.0, 30.0, 400.0]) @ Q.T
+    prob = {"dim": 4, "surfaces": [wl._ellipsoid([0.1, 0, 0, 0], A)], "parent": [-1], "sigma": [1.0],
+            "flux": [wl.zero_flux()], "M": 2}
+    with woi.Geometry(prob) as g:
+        assert g.surface_area(0) == pytest.approx(core.Prepared(prob).area[0], rel=1e-10)
+    # Omega_2 as printed (centre 1.4) reaches outside Omega_1
+    bad = wl.ellipsoids_problem(3)
+    bad["surfaces"][1]["center"][0] = 1.4
+    with pytest.raises(woi.WoiError) as e:
+        woi.Geometry(bad)
+    assert e.value.status == 2
+    # not positive definite / not symmetric / in 2D
+    for M_ in ([[1.0, 0, 0], [0, -1.0, 0], [0, 0, 1.0]], [[1.0, 0.5, 0], [0, 1.0, 0], [0, 0, 1.0]]):
+        with pytest.raises(woi.WoiError) as e:
+            woi.woi_create_geometry(3, [wl._ellipsoid([0, 0, 0], M_)], [-1])
+        assert e.value.status == 1
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(2, [wl._ellipsoid([0, 0], np.eye(2))], [-1])
+    assert e.value.status == 4
+    # a point charge inside the surface it sits on is not compatible (its flux integrates to -|S^{d-1}| (d-2) s)
+    prob = wl.ellipsoids_problem(3)
+    prob["flux"][2] = {"basis": "point_charge", "coef": [0.5, 1.6, 0.0, 0.0]}
+    with pytest.raises(woi.WoiError) as e:
+        woi.Geometry(prob)
+    assert e.value.status == 3

@@ -66,6 +66,9 @@ def cases():
     for dim in (2, 3):
         inst = wl.manufactured_instance(dim, rng, k_max=12)
         yield f"manufactured-{dim}d", inst, wl.ball_points(3, dim, 40 + dim, radius=0.9), "plain"
+    for dim in (3, 6):
+        ell = wl.ellipsoids_problem(dim)
+        yield f"ellipsoids-{dim}d", ell, wl.ellipsoid_points(ell, 3, seed=50 + dim), "plain"
 
 
 CASES = list(cases())
@@ -155,7 +158,7 @@ def test_shared_schedules(W, O):
 
 @pytest.mark.parametrize("name,variant,sched_group", [("3d-nested", "plain", 1), ("3d-nested", "plain", 32),
                                                       ("2d-concentric-vr", "vr", 1), ("star-3", "plain", 1),
-                                                      ("6d-nested", "plain", 1)])
+                                                      ("6d-nested", "plain", 1), ("ellipsoids-3d", "plain", 1)])
 def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
     estimate is still the mean over the same walks the oracle draws for that
@@ -164,6 +167,8 @@ def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     prob = dict((c[0], c[1]) for c in CASES)[name]
     if name.startswith("star"):
         x = wl.star_inclusions_points(prob, 70, seed=22)
+    elif name.startswith("ellipsoids"):
+        x = wl.ellipsoid_points(prob, 70, seed=22)
     else:
         x = wl.ball_points(70, prob["dim"], 23, radius=0.9)
     n_walks = 2048 + 160
