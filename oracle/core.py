@@ -16,8 +16,8 @@ module prepares its inputs from a problem dictionary with numpy/scipy:
   * |dOmega_i| (circle / d-sphere closed form, star by Gauss-Legendre quadrature,
     ellipsoid by a one-dimensional integral for the mean area ratio, see
     ellipsoid_area);
-  * ellipsoids (Sec. 5, Example 2): the eigen-decomposition A = R diag(1/a^2) R^T
-    that maps the unit sphere onto the surface;
+  * ellipsoids (Sec. 5, Example 2): the symmetric square root A^{-1/2} that
+    maps the unit sphere onto the surface, and sqrt of the largest eigenvalue;
   * Sec. 4.4: the beta >= 0 / beta < 0 arcs of 2D surfaces for the variance-
     reduced estimator, by a dense sign scan and Brent's method.
 """
@@ -101,7 +101,7 @@ class OrProblem(ctypes.Structure):
          "beta_scale", "thresh"]] + [("alpha_l1", ctypes.c_double)] + [
         (n, ctypes.c_void_p) for n in
         ["flux_basis", "flux_off", "flux_n", "flux_coef", "arc_off", "arc_n", "arc_t0", "arc_t1", "arc_sign",
-         "arc_len", "part_len", "ell_A", "ell_map", "ell_inva", "ell_jmax"]]
+         "arc_len", "part_len", "ell_A", "ell_map", "ell_jmax"]]
 
 
 class OrOpts(ctypes.Structure):
@@ -329,7 +329,6 @@ class Prepared:
         self.radius = np.array([s.get("radius", 0.0) for s in surfs], dtype=np.float64)
         self.ell_A = np.zeros((n, MAX_DIM, MAX_DIM))
         self.ell_map = np.zeros((n, MAX_DIM, MAX_DIM))
-        self.ell_inva = np.zeros((n, MAX_DIM))
         self.ell_jmax = np.zeros(n)
         self.star_K = np.zeros(n, dtype=np.int32)
         self.star_a = np.zeros((n, MAX_STAR + 1))
@@ -341,8 +340,7 @@ class Prepared:
             if s["kind"] == "ellipsoid":
                 lam, R = ellipsoid_axes(s)
                 self.ell_A[i, :d, :d] = np.asarray(s["matrix"], dtype=np.float64)
-                self.ell_map[i, :d, :d] = R * (lam ** -0.5)[None, :]
-                self.ell_inva[i, :d] = np.sqrt(lam)
+                self.ell_map[i, :d, :d] = (R * (lam ** -0.5)[None, :]) @ R.T     # A^{-1/2}
                 self.ell_jmax[i] = math.sqrt(float(np.max(lam)))
             if s["kind"] == "star":
                 K = len(s["star_a"]) - 1
@@ -391,7 +389,7 @@ class Prepared:
             self.flux_n.ctypes.data, self.flux_coef.ctypes.data, self.arc_off.ctypes.data,
             self.arc_n.ctypes.data, self.arc_t0.ctypes.data, self.arc_t1.ctypes.data, self.arc_sign.ctypes.data,
             self.arc_len.ctypes.data, self.part_len.ctypes.data, self.ell_A.ctypes.data, self.ell_map.ctypes.data,
-            self.ell_inva.ctypes.data, self.ell_jmax.ctypes.data)
+            self.ell_jmax.ctypes.data)
 
 
 VARIANTS = {"plain": 0, "vr": 1}

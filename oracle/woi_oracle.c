@@ -29,9 +29,11 @@
  *   - Sec. 5, Example 2: ellipsoids (y - c)^T A (y - c) = 1 as surfaces, with
  *     the point-charge potential |x - x0|^{2-d} as manufactured solution.
  *     Uniform points by surface measure come from a uniform point u of the
- *     unit sphere mapped to y = c + R diag(a) u (A = R diag(1/a^2) R^T),
- *     accepted with probability J(u) / max J, J(u) = |diag(1/a) u| the area
- *     ratio of the map (von Neumann rejection).
+ *     unit sphere mapped to y = c + A^{-1/2} u (the symmetric square root, so
+ *     that the map does not depend on how an eigen-decomposition orders or
+ *     signs its vectors), accepted with probability J(u) / max J, where
+ *     J(u) = |A^{1/2} u| = sqrt(u^T A u) is the area ratio of the map (von
+ *     Neumann rejection) and max J = sqrt(largest eigenvalue of A).
  *
  * Readings of the paper taken here (each one is listed with its reason in
  * the design notes of the repository):
@@ -101,9 +103,8 @@ typedef struct {
     const double *arc_len;
     const double *part_len;   /* [n_surf][2] |dOmega^+|, |dOmega^-| */
     const double *ell_A;      /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] ellipsoid matrix A (row-major) */
-    const double *ell_map;    /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] R diag(a): unit sphere -> ellipsoid */
-    const double *ell_inva;   /* [n_surf][OR_MAX_DIM] 1 / a_k (the columns of ell_map in order) */
-    const double *ell_jmax;   /* [n_surf] max_k 1 / a_k */
+    const double *ell_map;    /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] A^{-1/2}: unit sphere -> ellipsoid */
+    const double *ell_jmax;   /* [n_surf] sqrt of the largest eigenvalue of A */
 } or_problem;
 
 typedef struct {
@@ -351,14 +352,15 @@ static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, in
         for (int k = 0; k < d; ++k) y[k] = c[k] + P->radius[h] * z[k];
     } else if (P->type[h] == OR_ELLIPSOID) {
         /* u uniform on the unit sphere, accepted when v^2 max J^2 <= J(u)^2 with v the
-         * attempt's choice word and J(u)^2 = sum_k u_k^2 / a_k^2 */
+         * attempt's choice word and J(u)^2 = u^T A u */
         const double *c = or_center(P, h), *Mp = P->ell_map + (size_t)h * OR_MAX_DIM * OR_MAX_DIM;
-        const double *ia = P->ell_inva + (size_t)h * OR_MAX_DIM, jm = P->ell_jmax[h];
+        const double *A = P->ell_A + (size_t)h * OR_MAX_DIM * OR_MAX_DIM, jm = P->ell_jmax[h];
         double z[OR_MAX_DIM];
         for (int a = 0; a < OR_ELL_ATTEMPTS; ++a) {
             or_direction_at(r, d, step, chain, a, z);
             double J2 = 0.0;
-            for (int k = 0; k < d; ++k) J2 += z[k] * z[k] * ia[k] * ia[k];
+            for (int k = 0; k < d; ++k)
+                for (int j = 0; j < d; ++j) J2 += z[k] * A[k * OR_MAX_DIM + j] * z[j];
             double v = or_u01(or_word_at(r, step, chain, a, or_choice_word(d)));
             if (v * v * jm * jm <= J2) break;
         }
@@ -447,7 +449,7 @@ static int or_intersections(const or_problem *P, int h, const double *y, const d
         double qq = -(b1 + (b1 >= 0 ? sq : -sq));
         double r1 = qq / a2, r2 = (qq != 0.0) ? c0 / qq : 0.0;
         double cand[2] = {r1 < r2 ? r1 : r2, r1 < r2 ? r2 : r1};
-        double scale = 1.0 / P->ell_jmax[h];      /* smallest semi-axis */
+        double scale = 1.0 / P->ell_jmax[h];      /* shortest semi-axis */
         for (int j = 0; j < 2; ++j) {
             double t = cand[j];
             if (ray ? (t > tiny * scale) : (fabs(t) > tiny * scale)) ts[q++] = t;

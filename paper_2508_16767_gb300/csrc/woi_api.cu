@@ -126,9 +126,9 @@ struct woi_geometry {
     double star_rmin = 0.0, star_rmax = 0.0;
     struct Ellipsoid {
         double A[kMaxDim][kMaxDim];            // (y - c)^T A (y - c) = 1
-        double map[kMaxDim][kMaxDim];          // R diag(a): unit sphere -> surface (about c)
-        double inva[kMaxDim];                  // 1 / a_k
-        double jmax;                           // max_k 1 / a_k
+        double map[kMaxDim][kMaxDim];          // A^{-1/2}: unit sphere -> surface (about c)
+        double lam[kMaxDim];                   // eigenvalues of A
+        double jmax;                           // sqrt(max eigenvalue)
     };
     std::vector<Ellipsoid> ell;
     std::vector<int> ell_slot;                 // per surface, -1 if not an ellipsoid
@@ -547,12 +547,20 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
                     delete g;
                     return fail(WOI_E_INVALID_ARG, "surface %d: ellipsoid matrix is not positive definite", i);
                 }
+            // the symmetric square root A^{-1/2} = V diag(lam^{-1/2}) V^T: unlike V diag(a) it does
+            // not depend on the order or signs of the eigenvectors, so a uniform u on the unit
+            // sphere gives the same surface point whatever routine decomposed A
             e.jmax = 0.0;
             for (int k = 0; k < dim; ++k) {
-                e.inva[k] = std::sqrt(lam[k]);
-                e.jmax = std::max(e.jmax, e.inva[k]);
-                for (int a = 0; a < dim; ++a) e.map[a][k] = V[a][k] / e.inva[k];
+                e.lam[k] = lam[k];
+                e.jmax = std::max(e.jmax, std::sqrt(lam[k]));
             }
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) {
+                    double m = 0.0;
+                    for (int k = 0; k < dim; ++k) m += V[a][k] * V[b][k] / std::sqrt(lam[k]);
+                    e.map[a][b] = m;
+                }
             g->ell_slot[i] = (int)g->ell.size();
             g->ell.push_back(e);
         } else {
@@ -589,10 +597,7 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
         if (g->surf[i].type == WOI_SPHERE) {
             g->area[i] = omega_d(dim) * std::pow(g->surf[i].radius, dim - 1);
         } else if (g->surf[i].type == WOI_ELLIPSOID) {
-            const auto &e = g->ell[g->ell_slot[i]];
-            double lam[kMaxDim];
-            for (int k = 0; k < dim; ++k) lam[k] = e.inva[k] * e.inva[k];
-            g->area[i] = ellipsoid_area(dim, lam);
+            g->area[i] = ellipsoid_area(dim, g->ell[g->ell_slot[i]].lam);
         }
     }
     if (g->star_idx >= 0) {
@@ -992,7 +997,6 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
                 b.ell_A[e][a][c] = g.ell[e].A[a][c];
                 b.ell_map[e][a][c] = g.ell[e].map[a][c];
             }
-        for (int k = 0; k < kMaxDim; ++k) b.ell_inva[e][k] = g.ell[e].inva[k];
         b.ell_jmax[e] = g.ell[e].jmax;
     }
 }

@@ -280,9 +280,8 @@ template <typename Real>
 struct SEll {
     int slot[kMaxSurf];                  // slot of surface i, -1 if not an ellipsoid
     Real A[kMaxEll][kMaxDim][kMaxDim];   // (y - c)^T A (y - c) = 1
-    Real map[kMaxEll][kMaxDim][kMaxDim]; // R diag(a): unit sphere -> surface
-    Real inva[kMaxEll][kMaxDim];         // 1 / a_k: area ratio of the map |diag(inva) u|
-    Real jmax[kMaxEll];                  // max_k 1 / a_k
+    Real map[kMaxEll][kMaxDim][kMaxDim]; // A^{-1/2}: unit sphere -> surface, area ratio sqrt(u^T A u)
+    Real jmax[kMaxEll];                  // sqrt(max eigenvalue of A)
 };
 
 template <typename Real>
@@ -306,7 +305,6 @@ __device__ void load_geometry(SGeomE<Real> &g, const DevGeom *src)
         g.ell.A[e][r][c] = (Real)src->ell_A[e][r][c];
         g.ell.map[e][r][c] = (Real)src->ell_map[e][r][c];
     }
-    for (int i = tid; i < src->n_ell * kMaxDim; i += nt) g.ell.inva[i / kMaxDim][i % kMaxDim] = (Real)src->ell_inva[i / kMaxDim][i % kMaxDim];
     for (int i = tid; i < src->n_ell; i += nt) g.ell.jmax[i] = (Real)src->ell_jmax[i];
 }
 
@@ -792,9 +790,10 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
 // ---------------------------------------------------------------------------
 // uniform point by surface measure on ellipsoid slot e (Eq. naive_woi_p0): u uniform on
 // the unit sphere from the words of attempt a of the (step, chain) stream, accepted when
-// v^2 jmax^2 <= |diag(inva) u|^2 (v the attempt's choice word); y - c = map u and the
-// outward normal A (y - c) / |A (y - c)|.  After kEllAttempts rejections the last
-// attempt is kept (probability below (1 - 1/jmax a_max)^64 for every ellipsoid).
+// v^2 jmax^2 <= u^T A u (v the attempt's choice word; sqrt(u^T A u) is the area ratio of
+// the map A^{-1/2}); y - c = A^{-1/2} u and the outward normal A (y - c) / |A (y - c)|.
+// After kEllAttempts rejections the last attempt is kept (each attempt is accepted with
+// probability at least sqrt(lambda_min / lambda_max)).
 template <typename Real, int D>
 __device__ void ell_uniform(const SEll<Real> &E, int e, const Rng &rng, int step, int chain, const StepWords &w0,
                             Real *v, Real *nrm)
@@ -810,7 +809,12 @@ __device__ void ell_uniform(const SEll<Real> &E, int e, const Rng &rng, int step
         direction<Real, D>(w, u);
         Real J2 = 0;
 #pragma unroll
-        for (int k = 0; k < D; ++k) J2 += u[k] * u[k] * E.inva[e][k] * E.inva[e][k];
+        for (int r = 0; r < D; ++r) {
+            Real t = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) t += E.A[e][r][c] * u[c];
+            J2 += u[r] * t;
+        }
         const Real acc = u01<Real>(w.get(choice_word<D>()));
         if (acc * acc * jm * jm <= J2) break;
     }

@@ -49,13 +49,12 @@ struct DevGeom {
     const double *arc_len;
     const double *arc_s0;              // star: arc length at the arc's start angle
     const int *arc_sign;
-    // ellipsoids (d >= 3): A = R diag(1/a^2) R^T; map = R diag(a) takes the unit sphere onto
-    // the surface; inva = 1/a (the area ratio of the map is |diag(inva) u|), jmax = max inva
+    // ellipsoids (d >= 3): (y - c)^T A (y - c) = 1; map = A^{-1/2} (symmetric square root) takes
+    // the unit sphere onto the surface with area ratio sqrt(u^T A u); jmax = sqrt(max eigenvalue)
     int n_ell;
     int ell_slot[kMaxSurf];            // slot of surface i, -1 if it is not an ellipsoid
     double ell_A[kMaxEll][kMaxDim][kMaxDim];
     double ell_map[kMaxEll][kMaxDim][kMaxDim];
-    double ell_inva[kMaxEll][kMaxDim];
     double ell_jmax[kMaxEll];
 };
 
