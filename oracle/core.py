@@ -18,6 +18,9 @@ module prepares its inputs from a problem dictionary with numpy/scipy:
     ellipsoid_area);
   * ellipsoids (Sec. 5, Example 2): the symmetric square root A^{-1/2} that
     maps the unit sphere onto the surface, and sqrt of the largest eigenvalue;
+  * triangle meshes (3D): per triangle v0, e1, e2 and the unit normal of e1 x e2,
+    the area as the sum of the triangle areas, and the cumulative-area
+    thresholds floor(2^32 C_j / A) that pick a triangle by area;
   * Sec. 4.4: the beta >= 0 / beta < 0 arcs of 2D surfaces for the variance-
     reduced estimator, by a dense sign scan and Brent's method.
 """
@@ -40,8 +43,8 @@ MAX_DIM = 6
 MAX_STAR = 16
 STAR_PANELS = 256
 STAR_SCAN = 4096
-SPHERE, STAR, ELLIPSOID = 0, 1, 2
-KIND = {"sphere": SPHERE, "star": STAR, "ellipsoid": ELLIPSOID}
+SPHERE, STAR, ELLIPSOID, MESH = 0, 1, 2, 3
+KIND = {"sphere": SPHERE, "star": STAR, "ellipsoid": ELLIPSOID, "mesh": MESH}
 FLUX = {"zero": 0, "fourier": 1, "real_sh": 2, "harmonic_poly": 3, "point_charge": 4}
 
 
@@ -80,12 +83,12 @@ def lib():
         _lib.or_test_star_arclen.argtypes = [P(OrProblem), ctypes.c_int, ctypes.c_double]
         _lib.or_test_star_arclen.restype = ctypes.c_double
         _lib.or_test_intersections.argtypes = [P(OrProblem), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                               ctypes.c_int, ctypes.c_void_p]
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         _lib.or_test_intersections.restype = ctypes.c_int
-        _lib.or_test_flux.argtypes = [P(OrProblem), ctypes.c_int, ctypes.c_void_p]
+        _lib.or_test_flux.argtypes = [P(OrProblem), ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
         _lib.or_test_flux.restype = ctypes.c_double
         _lib.or_test_uniform_point.argtypes = [P(OrProblem), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
-                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
+                                               ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_test_uniform_part_point.argtypes = [P(OrProblem), ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                                     ctypes.c_uint64, ctypes.c_void_p]
         _lib.or_test_direction.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
@@ -101,7 +104,7 @@ class OrProblem(ctypes.Structure):
          "beta_scale", "thresh"]] + [("alpha_l1", ctypes.c_double)] + [
         (n, ctypes.c_void_p) for n in
         ["flux_basis", "flux_off", "flux_n", "flux_coef", "arc_off", "arc_n", "arc_t0", "arc_t1", "arc_sign",
-         "arc_len", "part_len", "ell_A", "ell_map", "ell_jmax"]]
+         "arc_len", "part_len", "ell_A", "ell_map", "ell_jmax", "mesh_off", "mesh_n", "tri", "tri_thresh"]]
 
 
 class OrOpts(ctypes.Structure):
@@ -254,7 +257,38 @@ def ellipsoid_area(dim, lam):
     return omega(dim) * float(np.prod(lam ** -0.5)) * e_sqrt_s / e_norm
 
 
+def mesh_triangles(s):
+    """[n, 12] rows (v0, e1, e2, unit normal of e1 x e2) and the triangle areas,
+    with the cross product and its length written out (no library norm)."""
+    V = np.asarray(s["vertices"], dtype=np.float64)
+    F = np.asarray(s["triangles"], dtype=np.int64)
+    v0, v1, v2 = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    e1, e2 = v1 - v0, v2 - v0
+    cx = e1[:, 1] * e2[:, 2] - e1[:, 2] * e2[:, 1]
+    cy = e1[:, 2] * e2[:, 0] - e1[:, 0] * e2[:, 2]
+    cz = e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]
+    ln = np.sqrt(cx * cx + cy * cy + cz * cz)
+    n = np.stack([cx / ln, cy / ln, cz / ln], axis=1)
+    return np.concatenate([v0, e1, e2, n], axis=1), 0.5 * ln
+
+
+def mesh_thresholds(areas):
+    """P(triangle j) = area_j / A as 32-bit thresholds T_j = floor(2^32 C_j / A), T_last = 2^32."""
+    A = 0.0
+    for a in areas:
+        A += float(a)
+    out = np.zeros(len(areas), dtype=np.uint64)
+    C = 0.0
+    for j, a in enumerate(areas):
+        C += float(a)
+        out[j] = np.uint64(math.floor(math.ldexp(C / A, 32)))
+    out[-1] = np.uint64(1 << 32)
+    return out, A
+
+
 def surface_area(dim, s):
+    if s["kind"] == "mesh":
+        return mesh_thresholds(mesh_triangles(s)[1])[1]
     if s["kind"] == "sphere":
         return omega(dim) * s["radius"] ** (dim - 1)
     if s["kind"] == "ellipsoid":
@@ -330,6 +364,20 @@ class Prepared:
         self.ell_A = np.zeros((n, MAX_DIM, MAX_DIM))
         self.ell_map = np.zeros((n, MAX_DIM, MAX_DIM))
         self.ell_jmax = np.zeros(n)
+        self.mesh_off = np.zeros(n, dtype=np.int32)
+        self.mesh_n = np.zeros(n, dtype=np.int32)
+        tris, thr = [np.zeros((0, 12))], [np.zeros(0, dtype=np.uint64)]
+        for i, s in enumerate(surfs):
+            if s["kind"] == "mesh":
+                if d != 3:
+                    raise ValueError("meshes are 3D surfaces")
+                T, ar = mesh_triangles(s)
+                self.mesh_off[i] = sum(len(t) for t in tris)
+                self.mesh_n[i] = len(T)
+                tris.append(T)
+                thr.append(mesh_thresholds(ar)[0])
+        self.tri = np.ascontiguousarray(np.concatenate(tris + [np.zeros((1, 12))]))
+        self.tri_thresh = np.ascontiguousarray(np.concatenate(thr + [np.zeros(1, dtype=np.uint64)]))
         self.star_K = np.zeros(n, dtype=np.int32)
         self.star_a = np.zeros((n, MAX_STAR + 1))
         self.star_b = np.zeros((n, MAX_STAR + 1))
@@ -389,7 +437,8 @@ class Prepared:
             self.flux_n.ctypes.data, self.flux_coef.ctypes.data, self.arc_off.ctypes.data,
             self.arc_n.ctypes.data, self.arc_t0.ctypes.data, self.arc_t1.ctypes.data, self.arc_sign.ctypes.data,
             self.arc_len.ctypes.data, self.part_len.ctypes.data, self.ell_A.ctypes.data, self.ell_map.ctypes.data,
-            self.ell_jmax.ctypes.data)
+            self.ell_jmax.ctypes.data, self.mesh_off.ctypes.data, self.mesh_n.ctypes.data, self.tri.ctypes.data,
+            self.tri_thresh.ctypes.data)
 
 
 VARIANTS = {"plain": 0, "vr": 1}
@@ -464,21 +513,22 @@ def walks(problem, x, walk_ids, seed=0, M=None, variant="plain", sched_group=1, 
     return {"u": fu, "grad": fg, "H": H, "Y": Y, "scale": sc, "Q": QT[..., 0], "T": QT[..., 1]}
 
 
-def flux_at(problem, h, y, prepared=None):
+def flux_at(problem, h, y, prepared=None, tri=-1):
     prep = prepared or Prepared(problem)
     yy = np.zeros(MAX_DIM)
     yy[:prep.dim] = y
-    return lib().or_test_flux(ctypes.byref(prep.struct), h, yy.ctypes.data)
+    return lib().or_test_flux(ctypes.byref(prep.struct), h, int(tri), yy.ctypes.data)
 
 
-def intersections(problem, h, y, z, ray, prepared=None):
+def intersections(problem, h, y, z, ray, prepared=None, exclude=-1, with_triangles=False):
     prep = prepared or Prepared(problem)
     yy = np.ascontiguousarray(y, dtype=np.float64)
     zz = np.ascontiguousarray(z, dtype=np.float64)
     ts = np.zeros(64)
+    hits = np.zeros(64, dtype=np.int32)
     q = lib().or_test_intersections(ctypes.byref(prep.struct), h, yy.ctypes.data, zz.ctypes.data, int(ray),
-                                    ts.ctypes.data)
-    return ts[:q]
+                                    ts.ctypes.data, int(exclude), hits.ctypes.data)
+    return (ts[:q], hits[:q]) if with_triangles else ts[:q]
 
 
 def real_sh(l, m, u):
@@ -491,14 +541,17 @@ def star_arclen(problem, h, t, prepared=None):
     return lib().or_test_star_arclen(ctypes.byref(prep.struct), h, t)
 
 
-def uniform_points(problem, h, n, seed=0, prepared=None):
+def uniform_points(problem, h, n, seed=0, prepared=None, with_triangles=False):
     prep = prepared or Prepared(problem)
     out = np.zeros((n, prep.dim))
+    tri = np.zeros(n, dtype=np.int32)
+    t = ctypes.c_int(0)
     for w in range(n):
         y = np.zeros(prep.dim)
-        lib().or_test_uniform_point(ctypes.byref(prep.struct), h, seed, 0, w, 0, y.ctypes.data)
+        lib().or_test_uniform_point(ctypes.byref(prep.struct), h, seed, 0, w, 0, y.ctypes.data, ctypes.byref(t))
         out[w] = y
-    return out
+        tri[w] = t.value
+    return (out, tri) if with_triangles else out
 
 
 def uniform_part_points(problem, h, part, n, seed=0, prepared=None):

@@ -34,6 +34,11 @@
  *     signs its vectors), accepted with probability J(u) / max J, where
  *     J(u) = |A^{1/2} u| = sqrt(u^T A u) is the area ratio of the map (von
  *     Neumann rejection) and max J = sqrt(largest eigenvalue of A).
+ *   - Closed triangle meshes (3D; the paper's primary surface representation,
+ *     Sec. 5): uniform points by area (a triangle by the cumulative-area
+ *     thresholds, then uniform barycentric coordinates), face normals, and
+ *     line / ray intersections by testing every triangle (no acceleration
+ *     structure); a line through a point of triangle j skips triangle j.
  *
  * Readings of the paper taken here (each one is listed with its reason in
  * the design notes of the repository):
@@ -58,7 +63,7 @@
 
 #define OR_ELL_ATTEMPTS 64   /* rejection attempts for a uniform point on an ellipsoid; the last one is kept */
 
-enum { OR_SPHERE = 0, OR_STAR = 1, OR_ELLIPSOID = 2 };
+enum { OR_SPHERE = 0, OR_STAR = 1, OR_ELLIPSOID = 2, OR_MESH = 3 };
 enum { OR_FLUX_ZERO = 0, OR_FLUX_FOURIER = 1, OR_FLUX_REAL_SH = 2, OR_FLUX_HARMONIC_POLY = 3,
        OR_FLUX_POINT_CHARGE = 4 };
 enum { OR_REL_SAME = 0, OR_REL_DESC = 1, OR_REL_OTHER = 2 };
@@ -105,6 +110,10 @@ typedef struct {
     const double *ell_A;      /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] ellipsoid matrix A (row-major) */
     const double *ell_map;    /* [n_surf][OR_MAX_DIM][OR_MAX_DIM] A^{-1/2}: unit sphere -> ellipsoid */
     const double *ell_jmax;   /* [n_surf] sqrt of the largest eigenvalue of A */
+    const int *mesh_off;      /* [n_surf] first triangle of a mesh surface */
+    const int *mesh_n;        /* [n_surf] number of triangles */
+    const double *tri;        /* [n_tri][4][3]: v0, e1 = v1 - v0, e2 = v2 - v0, unit normal (e1 x e2) */
+    const uint64_t *tri_thresh; /* [n_tri] cumulative-area thresholds floor(2^32 C_j / A), last = 2^32 */
 } or_problem;
 
 typedef struct {
@@ -282,10 +291,15 @@ static double or_param_angle(const or_problem *P, int h, const double *y)
     return t;
 }
 
-/* outward unit normal at a point y of surface h */
-static void or_normal(const or_problem *P, int h, const double *y, double *n)
+/* outward unit normal at a point y of surface h (on a mesh: of triangle `tri`) */
+static void or_normal(const or_problem *P, int h, int tri, const double *y, double *n)
 {
     int d = P->dim;
+    if (P->type[h] == OR_MESH) {
+        const double *t = P->tri + (size_t)tri * 12;
+        for (int k = 0; k < 3; ++k) n[k] = t[9 + k];
+        return;
+    }
     if (P->type[h] == OR_SPHERE) {
         const double *c = or_center(P, h);
         for (int k = 0; k < d; ++k) n[k] = (y[k] - c[k]) / P->radius[h];
@@ -341,10 +355,25 @@ static void or_direction_at(or_rng *r, int d, int step, int chain, int a, double
 static void or_direction(or_rng *r, int d, int step, int chain, double *z) { or_direction_at(r, d, step, chain, 0, z); }
 
 
-/* uniform point on dOmega_h (Eq. naive_woi_p0; by surface measure) */
-static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, int chain, double *y)
+/* uniform point on dOmega_h (Eq. naive_woi_p0; by surface measure); on a mesh
+ * *tri receives the triangle (word 1 picks it by area, words 2 and 3 give
+ * uniform barycentric coordinates (1 - s, s (1 - w), s w) with s = sqrt(u)) */
+static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, int chain, double *y, int *tri)
 {
     int d = P->dim;
+    *tri = -1;
+    if (P->type[h] == OR_MESH) {
+        uint32_t w1 = or_word(r, step, chain, 1);
+        int lo = P->mesh_off[h], hi = P->mesh_off[h] + P->mesh_n[h] - 1, j = hi;
+        for (int k = lo; k <= hi; ++k)            /* first triangle whose threshold exceeds the word */
+            if ((uint64_t)w1 < P->tri_thresh[k]) { j = k; break; }
+        double u = or_u01(or_word(r, step, chain, 2)), w = or_u01(or_word(r, step, chain, 3));
+        double sq = sqrt(u), b1 = sq * (1.0 - w), b2 = sq * w;
+        const double *t = P->tri + (size_t)j * 12;
+        for (int k = 0; k < 3; ++k) y[k] = t[k] + b1 * t[3 + k] + b2 * t[6 + k];
+        *tri = j;
+        return;
+    }
     if (P->type[h] == OR_SPHERE) {
         double z[OR_MAX_DIM];
         or_direction(r, d, step, chain, z);
@@ -407,10 +436,37 @@ static void or_uniform_part_point(const or_problem *P, int h, int part, or_rng *
  * Line: t != 0 (the start point itself is excluded), ray: t > 0.  Returns q
  * and the parameters sorted increasingly. */
 static int or_intersections(const or_problem *P, int h, const double *y, const double *z, int ray,
-                            double *ts)
+                            double *ts, int exclude, int *hit_tri)
 {
     int d = P->dim, q = 0;
     const double tiny = 1e-9;
+    if (P->type[h] == OR_MESH) {
+        /* every triangle (Moller-Trumbore: y + t z = v0 + a e1 + b e2, a, b >= 0, a + b <= 1) */
+        for (int j = P->mesh_off[h]; j < P->mesh_off[h] + P->mesh_n[h]; ++j) {
+            if (j == exclude) continue;
+            const double *T = P->tri + (size_t)j * 12, *e1 = T + 3, *e2 = T + 6;
+            double p[3] = {z[1] * e2[2] - z[2] * e2[1], z[2] * e2[0] - z[0] * e2[2], z[0] * e2[1] - z[1] * e2[0]};
+            double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+            if (det == 0.0) continue;
+            double sv[3] = {y[0] - T[0], y[1] - T[1], y[2] - T[2]};
+            double a = (sv[0] * p[0] + sv[1] * p[1] + sv[2] * p[2]) / det;
+            if (a < 0.0 || a > 1.0) continue;
+            double qv[3] = {sv[1] * e1[2] - sv[2] * e1[1], sv[2] * e1[0] - sv[0] * e1[2], sv[0] * e1[1] - sv[1] * e1[0]};
+            double b = (z[0] * qv[0] + z[1] * qv[1] + z[2] * qv[2]) / det;
+            if (b < 0.0 || a + b > 1.0) continue;
+            double t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) / det;
+            if (ray && !(t > 0.0)) continue;
+            if (q < OR_MAX_ROOTS) { ts[q] = t; hit_tri[q] = j; ++q; }
+        }
+        for (int a = 1; a < q; ++a) {            /* insertion sort by t, triangles alongside */
+            double v = ts[a];
+            int tv = hit_tri[a], b = a - 1;
+            while (b >= 0 && ts[b] > v) { ts[b + 1] = ts[b]; hit_tri[b + 1] = hit_tri[b]; --b; }
+            ts[b + 1] = v;
+            hit_tri[b + 1] = tv;
+        }
+        return q;
+    }
     if (P->type[h] == OR_SPHERE) {
         const double *c = or_center(P, h);
         double b = 0.0, c0 = 0.0, R = P->radius[h];
@@ -566,7 +622,7 @@ static double or_real_sh(int l, int m, const double *u)
 }
 
 /* flux datum b_h(y) at a point y of dOmega_h */
-static double or_flux(const or_problem *P, int h, const double *y)
+static double or_flux(const or_problem *P, int h, int tri, const double *y)
 {
     int d = P->dim, n = P->flux_n[h];
     const double *c = P->flux_coef + P->flux_off[h];
@@ -598,7 +654,7 @@ static double or_flux(const or_problem *P, int h, const double *y)
         double s = c[0];
         int T = (int)c[1];
         double nrm[OR_MAX_DIM], grad[OR_MAX_DIM] = {0};
-        or_normal(P, h, y, nrm);
+        or_normal(P, h, tri, y, nrm);
         for (int t = 0; t < T; ++t) {
             const double *row = c + 2 + t * (d + 1);
             for (int k = 0; k < d; ++k) {
@@ -618,7 +674,7 @@ static double or_flux(const or_problem *P, int h, const double *y)
     }
     case OR_FLUX_POINT_CHARGE: { /* [s, x0_1..x0_d]: b = s n . grad_y |y - x0|^{2-d} (d >= 3) */
         double nrm[OR_MAX_DIM], r2 = 0.0, dot = 0.0;
-        or_normal(P, h, y, nrm);
+        or_normal(P, h, tri, y, nrm);
         for (int k = 0; k < d; ++k) {
             double e = y[k] - c[1 + k];
             r2 += e * e;
@@ -633,7 +689,7 @@ static double or_flux(const or_problem *P, int h, const double *y)
 
 /* sum of the magnitudes of the terms that make up b_h(y): the scale against
  * which the rounding error of evaluating b_h is measured in the tests */
-static double or_flux_mag(const or_problem *P, int h, const double *y)
+static double or_flux_mag(const or_problem *P, int h, int tri, const double *y)
 {
     int d = P->dim, n = P->flux_n[h];
     const double *c = P->flux_coef + P->flux_off[h];
@@ -658,7 +714,7 @@ static double or_flux_mag(const or_problem *P, int h, const double *y)
     case OR_FLUX_HARMONIC_POLY: {
         int T = (int)c[1];
         double nrm[OR_MAX_DIM];
-        or_normal(P, h, y, nrm);
+        or_normal(P, h, tri, y, nrm);
         for (int t = 0; t < T; ++t) {
             const double *row = c + 2 + t * (d + 1);
             for (int k = 0; k < d; ++k) {
@@ -676,7 +732,7 @@ static double or_flux_mag(const or_problem *P, int h, const double *y)
     }
     case OR_FLUX_POINT_CHARGE: {
         double nrm[OR_MAX_DIM], r2 = 0.0;
-        or_normal(P, h, y, nrm);
+        or_normal(P, h, tri, y, nrm);
         for (int k = 0; k < d; ++k) r2 += (y[k] - c[1 + k]) * (y[k] - c[1 + k]);
         for (int k = 0; k < d; ++k) m += fabs((y[k] - c[1 + k]) * nrm[k]);
         return fabs(c[0] * (2.0 - d)) * pow(r2, -0.5 * d) * m;
@@ -686,11 +742,11 @@ static double or_flux_mag(const or_problem *P, int h, const double *y)
     }
 }
 
-static double or_beta(const or_problem *P, int h, const double *y)
+static double or_beta(const or_problem *P, int h, int tri, const double *y)
 {
     double sc = P->beta_scale[h];
     if (or_mutant == 6 && h > 0) sc = -sc;
-    return sc * or_flux(P, h, y);
+    return sc * or_flux(P, h, tri, y);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -732,6 +788,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     double y[2][OR_MAX_DIM], Q[2], T[2];
     double cond0 = 1.0;
     int alive[2] = {1, 1};
+    int tri[2] = {-1, -1};   /* mesh triangle of each chain's state (-1 elsewhere) */
     double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m})  (reading R1) */
     double Ai = 1.0;         /* ||alpha||_1^i */
     int h_prev = -1;
@@ -759,9 +816,9 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                 /* p0: uniform on dOmega_{h0} (plain) or on dOmega^{+/-} (Alg. 3) */
                 T[k] = 1.0;
                 if (o->variant == 0) {
-                    or_uniform_point(P, h, &rng, 0, k, y[k]);
-                    Q[k] = or_beta(P, h, y[k]) * P->area[h];
-                    double b0 = fabs(or_flux(P, h, y[k])), bm = or_flux_mag(P, h, y[k]);
+                    or_uniform_point(P, h, &rng, 0, k, y[k], &tri[k]);
+                    Q[k] = or_beta(P, h, tri[k], y[k]) * P->area[h];
+                    double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
                     if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
                 } else {
                     double L = P->part_len[2 * h + k];
@@ -771,23 +828,24 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                         for (int c = 0; c < d; ++c) y[k][c] = 0.0;
                     } else {
                         or_uniform_part_point(P, h, k, &rng, 0, k, y[k]);
-                        Q[k] = or_beta(P, h, y[k]) * L;
-                        double b0 = fabs(or_flux(P, h, y[k])), bm = or_flux_mag(P, h, y[k]);
+                        Q[k] = or_beta(P, h, -1, y[k]) * L;
+                        double b0 = fabs(or_flux(P, h, -1, y[k])), bm = or_flux_mag(P, h, -1, y[k]);
                         if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
                     }
                 }
             } else if (alive[k]) {
                 const int rel = or_relation(P, h_prev, h);
                 double ynew[OR_MAX_DIM];
+                int tnew = -1;
                 if (rel == OR_REL_OTHER) {
                     /* uniform on dOmega_h; Q *= K*(y_i, y_{i-1}) |dOmega_h|; T unchanged (R2, R3) */
-                    or_uniform_point(P, h, &rng, i, k, ynew);
+                    or_uniform_point(P, h, &rng, i, k, ynew, &tnew);
                     double nrm[OR_MAX_DIM], dot = 0.0;
                     if (or_mutant == 5) {
-                        or_normal(P, h_prev, y[k], nrm);
+                        or_normal(P, h_prev, tri[k], y[k], nrm);
                         for (int c = 0; c < d; ++c) dot += (y[k][c] - ynew[c]) * nrm[c];
                     } else {
-                        or_normal(P, h, ynew, nrm);
+                        or_normal(P, h, tnew, ynew, nrm);
                         for (int c = 0; c < d; ++c) dot += (ynew[c] - y[k][c]) * nrm[c];
                     }
                     double r = or_dist(d, ynew, y[k]);
@@ -797,8 +855,11 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                 } else {
                     /* isotropic line (same interface) or ray (from a descendant) */
                     double z[OR_MAX_DIM], ts[OR_MAX_ROOTS];
+                    int hits[OR_MAX_ROOTS];
                     or_direction(&rng, d, i, k, z);
-                    int q = or_intersections(P, h, y[k], z, rel == OR_REL_DESC, ts);
+                    /* a line through a point of a mesh triangle skips that triangle */
+                    int q = or_intersections(P, h, y[k], z, rel == OR_REL_DESC, ts,
+                                             rel == OR_REL_SAME ? tri[k] : -1, hits);
                     if (q == 0) {            /* reading R5 */
                         alive[k] = 0; T[k] = 0.0;
                         continue;
@@ -806,14 +867,16 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     uint32_t cw = or_word(&rng, i, k, or_choice_word(d));
                     int j = (int)(((uint64_t)cw * (uint64_t)q) >> 32);
                     for (int c = 0; c < d; ++c) ynew[c] = y[k][c] + ts[j] * z[c];
+                    tnew = P->type[h] == OR_MESH ? hits[j] : -1;
                     double nrm[OR_MAX_DIM], dot = 0.0;
-                    or_normal(P, h, ynew, nrm);
+                    or_normal(P, h, tnew, ynew, nrm);
                     for (int c = 0; c < d; ++c) dot += (ynew[c] - y[k][c]) * nrm[c];
                     double sg = dot > 0.0 ? 1.0 : (dot < 0.0 ? -1.0 : 0.0);
                     if (rel == OR_REL_SAME && or_mutant != 7) Q[k] *= 0.5;
                     T[k] *= (double)q * sg;
                 }
                 for (int c = 0; c < d; ++c) y[k][c] = ynew[c];
+                tri[k] = tnew;
             }
             if (tr && tr->Y)
                 for (int c = 0; c < d; ++c) tr->Y[((size_t)k * (M + 1) + i) * d + c] = y[k][c];
@@ -897,16 +960,20 @@ void or_walks(const or_problem *P, const or_opts *o, const double *x, uint32_t p
 /* exposed for the tests of the building blocks */
 double or_test_real_sh(int l, int m, const double *u) { return or_real_sh(l, m, u); }
 double or_test_star_arclen(const or_problem *P, int h, double t) { return or_star_arclen(P, h, t); }
-int or_test_intersections(const or_problem *P, int h, const double *y, const double *z, int ray, double *ts)
+int or_test_intersections(const or_problem *P, int h, const double *y, const double *z, int ray, double *ts,
+                          int exclude, int *hit_tri)
 {
-    return or_intersections(P, h, y, z, ray, ts);
+    int dummy[OR_MAX_ROOTS];
+    return or_intersections(P, h, y, z, ray, ts, exclude, hit_tri ? hit_tri : dummy);
 }
-double or_test_flux(const or_problem *P, int h, const double *y) { return or_flux(P, h, y); }
+double or_test_flux(const or_problem *P, int h, int tri, const double *y) { return or_flux(P, h, tri, y); }
 void or_test_uniform_point(const or_problem *P, int h, uint64_t seed, uint32_t point_id, uint64_t walk, int step,
-                           double *y)
+                           double *y, int *tri)
 {
     or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32)}, walk, -1, -1, -1, {0}};
-    or_uniform_point(P, h, &rng, step, 0, y);
+    int t;
+    or_uniform_point(P, h, &rng, step, 0, y, &t);
+    if (tri) *tri = t;
 }
 void or_test_uniform_part_point(const or_problem *P, int h, int part, uint64_t seed, uint64_t walk, double *y)
 {

@@ -9,11 +9,13 @@ it with its own code.
 Problem dictionary (JSON-compatible):
 
     dim       int, 2..6
-    surfaces  list of {"kind": "sphere" | "star" | "ellipsoid", "center": [dim],
-              "radius": R, "star_a": [K+1], "star_b": [K+1], "matrix": [dim][dim]}
+    surfaces  list of {"kind": "sphere" | "star" | "ellipsoid" | "mesh", "center": [dim],
+              "radius": R, "star_a": [K+1], "star_b": [K+1], "matrix": [dim][dim],
+              "vertices": [nv][3], "triangles": [nt][3]}
               (star: 2D only, r(t) = R (1 + sum_k a_k cos kt + b_k sin kt), index 0
               unused; ellipsoid: d >= 3, (y - c)^T A (y - c) = 1 with A = matrix
-              symmetric positive definite)
+              symmetric positive definite; mesh: 3D, closed, triangles counter-
+              clockwise seen from outside, "center" any reference point inside)
     parent    list of int, parent[0] = -1 (the outer boundary dOmega_1),
               parent[i] = index of the region that contains region i
     sigma     list of float, conductivity inside each region (sigma_1 > 0)
@@ -428,6 +430,132 @@ def point_charge(x):
     return r ** (2 - d), (2 - d) * (r ** -d)[:, None] * x
 
 
+# ---------------------------------------------------------------------------
+# triangle meshes: a star-shaped outer boundary with rock-like inclusions
+# ---------------------------------------------------------------------------
+
+def icosphere(subdiv):
+    """Unit icosphere: the icosahedron with every triangle split into four,
+    subdiv times, vertices projected to the sphere; faces counter-clockwise
+    seen from outside.  20 * 4^subdiv triangles."""
+    t = (1.0 + 5 ** 0.5) / 2.0
+    V = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    V = [np.asarray(v, dtype=np.float64) / np.linalg.norm(v) for v in V]
+    for _ in range(subdiv):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                m = V[a] + V[b]
+                V.append(m / np.linalg.norm(m))
+                mid[key] = len(V) - 1
+            return mid[key]
+
+        nf = []
+        for a, b, c in F:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        F = nf
+    V = np.asarray(V)
+    F = np.asarray(F, dtype=np.int64)
+    # orient outward: the signed volume must be positive
+    v0, v1, v2 = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    if np.sum(np.einsum("ij,ij->i", v0, np.cross(v1, v2))) < 0:
+        F = F[:, ::-1].copy()
+    return V, F
+
+
+def radial_mesh(center, radius, subdiv, amp, seed):
+    """A star-shaped closed mesh: icosphere vertices u moved to
+    center + radius (1 + amp f(u)) u with f a sum of six random plane waves
+    (|f| <= 1), which keeps the surface star-shaped and outward-oriented."""
+    V, F = icosphere(subdiv)
+    rng = np.random.default_rng(seed)
+    k = rng.standard_normal((6, 3)) * 1.5
+    ph = rng.uniform(0, 2 * np.pi, 6)
+    f = np.cos(V @ k.T + ph).sum(axis=1) / 6.0
+    Vr = np.asarray(center, dtype=np.float64) + radius * (1.0 + amp * f)[:, None] * V
+    return Vr, F
+
+
+def _mesh(V, F, center):
+    return {"kind": "mesh", "center": [float(c) for c in center],
+            "vertices": np.asarray(V, dtype=np.float64).tolist(), "triangles": np.asarray(F, dtype=np.int64).tolist()}
+
+
+def winding_number(V, F, P):
+    """Generalised winding number of the closed mesh (V, F) at points P [n, 3]
+    (solid angle of every triangle, Van Oosterom-Strackee): 1 inside, 0 outside."""
+    V = np.asarray(V, dtype=np.float64)
+    F = np.asarray(F, dtype=np.int64)
+    P = np.atleast_2d(np.asarray(P, dtype=np.float64))
+    out = np.zeros(len(P))
+    for lo in range(0, len(P), 256):
+        p = P[lo:lo + 256, None, :]
+        a, b, c = V[F[:, 0]][None] - p, V[F[:, 1]][None] - p, V[F[:, 2]][None] - p
+        la, lb, lc = (np.linalg.norm(v, axis=2) for v in (a, b, c))
+        num = np.einsum("pti,pti->pt", a, np.cross(b, c))
+        den = la * lb * lc + np.einsum("pti,pti->pt", a, b) * lc + np.einsum("pti,pti->pt", b, c) * la \
+            + np.einsum("pti,pti->pt", c, a) * lb
+        out[lo:lo + 256] = np.sum(2 * np.arctan2(num, den), axis=1) / (4 * np.pi)
+    return out
+
+
+def rocks_problem(n_rocks=6, seed=7, subdiv_outer=4, subdiv_rock=3, M=5):
+    """Rock-like inclusions in a star-shaped body, the shape of the paper's
+    groundwater example (a hill with rocks, Sec. 5) with synthetic meshes: the
+    outer boundary a radial mesh of mean radius 1 (amp 0.06, 20 4^subdiv_outer
+    triangles), n_rocks radial meshes of radius U[0.12, 0.2] (amp 0.2), placed
+    by rejection with bounding spheres 0.05 apart.  sigma = 0.2 outside, rocks
+    0.03 - 0.05 (the example's values).  Data of a random harmonic polynomial
+    u_h (degree <= 3), the manufactured solution: b_1 = sigma_1 dn u_h,
+    b_i = (sigma_1 - sigma_i) dn u_h."""
+    rng = np.random.default_rng(seed)
+    Vo, Fo = radial_mesh([0, 0, 0], 1.0, subdiv_outer, 0.06, seed + 1)
+    r_in = float(np.min(np.linalg.norm(Vo, axis=1)))
+    rocks = []
+    tries = 0
+    while len(rocks) < n_rocks and tries < 10000:
+        tries += 1
+        rad = rng.uniform(0.12, 0.2)
+        bound = rad * 1.2
+        c = rng.uniform(-1, 1, 3)
+        if np.linalg.norm(c) + bound > r_in - 0.05:
+            continue
+        if any(np.linalg.norm(c - c2) < bound + b2 + 0.05 for c2, b2, _ in rocks):
+            continue
+        rocks.append((c, bound, rad))
+    surfaces = [_mesh(Vo, Fo, [0, 0, 0])]
+    for j, (c, _, rad) in enumerate(rocks):
+        V, F = radial_mesh(c, rad, subdiv_rock, 0.2, seed + 10 + j)
+        surfaces.append(_mesh(V, F, c))
+    sigma = [0.2] + [float(v) for v in rng.uniform(0.03, 0.05, len(rocks))]
+    terms = random_harmonic_poly(3, rng)
+    flux = [harmonic_poly(sigma[0], terms, 3)] + [harmonic_poly(sigma[0] - s, terms, 3) for s in sigma[1:]]
+    return {"name": "3d-rocks", "dim": 3, "surfaces": surfaces, "parent": [-1] + [0] * len(rocks),
+            "sigma": sigma, "flux": flux, "M": M, "u_terms": terms}
+
+
+def mesh_points(problem, n, seed=17, margin=0.02):
+    """n points inside the outer mesh (winding number > 1/2, and more than
+    `margin` inside the outer mesh's inscribed radius bound), uniform."""
+    s = problem["surfaces"][0]
+    V = np.asarray(s["vertices"])
+    rmax = float(np.max(np.linalg.norm(V - np.asarray(s["center"]), axis=1)))
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        p = rng.uniform(-rmax, rmax, size=(2 * n, 3)) + np.asarray(s["center"])
+        w = winding_number(V, s["triangles"], p)
+        out += list(p[w > 0.5])
+    return np.ascontiguousarray(np.asarray(out[:n], dtype=np.float64))
+
+
 CONFIGS = {
     "2d-concentric": "unit disk + r=0.5 inclusion, 64 polar-grid points, W=1e4, M=4",
     "3d-nested": "spheres 1/0.8/0.5, sigma 1/5/0.2, 4096 ball points, W=1e5, M=6",
@@ -435,4 +563,5 @@ CONFIGS = {
     "6d-nested": "hyperspheres 1/0.6, sigma 1/4, 1024 ball points, W=1e6, M=8",
     "batch": "256 manufactured 2D/3D instances, 1-64 inclusions, P 16..4096, W 1e4..1e5",
     "ellipsoids": "3 nested ellipsoids (Example 2), point charge at the origin, 3D-6D, M = d + 2",
+    "3d-rocks": "star-shaped outer mesh + 6 rock meshes (12800 triangles), manufactured harmonic data, M = 5",
 }
