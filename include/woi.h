@@ -69,14 +69,22 @@ typedef enum {
 } woi_status;
 
 #define WOI_MAX_ELLIPSOIDS 8
+#define WOI_MAX_MESHES 16
+#define WOI_MAX_MESH_TRIANGLES (1 << 22)   /* per geometry, all meshes together */
 
 /* surface kinds */
 enum { WOI_SPHERE = 0,     /* circle (2D) or (d-1)-sphere: centre, radius */
        WOI_STAR = 1,       /* 2D star-shaped curve about `center`:
                               r(t) = radius (1 + sum_{k=1..K} a_k cos kt + b_k sin kt) */
-       WOI_ELLIPSOID = 2 }; /* d >= 3: (y - center)^T A (y - center) = 1, A = matrix symmetric
+       WOI_ELLIPSOID = 2,  /* d >= 3: (y - center)^T A (y - center) = 1, A = matrix symmetric
                               positive definite (Sec. 5, Example 2); at most WOI_MAX_ELLIPSOIDS
                               per geometry */
+       WOI_MESH = 3 };     /* d = 3: closed triangle mesh (Sec. 5), every edge shared by exactly two
+                              triangles with opposite orientations, triangles counter-clockwise
+                              seen from outside (positive enclosed volume); `center` is the
+                              reference point of the surface's local coordinates (any point near
+                              it).  A line crossing one mesh more than 32 times is not supported.
+                              At most WOI_MAX_MESHES per geometry */
 
 typedef struct {
     int type;                         /* WOI_SPHERE, WOI_STAR or WOI_ELLIPSOID */
@@ -86,6 +94,10 @@ typedef struct {
     const double *star_a;             /* [K+1], index 0 ignored (star only) */
     const double *star_b;             /* [K+1], index 0 ignored (star only) */
     const double *matrix;             /* [dim][dim] row-major A (ellipsoid only) */
+    int n_vertices;                   /* mesh only */
+    const double *vertices;           /* [n_vertices][3] (mesh only) */
+    int n_triangles;                  /* mesh only */
+    const int *triangles;             /* [n_triangles][3] vertex indices (mesh only) */
 } woi_surface_desc;
 
 /* flux bases (the data b_i of Sec. 1 on each surface) */

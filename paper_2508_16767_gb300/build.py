@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libwoi.so")
 SOURCES = ["woi_api.cu", "woi_kernels.cu", "woi_k2.cu", "woi_k2s.cu", "woi_k3.cu", "woi_k4.cu", "woi_k5.cu",
-           "woi_k6.cu", "woi_k3e.cu", "woi_k4e.cu", "woi_k5e.cu", "woi_k6e.cu"]
+           "woi_k6.cu", "woi_k3e.cu", "woi_k4e.cu", "woi_k5e.cu", "woi_k6e.cu", "woi_mesh_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

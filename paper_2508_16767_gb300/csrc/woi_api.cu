@@ -17,6 +17,7 @@
 #include "../../include/woi.h"
 #include "woi_kernels.h"
 #include "woi_layout.h"
+#include "woi_mesh_host.h"
 
 using namespace woi;
 
@@ -132,6 +133,8 @@ struct woi_geometry {
     };
     std::vector<Ellipsoid> ell;
     std::vector<int> ell_slot;                 // per surface, -1 if not an ellipsoid
+    std::vector<MeshHost> mesh;
+    std::vector<int> mesh_slot;                // per surface, -1 if not a mesh
 
     bool data_ready = false;
     std::vector<double> sigma, alpha, beta_scale, flux_coef;
@@ -152,6 +155,12 @@ struct woi_geometry {
     float *d_flux_f = nullptr;
     double *d_flux = nullptr, *d_arc_t0 = nullptr, *d_arc_t1 = nullptr, *d_arc_len = nullptr, *d_arc_s0 = nullptr;
     int *d_arc_sign = nullptr;
+    float *d_tri_f = nullptr;
+    double *d_tri_d = nullptr;
+    uint32_t *d_tri_tm1 = nullptr;
+    BvhNode *d_bvh = nullptr;
+    int *d_bvh_tri = nullptr;
+    unsigned int *d_mesh_overflow = nullptr;
     int blob_M = -1;
     // grow-only scratch
     void *d_scratch = nullptr;
@@ -160,7 +169,7 @@ struct woi_geometry {
     std::map<long long, int> occ_cache;        // (dim, vr, general surfaces, block) -> blocks per SM
 
     // kernels with non-sphere surfaces: the star (2D) or ellipsoids (d >= 3)
-    bool general() const { return star_idx >= 0 || !ell.empty(); }
+    bool general() const { return star_idx >= 0 || !ell.empty() || !mesh.empty(); }
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     bool timed = false;
 
@@ -179,6 +188,12 @@ struct woi_geometry {
         cudaFree(d_arc_len);
         cudaFree(d_arc_s0);
         cudaFree(d_arc_sign);
+        cudaFree(d_tri_f);
+        cudaFree(d_tri_d);
+        cudaFree(d_tri_tm1);
+        cudaFree(d_bvh);
+        cudaFree(d_bvh_tri);
+        cudaFree(d_mesh_overflow);
         cudaFree(d_scratch);
         if (ev_start) cudaEventDestroy(ev_start);
         if (ev_stop) cudaEventDestroy(ev_stop);
@@ -189,6 +204,12 @@ struct woi_geometry {
         d_flux = d_arc_t0 = d_arc_t1 = d_arc_len = d_arc_s0 = nullptr;
         d_flux_f = nullptr;
         d_arc_sign = nullptr;
+        d_tri_f = nullptr;
+        d_tri_d = nullptr;
+        d_tri_tm1 = nullptr;
+        d_bvh = nullptr;
+        d_bvh_tri = nullptr;
+        d_mesh_overflow = nullptr;
         d_scratch = nullptr;
         scratch_bytes = 0;
         device = -1;
@@ -304,6 +325,19 @@ std::vector<double> sample_surface(const woi_geometry &g, int i, int m)
         return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
     };
     const woi_surface_desc &s = g.surf[i];
+    if (s.type == WOI_MESH) {
+        // the triangles' corners and centroids (local rows v0, e1, e2 back to global)
+        const MeshHost &mh = g.mesh[g.mesh_slot[i]];
+        p.assign((size_t)mh.ntri * 2 * 3, 0.0);
+        for (int t = 0; t < mh.ntri; ++t) {
+            const double *r = &mh.tri[(size_t)t * 12];
+            for (int k = 0; k < 3; ++k) {
+                p[(size_t)t * 6 + k] = mh.center[k] + r[k];
+                p[(size_t)t * 6 + 3 + k] = mh.center[k] + r[k] + (r[3 + k] + r[6 + k]) / 3.0;
+            }
+        }
+        return p;
+    }
     for (int j = 0; j < m; ++j) {
         double u[kMaxDim + 1], nn = 0.0;
         for (int k = 0; k < d; k += 2) {
@@ -361,6 +395,7 @@ bool inside_surface(const woi_geometry &g, int i, const double *x)
     const woi_surface_desc &s = g.surf[i];
     if (s.type == WOI_SPHERE) return dist(g.dim, x, s.center) < s.radius;
     if (s.type == WOI_ELLIPSOID) return ellipsoid_form(g, i, x) < 1.0;
+    if (s.type == WOI_MESH) return mesh_inside(g.mesh[g.mesh_slot[i]], x);
     double t = std::atan2(x[1] - s.center[1], x[0] - s.center[0]);
     double r, dr;
     g.star.eval(t, &r, &dr);
@@ -381,8 +416,8 @@ woi_status check_nesting(const woi_geometry &g)
         } else if (d >= 3) {
             // convex surfaces: every point of surface i inside the parent (a dense sample)
             std::vector<double> pts = sample_surface(g, i, M * 4);
-            for (int j = 0; j < M * 4; ++j)
-                if (!inside_surface(g, p, &pts[(size_t)j * d]))
+            for (size_t j = 0; j < pts.size() / d; ++j)
+                if (!inside_surface(g, p, &pts[j * d]))
                     return fail(WOI_E_GEOMETRY, "surface %d is not strictly inside its parent %d", i, p);
         } else {
             std::vector<double> pts = sample_curve(g, i, M);
@@ -405,9 +440,10 @@ woi_status check_nesting(const woi_geometry &g)
                     return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
             } else if (d >= 3) {
                 std::vector<double> a = sample_surface(g, i, M * 4), b = sample_surface(g, j, M * 4);
-                for (int k = 0; k < M * 4; ++k)
-                    if (inside_surface(g, j, &a[(size_t)k * d]) || inside_surface(g, i, &b[(size_t)k * d]))
-                        return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
+                for (size_t k = 0; k < a.size() / d; ++k)
+                    if (inside_surface(g, j, &a[k * d])) return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
+                for (size_t k = 0; k < b.size() / d; ++k)
+                    if (inside_surface(g, i, &b[k * d])) return fail(WOI_E_GEOMETRY, "surfaces %d and %d overlap", i, j);
             } else {
                 std::vector<double> a = sample_curve(g, i, M), b = sample_curve(g, j, M);
                 for (int k = 0; k < M; ++k)
@@ -486,10 +522,14 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
     g->surf.assign(surfaces, surfaces + n_surf);
     g->parent.assign(parent, parent + n_surf);
     g->ell_slot.assign(n_surf, -1);
+    g->mesh_slot.assign(n_surf, -1);
+    size_t mesh_tris = 0;
     for (int i = 0; i < n_surf; ++i) {
         woi_surface_desc &s = g->surf[i];
         s.star_a = s.star_b = nullptr;         // deep copy below; no pointer retained
         s.matrix = nullptr;
+        s.vertices = nullptr;
+        s.triangles = nullptr;
         if (s.type == WOI_SPHERE) {
             if (!(s.radius > 0.0) || !std::isfinite(s.radius)) {
                 delete g;
@@ -563,6 +603,26 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
                 }
             g->ell_slot[i] = (int)g->ell.size();
             g->ell.push_back(e);
+        } else if (s.type == WOI_MESH) {
+            if (dim != 3) { delete g; return fail(WOI_E_UNSUPPORTED, "mesh surfaces need dim = 3"); }
+            if ((int)g->mesh.size() >= kMaxMesh) {
+                delete g;
+                return fail(WOI_E_UNSUPPORTED, "at most %d meshes per geometry", kMaxMesh);
+            }
+            const woi_surface_desc &in = surfaces[i];
+            mesh_tris += (size_t)std::max(0, in.n_triangles);
+            if (mesh_tris > (size_t)WOI_MAX_MESH_TRIANGLES) {
+                delete g;
+                return fail(WOI_E_UNSUPPORTED, "more than %d mesh triangles", WOI_MAX_MESH_TRIANGLES);
+            }
+            MeshHost mh;
+            std::string why = mesh_prepare(in.vertices, in.n_vertices, in.triangles, in.n_triangles, in.center, mh);
+            if (!why.empty()) {
+                delete g;
+                return fail(WOI_E_GEOMETRY, "surface %d: %s", i, why.c_str());
+            }
+            g->mesh_slot[i] = (int)g->mesh.size();
+            g->mesh.push_back(std::move(mh));
         } else {
             delete g;
             return fail(WOI_E_INVALID_ARG, "surface %d: unknown type %d", i, s.type);
@@ -598,6 +658,8 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
             g->area[i] = omega_d(dim) * std::pow(g->surf[i].radius, dim - 1);
         } else if (g->surf[i].type == WOI_ELLIPSOID) {
             g->area[i] = ellipsoid_area(dim, g->ell[g->ell_slot[i]].lam);
+        } else if (g->surf[i].type == WOI_MESH) {
+            g->area[i] = g->mesh[g->mesh_slot[i]].area;
         }
     }
     if (g->star_idx >= 0) {
@@ -717,7 +779,8 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             // integrates to zero over the surface (the potential is harmonic inside)
             const double *x0 = c.data() + 1;
             const bool outside = s.type == WOI_ELLIPSOID ? ellipsoid_form(*g, i, x0) > 1.0 + 1e-12
-                                                         : dist(d, x0, s.center) > s.radius * (1.0 + 1e-12);
+                                 : s.type == WOI_MESH   ? !inside_surface(*g, i, x0)
+                                                        : dist(d, x0, s.center) > s.radius * (1.0 + 1e-12);
             if (!outside) return fail(WOI_E_COMPAT, "flux[%d]: the charge lies inside the surface, int b dA != 0", i);
             break;
         }
@@ -990,6 +1053,19 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
         }
         for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g.star_panel_s[j];
     }
+    b.n_mesh = (int)g.mesh.size();
+    for (int i = 0; i < g.n; ++i) b.mesh_slot[i] = g.mesh_slot[i];
+    {
+        int tri_off = 0, node_off = 0;
+        for (int m = 0; m < b.n_mesh; ++m) {
+            b.mesh_tri_off[m] = tri_off;
+            b.mesh_ntri[m] = g.mesh[m].ntri;
+            b.mesh_node_off[m] = node_off;
+            b.mesh_scale[m] = g.mesh[m].scale;
+            tri_off += g.mesh[m].ntri;
+            node_off += (int)g.mesh[m].nodes.size();
+        }
+    }
     b.n_ell = (int)g.ell.size();
     for (int e = 0; e < b.n_ell; ++e) {
         for (int a = 0; a < kMaxDim; ++a)
@@ -1014,6 +1090,35 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
         if ((st = upload(&g->d_arc_len, g->arc_len, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_s0, g->arc_s0, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_sign, g->arc_sign, s)) != WOI_OK) return st;
+        if (!g->mesh.empty()) {
+            // all meshes concatenated: triangle rows, thresholds, nodes (children and leaf ranges
+            // shifted by the mesh's offsets) and leaf-triangle lists (global triangle indices)
+            std::vector<double> tri_d;
+            std::vector<uint32_t> tm1;
+            std::vector<BvhNode> nodes;
+            std::vector<int> leaf;
+            for (const MeshHost &mh : g->mesh) {
+                const int tri_off = (int)tm1.size(), node_off = (int)nodes.size();
+                tri_d.insert(tri_d.end(), mh.tri.begin(), mh.tri.end());
+                tm1.insert(tm1.end(), mh.tm1.begin(), mh.tm1.end());
+                for (BvhNode nd : mh.nodes) {
+                    if (nd.b < 0) nd.a += tri_off;
+                    else { nd.a += node_off; nd.b += node_off; }
+                    nodes.push_back(nd);
+                }
+                for (int t : mh.leaf_tri) leaf.push_back(t + tri_off);
+            }
+            std::vector<float> tri_f(tri_d.begin(), tri_d.end());
+            if ((st = upload(&g->d_tri_d, tri_d, s)) != WOI_OK) return st;
+            if ((st = upload(&g->d_tri_f, tri_f, s)) != WOI_OK) return st;
+            if ((st = upload(&g->d_tri_tm1, tm1, s)) != WOI_OK) return st;
+            if ((st = upload(&g->d_bvh, nodes, s)) != WOI_OK) return st;
+            if ((st = upload(&g->d_bvh_tri, leaf, s)) != WOI_OK) return st;
+            if (!g->d_mesh_overflow) WOI_CUDA(cudaMalloc((void **)&g->d_mesh_overflow, sizeof(unsigned int)));
+            WOI_CUDA(cudaMemsetAsync(g->d_mesh_overflow, 0, sizeof(unsigned int), s));
+            // the host vectors die at the end of this block: finish the pageable copies first
+            WOI_CUDA(cudaStreamSynchronize(s));
+        }
         if (!g->d_blob) WOI_CUDA(cudaMalloc((void **)&g->d_blob, sizeof(DevGeom)));
     }
     DevGeom &b = g->blob;
@@ -1025,6 +1130,12 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
     b.arc_len = g->d_arc_len;
     b.arc_s0 = g->d_arc_s0;
     b.arc_sign = g->d_arc_sign;
+    b.tri_f = g->d_tri_f;
+    b.tri_d = g->d_tri_d;
+    b.tri_tm1 = g->d_tri_tm1;
+    b.bvh = g->d_bvh;
+    b.bvh_tri = g->d_bvh_tri;
+    b.mesh_overflow = g->d_mesh_overflow;
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     WOI_CUDA(cudaMemcpyAsync(g->d_blob, &b, sizeof(DevGeom), cudaMemcpyHostToDevice, s));
     g->dev_dirty = false;
@@ -1238,7 +1349,18 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
             any_host = true;
         }
     }
-    if (any_host || !pointer_on_device(points)) WOI_CUDA(cudaStreamSynchronize(s));
+    if (any_host || !pointer_on_device(points)) {
+        WOI_CUDA(cudaStreamSynchronize(s));
+        if (g->d_mesh_overflow) {
+            unsigned int over = 0;
+            WOI_CUDA(cudaMemcpy(&over, g->d_mesh_overflow, sizeof(over), cudaMemcpyDeviceToHost));
+            if (over) {
+                WOI_CUDA(cudaMemset(g->d_mesh_overflow, 0, sizeof(over)));
+                return fail(WOI_E_GEOMETRY, "%u lines crossed a mesh more than %d times; estimates are invalid", over,
+                            kMaxHits);
+            }
+        }
+    }
     return WOI_OK;
 }
 
@@ -1703,6 +1825,7 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     if ((st = check_opts(g, o, n_pts, 0, n_walks)) != WOI_OK) return st;
     if (o->precision != WOI_MIXED) return fail(WOI_E_UNSUPPORTED, "the allocation-free estimate runs the mixed path only");
     if (o->tile_points) return fail(WOI_E_UNSUPPORTED, "the allocation-free estimate has no shared-trajectory mode");
+    if (!g->mesh.empty()) return fail(WOI_E_UNSUPPORTED, "the allocation-free estimate does not take meshes");
     if (n_pts > 0 && !pointer_on_device(points)) return fail(WOI_E_INVALID_ARG, "points must be device memory");
     double *outs[4] = {u, grad, se_u, se_grad};
     for (double *p : outs)

@@ -899,9 +899,160 @@ struct Chain {
     Real v[D];
     Real Q, T;
     bool alive;
-    int aj;       // on a star: the state's angle as node aj + offset ad
+    int aj;       // on a star: the state's angle as node aj + offset ad; on a mesh: its triangle
     Real ad;
 };
+
+// ---------------------------------------------------------------------------
+// triangle meshes (d = 3, Sec. 5): rows (v0, e1, e2, n) in the surface's local coordinates
+// ---------------------------------------------------------------------------
+template <typename Real> __device__ __forceinline__ const Real *tri_rows(const DevGeom *gd);
+template <> __device__ __forceinline__ const float *tri_rows<float>(const DevGeom *gd) { return gd->tri_f; }
+template <> __device__ __forceinline__ const double *tri_rows<double>(const DevGeom *gd) { return gd->tri_d; }
+
+// uniform point by area on mesh slot m (Eq. naive_woi_p0): word 1 picks triangle j, the
+// first with w1 <= T_j - 1; words 2 and 3 give barycentric (1 - s, s (1 - w), s w), s = sqrt(u)
+template <typename Real>
+__device__ void mesh_uniform(const DevGeom *gd, int m, const StepWords &w, Real *v, Real *nrm, int *tri)
+{
+    const uint32_t w1 = w.a.y;
+    int lo = gd->mesh_tri_off[m], hi = lo + gd->mesh_ntri[m] - 1;
+    while (lo < hi) {                       // first j in [lo, hi] with w1 <= tm1[j] (tm1[last] = 2^32 - 1)
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(gd->tri_tm1 + mid) < w1) lo = mid + 1;
+        else hi = mid;
+    }
+    const Real u = u01<Real>(w.a.z), ww = u01<Real>(w.a.w);
+    const Real sq = RealOps<Real>::sqrt_(u), b1 = sq * ((Real)1 - ww), b2 = sq * ww;
+    const Real *r = tri_rows<Real>(gd) + (size_t)lo * 12;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = __ldg(r + k) + b1 * __ldg(r + 3 + k) + b2 * __ldg(r + 6 + k);
+        nrm[k] = __ldg(r + 9 + k);
+    }
+    *tri = lo;
+}
+
+// crossings of the line (ray: t > 0) o + t z with mesh slot m, skipping triangle `exclude`,
+// through the hierarchy; up to kMaxHits (t, triangle) pairs, a count above that is reported
+// through the overflow counter and truncated
+template <typename Real>
+__device__ int mesh_hits(const DevGeom *gd, int m, const Real *o, const Real *z, bool ray, int exclude, Real *tt,
+                         int *tri)
+{
+    const Real *rows = tri_rows<Real>(gd);
+    const BvhNode *nodes = gd->bvh;
+    const Real iz[3] = {(Real)1 / z[0], (Real)1 / z[1], (Real)1 / z[2]};
+    int stack[kMeshStack];
+    int sp = 0, q = 0;
+    bool over = false;
+    stack[sp++] = gd->mesh_node_off[m];
+    while (sp > 0) {
+        const BvhNode n = nodes[stack[--sp]];
+        // slab test against the padded box
+        Real t0 = ray ? (Real)0 : (Real)-1e30, t1 = (Real)1e30;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const Real ta = ((Real)n.lo[k] - o[k]) * iz[k], tb = ((Real)n.hi[k] - o[k]) * iz[k];
+            const Real tmn = ta < tb ? ta : tb, tmx = ta < tb ? tb : ta;
+            t0 = tmn > t0 ? tmn : t0;
+            t1 = tmx < t1 ? tmx : t1;
+        }
+        if (!(t0 <= t1)) continue;
+        if (n.b < 0) {
+            for (int i = n.a; i < n.a - n.b; ++i) {
+                const int t = __ldg(gd->bvh_tri + i);
+                if (t == exclude) continue;
+                const Real *r = rows + (size_t)t * 12;
+                const Real e1[3] = {__ldg(r + 3), __ldg(r + 4), __ldg(r + 5)};
+                const Real e2[3] = {__ldg(r + 6), __ldg(r + 7), __ldg(r + 8)};
+                const Real p[3] = {z[1] * e2[2] - z[2] * e2[1], z[2] * e2[0] - z[0] * e2[2], z[0] * e2[1] - z[1] * e2[0]};
+                const Real det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+                if (det == (Real)0) continue;
+                const Real idet = (Real)1 / det;
+                const Real sv[3] = {o[0] - __ldg(r), o[1] - __ldg(r + 1), o[2] - __ldg(r + 2)};
+                const Real a = (sv[0] * p[0] + sv[1] * p[1] + sv[2] * p[2]) * idet;
+                if (a < (Real)0 || a > (Real)1) continue;
+                const Real qv[3] = {sv[1] * e1[2] - sv[2] * e1[1], sv[2] * e1[0] - sv[0] * e1[2], sv[0] * e1[1] - sv[1] * e1[0]};
+                const Real b = (z[0] * qv[0] + z[1] * qv[1] + z[2] * qv[2]) * idet;
+                if (b < (Real)0 || a + b > (Real)1) continue;
+                const Real th = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * idet;
+                if (ray && !(th > (Real)0)) continue;
+                if (q < kMaxHits) {
+                    tt[q] = th;
+                    tri[q] = t;
+                    ++q;
+                } else {
+                    over = true;
+                }
+            }
+        } else if (sp + 2 <= kMeshStack) {
+            stack[sp++] = n.a;
+            stack[sp++] = n.b;
+        } else {
+            over = true;
+        }
+    }
+    if (over && gd->mesh_overflow) atomicAdd(gd->mesh_overflow, 1u);
+    return q;
+}
+
+// transition i >= 1 to mesh h (relation rel); dy = y - c_h, the state's triangle in ch.aj.
+// Line (same surface, skipping the state's own triangle) or ray (from a descendant): the
+// pick-th crossing in line order (choice word 3), T *= q sign((y' - y).n(y')), Q *= 1/2 for the
+// line.  Otherwise: uniform by area with Q *= K*(y', y) |dOmega_h|.
+template <typename Real>
+__device__ void mesh_step(const DevGeom *gd, Real area, int h, int rel, const StepWords &w, const Real *dy,
+                          Chain<Real, 3> &ch)
+{
+    using O = RealOps<Real>;
+    constexpr double PI = 3.14159265358979323846;
+    const int m = gd->mesh_slot[h];
+    if (rel == 2) {
+        Real vn[3], nrm[3];
+        int t;
+        mesh_uniform<Real>(gd, m, w, vn, nrm, &t);
+        Real r2 = 0, dot = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const Real diff = vn[c] - dy[c];
+            r2 += diff * diff;
+            dot += diff * nrm[c];
+            ch.v[c] = vn[c];
+        }
+        const Real ir = O::rsqrt_(r2);
+        ch.Q *= dot * ir * ir * ir * (Real)(1.0 / (4.0 * PI)) * area;
+        ch.aj = t;
+    } else {
+        Real z[3];
+        direction<Real, 3>(w, z);
+        Real tt[kMaxHits];
+        int tri[kMaxHits];
+        const int q = mesh_hits<Real>(gd, m, dy, z, rel == 1, rel == 0 ? ch.aj : -1, tt, tri);
+        if (q == 0) {                          // reading R5
+            ch.alive = false;
+            ch.T = 0;
+            return;
+        }
+        const int pick = (int)(((uint64_t)w.get(choice_word<3>()) * (uint64_t)q) >> 32);
+        int sel = 0;
+        for (int a = 0; a < q; ++a) {
+            int rank = 0;
+            for (int b = 0; b < q; ++b) rank += (tt[b] < tt[a]) || (tt[b] == tt[a] && b < a);
+            if (rank == pick) sel = a;
+        }
+        const Real t = tt[sel];
+        const Real *r = tri_rows<Real>(gd) + (size_t)tri[sel] * 12;
+        const Real zn = z[0] * __ldg(r + 9) + z[1] * __ldg(r + 10) + z[2] * __ldg(r + 11);
+        const Real dot = t * zn;               // (y' - y) . n(y')
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ch.v[c] = dy[c] + t * z[c];
+        if (rel == 0) ch.Q *= (Real)0.5;
+        ch.T *= (Real)q * (dot > 0 ? (Real)1 : (dot < 0 ? (Real)-1 : (Real)0));
+        ch.aj = tri[sel];
+    }
+    ch.s = h;
+}
 
 // start (i = 0): y_0 uniform on dOmega_h (plain) or on dOmega_h^{+/-} (VR), Q = beta(y_0) |part|
 template <typename Real, int D, bool VR, bool STAR>
@@ -926,9 +1077,16 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
         }
     }
     const bool is_star = STAR && g.type[h] == kStar;
-    bool is_ell = false;
+    bool is_ell = false, is_mesh = false;
     if constexpr (STAR && D >= 3) is_ell = g.type[h] == kEllipsoid;
-    if (is_ell) {
+    if constexpr (STAR && D == 3) is_mesh = g.type[h] == kMesh;
+    if (is_mesh) {
+        if constexpr (STAR && D == 3) {
+            mesh_uniform<Real>(gd, gd->mesh_slot[h], w, ch.v, nrm, &ch.aj);
+#pragma unroll
+            for (int c = 0; c < D; ++c) u[c] = nrm[c];
+        }
+    } else if (is_ell) {
         if constexpr (STAR && D >= 3) {
             const SEll<Real> &E = static_cast<const SGeomE<Real> &>(g).ell;
             ell_uniform<Real, D>(E, E.slot[h], rng, 0, k, w, ch.v, nrm);
@@ -1064,8 +1222,8 @@ __device__ void ell_step(const SGeomE<Real> &g, int h, int rel, const StepWords 
 
 // transition i >= 1 from surface ch.s to h (relation rel)
 template <typename Real, int D, bool STAR>
-__device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords &w, const Rng &rng, int step,
-                           int chain, Chain<Real, D> &ch)
+__device__ void chain_step(const SGeom<Real> &g, const DevGeom *gd, int h, int rel, const StepWords &w, const Rng &rng,
+                           int step, int chain, Chain<Real, D> &ch)
 {
     using O = RealOps<Real>;
     constexpr double PI = 3.14159265358979323846;
@@ -1078,6 +1236,12 @@ __device__ void chain_step(const SGeom<Real> &g, int h, int rel, const StepWords
         center_diff<Real, D>(g, ch.s, h, dy);
 #pragma unroll
         for (int c = 0; c < D; ++c) dy[c] += ch.v[c];
+    }
+    if constexpr (STAR && D == 3) {
+        if (g.type[h] == kMesh) {
+            mesh_step<Real>(gd, g.area[h], h, rel, w, dy, ch);
+            return;
+        }
     }
     if constexpr (STAR && D >= 3) {
         if (g.type[h] == kEllipsoid) {
@@ -1215,7 +1379,7 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
             if (i == 0) {
                 chain_start<Real, D, VR, STAR>(g, gd, h, k, w, rng, ch[k]);
             } else if (ch[k].alive) {
-                chain_step<Real, D, STAR>(g, h, rel, w, rng, i, k, ch[k]);
+                chain_step<Real, D, STAR>(g, gd, h, rel, w, rng, i, k, ch[k]);
             }
             sink(i, k, ch[k], ch[k].alive ? g.coef[i] * S * ch[k].Q * ch[k].T : (Real)0);
         }

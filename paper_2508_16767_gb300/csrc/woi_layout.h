@@ -15,9 +15,20 @@ constexpr int kNodes = 256;            // angle nodes t_j = 2 pi j / kNodes: sta
                                        // arc-length panels and the angle-addition table
 constexpr int kMaxRoots = 2 * (kMaxStar + 1) + 2;
 constexpr int kMaxEll = 8;             // ellipsoids per instance (WOI_MAX_ELLIPSOIDS)
+constexpr int kMaxMesh = 16;           // meshes per instance (WOI_MAX_MESHES)
+constexpr int kMeshStack = 64;         // BVH traversal stack (the host caps the tree depth below it)
+constexpr int kMaxHits = 32;           // intersections of one line with one mesh
 constexpr int kEllAttempts = 64;       // rejection attempts for a uniform point on an ellipsoid
 
-enum { kSphere = 0, kStar = 1, kEllipsoid = 2 };
+enum { kSphere = 0, kStar = 1, kEllipsoid = 2, kMesh = 3 };
+
+// a node of a mesh's bounding-volume hierarchy (local coordinates of the surface, FP32 bounds
+// rounded outward and padded): internal node a, b = children; leaf a = first entry of the
+// leaf-triangle list, b = -(number of triangles)
+struct BvhNode {
+    float lo[3], hi[3];
+    int a, b;
+};
 enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4 };
 
 struct DevGeom {
@@ -56,6 +67,18 @@ struct DevGeom {
     double ell_A[kMaxEll][kMaxDim][kMaxDim];
     double ell_map[kMaxEll][kMaxDim][kMaxDim];
     double ell_jmax[kMaxEll];
+    // triangle meshes (d = 3), all meshes of the instance concatenated; triangle rows are
+    // (v0, e1 = v1 - v0, e2 = v2 - v0, unit normal of e1 x e2) in the surface's local coordinates
+    int n_mesh;
+    int mesh_slot[kMaxSurf];           // slot of surface i, -1 if it is not a mesh
+    int mesh_tri_off[kMaxMesh], mesh_ntri[kMaxMesh], mesh_node_off[kMaxMesh];
+    double mesh_scale[kMaxMesh];       // largest |vertex - centre|
+    const float *tri_f;                // [n_tri][12]
+    const double *tri_d;               // [n_tri][12]
+    const uint32_t *tri_tm1;           // [n_tri] T_j - 1 of the area-proportional triangle choice
+    const BvhNode *bvh;                // all meshes' nodes
+    const int *bvh_tri;                // leaf-triangle lists (indices into the triangle rows)
+    unsigned int *mesh_overflow;       // device counter of lines with more than kMaxHits crossings
 };
 
 // one instance of a (possibly batched) estimate

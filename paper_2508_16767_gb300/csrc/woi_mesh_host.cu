@@ -1,0 +1,234 @@
+// woi_mesh_host.cu -- host-side preparation of closed triangle meshes (no device code).
+#include "woi_mesh_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <utility>
+
+namespace woi {
+
+namespace {
+
+struct Box {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    void add(const double *p)
+    {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], p[k]);
+            hi[k] = std::max(hi[k], p[k]);
+        }
+    }
+};
+
+// float bounds that contain [lo, hi] with a margin for the FP32 slab test
+void to_node(const Box &b, double pad, BvhNode &n)
+{
+    for (int k = 0; k < 3; ++k) {
+        float l = (float)(b.lo[k] - pad), h = (float)(b.hi[k] + pad);
+        if ((double)l > b.lo[k] - pad) l = std::nextafter(l, -INFINITY);
+        if ((double)h < b.hi[k] + pad) h = std::nextafter(h, INFINITY);
+        n.lo[k] = l;
+        n.hi[k] = h;
+    }
+}
+
+struct Builder {
+    const MeshHost &m;
+    std::vector<double> cen;                 // [ntri][3] centroids
+    std::vector<BvhNode> &nodes;
+    std::vector<int> &ids;
+    double pad;
+    int max_depth = 0;
+
+    Box tri_box(int t) const
+    {
+        Box b;
+        const double *r = &m.tri[(size_t)t * 12];
+        double p[3];
+        b.add(r);
+        for (int k = 0; k < 3; ++k) p[k] = r[k] + r[3 + k];
+        b.add(p);
+        for (int k = 0; k < 3; ++k) p[k] = r[k] + r[6 + k];
+        b.add(p);
+        return b;
+    }
+
+    // node for ids[b, e); children built depth-first, the left child right after its parent
+    int build(int b, int e, int depth)
+    {
+        max_depth = std::max(max_depth, depth);
+        const int me = (int)nodes.size();
+        nodes.push_back(BvhNode{});
+        Box box, cbox;
+        for (int i = b; i < e; ++i) {
+            Box tb = tri_box(ids[i]);
+            box.add(tb.lo);
+            box.add(tb.hi);
+            cbox.add(&cen[(size_t)ids[i] * 3]);
+        }
+        BvhNode node{};
+        to_node(box, pad, node);
+        if (e - b <= 4) {
+            node.a = b;
+            node.b = -(e - b);
+            nodes[me] = node;
+            return me;
+        }
+        int axis = 0;
+        for (int k = 1; k < 3; ++k)
+            if (cbox.hi[k] - cbox.lo[k] > cbox.hi[axis] - cbox.lo[axis]) axis = k;
+        const int mid = (b + e) / 2;
+        std::nth_element(ids.begin() + b, ids.begin() + mid, ids.begin() + e, [&](int x, int y) {
+            const double cx = cen[(size_t)x * 3 + axis], cy = cen[(size_t)y * 3 + axis];
+            return cx < cy || (cx == cy && x < y);
+        });
+        const int l = build(b, mid, depth + 1);
+        const int r = build(mid, e, depth + 1);
+        node.a = l;
+        node.b = r;
+        nodes[me] = node;
+        return me;
+    }
+};
+
+// ray / triangle (Moller-Trumbore) in FP64 on a local-coordinate row; t > 0 hits counted
+bool ray_tri(const double *r, const double *o, const double *z, double *t_out)
+{
+    const double *e1 = r + 3, *e2 = r + 6;
+    const double p[3] = {z[1] * e2[2] - z[2] * e2[1], z[2] * e2[0] - z[0] * e2[2], z[0] * e2[1] - z[1] * e2[0]};
+    const double det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+    if (det == 0.0) return false;
+    const double s[3] = {o[0] - r[0], o[1] - r[1], o[2] - r[2]};
+    const double a = (s[0] * p[0] + s[1] * p[1] + s[2] * p[2]) / det;
+    if (a < 0.0 || a > 1.0) return false;
+    const double q[3] = {s[1] * e1[2] - s[2] * e1[1], s[2] * e1[0] - s[0] * e1[2], s[0] * e1[1] - s[1] * e1[0]};
+    const double bb = (z[0] * q[0] + z[1] * q[1] + z[2] * q[2]) / det;
+    if (bb < 0.0 || a + bb > 1.0) return false;
+    *t_out = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) / det;
+    return true;
+}
+
+}  // namespace
+
+std::string mesh_prepare(const double *V, int nv, const int *T, int nt, const double *center, MeshHost &m)
+{
+    char buf[256];
+    if (nv < 4 || nt < 4 || !V || !T) return "a closed mesh needs at least 4 vertices and 4 triangles";
+    for (int i = 0; i < 3 * nv; ++i)
+        if (!std::isfinite(V[i])) return "vertex coordinates must be finite";
+    // closed and consistently oriented: every directed edge once, and its reverse once
+    std::map<std::pair<int, int>, int> edges;
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int a = T[3 * t + k], b = T[3 * t + (k + 1) % 3];
+            if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) {
+                std::snprintf(buf, sizeof buf, "triangle %d has a bad vertex index", t);
+                return buf;
+            }
+            if (++edges[{a, b}] > 1) {
+                std::snprintf(buf, sizeof buf, "edge (%d, %d) is used twice in the same direction", a, b);
+                return buf;
+            }
+        }
+    for (const auto &e : edges)
+        if (!edges.count({e.first.second, e.first.first})) {
+            std::snprintf(buf, sizeof buf, "edge (%d, %d) has no opposite edge: the mesh is not closed", e.first.first,
+                          e.first.second);
+            return buf;
+        }
+    for (int k = 0; k < 3; ++k) m.center[k] = center[k];
+    m.ntri = nt;
+    m.tri.assign((size_t)nt * 12, 0.0);
+    m.tri_area.assign(nt, 0.0);
+    m.scale = 0.0;
+    for (int i = 0; i < nv; ++i) {
+        double r2 = 0.0;
+        for (int k = 0; k < 3; ++k) r2 += (V[3 * i + k] - center[k]) * (V[3 * i + k] - center[k]);
+        m.scale = std::max(m.scale, std::sqrt(r2));
+    }
+    double vol6 = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        const double *v0 = V + 3 * T[3 * t], *v1 = V + 3 * T[3 * t + 1], *v2 = V + 3 * T[3 * t + 2];
+        double *r = &m.tri[(size_t)t * 12];
+        for (int k = 0; k < 3; ++k) {
+            r[k] = v0[k] - center[k];
+            r[3 + k] = v1[k] - v0[k];
+            r[6 + k] = v2[k] - v0[k];
+        }
+        const double *e1 = r + 3, *e2 = r + 6;
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1];
+        const double cy = e1[2] * e2[0] - e1[0] * e2[2];
+        const double cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double ln = std::sqrt(cx * cx + cy * cy + cz * cz);
+        if (!(ln > 1e-14 * m.scale * m.scale)) {
+            std::snprintf(buf, sizeof buf, "triangle %d is degenerate", t);
+            return buf;
+        }
+        r[9] = cx / ln;
+        r[10] = cy / ln;
+        r[11] = cz / ln;
+        m.tri_area[t] = 0.5 * ln;
+        vol6 += r[0] * cx + r[1] * cy + r[2] * cz;     // (v0 - c) . (e1 x e2) = (v0-c).((v1-c) x (v2-c))
+    }
+    if (!(vol6 > 0.0)) return "the enclosed volume is not positive: triangles must be counter-clockwise seen from outside";
+    // P(triangle j) = area_j / A as thresholds T_j = floor(2^32 C_j / A) in input order
+    double A = 0.0;
+    for (int t = 0; t < nt; ++t) A += m.tri_area[t];
+    m.area = A;
+    m.tm1.assign(nt, 0);
+    double C = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        C += m.tri_area[t];
+        const uint64_t th = (t == nt - 1) ? (1ull << 32) : (uint64_t)std::floor(std::ldexp(C / A, 32));
+        m.tm1[t] = (uint32_t)(th - 1);
+    }
+    // the hierarchy: median split of the centroids along the widest axis, leaves of <= 4
+    m.nodes.clear();
+    m.leaf_tri.resize(nt);
+    for (int t = 0; t < nt; ++t) m.leaf_tri[t] = t;
+    Builder bld{m, std::vector<double>((size_t)nt * 3), m.nodes, m.leaf_tri, 1e-6 * m.scale};
+    for (int t = 0; t < nt; ++t) {
+        const double *r = &m.tri[(size_t)t * 12];
+        for (int k = 0; k < 3; ++k) bld.cen[(size_t)t * 3 + k] = r[k] + (r[3 + k] + r[6 + k]) / 3.0;
+    }
+    bld.build(0, nt, 0);
+    m.depth = bld.max_depth;
+    if (m.depth + 2 >= kMeshStack) return "the mesh hierarchy is too deep";
+    return std::string();
+}
+
+bool mesh_inside(const MeshHost &m, const double *x)
+{
+    // a direction with no special relation to the mesh; odd crossing count means inside
+    const double z[3] = {0.5773502691896258 + 1.234e-3, 0.5773502691896258 - 2.345e-3, 0.5773502691896258 + 0.987e-3};
+    const double o[3] = {x[0] - m.center[0], x[1] - m.center[1], x[2] - m.center[2]};
+    int count = 0;
+    int stack[kMeshStack], sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const BvhNode &n = m.nodes[stack[--sp]];
+        double t0 = 0.0, t1 = 1e300;
+        bool miss = false;
+        for (int k = 0; k < 3 && !miss; ++k) {
+            const double ta = ((double)n.lo[k] - o[k]) / z[k], tb = ((double)n.hi[k] - o[k]) / z[k];
+            t0 = std::max(t0, std::min(ta, tb));
+            t1 = std::min(t1, std::max(ta, tb));
+            miss = t0 > t1;
+        }
+        if (miss) continue;
+        if (n.b < 0) {
+            for (int i = n.a; i < n.a - n.b; ++i) {
+                double t;
+                if (ray_tri(&m.tri[(size_t)m.leaf_tri[i] * 12], o, z, &t) && t > 0.0) ++count;
+            }
+        } else {
+            stack[sp++] = n.a;
+            stack[sp++] = n.b;
+        }
+    }
+    return (count & 1) == 1;
+}
+
+}  // namespace woi

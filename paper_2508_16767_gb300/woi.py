@@ -21,8 +21,8 @@ import numpy as np
 from . import build as _build
 
 WOI_MAX_DIM = 6
-WOI_SPHERE, WOI_STAR, WOI_ELLIPSOID = 0, 1, 2
-KIND = {"sphere": WOI_SPHERE, "star": WOI_STAR, "ellipsoid": WOI_ELLIPSOID}
+WOI_SPHERE, WOI_STAR, WOI_ELLIPSOID, WOI_MESH = 0, 1, 2, 3
+KIND = {"sphere": WOI_SPHERE, "star": WOI_STAR, "ellipsoid": WOI_ELLIPSOID, "mesh": WOI_MESH}
 FLUX = {"zero": 0, "fourier": 1, "real_sh": 2, "harmonic_poly": 3, "point_charge": 4}
 WOI_PLAIN, WOI_VR = 0, 1
 WOI_MIXED, WOI_FP64_PLAIN = 0, 1
@@ -43,7 +43,9 @@ class WoiError(RuntimeError):
 class SurfaceDesc(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("center", ctypes.c_double * WOI_MAX_DIM), ("radius", ctypes.c_double),
                 ("star_degree", ctypes.c_int), ("star_a", ctypes.POINTER(ctypes.c_double)),
-                ("star_b", ctypes.POINTER(ctypes.c_double)), ("matrix", ctypes.POINTER(ctypes.c_double))]
+                ("star_b", ctypes.POINTER(ctypes.c_double)), ("matrix", ctypes.POINTER(ctypes.c_double)),
+                ("n_vertices", ctypes.c_int), ("vertices", ctypes.POINTER(ctypes.c_double)),
+                ("n_triangles", ctypes.c_int), ("triangles", ctypes.POINTER(ctypes.c_int))]
 
 
 class FluxDesc(ctypes.Structure):
@@ -160,7 +162,8 @@ def woi_last_kernel_ms(geom) -> float:
 # ---------------------------------------------------------------------------
 
 def woi_create_geometry(dim, surfaces, parent):
-    """surfaces: list of dicts {"kind", "center", "radius", "star_a", "star_b", "matrix"}."""
+    """surfaces: list of dicts {"kind", "center", "radius", "star_a", "star_b", "matrix", "vertices",
+    "triangles"}."""
     n = len(surfaces)
     arr = (SurfaceDesc * n)()
     keep = []
@@ -173,6 +176,14 @@ def woi_create_geometry(dim, surfaces, parent):
             m = np.ascontiguousarray(s["matrix"], dtype=np.float64)
             keep.append(m)
             arr[i].matrix = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if s["kind"] == "mesh":
+            V = np.ascontiguousarray(s["vertices"], dtype=np.float64)
+            F = np.ascontiguousarray(s["triangles"], dtype=np.int32)
+            keep += [V, F]
+            arr[i].n_vertices = len(V)
+            arr[i].vertices = V.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[i].n_triangles = len(F)
+            arr[i].triangles = F.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         if s["kind"] == "star":
             a = np.ascontiguousarray(s["star_a"], dtype=np.float64)
             b = np.ascontiguousarray(s["star_b"], dtype=np.float64)

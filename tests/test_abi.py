@@ -150,3 +150,33 @@ def test_ellipsoid_host_geometry(woi):
     with pytest.raises(woi.WoiError) as e:
         woi.Geometry(prob)
     assert e.value.status == 3
+
+
+def test_mesh_host_geometry(woi):
+    """Triangle meshes on the host side of the library: areas equal the oracle's,
+    the rock workload is accepted, and open, inverted or crossing meshes are
+    rejected (the crossing is found by the library's inside test)."""
+    from oracle import core
+    prob = wl.rocks_problem(n_rocks=3, subdiv_outer=3, subdiv_rock=2)
+    prep = core.Prepared(prob)
+    with woi.Geometry(prob) as g:
+        for i in range(len(prob["surfaces"])):
+            assert g.surface_area(i) == pytest.approx(prep.area[i], rel=1e-13)
+    V, F = wl.icosphere(2)
+    # an open mesh (one triangle removed)
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(3, [wl._mesh(V, F[1:], [0, 0, 0])], [-1])
+    assert e.value.status == 2
+    # inverted orientation
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(3, [wl._mesh(V, F[:, ::-1], [0, 0, 0])], [-1])
+    assert e.value.status == 2
+    # a rock crossing the outer mesh
+    bad = [wl._mesh(V, F, [0, 0, 0]), wl._mesh(0.3 * V + [0.85, 0, 0], F, [0.85, 0, 0])]
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(3, bad, [-1, 0])
+    assert e.value.status == 2
+    # a mesh in 2D
+    with pytest.raises(woi.WoiError) as e:
+        woi.woi_create_geometry(2, [wl._mesh(V, F, [0, 0, 0])], [-1])
+    assert e.value.status == 4

@@ -69,6 +69,8 @@ def cases():
     for dim in (3, 6):
         ell = wl.ellipsoids_problem(dim)
         yield f"ellipsoids-{dim}d", ell, wl.ellipsoid_points(ell, 3, seed=50 + dim), "plain"
+    rocks = wl.rocks_problem(n_rocks=3, subdiv_outer=3, subdiv_rock=2, M=4)
+    yield "mesh-rocks", rocks, wl.mesh_points(rocks, 3, seed=61), "plain"
 
 
 CASES = list(cases())
@@ -115,7 +117,9 @@ def test_replay_fp32_per_walk(W, O, case):
         viol = (eu > FP32_RTOL) | (eg > FP32_RTOL)
         bad += int(viol.sum())
         tot += len(eu)
-    allowed = 0 if "star" not in name else max(1, tot // 200)
+    # star curves (near-tangent lines) and meshes (lines through an edge, within FP32 rounding)
+    # may change an FP32 intersection count: a legitimate branch flip
+    allowed = 0 if ("star" not in name and "mesh" not in name) else max(1, tot // 200)
     assert bad <= allowed, f"{name}: {bad} of {tot} walks beyond {FP32_RTOL}"
 
 
@@ -158,7 +162,8 @@ def test_shared_schedules(W, O):
 
 @pytest.mark.parametrize("name,variant,sched_group", [("3d-nested", "plain", 1), ("3d-nested", "plain", 32),
                                                       ("2d-concentric-vr", "vr", 1), ("star-3", "plain", 1),
-                                                      ("6d-nested", "plain", 1), ("ellipsoids-3d", "plain", 1)])
+                                                      ("6d-nested", "plain", 1), ("ellipsoids-3d", "plain", 1),
+                                                      ("mesh-rocks", "plain", 1)])
 def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
     estimate is still the mean over the same walks the oracle draws for that
@@ -169,6 +174,8 @@ def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
         x = wl.star_inclusions_points(prob, 70, seed=22)
     elif name.startswith("ellipsoids"):
         x = wl.ellipsoid_points(prob, 70, seed=22)
+    elif name.startswith("mesh"):
+        x = wl.mesh_points(prob, 70, seed=22)
     else:
         x = wl.ball_points(70, prob["dim"], 23, radius=0.9)
     n_walks = 2048 + 160
@@ -178,7 +185,7 @@ def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     orr = O.estimate(prob, x, n_walks, seed=4, M=prob["M"], variant=variant, sched_group=sched_group, tile=32)
     zu = np.abs(gr["u"] - orr["u"]) / orr["se_u"]
     zg = np.abs(gr["grad"] - orr["grad"]) / orr["se_grad"]
-    if name.startswith("star"):
+    if name.startswith("star") or name.startswith("mesh"):
         # a near-tangent line can change the FP32 intersection count of one shared walk
         # (a legitimate branch flip, as in the per-walk replay); it moves every point of
         # its tile by a small fraction of an SE, and the other tiles still agree to rounding
