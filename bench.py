@@ -61,6 +61,7 @@ WORKLOADS = {
     "6d-nested": dict(points=1024, walks=1_000_000, M=8),
     "3d-ellipsoids": dict(points=4096, walks=100_000, M=5),
     "6d-ellipsoids": dict(points=1024, walks=1_000_000, M=8),
+    "3d-rocks": dict(points=4096, walks=100_000, M=5),
     "batch": dict(points=None, walks=None, M=None),
 }
 
@@ -76,6 +77,9 @@ def make_workload(name):
         return p, wl.star_inclusions_points(p, 16384)
     if name == "6d-nested":
         return wl.nested_6d_problem(), wl.ball_points(1024, 6, 14)
+    if name == "3d-rocks":
+        p = wl.rocks_problem()
+        return p, wl.mesh_points(p, WORKLOADS[name]["points"], seed=17)
     if name in ("3d-ellipsoids", "6d-ellipsoids"):
         d = int(name[0])
         p = wl.ellipsoids_problem(d)
