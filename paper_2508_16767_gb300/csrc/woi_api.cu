@@ -158,6 +158,7 @@ struct woi_geometry {
     float *d_tri_f = nullptr;
     double *d_tri_d = nullptr;
     uint32_t *d_tri_tm1 = nullptr;
+    int *d_tri_bucket = nullptr;
     BvhNode *d_bvh = nullptr;
     int *d_bvh_tri = nullptr;
     unsigned int *d_mesh_overflow = nullptr;
@@ -191,6 +192,7 @@ struct woi_geometry {
         cudaFree(d_tri_f);
         cudaFree(d_tri_d);
         cudaFree(d_tri_tm1);
+        cudaFree(d_tri_bucket);
         cudaFree(d_bvh);
         cudaFree(d_bvh_tri);
         cudaFree(d_mesh_overflow);
@@ -207,6 +209,7 @@ struct woi_geometry {
         d_tri_f = nullptr;
         d_tri_d = nullptr;
         d_tri_tm1 = nullptr;
+        d_tri_bucket = nullptr;
         d_bvh = nullptr;
         d_bvh_tri = nullptr;
         d_mesh_overflow = nullptr;
@@ -1095,12 +1098,20 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
             // shifted by the mesh's offsets) and leaf-triangle lists (global triangle indices)
             std::vector<double> tri_d;
             std::vector<uint32_t> tm1;
+            std::vector<int> bucket;
             std::vector<BvhNode> nodes;
             std::vector<int> leaf;
             for (const MeshHost &mh : g->mesh) {
                 const int tri_off = (int)tm1.size(), node_off = (int)nodes.size();
                 tri_d.insert(tri_d.end(), mh.tri.begin(), mh.tri.end());
                 tm1.insert(tm1.end(), mh.tm1.begin(), mh.tm1.end());
+                // bucket b: the first triangle whose threshold T_j - 1 reaches b 2^22
+                int j = 0;
+                for (int b = 0; b <= kTriBuckets; ++b) {
+                    const uint64_t start = (uint64_t)b << 22;
+                    while (j < mh.ntri && (uint64_t)mh.tm1[j] < start) ++j;
+                    bucket.push_back(tri_off + std::min(j, mh.ntri - 1));
+                }
                 for (BvhNode nd : mh.nodes) {
                     if (nd.b < 0) nd.a += tri_off;
                     else { nd.a += node_off; nd.b += node_off; }
@@ -1112,6 +1123,7 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
             if ((st = upload(&g->d_tri_d, tri_d, s)) != WOI_OK) return st;
             if ((st = upload(&g->d_tri_f, tri_f, s)) != WOI_OK) return st;
             if ((st = upload(&g->d_tri_tm1, tm1, s)) != WOI_OK) return st;
+            if ((st = upload(&g->d_tri_bucket, bucket, s)) != WOI_OK) return st;
             if ((st = upload(&g->d_bvh, nodes, s)) != WOI_OK) return st;
             if ((st = upload(&g->d_bvh_tri, leaf, s)) != WOI_OK) return st;
             if (!g->d_mesh_overflow) WOI_CUDA(cudaMalloc((void **)&g->d_mesh_overflow, sizeof(unsigned int)));
@@ -1133,6 +1145,7 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
     b.tri_f = g->d_tri_f;
     b.tri_d = g->d_tri_d;
     b.tri_tm1 = g->d_tri_tm1;
+    b.tri_bucket = g->d_tri_bucket;
     b.bvh = g->d_bvh;
     b.bvh_tri = g->d_bvh_tri;
     b.mesh_overflow = g->d_mesh_overflow;

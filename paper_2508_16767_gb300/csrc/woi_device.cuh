@@ -916,7 +916,11 @@ template <typename Real>
 __device__ void mesh_uniform(const DevGeom *gd, int m, const StepWords &w, Real *v, Real *nrm, int *tri)
 {
     const uint32_t w1 = w.a.y;
-    int lo = gd->mesh_tri_off[m], hi = lo + gd->mesh_ntri[m] - 1;
+    // the answer lies between the first triangles of the word's bucket and of the next one
+    const int *bk = gd->tri_bucket + (size_t)m * (kTriBuckets + 1) + (w1 >> 22);
+    int lo = __ldg(bk), hi = __ldg(bk + 1);
+    const int last = gd->mesh_tri_off[m] + gd->mesh_ntri[m] - 1;
+    hi = hi < last ? hi : last;
     while (lo < hi) {                       // first j in [lo, hi] with w1 <= tm1[j] (tm1[last] = 2^32 - 1)
         const int mid = (lo + hi) >> 1;
         if (__ldg(gd->tri_tm1 + mid) < w1) lo = mid + 1;
@@ -948,7 +952,12 @@ __device__ int mesh_hits(const DevGeom *gd, int m, const Real *o, const Real *z,
     bool over = false;
     stack[sp++] = gd->mesh_node_off[m];
     while (sp > 0) {
-        const BvhNode n = nodes[stack[--sp]];
+        const int ni = stack[--sp];
+        const float4 n0 = __ldg(reinterpret_cast<const float4 *>(nodes + ni));
+        const float4 n1 = __ldg(reinterpret_cast<const float4 *>(nodes + ni) + 1);
+        BvhNode n;
+        n.lo[0] = n0.x; n.lo[1] = n0.y; n.lo[2] = n0.z; n.hi[0] = n0.w;
+        n.hi[1] = n1.x; n.hi[2] = n1.y; n.a = __float_as_int(n1.z); n.b = __float_as_int(n1.w);
         // slab test against the padded box
         Real t0 = ray ? (Real)0 : (Real)-1e30, t1 = (Real)1e30;
 #pragma unroll

@@ -18,6 +18,7 @@ constexpr int kMaxEll = 8;             // ellipsoids per instance (WOI_MAX_ELLIP
 constexpr int kMaxMesh = 16;           // meshes per instance (WOI_MAX_MESHES)
 constexpr int kMeshStack = 64;         // BVH traversal stack (the host caps the tree depth below it)
 constexpr int kMaxHits = 32;           // intersections of one line with one mesh
+constexpr int kTriBuckets = 1024;      // per mesh: the triangle range of each top-10-bit word bucket
 constexpr int kEllAttempts = 64;       // rejection attempts for a uniform point on an ellipsoid
 
 enum { kSphere = 0, kStar = 1, kEllipsoid = 2, kMesh = 3 };
@@ -29,6 +30,7 @@ struct BvhNode {
     float lo[3], hi[3];
     int a, b;
 };
+static_assert(sizeof(BvhNode) == 32, "nodes are read as two float4");
 enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4 };
 
 struct DevGeom {
@@ -76,6 +78,7 @@ struct DevGeom {
     const float *tri_f;                // [n_tri][12]
     const double *tri_d;               // [n_tri][12]
     const uint32_t *tri_tm1;           // [n_tri] T_j - 1 of the area-proportional triangle choice
+    const int *tri_bucket;             // [n_mesh][kTriBuckets + 1]: first j with T_j - 1 >= b 2^22 (global j)
     const BvhNode *bvh;                // all meshes' nodes
     const int *bvh_tri;                // leaf-triangle lists (indices into the triangle rows)
     unsigned int *mesh_overflow;       // device counter of lines with more than kMaxHits crossings
