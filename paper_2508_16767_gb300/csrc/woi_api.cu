@@ -1017,6 +1017,14 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
     b.star_rmin = g.star_rmin;
     b.star_rmax = g.star_rmax;
     for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g.n ? (uint32_t)(g.thresh[i] - 1) : 0xFFFFFFFFu;
+    {
+        int n = 0;   // bucket k: the first surface whose threshold T_n - 1 reaches k 2^24
+        for (int k = 0; k <= kSchedBuckets; ++k) {
+            const uint64_t start = (uint64_t)k << 24;
+            while (n < g.n - 1 && (uint64_t)b.sched_tm1[n] < start) ++n;
+            b.sched_bucket[k] = n;
+        }
+    }
     for (int i = 0; i < g.n; ++i) {
         for (int k = 0; k < g.dim; ++k) b.center[i][k] = g.surf[i].center[k];
         b.radius[i] = g.surf[i].radius;

@@ -209,6 +209,7 @@ template <typename Real>
 struct SGeom {
     int n, npad, M, star_idx, star_K;
     uint32_t sched_tm1[kMaxSurfPad];     // T_n - 1 (schedule thresholds), padded with 0xFFFFFFFF
+    int sched_bucket[kSchedBuckets + 1]; // first n with T_n - 1 >= b 2^24
     Real c_hi[kMaxSurf][kMaxDim];        // centres as hi + lo
     Real c_lo[kMaxSurf][kMaxDim];
     Real radius[kMaxSurf];
@@ -242,6 +243,7 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.star_rmax = (Real)src->star_rmax;
     }
     for (int i = tid; i < kMaxSurfPad; i += nt) g.sched_tm1[i] = src->sched_tm1[i];
+    for (int i = tid; i <= kSchedBuckets; i += nt) g.sched_bucket[i] = src->sched_bucket[i];
     for (int i = tid; i < src->n; i += nt) {
         for (int k = 0; k < kMaxDim; ++k) {
             const double c = src->center[i][k];
@@ -309,16 +311,16 @@ __device__ void load_geometry(SGeomE<Real> &g, const DevGeom *src)
 }
 
 // H_i from a 32-bit word: i = 0 uniform over the N surfaces, i >= 1 the first n
-// with w <= T_n - 1 (binary search over the padded thresholds)
+// with w <= T_n - 1: a scan that starts at the first threshold of the word's top-8-bit
+// bucket (no threshold before it can be the answer; T_N - 1 = 2^32 - 1 ends the scan)
 template <typename Real>
 __device__ __forceinline__ int schedule(const SGeom<Real> &g, int i, uint32_t w)
 {
     if (i == 0) return (int)(((uint64_t)w * (uint64_t)g.n) >> 32);
-    int lo = 0;
+    int n = g.sched_bucket[w >> 24];
 #pragma unroll 1
-    for (int step = g.npad >> 1; step > 0; step >>= 1)
-        if (g.sched_tm1[lo + step - 1] < w) lo += step;
-    return lo;
+    while (g.sched_tm1[n] < w) ++n;
+    return n;
 }
 
 // 0: same surface, 1: prev is a strict descendant of cur, 2: otherwise

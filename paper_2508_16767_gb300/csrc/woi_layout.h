@@ -9,6 +9,7 @@ namespace woi {
 constexpr int kMaxDim = 6;
 constexpr int kMaxSurf = 128;          // surfaces per instance (WOI_MAX_SURF)
 constexpr int kMaxSurfPad = 128;       // schedule thresholds padded to a power of two
+constexpr int kSchedBuckets = 256;     // index of the schedule thresholds by the top 8 bits of the word
 constexpr int kMaxM = 32;              // truncation (WOI_MAX_M)
 constexpr int kMaxStar = 16;           // star Fourier degree (WOI_MAX_STAR_DEGREE)
 constexpr int kNodes = 256;            // angle nodes t_j = 2 pi j / kNodes: star scan samples,
@@ -39,6 +40,7 @@ struct DevGeom {
     double star_lmax;                  // bound on |gamma'| of the star
     double star_rmin, star_rmax;       // bounds on r(t): every point of the star lies in this annulus
     uint32_t sched_tm1[kMaxSurfPad];   // T_n - 1, padded with 0xFFFFFFFF
+    int sched_bucket[kSchedBuckets + 1]; // first n with T_n - 1 >= b 2^24 (N - 1 if none)
     double center[kMaxSurf][kMaxDim];
     double radius[kMaxSurf];
     double area[kMaxSurf];
