@@ -1461,8 +1461,8 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
         if ((st = stage_geometry(geoms[k], oi[k].M, s)) != WOI_OK) return st;
     const bool vr = o->variant == WOI_VR;
     const int block = o->block_size ? o->block_size : 256;
-    const int L = o->walks_per_lane ? o->walks_per_lane : 8;
-    const int64_t unit_walks = (int64_t)block * L;
+    const int L = o->walks_per_lane ? o->walks_per_lane : 32;
+    const int64_t unit_walks = 32LL * L;        // warp-level work units
 
     // groups of instances that share a kernel: (dimension, star)
     std::map<int, std::vector<int>> groups;
@@ -1477,6 +1477,7 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
         std::vector<InstDesc> desc;
         size_t o_desc, o_queue, o_part;
         int64_t units, points;
+        int max_surf;
     };
     std::vector<Group> gs;
     size_t off = 0;
@@ -1486,7 +1487,9 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
         gr.star = kv.first % 2;
         gr.members = kv.second;
         gr.units = gr.points = 0;
+        gr.max_surf = 1;
         for (int k : gr.members) {
+            gr.max_surf = std::max(gr.max_surf, geoms[k]->n);
             const int64_t chunks = (n_walks[k] + unit_walks - 1) / unit_walks;
             InstDesc d{};
             d.geom = geoms[k]->d_blob;
@@ -1503,7 +1506,7 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
             gr.desc.push_back(d);
         }
         gr.o_desc = off; off = align_up(off + gr.desc.size() * sizeof(InstDesc), 256);
-        gr.o_queue = off; off = align_up(off + sizeof(unsigned long long), 256);
+        gr.o_queue = off; off = align_up(off + gr.desc.size() * sizeof(unsigned long long), 256);
         gr.o_part = off; off = align_up(off + (size_t)gr.units * 2 * (gr.dim + 1) * sizeof(double), 256);
         gs.push_back(std::move(gr));
     }
@@ -1569,18 +1572,22 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
             g_batch.exec = nullptr;
         }
         std::vector<int> grid(gs.size());
+        std::vector<size_t> smem(gs.size());
         int num_sms = geoms[0]->num_sms;
         for (size_t i = 0; i < gs.size(); ++i) {
             int per_sm = 0;
-            WOI_CUDA(mixed_occupancy(gs[i].dim, vr, gs[i].star, block, &per_sm));
-            grid[i] = (int)std::min<int64_t>((int64_t)num_sms * std::max(per_sm, 1), gs[i].units);
+            smem[i] = (size_t)(block / 32) * gs[i].max_surf * kMaxDim * sizeof(float);
+            WOI_CUDA(mixed_occupancy(gs[i].dim, vr, gs[i].star, block, smem[i], &per_sm));
+            if (per_sm < 1) return fail(WOI_E_UNSUPPORTED, "batched walk kernel does not fit on an SM");
+            const int64_t warps = gs[i].units, per_block = block / 32;
+            grid[i] = (int)std::min<int64_t>((int64_t)num_sms * per_sm, (warps + per_block - 1) / per_block);
         }
         cudaGraph_t graph = nullptr;
         WOI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = cudaSuccess;
         for (size_t i = 0; i < gs.size() && ce == cudaSuccess; ++i) {
             Group &gr = gs[i];
-            ce = cudaMemsetAsync(base + gr.o_queue, 0, sizeof(unsigned long long), s);
+            ce = cudaMemsetAsync(base + gr.o_queue, 0, gr.desc.size() * sizeof(unsigned long long), s);
             if (ce != cudaSuccess) break;
             MixedParams mp{};
             mp.inst = (const InstDesc *)(base + gr.o_desc);
@@ -1590,7 +1597,8 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
             mp.partials = (double *)(base + gr.o_part);
             mp.walks_per_lane = L;
             mp.seed = seed;
-            ce = launch_mixed(gr.dim, vr, gr.star, mp, grid[i], block, s);
+            mp.max_surf = gr.max_surf;
+            ce = launch_mixed(gr.dim, vr, gr.star, mp, grid[i], block, smem[i], s);
             if (ce != cudaSuccess) break;
             BatchFinalizeParams bp{};
             bp.inst = (const InstDesc *)(base + gr.o_desc);

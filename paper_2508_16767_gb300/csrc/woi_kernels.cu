@@ -131,14 +131,15 @@ static cudaError_t by_dim(int dim, bool star, F &&f)
     }
 }
 
-cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, cudaStream_t s)
+cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,
+                         cudaStream_t s)
 {
-    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::mixed(vr, p, grid, block, s); });
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::mixed(vr, p, grid, block, smem, s); });
 }
 
-cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_per_sm)
+cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm)
 {
-    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy(vr, block, blocks_per_sm); });
+    return by_dim(dim, star, [&](auto t) { return decltype(t)::L::occupancy(vr, block, smem, blocks_per_sm); });
 }
 
 cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,

@@ -19,7 +19,8 @@ struct MixedParams {
     const InstDesc *inst;              // device [n_inst], sorted by unit_begin
     int n_inst;
     int64_t total_units;
-    unsigned long long *queue;         // device work-queue head, zero before the launch
+    unsigned long long *queue;         // device work-queue head (batch: one per instance), zero before the launch
+    int max_surf;                      // batch: the most surfaces of any instance (per-warp table size)
     double *partials;                  // device [total_units][2 (dim+1)]
     int walks_per_lane;
     uint64_t seed;
@@ -64,8 +65,8 @@ struct WalkValuesParams {
 // explicitly instantiated in woi_k<d>.cu
 template <int D, bool STAR>
 struct DimLaunchers {
-    static cudaError_t mixed(bool vr, const MixedParams &p, int grid, int block, cudaStream_t s);
-    static cudaError_t occupancy(bool vr, int block, int *blocks_per_sm);
+    static cudaError_t mixed(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s);
+    static cudaError_t occupancy(bool vr, int block, size_t smem, int *blocks_per_sm);
     static cudaError_t mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s);
     static cudaError_t occupancy_warp(bool vr, int block, size_t smem, int *blocks_per_sm);
     static cudaError_t shared(bool vr, const MixedParams &p, int grid, size_t smem, cudaStream_t s);
@@ -95,9 +96,12 @@ struct BatchFinalizeParams {
     const double *partials;            // unit partials of all instances
 };
 
-cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, cudaStream_t s);
+// batched kernel: warp units of many instances, queue = one head per instance; dynamic shared
+// memory (block / 32) * max_surf * kMaxDim floats
+cudaError_t launch_mixed(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,
+                         cudaStream_t s);
 cudaError_t launch_finalize_batch(const BatchFinalizeParams &p, cudaStream_t s);
-cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, int *blocks_per_sm);
+cudaError_t mixed_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm);
 // single-instance kernel with warp-level work units of 32 x walks_per_lane walks;
 // dynamic shared memory: (block / 32) * n_surf * kMaxDim floats
 cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p, int grid, int block, size_t smem,

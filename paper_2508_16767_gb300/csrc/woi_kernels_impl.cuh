@@ -1,10 +1,13 @@
 // woi_kernels_impl.cuh -- Walk-on-Interfaces kernel templates for sm_103a
 // (instantiated per dimension in woi_k<d>.cu).
 //
-//   k_walk_mixed      persistent kernel: FP32 walks, one walk per thread; each CTA
-//                     takes (instance, point, walk-chunk) units from a device work
-//                     queue, accumulates compensated FP32 sums per lane and reduces
-//                     them in FP64 to one partial per unit (deterministic order)
+//   k_walk_mixed      batched persistent kernel: FP32 walks, one walk per thread;
+//                     warps take (point, walk-chunk) units of the instance their
+//                     block serves from that instance's queue, accumulate
+//                     compensated FP32 sums per lane and reduce them (TwoSum) to
+//                     one partial per unit (deterministic order)
+//   k_walk_mixed_warp the same for one instance (all blocks share one queue)
+//   k_walk_shared     tiles of 32 points sharing their walks (Sec. 4.6)
 //   k_finalize        per (instance, point, component): ordered sum of the unit
 //                     partials, mean and standard error from the schedule-group
 //                     means (Algorithm 1)
@@ -68,95 +71,95 @@ __device__ __forceinline__ int find_instance(const InstDesc *inst, int n_inst, i
 }
 
 // ---------------------------------------------------------------------------
-// persistent mixed-precision walk kernel
+// batched walk kernel: warp-level work units (point, 32 x L walks) of many
+// instances.  A block serves one instance at a time (its geometry staged in
+// shared memory); its warps take units from that instance's own queue head
+// until it is exhausted, then the block moves on.  Block b starts at instance
+// b mod n and visits every instance once: an instance it leaves is exhausted
+// for good, so one round covers all the work.
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams p)
 {
     __shared__ SGeomFor<float, D, STAR> g;
-    __shared__ float xc[kMaxSurf][kMaxDim];
-    __shared__ double red[kMixedMaxBlock / 32][2 * (D + 1)];
-    __shared__ long long unit_sh;
-    __shared__ int inst_sh;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int B = blockDim.x, L = p.walks_per_lane;
-    int cur_inst = -1;
-
-    for (;;) {
-        if (tid == 0) {
-            const unsigned long long u = atomicAdd(p.queue, 1ull);
-            unit_sh = (long long)u;
-            inst_sh = (u < (unsigned long long)p.total_units) ? find_instance(p.inst, p.n_inst, (int64_t)u) : -1;
-        }
-        __syncthreads();
-        const long long unit = unit_sh;
-        const int k = inst_sh;
-        if (unit >= p.total_units) break;
+    __shared__ int left_sh;
+    extern __shared__ float xc_all[];   // [warps][max_surf][kMaxDim]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float(*xc)[kMaxDim] = reinterpret_cast<float(*)[kMaxDim]>(xc_all + (size_t)warp * p.max_surf * kMaxDim);
+    const int L = p.walks_per_lane;
+    int k = blockIdx.x % p.n_inst;
+    for (int visit = 0; visit < p.n_inst; ++visit, k = (k + 1 == p.n_inst) ? 0 : k + 1) {
         const InstDesc &id = p.inst[k];
-        if (k != cur_inst) {
-            load_geometry(g, id.geom);
-            cur_inst = k;
-            __syncthreads();
-        }
-        const int64_t local = unit - id.unit_begin;
-        const int64_t point = local / id.chunks_per_point;
-        const int64_t chunk = local - point * id.chunks_per_point;
-        fill_xc<float>(xc, id.geom, g.n, D, id.points + point * D);
+        const unsigned long long units_k = (unsigned long long)(id.n_pts * id.chunks_per_point);
+        if (tid == 0) left_sh = atomicAdd(p.queue + k, 0ull) < units_k;
+        __syncthreads();
+        const bool left = left_sh != 0;
+        __syncthreads();
+        if (!left) continue;
+        load_geometry(g, id.geom);
         __syncthreads();
         Rng rng;
-        rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
         rng.k1 = (uint32_t)(p.seed >> 32) ^ id.instance_id;
         const int64_t w_end = id.walk_begin + id.n_walks;
-        const int64_t w_base = id.walk_begin + chunk * (int64_t)B * L;
-
-        float s1[D + 1], c1[D + 1], s2[D + 1];
-#pragma unroll
-        for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
-        for (int j = 0; j < L; ++j) {
-            const int64_t w = w_base + (int64_t)j * B + tid;
-            float f[D + 1];
-            const bool valid = w < w_end;
-            if (valid) {
-                rng.w0 = (uint32_t)w;
-                rng.w1 = (uint32_t)((uint64_t)w >> 32);
-                walk<float, D, VR, STAR>(g, id.geom, xc, rng, id.sched_group, (uint64_t)w / 32u, f);
-            } else {
-#pragma unroll
-                for (int c = 0; c <= D; ++c) f[c] = 0.f;
+        for (;;) {
+            unsigned long long u = 0;
+            if (lane == 0) u = atomicAdd(p.queue + k, 1ull);
+            u = __shfl_sync(0xFFFFFFFFu, u, 0);
+            if (u >= units_k) break;
+            const int64_t local = (int64_t)u;
+            const int64_t point = local / id.chunks_per_point;
+            const int64_t chunk = local - point * id.chunks_per_point;
+            const double *x = id.points + point * D;
+            for (int i = lane; i < g.n * D; i += 32) {
+                const int sidx = i / D, c = i - sidx * D;
+                xc[sidx][c] = (float)(x[c] - id.geom->center[sidx][c]);
             }
+            __syncwarp();
+            rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
+            const int64_t w_base = id.walk_begin + chunk * 32LL * L;
+            float s1[D + 1], c1[D + 1], s2[D + 1];
 #pragma unroll
-            for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
-            if (id.sched_group == 1) {
+            for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
+            for (int j = 0; j < L; ++j) {
+                const int64_t w = w_base + (int64_t)j * 32 + lane;
+                float f[D + 1];
+                const bool valid = w < w_end;
+                if (valid) {
+                    rng.w0 = (uint32_t)w;
+                    rng.w1 = (uint32_t)((uint64_t)w >> 32);
+                    walk<float, D, VR, STAR>(g, id.geom, xc, rng, id.sched_group, (uint64_t)w / 32u, f);
+                } else {
 #pragma unroll
-                for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
-            } else {
-                // the 32 lanes of a warp share one schedule (walks w .. w+31 form a group);
-                // a warp's round is entirely valid or entirely past the end
+                    for (int c = 0; c <= D; ++c) f[c] = 0.f;
+                }
 #pragma unroll
-                for (int c = 0; c <= D; ++c) {
-                    const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
-                    if (lane == 0 && valid) s2[c] += gm * gm;
+                for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
+                if (id.sched_group == 1) {
+#pragma unroll
+                    for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
+                } else {
+                    // the 32 lanes share one schedule; a warp's round is all valid or all past the end
+#pragma unroll
+                    for (int c = 0; c <= D; ++c) {
+                        const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
+                        if (lane == 0 && valid) s2[c] += gm * gm;
+                    }
                 }
             }
-        }
-        // warp sums as FP32 (hi, lo) pairs, FP64 only in lane 0; CTA sum in FP64, fixed order
+            const int64_t row = id.unit_begin + local;
 #pragma unroll
-        for (int c = 0; c <= D; ++c) {
-            float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
-            warp_sum_pair(h1, l1);
-            warp_sum_pair(h2, l2);
-            if (lane == 0) {
-                red[warp][c] = (double)h1 + (double)l1;
-                red[warp][D + 1 + c] = (double)h2 + (double)l2;
+            for (int c = 0; c <= D; ++c) {
+                float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
+                warp_sum_pair(h1, l1);
+                warp_sum_pair(h2, l2);
+                if (lane == 0) {
+                    p.partials[row * (2 * (D + 1)) + c] = (double)h1 + (double)l1;
+                    p.partials[row * (2 * (D + 1)) + D + 1 + c] = (double)h2 + (double)l2;
+                }
             }
+            __syncwarp();   // the table is rewritten for the next unit
         }
-        __syncthreads();
-        if (tid < 2 * (D + 1)) {
-            double acc = 0.0;
-            for (int wi = 0; wi < nwarp; ++wi) acc += red[wi][tid];
-            p.partials[unit * (2 * (D + 1)) + tid] = acc;
-        }
-        __syncthreads();
+        __syncthreads();    // every warp is done with this instance before its geometry is replaced
     }
 }
 
@@ -454,17 +457,17 @@ __global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
 
 // launchers of one dimension / star flag (explicitly instantiated in woi_k<d>.cu)
 template <int D, bool STAR>
-cudaError_t DimLaunchers<D, STAR>::mixed(bool vr, const MixedParams &p, int grid, int block, cudaStream_t s)
-    {
-        if constexpr (D == 2) {
-            if (vr) {
-                k_walk_mixed<2, true, STAR><<<grid, block, 0, s>>>(p);
-                return cudaGetLastError();
-            }
+cudaError_t DimLaunchers<D, STAR>::mixed(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    if constexpr (D == 2) {
+        if (vr) {
+            k_walk_mixed<2, true, STAR><<<grid, block, smem, s>>>(p);
+            return cudaGetLastError();
         }
-        k_walk_mixed<D, false, STAR><<<grid, block, 0, s>>>(p);
-        return cudaGetLastError();
     }
+    k_walk_mixed<D, false, STAR><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem,
                                              cudaStream_t s)
@@ -527,13 +530,13 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *b
 }
 
 template <int D, bool STAR>
-cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, int *blocks_per_sm)
-    {
-        if constexpr (D == 2) {
-            if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<2, true, STAR>, block, 0);
-        }
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, false, STAR>, block, 0);
+cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, size_t smem, int *blocks_per_sm)
+{
+    if constexpr (D == 2) {
+        if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<2, true, STAR>, block, smem);
     }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, false, STAR>, block, smem);
+}
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s)
     {
