@@ -1433,15 +1433,4 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[k
     walk_steps<Real, D, VR, STAR>(g, gd, rng, sched_group, group, sink);
 }
 
-// c Phi(x, y) and c grad_x Phi(x, y) for y = c_s + v with x as an FP32 (hi, lo) pair
-template <int D>
-__device__ __forceinline__ void tally_hl(const SGeom<float> &g, const float *xhi, const float *xlo, int s,
-                                         const float *v, float c, float *acc)
-{
-    float dx[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) dx[k] = ((xhi[k] - g.c_hi[s][k]) + (xlo[k] - g.c_lo[s][k])) - v[k];
-    tally_dx<float, D>(dx, c, acc);
-}
-
 }  // namespace woi

@@ -60,16 +60,6 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
     s = t;
 }
 
-__device__ __forceinline__ int find_instance(const InstDesc *inst, int n_inst, int64_t unit)
-{
-    int lo = 0, hi = n_inst;  // last k with unit_begin <= unit
-    while (hi - lo > 1) {
-        const int m = (lo + hi) >> 1;
-        if (inst[m].unit_begin <= unit) lo = m; else hi = m;
-    }
-    return lo;
-}
-
 // ---------------------------------------------------------------------------
 // batched walk kernel: warp-level work units (point, 32 x L walks) of many
 // instances.  A block serves one instance at a time (its geometry staged in
