@@ -1433,4 +1433,38 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[k
     walk_steps<Real, D, VR, STAR>(g, gd, rng, sched_group, group, sink);
 }
 
+// Two independent walks of one lane, advanced step by step in the same loop so that the
+// scheduler can overlap their dependency chains (plain variant; each walk has its own
+// stream, schedule and state, exactly as if walked alone): f[q] receives walk q's tally
+template <typename Real, int D, bool STAR>
+__device__ void walk_pair(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[kMaxDim], const Rng *rng,
+                          int sched_group, const uint64_t *group, Real (*f)[D + 1])
+{
+    Chain<Real, D> ch[2];
+    Real S[2] = {1, 1};
+    int hp[2] = {0, 0};
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c <= D; ++c) f[q][c] = 0;
+    for (int i = 0; i <= g.M; ++i) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            StepWords w;
+            w.a = rng[q].words(i, 0, 0);
+            if constexpr (two_calls<D>()) w.b = rng[q].words(i, 0, 1);
+            uint32_t hw = w.a.x;
+            if (sched_group > 1)
+                hw = philox10((uint32_t)group[q], (uint32_t)(group[q] >> 32), (uint32_t)i, 0x100u, rng[q].k0, rng[q].k1).x;
+            const int h = schedule(g, i, hw);
+            if (i > 0) S[q] *= g.alpha_sign[h];
+            const int rel = (i > 0) ? relation(g, hp[q], h) : 0;
+            if (i == 0) chain_start<Real, D, false, STAR>(g, gd, h, 0, w, rng[q], ch[q]);
+            else if (ch[q].alive) chain_step<Real, D, STAR>(g, gd, h, rel, w, rng[q], i, 0, ch[q]);
+            if (ch[q].alive) tally<Real, D>(xc, ch[q].s, ch[q].v, g.coef[i] * S[q] * ch[q].Q * ch[q].T, f[q]);
+            hp[q] = h;
+        }
+    }
+}
+
 }  // namespace woi

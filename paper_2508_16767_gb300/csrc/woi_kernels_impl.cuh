@@ -190,7 +190,35 @@ __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed_warp(MixedP
         float s1[D + 1], c1[D + 1], s2[D + 1];
 #pragma unroll
         for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
-        for (int j = 0; j < L; ++j) {
+        // the plain variant in d <= 3 with per-walk schedules advances rounds j and j + 1 together
+        // (two independent walks per lane overlap their dependency chains); in higher dimensions
+        // the second walk's state would not fit in the registers
+        constexpr bool PAIR = !VR && D <= 3;
+        int j = 0;
+        if (PAIR && id.sched_group == 1) {
+            for (; j + 1 < L; j += 2) {
+                const int64_t wa = w_base + (int64_t)j * 32 + lane, wb = wa + 32;
+                float f2[2][D + 1];
+                Rng r2[2] = {rng, rng};
+                r2[0].w0 = (uint32_t)wa;
+                r2[0].w1 = (uint32_t)((uint64_t)wa >> 32);
+                r2[1].w0 = (uint32_t)wb;
+                r2[1].w1 = (uint32_t)((uint64_t)wb >> 32);
+                const uint64_t grp[2] = {(uint64_t)wa / 32u, (uint64_t)wb / 32u};
+                if (wa < w_end) walk_pair<float, D, STAR>(g, id.geom, xc, r2, 1, grp, f2);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const bool valid = (q == 0 ? wa : wb) < w_end;
+#pragma unroll
+                    for (int c = 0; c <= D; ++c) {
+                        const float fv = valid ? f2[q][c] : 0.f;
+                        kahan_add(s1[c], c1[c], fv);
+                        s2[c] += fv * fv;
+                    }
+                }
+            }
+        }
+        for (; j < L; ++j) {
             const int64_t w = w_base + (int64_t)j * 32 + lane;
             float f[D + 1];
             const bool valid = w < w_end;
