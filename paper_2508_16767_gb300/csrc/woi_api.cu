@@ -140,6 +140,7 @@ struct woi_geometry {
     std::vector<double> sigma, alpha, beta_scale, flux_coef;
     std::vector<double> flux_dev;              // device format of flux_coef
     std::vector<float> flux_dev_f;
+    std::vector<int> flux_basis_dev, flux_off_dev, flux_n_dev;   // device basis codes and layout
     std::vector<uint64_t> thresh;
     double alpha_l1 = 0.0;
     std::vector<int> flux_basis, flux_off, flux_n;
@@ -895,6 +896,65 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             g->flux_dev[off[i] + idx] *= nlm;
         }
     }
+    // device format: a harmonic polynomial of degree <= 3 becomes the dense quadratic form of
+    // its gradient, dP/dy_k = a_k + sum_j b_kj y_j + sum_{j<=l} c_kjl y_j y_l, so that the
+    // kernels evaluate it with fused multiply-adds instead of decoding monomials
+    {
+        std::vector<double> dev;
+        g->flux_basis_dev.assign(n, 0);
+        g->flux_off_dev.assign(n, 0);
+        g->flux_n_dev.assign(n, 0);
+        const int nq = d * d * (d + 1) / 2 + d * d + d;    // per surface after the scale s
+        for (int i = 0; i < n; ++i) {
+            const double *c = g->flux_dev.data() + off[i];
+            bool quad = basis[i] == WOI_FLUX_HARMONIC_POLY;
+            if (quad) {
+                const int T = (int)c[1];
+                for (int t = 0; t < T && quad; ++t) {
+                    int deg = 0;
+                    for (int k = 0; k < d; ++k) deg += (int)c[2 + t * (d + 1) + 1 + k];
+                    quad = deg <= 3;
+                }
+            }
+            g->flux_off_dev[i] = (int)dev.size();
+            if (!quad) {
+                g->flux_basis_dev[i] = basis[i];
+                g->flux_n_dev[i] = nc[i];
+                dev.insert(dev.end(), c, c + nc[i]);
+                continue;
+            }
+            g->flux_basis_dev[i] = kFluxHarmonicQuad;
+            g->flux_n_dev[i] = 1 + nq;
+            std::vector<double> q(1 + nq, 0.0);
+            q[0] = c[0];
+            const int T = (int)c[1];
+            const int per_k = 1 + d + d * (d + 1) / 2;
+            for (int t = 0; t < T; ++t) {
+                const double *row = c + 2 + t * (d + 1);
+                for (int k = 0; k < d; ++k) {
+                    int e[kMaxDim];
+                    for (int j = 0; j < d; ++j) e[j] = (int)row[1 + j];
+                    if (e[k] == 0) continue;
+                    const double coef = row[0] * e[k];
+                    e[k] -= 1;                              // the monomial of dP/dy_k, degree <= 2
+                    int vars[2], nv = 0;
+                    for (int j = 0; j < d; ++j)
+                        for (int r = 0; r < e[j]; ++r) vars[nv++] = j;
+                    double *qk = &q[1 + k * per_k];
+                    if (nv == 0) {
+                        qk[0] += coef;
+                    } else if (nv == 1) {
+                        qk[1 + vars[0]] += coef;
+                    } else {
+                        const int a = std::min(vars[0], vars[1]), b2 = std::max(vars[0], vars[1]);
+                        qk[1 + d + a * d - a * (a - 1) / 2 + (b2 - a)] += coef;
+                    }
+                }
+            }
+            dev.insert(dev.end(), q.begin(), q.end());
+        }
+        g->flux_dev = dev;
+    }
     g->flux_dev_f.assign(g->flux_dev.begin(), g->flux_dev.end());
     g->vr_ok = vr_ok;
     g->arc_t0 = at0; g->arc_t1 = at1; g->arc_len = alen; g->arc_s0 = as0; g->arc_sign = asg;
@@ -1034,9 +1094,9 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
         b.tin[i] = g.tin[i];
         b.tout[i] = g.tout[i];
         b.type[i] = g.surf[i].type;
-        b.flux_basis[i] = g.flux_basis[i];
-        b.flux_off[i] = g.flux_off[i];
-        b.flux_n[i] = g.flux_n[i];
+        b.flux_basis[i] = g.flux_basis_dev[i];
+        b.flux_off[i] = g.flux_off_dev[i];
+        b.flux_n[i] = g.flux_n_dev[i];
         b.part_len[i][0] = g.part_len.empty() ? 0.0 : g.part_len[2 * i];
         b.part_len[i][1] = g.part_len.empty() ? 0.0 : g.part_len[2 * i + 1];
         b.arc_off[i] = g.arc_off.empty() ? 0 : g.arc_off[i];

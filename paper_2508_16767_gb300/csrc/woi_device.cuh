@@ -769,6 +769,28 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
         for (int k = 0; k < D; ++k) v += n[k] * grad[k];
         return s * v;
     }
+    if (basis == kFluxHarmonicQuad) {
+        // s n . grad P with dP/dy_k = a_k + sum_j b_kj y_j + sum_{j<=l} c_kjl y_j y_l
+        constexpr int per_k = 1 + D + D * (D + 1) / 2;
+        Real yy[D * (D + 1) / 2];
+        int t = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+            for (int l = j; l < D; ++l) yy[t++] = y[j] * y[l];
+        Real v = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const Real *q = c + 1 + k * per_k;
+            Real gk = q[0];
+#pragma unroll
+            for (int j = 0; j < D; ++j) gk += q[1 + j] * y[j];
+#pragma unroll
+            for (int m = 0; m < D * (D + 1) / 2; ++m) gk += q[1 + D + m] * yy[m];
+            v += n[k] * gk;
+        }
+        return c[0] * v;
+    }
     if (basis == kFluxPointCharge) {
         // s n . grad_y |y - x0|^{2-d} = s (2 - d) |y - x0|^{-d} (y - x0) . n
         Real r2 = 0, dot = 0;

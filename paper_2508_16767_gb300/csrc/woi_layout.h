@@ -32,7 +32,8 @@ struct BvhNode {
     int a, b;
 };
 static_assert(sizeof(BvhNode) == 32, "nodes are read as two float4");
-enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4 };
+enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4,
+       kFluxHarmonicQuad = 16 };   // device only: [s, (a_k, b_k[d], c_k[d(d+1)/2]) x d], grad P quadratic
 
 struct DevGeom {
     int dim, n, npad, M;
