@@ -917,6 +917,27 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
                 }
             }
             g->flux_off_dev[i] = (int)dev.size();
+            if (basis[i] == WOI_FLUX_REAL_SH && nc[i] <= 9) {
+                // degree <= 2 on a sphere: a quadratic polynomial of the unit vector u (coefficients
+                // here already carry N_lm and sqrt 2); P_2^0 = (3z^2 - 1)/2, P_2^1 cos = 3zx,
+                // P_2^1 sin = 3zy, P_2^2 cos = 3(x^2 - y^2), P_2^2 sin = 6xy (no Condon-Shortley phase)
+                double cf[9] = {0};
+                for (int idx = 0; idx < nc[i]; ++idx) cf[idx] = c[idx];
+                // indices l*l + l + m: (0,0) 0; (1,-1) 1, (1,0) 2, (1,1) 3; (2,-2) 4 ... (2,2) 8
+                double q[10] = {0};
+                q[0] = cf[0] - 0.5 * cf[6];                  // constant
+                q[1] = cf[3]; q[2] = cf[1]; q[3] = cf[2];    // x, y, z
+                q[4] = 3.0 * cf[8];                          // xx
+                q[5] = 6.0 * cf[4];                          // xy
+                q[6] = 3.0 * cf[7];                          // xz
+                q[7] = -3.0 * cf[8];                         // yy
+                q[8] = 3.0 * cf[5];                          // yz
+                q[9] = 1.5 * cf[6];                          // zz
+                g->flux_basis_dev[i] = kFluxSphQuad;
+                g->flux_n_dev[i] = 10;
+                dev.insert(dev.end(), q, q + 10);
+                continue;
+            }
             if (!quad) {
                 g->flux_basis_dev[i] = basis[i];
                 g->flux_n_dev[i] = nc[i];

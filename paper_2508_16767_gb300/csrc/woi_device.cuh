@@ -769,6 +769,14 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
         for (int k = 0; k < D; ++k) v += n[k] * grad[k];
         return s * v;
     }
+    if (basis == kFluxSphQuad) {
+        if constexpr (D == 3) {
+            const Real x = u[0], yv = u[1], z = u[2];
+            return c[0] + c[1] * x + c[2] * yv + c[3] * z + x * (c[4] * x + c[5] * yv + c[6] * z) +
+                   yv * (c[7] * yv + c[8] * z) + c[9] * z * z;
+        }
+        return 0;
+    }
     if (basis == kFluxHarmonicQuad) {
         // s n . grad P with dP/dy_k = a_k + sum_j b_kj y_j + sum_{j<=l} c_kjl y_j y_l
         constexpr int per_k = 1 + D + D * (D + 1) / 2;

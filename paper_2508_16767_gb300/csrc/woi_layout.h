@@ -33,7 +33,9 @@ struct BvhNode {
 };
 static_assert(sizeof(BvhNode) == 32, "nodes are read as two float4");
 enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4,
-       kFluxHarmonicQuad = 16 };   // device only: [s, (a_k, b_k[d], c_k[d(d+1)/2]) x d], grad P quadratic
+       kFluxHarmonicQuad = 16,     // device only: [s, (a_k, b_k[d], c_k[d(d+1)/2]) x d], grad P quadratic
+       kFluxSphQuad = 17 };        // device only, 3D spheres: real harmonics of degree <= 2 as
+                                   // [1, x, y, z, xx, xy, xz, yy, yz, zz] coefficients of the unit vector
 
 struct DevGeom {
     int dim, n, npad, M;
