@@ -190,10 +190,11 @@ __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed_warp(MixedP
         float s1[D + 1], c1[D + 1], s2[D + 1];
 #pragma unroll
         for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
-        // the plain variant in d <= 3 with per-walk schedules advances rounds j and j + 1 together
-        // (two independent walks per lane overlap their dependency chains); in higher dimensions
-        // the second walk's state would not fit in the registers
-        constexpr bool PAIR = !VR && D <= 3;
+        // the plain variant on spheres in d <= 3 with per-walk schedules advances rounds j and j + 1
+        // together (two independent walks per lane overlap their dependency chains); in higher
+        // dimensions, and with the larger code of stars, ellipsoids and meshes, the second walk's
+        // state does not fit in the registers
+        constexpr bool PAIR = !VR && !STAR && D <= 3;
         int j = 0;
         if (PAIR && id.sched_group == 1) {
             for (; j + 1 < L; j += 2) {
