@@ -291,3 +291,35 @@ def test_batch_matches_oracle_and_fp64_path(W, O):
         assert np.all(np.abs(fp64[k]["u"] - orr["u"]) <= 1e-10 * scale), k
     for g in geoms:
         g.close()
+
+
+@pytest.mark.parametrize("name,n_pts,n_walks,precision", [("2d-concentric", 64, 10_000, "fp64"),
+                                                          ("2d-concentric", 64, 10_000, "mixed"),
+                                                          ("3d-nested", 256, 100_000, "mixed"),
+                                                          ("6d-nested", 64, 100_000, "mixed")])
+def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, precision):
+    """The GPU estimates at the workloads' sizes against the exact mean of the truncated
+    estimator on concentric spheres (the per-mode series of the oracle's closed forms):
+    every point within 4.5 SE, and the RMS error over the points consistent with the RMS
+    standard error (between 0.7 and 1.3 times it)."""
+    from oracle import closed_form as cf
+    if name == "2d-concentric":
+        prob, x = wl.concentric_2d_problem(), wl.concentric_2d_points()
+    elif name == "3d-nested":
+        prob, x = wl.nested_3d_problem(), wl.ball_points(4096, 3, 12)
+    else:
+        prob, x = wl.nested_6d_problem(), wl.ball_points(1024, 6, 14)
+    x = np.ascontiguousarray(x[:n_pts])
+    radii = [s["radius"] for s in prob["surfaces"]]
+    u_ex, g_ex = cf.concentric_truncated_mean(prob["dim"], radii, prob["sigma"], prob["parent"],
+                                              cf.modes_from_problem(prob), prob["M"], x)
+    g = W.Geometry(prob)
+    gr = W.woi_estimate(g, x, n_walks, seed=0, M=prob["M"], precision=precision)
+    g.close()
+    z = (gr["u"] - u_ex) / gr["se_u"]
+    assert np.all(np.abs(z) < 4.5), (name, np.abs(z).max())
+    zg = (gr["grad"] - g_ex) / gr["se_grad"]
+    assert np.all(np.abs(zg) < 4.5), (name, np.abs(zg).max())
+    rms_err = np.sqrt(np.mean((gr["u"] - u_ex) ** 2))
+    rms_se = np.sqrt(np.mean(gr["se_u"] ** 2))
+    assert 0.7 * rms_se < rms_err < 1.3 * rms_se, (name, rms_err, rms_se)
