@@ -52,7 +52,7 @@ def alg_tally_flops(dim: int) -> float:
 # DRAM bytes per launch of the walk kernel from the ncu capture of the
 # workload named as key, scaled to one full launch (None once the kernel has
 # changed since the counters were taken).
-TRAFFIC = {"3d-nested": 530_180}   # ncu dram__bytes_read.sum + dram__bytes_write.sum, full-size launch
+TRAFFIC = {"3d-nested": 312_060}   # ncu dram__bytes_read.sum + dram__bytes_write.sum, full-size launch
 
 WORKLOADS = {
     "3d-nested": dict(points=4096, walks=100_000, M=6),
