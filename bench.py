@@ -57,7 +57,9 @@ TRAFFIC = {"3d-nested": 312_060}   # ncu dram__bytes_read.sum + dram__bytes_writ
 WORKLOADS = {
     "3d-nested": dict(points=4096, walks=100_000, M=6),
     "2d-concentric": dict(points=64, walks=10_000, M=4),
-    "2d-star-inclusions": dict(points=16384, walks=100_000, M=4),
+    # the star workload shares each schedule among the 32 walks of a warp (Alg. 1's S x W
+    # structure): on the star the lanes of a warp then take the same transition
+    "2d-star-inclusions": dict(points=16384, walks=100_000, M=4, sched_group=32),
     "6d-nested": dict(points=1024, walks=1_000_000, M=8),
     "3d-ellipsoids": dict(points=4096, walks=100_000, M=5),
     "6d-ellipsoids": dict(points=1024, walks=1_000_000, M=8),
@@ -154,7 +156,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0):
+def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0, sched_group=1):
     """The CPU oracle as it stands on a bounded sample of the workload: all host
     threads, a subset of points and walks sized to ~target_s seconds; returns
     estimates/s at W_full walks per point (time is linear in walks)."""
@@ -162,13 +164,14 @@ def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0):
     prep = core.Prepared(problem)
     n_pts, w = 16, 2048
     t0 = time.perf_counter()
-    core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep)
+    core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep, sched_group=sched_group)
     t1 = time.perf_counter() - t0
     scale = max(1.0, target_s / max(t1, 1e-3))
     n_pts = int(min(len(points), max(16, n_pts * math.sqrt(scale))))
     w = int(max(2048, 2048 * scale * 16 / n_pts)) // 32 * 32
+    w = min(w, W_full)                          # never more than the workload itself
     t0 = time.perf_counter()
-    core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep)
+    core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep, sched_group=sched_group)
     t = time.perf_counter() - t0
     est_per_s = n_pts / (t * W_full / w)
     return {"value": est_per_s, "cores": core.threads_used(), "kind": "oracle",
@@ -185,7 +188,8 @@ def run_reference(args, workload):
     cfg = WORKLOADS[workload]
     times = []
     for s in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(problem, points, cfg["M"], cfg["walks"], target_s=max(2.0, 60.0 / max(args.steps, 1)))
+        r = cpu_oracle_sample(problem, points, cfg["M"], cfg["walks"], target_s=max(2.0, 60.0 / max(args.steps, 1)),
+                              sched_group=args.sched_group)
         if s >= args.warmup:
             times.append(r)
     v = float(np.mean([r["value"] for r in times]))
@@ -193,7 +197,9 @@ def run_reference(args, workload):
             "unit": "estimates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * cfg["points"] / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload, "points": cfg["points"], "walks_per_point": cfg["walks"], "M": cfg["M"]},
+            "config": {"workload": workload, "points": len(points), "walks_per_point": cfg["walks"], "M": cfg["M"],
+                       "dim": problem["dim"], "precision": "fp64 (CPU oracle)", "sched_group": args.sched_group,
+                       "tile_points": 0, "l2": "n/a (host cores)", "parallelism": f"host threads x{times[-1]['cores']}"},
             "cpu_baseline": {"value": v, "unit": "estimates/s", "cores": times[-1]["cores"], "kind": "oracle",
                              "sample": times[-1]["sample"]},
             "e2e": {"value": v, "unit": "estimates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -213,13 +219,15 @@ def main():
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--walks-per-lane", type=int, default=0)
-    ap.add_argument("--sched-group", type=int, default=1)
+    ap.add_argument("--sched-group", type=int, default=0, help="walkers per schedule (default: the workload's)")
     ap.add_argument("--points", type=int, default=0, help="use only the first N points (profiling)")
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
     ap.add_argument("--tile-points", type=int, default=0, choices=[0, 32],
                     help="32: tiles of 32 points share their walks (Sec. 4.6)")
     ap.add_argument("--no-shared", action="store_true", help="skip the shared-trajectory comparison")
     args = ap.parse_args()
+    if not args.sched_group:
+        args.sched_group = WORKLOADS.get(args.workload, {}).get("sched_group", 1) or 1
     if args.impl == "reference":
         return run_reference(args, args.workload)
 
@@ -361,7 +369,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(problem, points, M, Wk)
+        cpu = cpu_oracle_sample(problem, points, M, Wk, sched_group=args.sched_group)
         cpu = {k: cpu[k] for k in ("value", "cores", "kind", "sample")} | {"unit": "estimates/s"}
 
     if rank == 0:
