@@ -124,6 +124,7 @@ struct woi_geometry {
     std::vector<double> star_panel_s;          // kNodes + 1
     std::vector<double> star_scan;             // kNodes * 2
     double star_lmax = 0.0;
+    double star_kpp = 0.0;                     // bound on |gamma''|
     double star_rmin = 0.0, star_rmax = 0.0;
     struct Ellipsoid {
         double A[kMaxDim][kMaxDim];            // (y - c)^T A (y - c) = 1
@@ -679,8 +680,12 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
             g->star_scan[2 * j] = r * std::cos(t);
             g->star_scan[2 * j + 1] = r * std::sin(t);
         }
-        double lm = 0.0, rmin = 1e300, rmax = 0.0, b2 = 0.0;
-        for (int k = 1; k <= g->star.K; ++k) b2 += (double)k * k * (std::fabs(g->star.a[k]) + std::fabs(g->star.b[k]));
+        double lm = 0.0, rmin = 1e300, rmax = 0.0, b1 = 0.0, b2 = 0.0;
+        for (int k = 1; k <= g->star.K; ++k) {
+            b1 += (double)k * (std::fabs(g->star.a[k]) + std::fabs(g->star.b[k]));
+            b2 += (double)k * k * (std::fabs(g->star.a[k]) + std::fabs(g->star.b[k]));
+        }
+        b1 *= g->star.R;                                   // bound on |r'|
         b2 *= g->star.R;                                   // bound on |r''|
         const int ms = 16384;
         for (int j = 0; j < ms; ++j) {
@@ -695,6 +700,8 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
         g->star_lmax = lm * 1.02 + 1e-12;
         g->star_rmin = std::max(0.0, rmin - margin);
         g->star_rmax = rmax + margin;
+        // gamma'' = (r'' - r) e_r + 2 r' e_t, so |gamma''| <= |r''| + r + 2 |r'|
+        g->star_kpp = b2 + g->star_rmax + 2.0 * b1;
     }
     *out = g;
     return WOI_OK;
@@ -1095,6 +1102,7 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
     b.star_idx = g.star_idx;
     b.star_K = g.star_idx >= 0 ? g.star.K : 0;
     b.star_lmax = g.star_lmax;
+    b.star_kpp = g.star_kpp;
     b.star_rmin = g.star_rmin;
     b.star_rmax = g.star_rmax;
     for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g.n ? (uint32_t)(g.thresh[i] - 1) : 0xFFFFFFFFu;

@@ -223,6 +223,7 @@ struct SGeom {
     // star (at most one per instance)
     Real star_a[kMaxStar + 1], star_b[kMaxStar + 1];
     Real star_lmax;                      // bound on |gamma'|
+    Real star_kpp;                       // bound on |gamma''|
     Real star_rmin, star_rmax;           // annulus that contains the star
     Real scan[kNodes][2];                // gamma(t_j) - centre
     double panel_s[kNodes + 1];          // arc length at t_j
@@ -239,6 +240,7 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.star_idx = src->star_idx;
         g.star_K = src->star_K;
         g.star_lmax = (Real)src->star_lmax;
+        g.star_kpp = (Real)src->star_kpp;
         g.star_rmin = (Real)src->star_rmin;
         g.star_rmax = (Real)src->star_rmax;
     }
@@ -536,7 +538,11 @@ __device__ __forceinline__ int star_interval_roots(const SGeom<Real> &g, int j, 
                                                    const Real *z, Real *cand)
 {
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
-    const Real guard = g.star_lmax * H * (Real)0.5;
+    // f = (gamma - y) x z has |f''| <= |gamma''| <= K, so on [0, H] f stays above the chord
+    // minus K H^2 / 8: with f(0), f(H) of one sign and both beyond that (plus the rounding of
+    // f), the interval holds no root; only the others need the search for an extremum
+    const Real guard = g.star_kpp * H * H * (Real)0.125 +
+                       (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_rmax;
     int nc = 0;
     if ((fa < 0) != (fb < 0)) {
         cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z, H * fa / (fa - fb));   // secant start
@@ -597,8 +603,7 @@ __device__ __forceinline__ void star_mark_window(const Real *yc, const Real *z, 
     int j0 = (int)(pa / H) - 1;
     const int count = (int)(span / H) + 3;
     for (int c = 0; c < count && c < kNodes; ++c) {
-        int j = j0 + c;
-        j = (j % kNodes + kNodes) % kNodes;
+        const int j = (j0 + c) & (kNodes - 1);   // kNodes is a power of two
         mask[j >> 5] |= 1u << (j & 31);
     }
 }

@@ -15,6 +15,7 @@ constexpr int kMaxStar = 16;           // star Fourier degree (WOI_MAX_STAR_DEGR
 constexpr int kNodes = 256;            // angle nodes t_j = 2 pi j / kNodes: star scan samples,
                                        // arc-length panels and the angle-addition table
 constexpr int kMaxRoots = 2 * (kMaxStar + 1) + 2;
+static_assert((kNodes & (kNodes - 1)) == 0, "node indices wrap with a mask");
 constexpr int kMaxEll = 8;             // ellipsoids per instance (WOI_MAX_ELLIPSOIDS)
 constexpr int kMaxMesh = 16;           // meshes per instance (WOI_MAX_MESHES)
 constexpr int kMeshStack = 64;         // BVH traversal stack (the host caps the tree depth below it)
@@ -41,6 +42,7 @@ struct DevGeom {
     int dim, n, npad, M;
     int star_idx, star_K;              // star_idx = -1: no star in this instance
     double star_lmax;                  // bound on |gamma'| of the star
+    double star_kpp;                   // bound on |gamma''| of the star
     double star_rmin, star_rmax;       // bounds on r(t): every point of the star lies in this annulus
     uint32_t sched_tm1[kMaxSurfPad];   // T_n - 1, padded with 0xFFFFFFFF
     int sched_bucket[kSchedBuckets + 1]; // first n with T_n - 1 >= b 2^24 (N - 1 if none)
