@@ -323,3 +323,38 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
     rms_err = np.sqrt(np.mean((gr["u"] - u_ex) ** 2))
     rms_se = np.sqrt(np.mean(gr["se_u"] ** 2))
     assert 0.7 * rms_se < rms_err < 1.3 * rms_se, (name, rms_err, rms_se)
+
+
+@pytest.mark.parametrize("name", ["3d-nested", "ellipsoids-3d", "mesh-rocks", "star-3"])
+def test_walk_trace_states_match_oracle(W, O, name):
+    """woi_walk_trace (FP64): every state y_i, Q_i and T_i of every walk equals the
+    oracle's (Eqs. naive_woi_Q, naive_woi_T) to 1e-12 of its magnitude scale."""
+    prob, x, variant = next((c[1], c[2], c[3]) for c in CASES if c[0] == name)
+    g = W.Geometry(prob)
+    ids = walk_ids(64)
+    tr = W.woi_walk_trace(g, x[0], ids, seed=7, point_id=0, M=prob["M"], variant=variant, precision="fp64")
+    g.close()
+    ow = O.walks(prob, x[0], ids, seed=7, M=prob["M"], variant=variant, point_id=0)
+    chains = 2 if variant == "vr" else 1
+    alive = ow["T"][:, :chains] != 0           # a chain that ended keeps its last state on both sides
+    dy = np.abs(tr["Y"] - ow["Y"][:, :chains]).max(axis=-1)
+    assert np.all(dy[alive] <= 1e-12 * (1 + np.abs(ow["Y"][:, :chains]).max(axis=-1)[alive])), name
+    for key in ("Q", "T"):
+        ref = ow[key][:, :chains]
+        assert np.all(np.abs(tr[key] - ref)[alive] <= 1e-12 * (np.abs(ref)[alive] + 1e-300) + 1e-300), (name, key)
+
+
+def test_autotune_keeps_the_estimate(W):
+    """woi_autotune picks a (block, walks per lane) from its candidates; estimates after
+    it (default shape) equal the ones before up to the summation order of the FP32 sums."""
+    prob = wl.nested_3d_problem()
+    x = wl.ball_points(96, 3, 31)
+    g = W.Geometry(prob)
+    before = W.woi_estimate(g, x, 8192, seed=2, M=prob["M"], block_size=256, walks_per_lane=32)
+    b, l = W.woi_autotune(g, x, 8192, seed=2, M=prob["M"])
+    assert b in (128, 256) and l in (8, 16, 32, 64)
+    after = W.woi_estimate(g, x, 8192, seed=2, M=prob["M"])
+    g.close()
+    assert np.all(np.abs(after["u"] - before["u"]) <= 1e-3 * before["se_u"] + 1e-12)
+    assert np.all(np.abs(after["grad"] - before["grad"]) <= 1e-3 * before["se_grad"] + 1e-12)
+    assert np.allclose(after["se_u"], before["se_u"], rtol=1e-4)
