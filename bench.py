@@ -225,6 +225,7 @@ def main():
     ap.add_argument("--tile-points", type=int, default=0, choices=[0, 32],
                     help="32: tiles of 32 points share their walks (Sec. 4.6)")
     ap.add_argument("--no-shared", action="store_true", help="skip the shared-trajectory comparison")
+    ap.add_argument("--no-vr", action="store_true", help="skip the variance-reduced comparison (2D workloads)")
     args = ap.parse_args()
     if not args.sched_group:
         args.sched_group = WORKLOADS.get(args.workload, {}).get("sched_group", 1) or 1
@@ -367,6 +368,31 @@ def main():
                   "rms_se_u": float(torch.sqrt(torch.mean(outs[2] ** 2)).item()),
                   "roofline_frac": fl / (k_s / 1000.0) / 1e12 / peak_tflops, "speedup_of_per_point": (P / t_s) / value}
 
+    # the variance-reduced variant (Alg. 3, 2D): two chains per walk from the beta >= 0 and
+    # beta < 0 parts; at the plain path's RMS error it needs (se_vr / se_plain)^2 of the walks
+    vr = None
+    if rank == 0 and ws == 1 and d == 2 and args.precision == "mixed" and not args.tile_points and not args.no_vr:
+        vo = dict(opt, variant="vr")
+        for _ in range(args.warmup):
+            woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, **vo)
+        vms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, **vo)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            vms.append(e0.elapsed_time(e1))
+        t_v = float(np.mean(vms)) / 1000.0
+        se_v = float(torch.sqrt(torch.mean(outs[2] ** 2)).item())
+        ratio = (se_v / rms_se) ** 2 if rms_se else None
+        vr = {"value": P / t_v, "unit": "estimates/s", "ms_per_step": 1000.0 * t_v, "rms_se_u": se_v,
+              "walk_steps_per_s": 2 * P * Wk * (M + 1) / t_v,
+              "value_at_plain_rms_error": (P / (t_v * ratio)) if ratio else None,
+              "note": "two chains per walk; value_at_plain_rms_error scales the walks by (se_vr / se_plain)^2"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(problem, points, M, Wk, sched_group=args.sched_group)
@@ -389,7 +415,8 @@ def main():
                          "frac": achieved / peak_tflops, "traffic": TRAFFIC.get(args.workload),
                          "peak_source": f"FP32: SMs x 128 lanes x 2 x sm_max_mhz ({src})",
                          "kernel_ms": k_ms, "alg_flops_per_walk_step": alg_flops_per_walk_step(d, ell)},
-            "cpu_baseline": cpu, "fp64_plain_gpu_path": fp64, "shared_trajectories": shared, "e2e": e2e,
+            "cpu_baseline": cpu, "fp64_plain_gpu_path": fp64, "shared_trajectories": shared,
+            "variance_reduced": vr, "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": args.steps * (2 if args.precision == "mixed" else P + 1),
         }
