@@ -62,8 +62,9 @@ WORKLOADS = {
     "2d-star-inclusions": dict(points=16384, walks=100_000, M=4, sched_group=32),
     "6d-nested": dict(points=1024, walks=1_000_000, M=8),
     "3d-ellipsoids": dict(points=4096, walks=100_000, M=5),
-    "6d-ellipsoids": dict(points=1024, walks=1_000_000, M=8),
-    "3d-rocks": dict(points=4096, walks=100_000, M=5),
+    "6d-ellipsoids": dict(points=1024, walks=1_000_000, M=8, sched_group=32),   # same SE as W_g = 1
+    "3d-rocks": dict(points=4096, walks=100_000, M=5, sched_group=32),   # warp-shared schedules: the
+                                                                       # lanes traverse the same mesh
     "batch": dict(points=None, walks=None, M=None),
 }
 

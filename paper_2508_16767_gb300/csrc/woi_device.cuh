@@ -988,55 +988,65 @@ __device__ int mesh_hits(const DevGeom *gd, int m, const Real *o, const Real *z,
     int sp = 0, q = 0;
     bool over = false;
     stack[sp++] = gd->mesh_node_off[m];
-    while (sp > 0) {
-        const int ni = stack[--sp];
-        const float4 n0 = __ldg(reinterpret_cast<const float4 *>(nodes + ni));
-        const float4 n1 = __ldg(reinterpret_cast<const float4 *>(nodes + ni) + 1);
-        BvhNode n;
-        n.lo[0] = n0.x; n.lo[1] = n0.y; n.lo[2] = n0.z; n.hi[0] = n0.w;
-        n.hi[1] = n1.x; n.hi[2] = n1.y; n.a = __float_as_int(n1.z); n.b = __float_as_int(n1.w);
-        // slab test against the padded box
-        Real t0 = ray ? (Real)0 : (Real)-1e30, t1 = (Real)1e30;
+    // "while-while" order: each lane walks inner nodes until it holds a leaf (or its stack
+    // is empty), then the lanes test their leaves' triangles together, so that the leaf
+    // code is not run once per lane while the other lanes wait in the node code
+    for (;;) {
+        int leaf_first = 0, leaf_count = 0;
+        while (sp > 0) {
+            const int ni = stack[--sp];
+            const float4 n0 = __ldg(reinterpret_cast<const float4 *>(nodes + ni));
+            const float4 n1 = __ldg(reinterpret_cast<const float4 *>(nodes + ni) + 1);
+            const float lo[3] = {n0.x, n0.y, n0.z}, hi[3] = {n0.w, n1.x, n1.y};
+            const int na = __float_as_int(n1.z), nb = __float_as_int(n1.w);
+            // slab test against the padded box
+            Real t0 = ray ? (Real)0 : (Real)-1e30, t1 = (Real)1e30;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const Real ta = ((Real)n.lo[k] - o[k]) * iz[k], tb = ((Real)n.hi[k] - o[k]) * iz[k];
-            const Real tmn = ta < tb ? ta : tb, tmx = ta < tb ? tb : ta;
-            t0 = tmn > t0 ? tmn : t0;
-            t1 = tmx < t1 ? tmx : t1;
-        }
-        if (!(t0 <= t1)) continue;
-        if (n.b < 0) {
-            for (int i = n.a; i < n.a - n.b; ++i) {
-                const int t = __ldg(gd->bvh_tri + i);
-                if (t == exclude) continue;
-                const Real *r = rows + (size_t)t * 12;
-                const Real e1[3] = {__ldg(r + 3), __ldg(r + 4), __ldg(r + 5)};
-                const Real e2[3] = {__ldg(r + 6), __ldg(r + 7), __ldg(r + 8)};
-                const Real p[3] = {z[1] * e2[2] - z[2] * e2[1], z[2] * e2[0] - z[0] * e2[2], z[0] * e2[1] - z[1] * e2[0]};
-                const Real det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
-                if (det == (Real)0) continue;
-                const Real idet = (Real)1 / det;
-                const Real sv[3] = {o[0] - __ldg(r), o[1] - __ldg(r + 1), o[2] - __ldg(r + 2)};
-                const Real a = (sv[0] * p[0] + sv[1] * p[1] + sv[2] * p[2]) * idet;
-                if (a < (Real)0 || a > (Real)1) continue;
-                const Real qv[3] = {sv[1] * e1[2] - sv[2] * e1[1], sv[2] * e1[0] - sv[0] * e1[2], sv[0] * e1[1] - sv[1] * e1[0]};
-                const Real b = (z[0] * qv[0] + z[1] * qv[1] + z[2] * qv[2]) * idet;
-                if (b < (Real)0 || a + b > (Real)1) continue;
-                const Real th = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * idet;
-                if (ray && !(th > (Real)0)) continue;
-                if (q < kMaxHits) {
-                    tt[q] = th;
-                    tri[q] = t;
-                    ++q;
-                } else {
-                    over = true;
-                }
+            for (int k = 0; k < 3; ++k) {
+                const Real ta = ((Real)lo[k] - o[k]) * iz[k], tb = ((Real)hi[k] - o[k]) * iz[k];
+                const Real tmn = ta < tb ? ta : tb, tmx = ta < tb ? tb : ta;
+                t0 = tmn > t0 ? tmn : t0;
+                t1 = tmx < t1 ? tmx : t1;
             }
-        } else if (sp + 2 <= kMeshStack) {
-            stack[sp++] = n.a;
-            stack[sp++] = n.b;
-        } else {
-            over = true;
+            if (!(t0 <= t1)) continue;
+            if (nb < 0) {
+                leaf_first = na;
+                leaf_count = -nb;
+                break;
+            }
+            if (sp + 2 <= kMeshStack) {
+                stack[sp++] = na;
+                stack[sp++] = nb;
+            } else {
+                over = true;
+            }
+        }
+        if (leaf_count == 0) break;              // the stack ran empty without another leaf
+        for (int i = leaf_first; i < leaf_first + leaf_count; ++i) {
+            const int t = __ldg(gd->bvh_tri + i);
+            if (t == exclude) continue;
+            const Real *r = rows + (size_t)t * 12;
+            const Real e1[3] = {__ldg(r + 3), __ldg(r + 4), __ldg(r + 5)};
+            const Real e2[3] = {__ldg(r + 6), __ldg(r + 7), __ldg(r + 8)};
+            const Real p[3] = {z[1] * e2[2] - z[2] * e2[1], z[2] * e2[0] - z[0] * e2[2], z[0] * e2[1] - z[1] * e2[0]};
+            const Real det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+            if (det == (Real)0) continue;
+            const Real idet = (Real)1 / det;
+            const Real sv[3] = {o[0] - __ldg(r), o[1] - __ldg(r + 1), o[2] - __ldg(r + 2)};
+            const Real a = (sv[0] * p[0] + sv[1] * p[1] + sv[2] * p[2]) * idet;
+            if (a < (Real)0 || a > (Real)1) continue;
+            const Real qv[3] = {sv[1] * e1[2] - sv[2] * e1[1], sv[2] * e1[0] - sv[0] * e1[2], sv[0] * e1[1] - sv[1] * e1[0]};
+            const Real b = (z[0] * qv[0] + z[1] * qv[1] + z[2] * qv[2]) * idet;
+            if (b < (Real)0 || a + b > (Real)1) continue;
+            const Real th = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * idet;
+            if (ray && !(th > (Real)0)) continue;
+            if (q < kMaxHits) {
+                tt[q] = th;
+                tri[q] = t;
+                ++q;
+            } else {
+                over = true;
+            }
         }
     }
     if (over && gd->mesh_overflow) atomicAdd(gd->mesh_overflow, 1u);
