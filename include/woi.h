@@ -225,12 +225,13 @@ WOI_API woi_status woi_walk_trace(woi_geometry *geometry, const woi_opts *opts, 
 /*
  * Batched heterogeneous estimate: n_inst geometries (each with data set),
  * instance k with n_pts[k] points at points[k] (host or device) and n_walks[k]
- * walks per point.  All instances run in one persistent kernel that takes
- * (instance, point, walk-chunk) units from a device work queue; outputs per
+ * walks per point.  All instances of one group run in one persistent kernel:
+ * a block serves one instance at a time and its warps take (point, walk-chunk)
+ * units from that instance's device work-queue head; outputs per
  * instance as for woi_estimate (u[k], grad[k], se_u[k], se_grad[k], each may
  * be NULL).  Random streams use instance id k.  opts applies to all instances
  * except M, which comes from m_per_inst[k] when m_per_inst is not NULL.
- * Instances are grouped by (dimension, star surface): one persistent launch per
+ * Instances are grouped by (dimension, non-sphere surfaces): one persistent launch per
  * group, then one finalize; the sequence is captured as a CUDA graph and
  * replayed while the same batch (handles, sizes, pointers, seed, options) is
  * run again.  With WOI_FP64_PLAIN the instances run one after another, one

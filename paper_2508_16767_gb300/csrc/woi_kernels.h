@@ -16,7 +16,7 @@ constexpr int kSharedBlock = 128;     // threads per block of the shared-traject
 constexpr int kTile = 32;             // points per shared-trajectory tile
 
 struct MixedParams {
-    const InstDesc *inst;              // device [n_inst], sorted by unit_begin
+    const InstDesc *inst;              // device [n_inst]; units of instance k start at inst[k].unit_begin
     int n_inst;
     int64_t total_units;
     unsigned long long *queue;         // device work-queue head (batch: one per instance), zero before the launch
