@@ -226,7 +226,7 @@ def main():
     ap.add_argument("--tile-points", type=int, default=0, choices=[0, 32],
                     help="32: tiles of 32 points share their walks (Sec. 4.6)")
     ap.add_argument("--no-shared", action="store_true", help="skip the shared-trajectory comparison")
-    ap.add_argument("--no-vr", action="store_true", help="skip the variance-reduced comparison (2D workloads)")
+    ap.add_argument("--no-vr", action="store_true", help="skip the variance-reduced comparison")
     args = ap.parse_args()
     if not args.sched_group:
         args.sched_group = WORKLOADS.get(args.workload, {}).get("sched_group", 1) or 1
@@ -369,11 +369,20 @@ def main():
                   "rms_se_u": float(torch.sqrt(torch.mean(outs[2] ** 2)).item()),
                   "roofline_frac": fl / (k_s / 1000.0) / 1e12 / peak_tflops, "speedup_of_per_point": (P / t_s) / value}
 
-    # the variance-reduced variant (Alg. 3, 2D): two chains per walk from the beta >= 0 and
-    # beta < 0 parts; at the plain path's RMS error it needs (se_vr / se_plain)^2 of the walks
+    # the variance-reduced variant (Alg. 3; 2D Fourier data, or hemisphere parts of data linear
+    # in the unit vector in d >= 3): two chains per walk from the beta >= 0 and beta < 0 parts;
+    # at the plain path's RMS error it needs (se_vr / se_plain)^2 of the walks
     vr = None
-    if rank == 0 and ws == 1 and d == 2 and args.precision == "mixed" and not args.tile_points and not args.no_vr:
-        vo = dict(opt, variant="vr")
+    vo = dict(opt, variant="vr")
+    vr_ok = rank == 0 and ws == 1 and args.precision == "mixed" and not args.tile_points and not args.no_vr
+    if vr_ok:
+        try:
+            woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, **vo)
+        except woi.WoiError as e:
+            if e.status != 4:                     # WOI_E_UNSUPPORTED
+                raise
+            vr_ok = False                          # no closed-form parts for this data
+    if vr_ok:
         for _ in range(args.warmup):
             woi.woi_estimate(geom, xd, Wk, seed=0, out=outs, stream=stream.cuda_stream, **vo)
         vms = []

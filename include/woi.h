@@ -122,7 +122,10 @@ typedef struct {
 } woi_flux_desc;
 
 enum { WOI_PLAIN = 0,                 /* Algorithm 2 */
-       WOI_VR = 1 };                  /* Algorithm 3: two chains from dOmega^+ / dOmega^- (2D) */
+       WOI_VR = 1 };                  /* Algorithm 3: two chains from dOmega^+ / dOmega^-; available for
+                                         2D Fourier (or zero) data, and in d >= 3 for spheres whose data
+                                         is linear in the unit vector (or zero), where the parts are
+                                         hemispheres; WOI_E_UNSUPPORTED otherwise */
 enum { WOI_MIXED = 0,                 /* FP32 walks, compensated FP32 per-lane sums, FP64 reductions */
        WOI_FP64_PLAIN = 1 };          /* FP64 everywhere, one kernel launch per evaluation point */
 

@@ -260,6 +260,8 @@ def modes_from_problem(problem):
             for t in range(T):
                 row = c[2 + t * (d + 1): 2 + (t + 1) * (d + 1)]
                 e = [int(v) for v in row[1:]]
+                if sum(e) == 0:
+                    continue        # a constant term of P has no gradient: no flux
                 assert sum(e) == 1, "only linear harmonic polynomials have a single mode"
                 k = e.index(1)
                 # b = s n . grad(c x_k) = s c x_hat_k on any sphere about the origin

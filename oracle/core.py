@@ -22,7 +22,8 @@ module prepares its inputs from a problem dictionary with numpy/scipy:
     the area as the sum of the triangle areas, and the cumulative-area
     thresholds floor(2^32 C_j / A) that pick a triangle by area;
   * Sec. 4.4: the beta >= 0 / beta < 0 arcs of 2D surfaces for the variance-
-    reduced estimator, by a dense sign scan and Brent's method.
+    reduced estimator, by a dense sign scan and Brent's method; in d >= 3 the
+    hemispheres of data linear in the unit vector.
 """
 from __future__ import annotations
 
@@ -308,6 +309,31 @@ def fourier_eval(coef, t):
     return v
 
 
+def linear_on_sphere(dim, s, flux):
+    """Data whose value on the sphere is linear in the unit vector u (degree-1 real
+    harmonics, harmonic polynomials of degree 1): its sign parts are hemispheres."""
+    if s["kind"] != "sphere":
+        return False
+    if flux["basis"] == "real_sh":
+        return dim == 3 and all(v == 0.0 for i, v in enumerate(flux["coef"]) if not 1 <= i <= 3)
+    if flux["basis"] == "harmonic_poly":
+        c = flux["coef"]
+        T = int(c[1])
+        return all(sum(c[2 + t * (dim + 1) + 1: 2 + (t + 1) * (dim + 1)]) <= 1 for t in range(T))
+    return False
+
+
+def vr_parts(dim, s, flux):
+    """|dOmega^+|, |dOmega^-| in d >= 3 (Sec. 4.4): zero data puts the whole sphere in the
+    beta >= 0 part; data linear in u splits it into two hemispheres; None otherwise."""
+    A = surface_area(dim, s)
+    if flux["basis"] == "zero" and s["kind"] == "sphere":
+        return (A, 0.0)
+    if linear_on_sphere(dim, s, flux):
+        return (0.5 * A, 0.5 * A)
+    return None
+
+
 def vr_arcs(dim, s, flux, bscale, n_scan=20000):
     """Arcs of dOmega^+ = {beta >= 0} and dOmega^- = {beta < 0} (Sec. 4.4) of a
     2D surface with Fourier flux, cut at t = 0 and at every sign change."""
@@ -413,6 +439,15 @@ class Prepared:
         arc_off, arc_n, t0, t1, sg, ln = [], [], [], [], [], []
         self.part_len = np.zeros((n, 2))
         for i in range(n):
+            if variant == "vr" and d >= 3:
+                parts = vr_parts(d, surfs[i], fl[i])
+                if parts is None:
+                    raise ValueError("variance reduction in d >= 3 needs spheres with data linear in the "
+                                     "unit vector (or zero) on every surface")
+                self.part_len[i] = parts
+                arc_off.append(len(t0))
+                arc_n.append(0)
+                continue
             arcs = vr_arcs(d, surfs[i], fl[i], self.beta_scale[i]) if variant == "vr" else None
             if variant == "vr" and arcs is None:
                 raise ValueError("variance reduction needs 2D Fourier (or zero) flux on every surface")

@@ -23,7 +23,8 @@
  *     N ||alpha||_1^i prod_{m=1}^{i} sign(alpha_{H_m}).
  *   - Algorithms 1-2 (plain walk), Algorithm 3 and Eq.
  *     variance_reduced_woi_estimator (two chains from the beta >= 0 and
- *     beta < 0 parts of the first interface).
+ *     beta < 0 parts of the first interface; in 2D the parts are arcs, in
+ *     d >= 3 they are the hemispheres of data linear in the unit vector).
  *   - Sec. 4.5, Eq. naive_woi_grad_estimator: the gradient tally uses
  *     grad_x Phi on the same trajectory.
  *   - Sec. 5, Example 2: ellipsoids (y - c)^T A (y - c) = 1 as surfaces, with
@@ -74,7 +75,8 @@ enum { OR_REL_SAME = 0, OR_REL_DESC = 1, OR_REL_OTHER = 2 };
  *   2 alpha-sign product over m = 0..i          3 no half weight at i = M
  *   4 no factor N                               5 K* with the normal at the old point
  *   6 beta_i scaled by +2/(sigma_p + sigma_i)   7 line case keeps Q (no 1/2)
- *   8 gradient of Phi with the wrong sign       9 H_0 drawn like H_i (by |alpha|) */
+ *   8 gradient of Phi with the wrong sign       9 H_0 drawn like H_i (by |alpha|)
+ *  10 d >= 3 part sampler without the reflection u -> -u */
 static int or_mutant = 0;
 void or_set_mutant(int m) { or_mutant = m; }
 
@@ -406,9 +408,25 @@ static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, in
 
 /* uniform point on dOmega_h^+ (part = 0) or dOmega_h^- (part = 1): the arcs of
  * the requested sign are concatenated in increasing parameter angle */
+static double or_beta(const or_problem *P, int h, int tri, const double *y);
+
 static void or_uniform_part_point(const or_problem *P, int h, int part, or_rng *r, int step, int chain,
                                   double *y)
 {
+    if (P->dim >= 3) {
+        /* a sphere whose data is linear in the unit vector u (degree-1 harmonics, linear
+         * harmonic polynomials): the parts beta >= 0 and beta < 0 are the two hemispheres
+         * {beta(u) >= 0} and its mirror image, so a uniform u that lands in the wrong one
+         * is reflected, u -> -u, which keeps it uniform on the right one */
+        double z[OR_MAX_DIM];
+        const double *c = or_center(P, h);
+        or_direction(r, P->dim, step, chain, z);
+        for (int k = 0; k < P->dim; ++k) y[k] = c[k] + P->radius[h] * z[k];
+        const double b = or_beta(P, h, -1, y);
+        if ((part == 0) != (b >= 0.0) && or_mutant != 10)
+            for (int k = 0; k < P->dim; ++k) y[k] = c[k] - P->radius[h] * z[k];
+        return;
+    }
     double s = or_u01(or_word(r, step, chain, 1)) * P->part_len[2 * h + part];
     int want = part == 0 ? 1 : -1, last = -1;
     for (int a = P->arc_off[h]; a < P->arc_off[h] + P->arc_n[h]; ++a) {

@@ -879,6 +879,35 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             an[i]++;
         }
     }
+    // Sec. 4.4 in d >= 3: on a sphere, data linear in the unit vector u (degree-1 real
+    // harmonics, harmonic polynomials of degree <= 1) is negative exactly on the mirror
+    // image of the half where it is positive, so each part is a hemisphere of half the
+    // area; zero data puts the whole sphere in dOmega^+.  Other surfaces or data have
+    // parts of no closed form here, and the variant stays unavailable for them.
+    if (d >= 3) {
+        vr_ok = true;
+        for (int i = 0; i < n && vr_ok; ++i) {
+            if (g->surf[i].type != WOI_SPHERE) { vr_ok = false; break; }
+            if (basis[i] == WOI_FLUX_ZERO) { plen[2 * i] = g->area[i]; continue; }
+            const double *c = coef.data() + off[i];
+            bool linear = false;
+            if (basis[i] == WOI_FLUX_REAL_SH && d == 3) {
+                linear = true;
+                for (int idx = 0; idx < nc[i]; ++idx)
+                    if ((idx < 1 || idx > 3) && c[idx] != 0.0) linear = false;
+            } else if (basis[i] == WOI_FLUX_HARMONIC_POLY) {
+                linear = true;
+                const int T = (int)c[1];
+                for (int t = 0; t < T; ++t) {
+                    double deg = 0.0;
+                    for (int k = 0; k < d; ++k) deg += c[2 + t * (d + 1) + 1 + k];
+                    if (deg > 1.0) linear = false;
+                }
+            }
+            if (!linear) { vr_ok = false; break; }
+            plen[2 * i] = plen[2 * i + 1] = 0.5 * g->area[i];
+        }
+    }
     g->sigma.assign(sigma, sigma + n);
     g->alpha = alpha;
     g->beta_scale = bsc;
@@ -1283,7 +1312,8 @@ woi_status check_opts(const woi_geometry *g, const woi_opts *o, int64_t n_pts, i
     if (n_walks % o->sched_group || walk_begin % o->sched_group)
         return fail(WOI_E_INVALID_ARG, "walk range must be a multiple of sched_group");
     if (o->variant == WOI_VR && !g->vr_ok)
-        return fail(WOI_E_UNSUPPORTED, "variance reduction needs 2D Fourier (or zero) flux on every surface");
+        return fail(WOI_E_UNSUPPORTED, "variance reduction needs 2D Fourier (or zero) flux on every surface, or in "
+                                        "d >= 3 spheres with data linear in the unit vector (or zero)");
     if (o->block_size != 0 && (o->block_size % 32 || o->block_size < 32 || o->block_size > kMixedMaxBlock))
         return fail(WOI_E_INVALID_ARG, "block_size must be a multiple of 32 in [32, %d]", kMixedMaxBlock);
     if (o->walks_per_lane < 0 || o->walks_per_lane > 4096) return fail(WOI_E_INVALID_ARG, "walks_per_lane out of range");

@@ -1202,6 +1202,27 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
             }
             u[0] = ct;
             u[1] = st;
+        } else {
+            // VR on a d >= 3 sphere whose data is linear in u: the two parts are mirror-image
+            // hemispheres, so a uniform direction that lands in the part of the wrong sign is
+            // reflected, u -> -u, which leaves it uniform on the requested one
+            direction<Real, D>(w, u);
+            Real y0[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                ch.v[c] = g.radius[h] * u[c];
+                nrm[c] = u[c];
+                y0[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + ch.v[c];
+            }
+            const Real b = g.beta_scale[h] * flux_value<Real, D>(gd, h, y0, u, nrm);
+            if ((k == 0) != (b >= (Real)0)) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    u[c] = -u[c];
+                    nrm[c] = -nrm[c];
+                    ch.v[c] = -ch.v[c];
+                }
+            }
         }
     }
     Real y[D];

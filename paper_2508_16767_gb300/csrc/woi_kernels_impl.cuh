@@ -478,9 +478,9 @@ __global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::mixed(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
-    if constexpr (D == 2) {
+    if constexpr (D == 2 || !STAR) {
         if (vr) {
-            k_walk_mixed<2, true, STAR><<<grid, block, smem, s>>>(p);
+            k_walk_mixed<D, true, STAR><<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
@@ -491,9 +491,9 @@ template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem,
                                              cudaStream_t s)
 {
-    if constexpr (D == 2) {
+    if constexpr (D == 2 || !STAR) {
         if (vr) {
-            k_walk_mixed_warp<2, true, STAR><<<grid, block, smem, s>>>(p);
+            k_walk_mixed_warp<D, true, STAR><<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
@@ -504,8 +504,8 @@ cudaError_t DimLaunchers<D, STAR>::mixed_warp(bool vr, const MixedParams &p, int
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t smem, int *blocks_per_sm)
 {
-    if constexpr (D == 2) {
-        if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<2, true, STAR>, block, smem);
+    if constexpr (D == 2 || !STAR) {
+        if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, true, STAR>, block, smem);
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, false, STAR>, block, smem);
 }
@@ -515,12 +515,12 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t sme
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::shared(bool vr, const MixedParams &p, int grid, size_t smem, cudaStream_t s)
 {
-    if constexpr (D == 2) {
+    if constexpr (D == 2 || !STAR) {
         if (vr) {
-            cudaError_t e = cudaFuncSetAttribute(k_walk_shared<2, true, STAR>,
+            cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, true, STAR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k_walk_shared<2, true, STAR><<<grid, kSharedBlock, smem, s>>>(p);
+            k_walk_shared<D, true, STAR><<<grid, kSharedBlock, smem, s>>>(p);
             return cudaGetLastError();
         }
     }
@@ -534,12 +534,12 @@ cudaError_t DimLaunchers<D, STAR>::shared(bool vr, const MixedParams &p, int gri
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *blocks_per_sm)
 {
-    if constexpr (D == 2) {
+    if constexpr (D == 2 || !STAR) {
         if (vr) {
-            cudaError_t e = cudaFuncSetAttribute(k_walk_shared<2, true, STAR>,
+            cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, true, STAR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_shared<2, true, STAR>, kSharedBlock, smem);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_shared<D, true, STAR>, kSharedBlock, smem);
         }
     }
     cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, false, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -551,17 +551,17 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *b
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, size_t smem, int *blocks_per_sm)
 {
-    if constexpr (D == 2) {
-        if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<2, true, STAR>, block, smem);
+    if constexpr (D == 2 || !STAR) {
+        if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, true, STAR>, block, smem);
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, false, STAR>, block, smem);
 }
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s)
     {
-        if constexpr (D == 2) {
+        if constexpr (D == 2 || !STAR) {
             if (vr) {
-                k_walk_fp64_point<2, true, STAR><<<grid, 256, 0, s>>>(p);
+                k_walk_fp64_point<D, true, STAR><<<grid, 256, 0, s>>>(p);
                 return cudaGetLastError();
             }
         }
@@ -572,10 +572,10 @@ template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::values(bool vr, bool fp64, const WalkValuesParams &p, cudaStream_t s)
     {
         const int grid = (int)((p.n + 127) / 128);
-        if constexpr (D == 2) {
+        if constexpr (D == 2 || !STAR) {
             if (vr) {
-                if (fp64) k_walk_values<double, 2, true, STAR><<<grid, 128, 0, s>>>(p);
-                else k_walk_values<float, 2, true, STAR><<<grid, 128, 0, s>>>(p);
+                if (fp64) k_walk_values<double, D, true, STAR><<<grid, 128, 0, s>>>(p);
+                else k_walk_values<float, D, true, STAR><<<grid, 128, 0, s>>>(p);
                 return cudaGetLastError();
             }
         }

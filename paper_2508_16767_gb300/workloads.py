@@ -129,6 +129,21 @@ def nested_3d_problem(seed=2):
     }
 
 
+def linear_3d_problem():
+    """Concentric spheres r = 1, 0.7, 0.4, sigma = (1, 3, 0.5) with data linear in the
+    unit vector: Neumann flux Y_1^0 + 0.4 Y_1^{-1}, no jump on r = 0.7, and the jump
+    0.5 n . grad(x_1 + 0.6 x_3 + 2) on r = 0.4 (the constant term has no gradient).
+    Every sign part is a hemisphere, the case of the variance-reduced walk in 3D."""
+    return {
+        "name": "3d-linear", "dim": 3,
+        "surfaces": [_sphere([0, 0, 0], 1.0), _sphere([0, 0, 0], 0.7), _sphere([0, 0, 0], 0.4)],
+        "parent": [-1, 0, 1], "sigma": [1.0, 3.0, 0.5],
+        "flux": [real_sh({(1, 0): 1.0, (1, -1): 0.4}, 1), zero_flux(),
+                 harmonic_poly(0.5, [(1.0, (1, 0, 0)), (0.6, (0, 0, 1)), (2.0, (0, 0, 0))], 3)],
+        "M": 6,
+    }
+
+
 def ball_points(n, dim, seed, radius=1.0):
     """n points uniform in the ball of the given radius (r = R U^{1/d})."""
     rng = np.random.default_rng(seed)

@@ -97,7 +97,7 @@ def test_estimate_argument_checks_and_no_device(woi):
         woi.woi_estimate(g, pts, 1000, sched_group=32)           # 1000 is not a multiple of 32
     assert e.value.status == 1
     with pytest.raises(woi.WoiError) as e:
-        woi.woi_estimate(g, pts, 1024, variant="vr")              # VR needs 2D Fourier data
+        woi.woi_estimate(g, pts, 1024, variant="vr")              # VR needs linear data in 3D
     assert e.value.status == 4
     with pytest.raises(woi.WoiError) as e:
         woi.woi_estimate(g, pts, 1024, M=40)

@@ -57,6 +57,8 @@ def cases():
     yield "3d-nested", wl.nested_3d_problem(), wl.ball_points(4, 3, 12), "plain"
     yield "e3b", e3b_problem(), wl.ball_points(3, 3, 5), "plain"
     yield "6d-nested", wl.nested_6d_problem(), wl.ball_points(3, 6, 14), "plain"
+    yield "6d-nested-vr", wl.nested_6d_problem(), wl.ball_points(3, 6, 15), "vr"
+    yield "3d-linear-vr", wl.linear_3d_problem(), wl.ball_points(3, 3, 16, radius=0.95), "vr"
     star3 = wl.star_inclusions_problem(seed=3, n_incl=3)
     yield "star-3", star3, np.array([[0.1, 0.2], [-0.5, 0.3], [0.6, -0.4]]), "plain"
     yield "star-3-vr", star3, np.array([[0.1, 0.2], [0.0, -0.7]]), "vr"
@@ -163,7 +165,8 @@ def test_shared_schedules(W, O):
 @pytest.mark.parametrize("name,variant,sched_group", [("3d-nested", "plain", 1), ("3d-nested", "plain", 32),
                                                       ("2d-concentric-vr", "vr", 1), ("star-3", "plain", 1),
                                                       ("6d-nested", "plain", 1), ("ellipsoids-3d", "plain", 1),
-                                                      ("mesh-rocks", "plain", 1)])
+                                                      ("mesh-rocks", "plain", 1), ("3d-linear-vr", "vr", 1),
+                                                      ("6d-nested-vr", "vr", 32)])
 def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
     estimate is still the mean over the same walks the oracle draws for that
@@ -293,20 +296,25 @@ def test_batch_matches_oracle_and_fp64_path(W, O):
         g.close()
 
 
-@pytest.mark.parametrize("name,n_pts,n_walks,precision", [("2d-concentric", 64, 10_000, "fp64"),
-                                                          ("2d-concentric", 64, 10_000, "mixed"),
-                                                          ("3d-nested", 256, 100_000, "mixed"),
-                                                          ("6d-nested", 64, 100_000, "mixed")])
-def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, precision):
+@pytest.mark.parametrize("name,n_pts,n_walks,precision,variant", [("2d-concentric", 64, 10_000, "fp64", "plain"),
+                                                                  ("2d-concentric", 64, 10_000, "mixed", "plain"),
+                                                                  ("2d-concentric", 64, 10_000, "mixed", "vr"),
+                                                                  ("3d-nested", 256, 100_000, "mixed", "plain"),
+                                                                  ("3d-linear", 256, 100_000, "mixed", "vr"),
+                                                                  ("6d-nested", 64, 100_000, "mixed", "plain"),
+                                                                  ("6d-nested", 64, 100_000, "mixed", "vr")])
+def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, precision, variant):
     """The GPU estimates at the workloads' sizes against the exact mean of the truncated
     estimator on concentric spheres (the per-mode series of the oracle's closed forms):
     every point within 4.5 SE, and the RMS error over the points consistent with the RMS
-    standard error (between 0.7 and 1.3 times it)."""
+    standard error (between 0.7 and 1.3 times it).  Algorithm 3 has the same mean."""
     from oracle import closed_form as cf
     if name == "2d-concentric":
         prob, x = wl.concentric_2d_problem(), wl.concentric_2d_points()
     elif name == "3d-nested":
         prob, x = wl.nested_3d_problem(), wl.ball_points(4096, 3, 12)
+    elif name == "3d-linear":
+        prob, x = wl.linear_3d_problem(), wl.ball_points(4096, 3, 12, radius=0.95)
     else:
         prob, x = wl.nested_6d_problem(), wl.ball_points(1024, 6, 14)
     x = np.ascontiguousarray(x[:n_pts])
@@ -314,7 +322,7 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
     u_ex, g_ex = cf.concentric_truncated_mean(prob["dim"], radii, prob["sigma"], prob["parent"],
                                               cf.modes_from_problem(prob), prob["M"], x)
     g = W.Geometry(prob)
-    gr = W.woi_estimate(g, x, n_walks, seed=0, M=prob["M"], precision=precision)
+    gr = W.woi_estimate(g, x, n_walks, seed=0, M=prob["M"], precision=precision, variant=variant)
     g.close()
     z = (gr["u"] - u_ex) / gr["se_u"]
     assert np.all(np.abs(z) < 4.5), (name, np.abs(z).max())
@@ -325,7 +333,7 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
     assert 0.7 * rms_se < rms_err < 1.3 * rms_se, (name, rms_err, rms_se)
 
 
-@pytest.mark.parametrize("name", ["3d-nested", "ellipsoids-3d", "mesh-rocks", "star-3"])
+@pytest.mark.parametrize("name", ["3d-nested", "ellipsoids-3d", "mesh-rocks", "star-3", "3d-linear-vr", "6d-nested-vr"])
 def test_walk_trace_states_match_oracle(W, O, name):
     """woi_walk_trace (FP64): every state y_i, Q_i and T_i of every walk equals the
     oracle's (Eqs. naive_woi_Q, naive_woi_T) to 1e-12 of its magnitude scale."""

@@ -4,7 +4,8 @@ Each case compares the oracle's per-point estimate of u and grad u with the
 exact mean of the truncated estimator (Thms 4.1-4.2): the concentric-sphere
 series (2D, 3D, 6D workloads), the Nystrom series on a star with inclusions
 (plain and variance-reduced, Algorithm 3), the pure Neumann problem (N = 1,
-the Walk-on-Boundary special case of Sec. 2), an invisible interface
+the Walk-on-Boundary special case of Sec. 2), the variance-reduced walk on
+hemisphere parts in 3D and 6D, an invisible interface
 (sigma_i = sigma_p, b_i = 0) and shared schedules (Algorithm 1 with W
 walkers per schedule).  The test statistic is z = (estimate - exact) / SE with
 the SE from the schedule-group means; with fixed seeds the outcome is
@@ -80,6 +81,39 @@ def test_variance_reduced_concentric_2d(oracle_core):
     res = oracle_core.estimate(p1, x1, 60000, seed=4, M=4, variant="vr")
     u_ex, g_ex = concentric_exact(p1, 4, x1)
     assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS
+
+
+def test_variance_reduced_hemispheres_nd(oracle_core):
+    """Algorithm 3 in d >= 3 on data linear in the unit vector (hemisphere parts,
+    a zero-data interface with a dead second chain): the exact mean of the plain
+    estimator, with a smaller SE than the plain walk on the same seeds."""
+    p3 = wl.linear_3d_problem()
+    x3 = wl.ball_points(10, 3, 31, radius=0.95)
+    p6 = wl.nested_6d_problem()
+    x6 = wl.ball_points(6, 6, 32)
+    for prob, x, M in ((p3, x3, 6), (p6, x6, 8)):
+        res = oracle_core.estimate(prob, x, 60000, seed=5, M=M, variant="vr")
+        u_ex, g_ex = concentric_exact(prob, M, x)
+        assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS
+
+
+def test_vr_without_reflection_is_detected(oracle_core):
+    """A planted mistake: the part sampler keeps directions of the wrong sign (no
+    reflection), so each chain draws from the whole sphere.  Each chain then averages
+    beta |dOmega| / 2 over the whole sphere and their sum is still unbiased, so the
+    exact-mean test cannot see it; the sign of the start samples does."""
+    prob, x = wl.linear_3d_problem(), wl.ball_points(10, 3, 31, radius=0.95)
+    prep = oracle_core.Prepared(prob, "vr")
+    oracle_core.set_mutant(10)
+    try:
+        res = oracle_core.estimate(prob, x, 30000, seed=5, M=6, variant="vr", prepared=prep)
+        y = oracle_core.uniform_part_points(prob, 0, 0, 200, seed=1, prepared=prep)
+    finally:
+        oracle_core.set_mutant(0)
+    u_ex, g_ex = concentric_exact(prob, 6, x)
+    assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS          # the mean is blind to it
+    beta = np.array([oracle_core.flux_at(prob, 0, yy, prepared=prep) for yy in y])
+    assert np.sum(beta < 0) > 50                                     # the sampler check is not
 
 
 @pytest.mark.parametrize("variant", ["plain", "vr"])

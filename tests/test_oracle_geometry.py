@@ -196,3 +196,48 @@ def test_vr_arcs(oracle_core):
             y = oracle_core.uniform_part_points(prob, h, part, 300, seed=7 + h, prepared=prep)
             beta = np.array([prep.beta_scale[h] * oracle_core.flux_at(prob, h, yy, prepared=prep) for yy in y])
             assert np.all(beta >= -1e-9) if part == 0 else np.all(beta < 1e-9)
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_vr_hemispheres(oracle_core, d):
+    """Sec. 4.4 in d >= 3: data linear in the unit vector, beta = a . u, has the
+    hemispheres {a . u >= 0} and {a . u < 0} as parts, each of half the area.  The
+    samples of each part lie on the sphere, carry the part's sign and are uniform
+    there: E[a^ . u] = +/- Gamma(d/2) / (sqrt(pi) Gamma((d+1)/2)) (the mean of |u_1| on
+    S^{d-1}), the orthogonal components average to 0 and E[u_k^2] = 1/d."""
+    from math import gamma, pi, sqrt
+    c = np.linspace(-0.1, 0.2, d)
+    R = 0.8
+    a = np.zeros(d)
+    if d == 3:
+        flux = wl.real_sh({(1, 1): 0.6, (1, 0): -0.8}, 1)            # Y_1^1 ~ x, Y_1^0 ~ z
+        a[0], a[2] = 0.6, -0.8
+    else:
+        flux = wl.harmonic_poly(2.0, [(0.6, tuple(int(k == 1) for k in range(d))),
+                                      (0.8, tuple(int(k == 3) for k in range(d))),
+                                      (5.0, (0,) * d)], d)
+        a[1], a[3] = 0.6, 0.8
+    prob = {"dim": d, "surfaces": [wl._sphere(c, R)], "parent": [-1], "sigma": [1.0], "flux": [flux], "M": 1}
+    prep = oracle_core.Prepared(prob, "vr")
+    area = oracle_core.omega(d) * R ** (d - 1)
+    assert prep.part_len[0] == pytest.approx([area / 2, area / 2], rel=1e-14)
+    m1 = gamma(d / 2) / (sqrt(pi) * gamma((d + 1) / 2))
+    n = 20000
+    Q = np.linalg.qr(np.column_stack([a] + [np.eye(d)[k] for k in range(d)]))[0][:, 1:d]   # a^-perp basis
+    for part, sgn in ((0, 1.0), (1, -1.0)):
+        y = oracle_core.uniform_part_points(prob, 0, part, n, seed=3 + part, prepared=prep)
+        u = (y - c) / R
+        assert np.allclose(np.linalg.norm(u, axis=1), 1.0, atol=1e-13)
+        beta = np.array([oracle_core.flux_at(prob, 0, yy, prepared=prep) for yy in y[:500]])
+        assert np.all(sgn * beta >= 0)
+        t = u @ a
+        assert abs(t.mean() - sgn * m1) < 5 * t.std() / sqrt(n)
+        p = u @ Q
+        assert np.all(np.abs(p.mean(axis=0)) < 5 * p.std(axis=0) / sqrt(n))
+        assert np.all(np.abs((u ** 2).mean(axis=0) - 1 / d) < 5 * (u ** 2).std(axis=0) / sqrt(n))
+
+
+def test_vr_parts_need_linear_data(oracle_core):
+    """Degree-2 data on a 3D sphere has no hemisphere parts: the VR variant refuses it."""
+    with pytest.raises(ValueError):
+        oracle_core.Prepared(wl.nested_3d_problem(), "vr")
