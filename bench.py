@@ -157,7 +157,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0, sched_group=1):
+def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0, sched_group=1, single_core=False):
     """The CPU oracle as it stands on a bounded sample of the workload: all host
     threads, a subset of points and walks sized to ~target_s seconds; returns
     estimates/s at W_full walks per point (time is linear in walks)."""
@@ -175,10 +175,26 @@ def cpu_oracle_sample(problem, points, M, W_full, target_s=12.0, sched_group=1):
     core.estimate(problem, points[:n_pts], w, seed=0, M=M, prepared=prep, sched_group=sched_group)
     t = time.perf_counter() - t0
     est_per_s = n_pts / (t * W_full / w)
-    return {"value": est_per_s, "cores": core.threads_used(), "kind": "oracle",
-            "sample": f"{n_pts} points x {w} walks (of {len(points)} x {W_full}), {t:.1f} s, "
-                      f"extrapolated linearly in walks", "seconds": t,
-            "walk_steps_per_s": n_pts * w * (M + 1) / t}
+    cores = core.threads_used()
+    out = {"value": est_per_s, "cores": cores, "kind": "oracle",
+           "sample": f"{n_pts} points x {w} walks (of {len(points)} x {W_full}), {t:.1f} s, "
+                     f"extrapolated linearly in walks", "seconds": t,
+           "walk_steps_per_s": n_pts * w * (M + 1) / t}
+    if single_core and cores > 1:
+        # the same oracle on one host thread, on a sample sized to ~target_s / 4
+        budget = w * n_pts / cores / 4
+        w1 = int(min(W_full, max(256, budget))) // 32 * 32
+        n1 = int(min(len(points), max(1, round(budget / w1))))
+        core.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            core.estimate(problem, points[:n1], w1, seed=0, M=M, prepared=prep, sched_group=sched_group)
+            t1 = time.perf_counter() - t0
+        finally:
+            core.set_threads(cores)
+        out["single_core"] = {"value": n1 / (t1 * W_full / w1), "cores": 1,
+                              "sample": f"{n1} points x {w1} walks, {t1:.1f} s"}
+    return out
 
 
 def run_reference(args, workload):
@@ -405,8 +421,8 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(problem, points, M, Wk, sched_group=args.sched_group)
-        cpu = {k: cpu[k] for k in ("value", "cores", "kind", "sample")} | {"unit": "estimates/s"}
+        cpu = cpu_oracle_sample(problem, points, M, Wk, sched_group=args.sched_group, single_core=True)
+        cpu = {k: cpu[k] for k in ("value", "cores", "kind", "sample", "single_core") if k in cpu} | {"unit": "estimates/s"}
 
     if rank == 0:
         clocks = clk.summary()

@@ -78,6 +78,8 @@ def lib():
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p]
         _lib.or_set_mutant.argtypes = [ctypes.c_int]
+        _lib.or_threads.argtypes = [ctypes.c_int]
+        _lib.or_threads.restype = ctypes.c_int
         _lib.or_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_test_real_sh.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
         _lib.or_test_real_sh.restype = ctypes.c_double
@@ -609,7 +611,13 @@ def directions(d, n, seed=0):
 
 
 def threads_used():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    """Host threads the estimator over points runs on."""
+    return int(lib().or_threads(0))
+
+
+def set_threads(n):
+    """Run the estimator over points on n host threads (n > 0); returns the count in use."""
+    return int(lib().or_threads(int(n)))
 
 
 if __name__ == "__main__":

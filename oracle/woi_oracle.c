@@ -80,6 +80,18 @@ enum { OR_REL_SAME = 0, OR_REL_DESC = 1, OR_REL_OTHER = 2 };
 static int or_mutant = 0;
 void or_set_mutant(int m) { or_mutant = m; }
 
+/* host threads of the estimator over points: n > 0 sets them; returns the count in use */
+#ifdef _OPENMP
+#include <omp.h>
+int or_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
+#else
+int or_threads(int n) { (void)n; return 1; }
+#endif
+
 /* Problem description.  All arrays are owned by the caller (oracle.py). */
 typedef struct {
     int dim;
