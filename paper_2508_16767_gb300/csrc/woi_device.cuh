@@ -533,16 +533,23 @@ __device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa
 // Roots of f in the scan interval [t_j, t_j+1] (j in [0, kNodes)) appended as candidates:
 // a sign change gives one root; otherwise, where |f| may reach 0 (|f'| <= lmax) and f'
 // changes sign, the extremum decides whether a pair of roots hides in the interval.
+// f = (gamma - y) x z has |f''| <= |gamma''| <= K, so on a scan interval [0, H] f stays
+// above the chord minus K H^2 / 8: with f(0), f(H) of one sign and both beyond that (plus
+// the rounding of f), the interval holds no root; only the others need the search for an
+// extremum
+template <typename Real>
+__device__ __forceinline__ Real star_guard(const SGeom<Real> &g)
+{
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
+    return g.star_kpp * H * H * (Real)0.125 + (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_rmax;
+}
+
 template <typename Real>
 __device__ __forceinline__ int star_interval_roots(const SGeom<Real> &g, int j, Real fa, Real fb, const Real *yc,
                                                    const Real *z, Real *cand)
 {
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
-    // f = (gamma - y) x z has |f''| <= |gamma''| <= K, so on [0, H] f stays above the chord
-    // minus K H^2 / 8: with f(0), f(H) of one sign and both beyond that (plus the rounding of
-    // f), the interval holds no root; only the others need the search for an extremum
-    const Real guard = g.star_kpp * H * H * (Real)0.125 +
-                       (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_rmax;
+    const Real guard = star_guard(g);
     int nc = 0;
     if ((fa < 0) != (fb < 0)) {
         cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z, H * fa / (fa - fb));   // secant start
@@ -638,40 +645,63 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
     }
     int q = 0, self = -1;
     Real self_dist = (Real)1e30;
-    for (int w = 0; w < kNodes / 32; ++w) {
-        uint32_t bits = mask[w];
-        while (bits) {
+    // the roots of one candidate interval, appended in scan order
+    auto roots_of = [&](int j, Real fa, Real fb) {
+        Real cand[2];
+        const int nc = star_interval_roots(g, j, fa, fb, yc, z, cand);
+        for (int c = 0; c < nc; ++c) {
+            Real ct, st, p[2];
+            angle_cs(g, j, cand[c], &ct, &st);
+            star_local(g, ct, st, p, (Real *)nullptr);
+            const Real s = (p[0] - yc[0]) * z[0] + (p[1] - yc[1]) * z[1];
+            const bool ok = ray ? (s > tiny) : true;
+            if (ok && q < kMaxRoots) {
+                tt[q] = s;
+                jj[q] = j;
+                dd[q] = cand[c];
+                if (!ray) {
+                    int dj = j - sj;  // cyclic angular distance to the start point
+                    if (dj > kNodes / 2) dj -= kNodes;
+                    if (dj < -kNodes / 2) dj += kNodes;
+                    const Real dist = RealOps<Real>::fabs_((Real)dj * H + (cand[c] - sd));
+                    if (dist < self_dist) {
+                        self_dist = dist;
+                        self = q;
+                    }
+                }
+                ++q;
+            }
+        }
+    };
+    // two phases, so that the lanes of a warp refine their roots together: the scan (cheap,
+    // of a different length in every lane) keeps up to kCand intervals that can hold a root
+    // (a sign change, or an end within the guard); the refinement then runs candidate by
+    // candidate in lock-step.  More candidates than that take further rounds, in scan order.
+    constexpr int kCand = 8;
+    int cj[kCand];
+    Real cfa[kCand], cfb[kCand];
+    const Real guard = star_guard(g);
+    int w = 0;
+    uint32_t bits = mask[0];
+    for (int round = 0; round <= kNodes / kCand; ++round) {
+        int n_cand = 0;
+        for (;;) {
+            while (bits == 0u && w + 1 < kNodes / 32) bits = mask[++w];
+            if (bits == 0u || n_cand == kCand) break;
             const int j = w * 32 + __ffs(bits) - 1;
             bits &= bits - 1;
             const int jn = (j + 1 == kNodes) ? 0 : j + 1;
             const Real fa = g.scan[j][0] * z[1] - g.scan[j][1] * z[0] - e;
             const Real fb = g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
-            Real cand[2];
-            const int nc = star_interval_roots(g, j, fa, fb, yc, z, cand);
-            for (int c = 0; c < nc; ++c) {
-                Real ct, st, p[2];
-                angle_cs(g, j, cand[c], &ct, &st);
-                star_local(g, ct, st, p, (Real *)nullptr);
-                const Real s = (p[0] - yc[0]) * z[0] + (p[1] - yc[1]) * z[1];
-                const bool ok = ray ? (s > tiny) : true;
-                if (ok && q < kMaxRoots) {
-                    tt[q] = s;
-                    jj[q] = j;
-                    dd[q] = cand[c];
-                    if (!ray) {
-                        int dj = j - sj;  // cyclic angular distance to the start point
-                        if (dj > kNodes / 2) dj -= kNodes;
-                        if (dj < -kNodes / 2) dj += kNodes;
-                        const Real dist = RealOps<Real>::fabs_((Real)dj * H + (cand[c] - sd));
-                        if (dist < self_dist) {
-                            self_dist = dist;
-                            self = q;
-                        }
-                    }
-                    ++q;
-                }
+            if ((fa < 0) != (fb < 0) || RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
+                cj[n_cand] = j;
+                cfa[n_cand] = fa;
+                cfb[n_cand] = fb;
+                ++n_cand;
             }
         }
+        for (int c = 0; c < n_cand; ++c) roots_of(cj[c], cfa[c], cfb[c]);
+        if (bits == 0u) break;   // the mask is exhausted
     }
     if (!ray && self >= 0) {  // drop the start point
         for (int a = self; a + 1 < q; ++a) {

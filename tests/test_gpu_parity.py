@@ -296,6 +296,24 @@ def test_batch_matches_oracle_and_fp64_path(W, O):
         g.close()
 
 
+def test_batch_variance_reduced_matches_oracle(W, O):
+    """woi_estimate_batch with Algorithm 3 over instances of three dimensions (2D arcs,
+    3D and 6D hemispheres): one persistent launch per dimension against the oracle
+    with each instance's random-stream id."""
+    insts = [(wl.concentric_2d_problem(), wl.concentric_2d_points()[::7], 2048 + 640),
+             (wl.linear_3d_problem(), wl.ball_points(9, 3, 71, radius=0.95), 4096),
+             (wl.nested_6d_problem(), wl.ball_points(5, 6, 72), 2048 + 160),
+             (wl.linear_3d_problem(), wl.ball_points(4, 3, 73, radius=0.95), 1024)]
+    geoms = [W.Geometry(p) for p, _, _ in insts]
+    res = W.woi_estimate_batch([(g, x, n) for g, (p, x, n) in zip(geoms, insts)], seed=9, variant="vr")
+    for k, (prob, x, n) in enumerate(insts):
+        orr = O.estimate(prob, x, n, seed=9, M=prob["M"], instance=k, variant="vr")
+        u = res[k]["u"].cpu().numpy() if hasattr(res[k]["u"], "cpu") else res[k]["u"]
+        assert np.all(np.abs(u - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12), k
+    for g in geoms:
+        g.close()
+
+
 @pytest.mark.parametrize("name,n_pts,n_walks,precision,variant", [("2d-concentric", 64, 10_000, "fp64", "plain"),
                                                                   ("2d-concentric", 64, 10_000, "mixed", "plain"),
                                                                   ("2d-concentric", 64, 10_000, "mixed", "vr"),
