@@ -327,13 +327,17 @@ def linear_on_sphere(dim, s, flux):
 
 def vr_parts(dim, s, flux):
     """|dOmega^+|, |dOmega^-| in d >= 3 (Sec. 4.4): zero data puts the whole sphere in the
-    beta >= 0 part; data linear in u splits it into two hemispheres; None otherwise."""
+    beta >= 0 part; data linear in u splits it into two hemispheres; other data on a sphere
+    has parts of no closed form, marked (-1, -1): the start is then drawn from uniform
+    trials (reading R22).  None for other surfaces."""
+    if s["kind"] != "sphere":
+        return None
     A = surface_area(dim, s)
-    if flux["basis"] == "zero" and s["kind"] == "sphere":
+    if flux["basis"] == "zero":
         return (A, 0.0)
     if linear_on_sphere(dim, s, flux):
         return (0.5 * A, 0.5 * A)
-    return None
+    return (-1.0, -1.0)
 
 
 def vr_arcs(dim, s, flux, bscale, n_scan=20000):
@@ -444,8 +448,7 @@ class Prepared:
             if variant == "vr" and d >= 3:
                 parts = vr_parts(d, surfs[i], fl[i])
                 if parts is None:
-                    raise ValueError("variance reduction in d >= 3 needs spheres with data linear in the "
-                                     "unit vector (or zero) on every surface")
+                    raise ValueError("variance reduction in d >= 3 needs spheres on every surface")
                 self.part_len[i] = parts
                 arc_off.append(len(t0))
                 arc_n.append(0)

@@ -24,7 +24,8 @@
  *   - Algorithms 1-2 (plain walk), Algorithm 3 and Eq.
  *     variance_reduced_woi_estimator (two chains from the beta >= 0 and
  *     beta < 0 parts of the first interface; in 2D the parts are arcs, in
- *     d >= 3 they are the hemispheres of data linear in the unit vector).
+ *     d >= 3 they are the hemispheres of data linear in the unit vector, and
+ *     on other d >= 3 spheres the start is drawn from uniform trials).
  *   - Sec. 4.5, Eq. naive_woi_grad_estimator: the gradient tally uses
  *     grad_x Phi on the same trajectory.
  *   - Sec. 5, Example 2: ellipsoids (y - c)^T A (y - c) = 1 as surfaces, with
@@ -63,6 +64,7 @@
 #define OR_STAR_PANELS 256
 
 #define OR_ELL_ATTEMPTS 64   /* rejection attempts for a uniform point on an ellipsoid; the last one is kept */
+#define OR_VR_TRIALS 16      /* uniform trials of the VR start where |dOmega^+/-| has no closed form */
 
 enum { OR_SPHERE = 0, OR_STAR = 1, OR_ELLIPSOID = 2, OR_MESH = 3 };
 enum { OR_FLUX_ZERO = 0, OR_FLUX_FOURIER = 1, OR_FLUX_REAL_SH = 2, OR_FLUX_HARMONIC_POLY = 3,
@@ -76,7 +78,8 @@ enum { OR_REL_SAME = 0, OR_REL_DESC = 1, OR_REL_OTHER = 2 };
  *   4 no factor N                               5 K* with the normal at the old point
  *   6 beta_i scaled by +2/(sigma_p + sigma_i)   7 line case keeps Q (no 1/2)
  *   8 gradient of Phi with the wrong sign       9 H_0 drawn like H_i (by |alpha|)
- *  10 d >= 3 part sampler without the reflection u -> -u */
+ *  10 d >= 3 part sampler without the reflection u -> -u
+ *  11 VR start by trials weighs beta by |dOmega| / 2 instead of |dOmega| C_k / K */
 static int or_mutant = 0;
 void or_set_mutant(int m) { or_mutant = m; }
 
@@ -786,7 +789,8 @@ typedef struct {
     int *H;          /* [M+1] scheduled interfaces (0-based), or NULL */
     double *Y;       /* [2][M+1][dim] states of each chain, or NULL */
     double *scale;   /* [4]: sum_i |c_i Phi_i|, sum_i |c_i|, sum_i |c_i| |grad Phi_i| (both chains), and
-                        max over chains of (term magnitude of beta(y_0)) / |beta(y_0)| (>= 1) */
+                        the walk's conditioning (>= 1): the larger of (term magnitude of beta(y_0)) /
+                        |beta(y_0)| and, over its chords on curved surfaces, (|y - c| + |y' - c|) / |t| */
     double *QT;      /* [2][M+1][2]: Q_i and T_i of each chain, or NULL */
 } or_trace;
 
@@ -819,6 +823,8 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     double cond0 = 1.0;
     int alive[2] = {1, 1};
     int tri[2] = {-1, -1};   /* mesh triangle of each chain's state (-1 elsewhere) */
+    int trial_n[2] = {0, 0}, trial_tri[2] = {-1, -1};   /* VR start by trials (reading R22) */
+    double trial_y[2][OR_MAX_DIM] = {{0}};
     double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m})  (reading R1) */
     double Ai = 1.0;         /* ||alpha||_1^i */
     int h_prev = -1;
@@ -850,6 +856,36 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     Q[k] = or_beta(P, h, tri[k], y[k]) * P->area[h];
                     double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
                     if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
+                } else if (P->part_len[2 * h] < 0.0) {
+                    /* parts of no closed form (reading R22): K uniform trials on dOmega_h, shared by
+                     * both chains (trial t draws the step-0 words of chain id t << 12).  Chain k starts
+                     * at the first trial of its sign and weighs beta by |dOmega| C_k / K, C_k the
+                     * trials of that sign: C_k / K is an unbiased estimate of |dOmega^+/-| / |dOmega|,
+                     * independent of where the first trial of that sign lies */
+                    if (k == 0) {
+                        trial_n[0] = trial_n[1] = 0;
+                        for (int t = 0; t < OR_VR_TRIALS; ++t) {
+                            double yt[OR_MAX_DIM];
+                            int tt;
+                            or_uniform_point(P, h, &rng, 0, t << 12, yt, &tt);
+                            const int part = or_beta(P, h, tt, yt) >= 0.0 ? 0 : 1;
+                            if (trial_n[part]++ == 0) {
+                                for (int c = 0; c < d; ++c) trial_y[part][c] = yt[c];
+                                trial_tri[part] = tt;
+                            }
+                        }
+                    }
+                    if (trial_n[k] == 0 || P->flux_basis[h] == OR_FLUX_ZERO) {
+                        alive[k] = 0; Q[k] = 0.0;
+                        for (int c = 0; c < d; ++c) y[k][c] = 0.0;
+                    } else {
+                        for (int c = 0; c < d; ++c) y[k][c] = trial_y[k][c];
+                        tri[k] = trial_tri[k];
+                        const double frac = or_mutant == 11 ? 0.5 : (double)trial_n[k] / OR_VR_TRIALS;
+                        Q[k] = or_beta(P, h, tri[k], y[k]) * P->area[h] * frac;
+                        double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
+                        if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
+                    }
                 } else {
                     double L = P->part_len[2 * h + k];
                     if (L <= 0.0 || P->flux_basis[h] == OR_FLUX_ZERO) {
@@ -904,6 +940,19 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     double sg = dot > 0.0 ? 1.0 : (dot < 0.0 ? -1.0 : 0.0);
                     if (rel == OR_REL_SAME && or_mutant != 7) Q[k] *= 0.5;
                     T[k] *= (double)q * sg;
+                    if (rel == OR_REL_SAME && P->type[h] != OR_MESH) {
+                        /* a chord nearly tangent to a curved surface moves its far end by
+                         * (|y - c| + |y' - c|) / |t| times any rounding of the start's distance
+                         * from the surface: a conditioning factor of the walk (replay tolerance) */
+                        const double *ch = or_center(P, h);
+                        double ra = 0.0, rb = 0.0;
+                        for (int c = 0; c < d; ++c) {
+                            ra += (y[k][c] - ch[c]) * (y[k][c] - ch[c]);
+                            rb += (ynew[c] - ch[c]) * (ynew[c] - ch[c]);
+                        }
+                        const double amp = (sqrt(ra) + sqrt(rb)) / fabs(ts[j]);
+                        if (amp > cond0) cond0 = amp;
+                    }
                 }
                 for (int c = 0; c < d; ++c) y[k][c] = ynew[c];
                 tri[k] = tnew;

@@ -147,6 +147,7 @@ struct woi_geometry {
     std::vector<int> flux_basis, flux_off, flux_n;
     bool vr_ok = false;
     std::vector<double> arc_t0, arc_t1, arc_len, arc_s0, part_len;
+    std::vector<double> vr_tol;                                  // per surface, d >= 3 VR (FP64 sign check)
     std::vector<int> arc_sign, arc_off, arc_n;
 
     // device side
@@ -879,35 +880,6 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             an[i]++;
         }
     }
-    // Sec. 4.4 in d >= 3: on a sphere, data linear in the unit vector u (degree-1 real
-    // harmonics, harmonic polynomials of degree <= 1) is negative exactly on the mirror
-    // image of the half where it is positive, so each part is a hemisphere of half the
-    // area; zero data puts the whole sphere in dOmega^+.  Other surfaces or data have
-    // parts of no closed form here, and the variant stays unavailable for them.
-    if (d >= 3) {
-        vr_ok = true;
-        for (int i = 0; i < n && vr_ok; ++i) {
-            if (g->surf[i].type != WOI_SPHERE) { vr_ok = false; break; }
-            if (basis[i] == WOI_FLUX_ZERO) { plen[2 * i] = g->area[i]; continue; }
-            const double *c = coef.data() + off[i];
-            bool linear = false;
-            if (basis[i] == WOI_FLUX_REAL_SH && d == 3) {
-                linear = true;
-                for (int idx = 0; idx < nc[i]; ++idx)
-                    if ((idx < 1 || idx > 3) && c[idx] != 0.0) linear = false;
-            } else if (basis[i] == WOI_FLUX_HARMONIC_POLY) {
-                linear = true;
-                const int T = (int)c[1];
-                for (int t = 0; t < T; ++t) {
-                    double deg = 0.0;
-                    for (int k = 0; k < d; ++k) deg += c[2 + t * (d + 1) + 1 + k];
-                    if (deg > 1.0) linear = false;
-                }
-            }
-            if (!linear) { vr_ok = false; break; }
-            plen[2 * i] = plen[2 * i + 1] = 0.5 * g->area[i];
-        }
-    }
     g->sigma.assign(sigma, sigma + n);
     g->alpha = alpha;
     g->beta_scale = bsc;
@@ -1013,6 +985,53 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
         g->flux_dev = dev;
     }
     g->flux_dev_f.assign(g->flux_dev.begin(), g->flux_dev.end());
+    // Sec. 4.4 in d >= 3, spheres only.  Data linear in the unit vector u (degree-1 real
+    // harmonics, harmonic polynomials of degree <= 1) is negative exactly on the mirror image
+    // of the half where it is positive: the parts are hemispheres of half the area.  Zero
+    // data puts the whole sphere in dOmega^+.  Other data in the quadratic device formats has
+    // parts of no closed form, marked -1: the start is drawn from uniform trials (the areas
+    // are estimated by the trials themselves).  vr_tol[i] bounds where an FP32 evaluation of
+    // beta may have the wrong sign: 1e-4 of a bound on the magnitude of its terms (the FP32
+    // error is about 1e-6 of it); below it the kernels decide the sign in FP64.
+    std::vector<double> vtol(n, 0.0);
+    if (d >= 3) {
+        vr_ok = true;
+        for (int i = 0; i < n && vr_ok; ++i) {
+            if (g->surf[i].type != WOI_SPHERE) { vr_ok = false; break; }
+            if (basis[i] == WOI_FLUX_ZERO) { plen[2 * i] = g->area[i]; continue; }
+            const int fb = g->flux_basis_dev[i];
+            if (fb != kFluxSphQuad && fb != kFluxHarmonicQuad) { vr_ok = false; break; }
+            const double *c = coef.data() + off[i];
+            bool linear = false;
+            if (basis[i] == WOI_FLUX_REAL_SH) {
+                linear = true;
+                for (int idx = 0; idx < nc[i]; ++idx)
+                    if ((idx < 1 || idx > 3) && c[idx] != 0.0) linear = false;
+            } else {
+                linear = true;
+                const int T = (int)c[1];
+                for (int t = 0; t < T; ++t) {
+                    double deg = 0.0;
+                    for (int k = 0; k < d; ++k) deg += c[2 + t * (d + 1) + 1 + k];
+                    if (deg > 1.0) linear = false;
+                }
+            }
+            plen[2 * i] = plen[2 * i + 1] = linear ? 0.5 * g->area[i] : -1.0;
+            // |terms| <= sum |q| rho^deg with rho = max |y_k| on the sphere (rho = 1 for u)
+            const double *q = g->flux_dev.data() + g->flux_off_dev[i];
+            double bound = 0.0;
+            if (fb == kFluxSphQuad) {
+                for (int k = 0; k < 10; ++k) bound += std::fabs(q[k]);
+            } else {
+                double rho = 1.0;
+                for (int k = 0; k < d; ++k) rho = std::max(rho, std::fabs(g->surf[i].center[k]) + g->surf[i].radius);
+                for (int k = 1; k < g->flux_n_dev[i]; ++k) bound += std::fabs(q[k]);
+                bound *= std::fabs(q[0]) * rho * rho;
+            }
+            vtol[i] = 1e-4 * std::fabs(bsc[i]) * bound;
+        }
+    }
+    g->vr_tol = vtol;
     g->vr_ok = vr_ok;
     g->arc_t0 = at0; g->arc_t1 = at1; g->arc_len = alen; g->arc_s0 = as0; g->arc_sign = asg;
     g->arc_off = aoff; g->arc_n = an; g->part_len = plen;
@@ -1157,6 +1176,7 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
         b.flux_n[i] = g.flux_n_dev[i];
         b.part_len[i][0] = g.part_len.empty() ? 0.0 : g.part_len[2 * i];
         b.part_len[i][1] = g.part_len.empty() ? 0.0 : g.part_len[2 * i + 1];
+        b.vr_tol[i] = g.vr_tol.empty() ? 0.0 : g.vr_tol[i];
         b.arc_off[i] = g.arc_off.empty() ? 0 : g.arc_off[i];
         b.arc_n[i] = g.arc_n.empty() ? 0 : g.arc_n[i];
         b.ell_slot[i] = g.ell_slot[i];
@@ -1313,7 +1333,8 @@ woi_status check_opts(const woi_geometry *g, const woi_opts *o, int64_t n_pts, i
         return fail(WOI_E_INVALID_ARG, "walk range must be a multiple of sched_group");
     if (o->variant == WOI_VR && !g->vr_ok)
         return fail(WOI_E_UNSUPPORTED, "variance reduction needs 2D Fourier (or zero) flux on every surface, or in "
-                                        "d >= 3 spheres with data linear in the unit vector (or zero)");
+                                        "d >= 3 spheres with real-harmonic data of degree <= 2 or harmonic-polynomial "
+                                        "data of degree <= 3 (or zero)");
     if (o->block_size != 0 && (o->block_size % 32 || o->block_size < 32 || o->block_size > kMixedMaxBlock))
         return fail(WOI_E_INVALID_ARG, "block_size must be a multiple of 32 in [32, %d]", kMixedMaxBlock);
     if (o->walks_per_lane < 0 || o->walks_per_lane > 4096) return fail(WOI_E_INVALID_ARG, "walks_per_lane out of range");

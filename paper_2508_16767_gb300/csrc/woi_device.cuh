@@ -1140,6 +1140,79 @@ __device__ void mesh_step(const DevGeom *gd, Real area, int h, int rel, const St
     ch.s = h;
 }
 
+// the part (0: beta >= 0, 1: beta < 0) of a uniform start point on a d >= 3 sphere, from
+// its direction's words w and beta b evaluated in Real.  In FP32, where |b| is within the
+// surface's tolerance of 0 (the FP32 error is far below it), the sign is taken again in
+// FP64 from the same words, so that the part is the one an FP64 evaluation gives.
+template <typename Real, int D>
+__device__ __forceinline__ int vr_part(const DevGeom *gd, int h, const StepWords &w, Real b)
+{
+    if constexpr (sizeof(Real) == 4) {
+        if (fabsf(b) < (float)gd->vr_tol[h]) {
+            double u[D], y[D];
+            direction<double, D>(w, u);
+#pragma unroll
+            for (int c = 0; c < D; ++c) y[c] = gd->center[h][c] + gd->radius[h] * u[c];
+            return gd->beta_scale[h] * flux_value<double, D>(gd, h, y, u, u) >= 0.0 ? 0 : 1;
+        }
+    }
+    return b >= (Real)0 ? 0 : 1;
+}
+
+// VR start on a d >= 3 sphere whose parts have no closed form: kVrTrials uniform trials on
+// dOmega_h shared by both chains (trial t draws the step-0 words of chain id t << 12; trial 0
+// is chain 0's own).  Chain k starts at the first trial of its sign with
+// Q = beta |dOmega| C_k / kVrTrials, C_k the trials of that sign: an unbiased estimate of
+// |dOmega^+/-| / |dOmega| that is independent of where the first trial of that sign lies,
+// so the chain's term has Algorithm 3's mean.  No trial of a sign: that chain is dead.
+template <typename Real, int D>
+__device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, const StepWords &w0, const Rng &rng,
+                                Chain<Real, D> *ch)
+{
+    int n[2] = {0, 0};
+    Real uf[2][D];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < D; ++c) uf[k][c] = 0;
+    for (int t = 0; t < kVrTrials; ++t) {
+        StepWords w = w0;
+        if (t > 0) {
+            w.a = rng.words(0, t << 12, 0);
+            if constexpr (two_calls<D>()) w.b = rng.words(0, t << 12, 1);
+        }
+        Real u[D], y[D];
+        direction<Real, D>(w, u);
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + g.radius[h] * u[c];
+        const Real b = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, u, u);
+        const int part = vr_part<Real, D>(gd, h, w, b);
+        if (n[part] == 0) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) uf[part][c] = u[c];
+        }
+        ++n[part];
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        Chain<Real, D> &q = ch[k];
+        q.T = 1;
+        q.s = h;
+        q.aj = 0;
+        q.ad = 0;
+        q.alive = n[k] > 0 && gd->flux_basis[h] != kFluxZero;
+        Real y[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            q.v[c] = q.alive ? g.radius[h] * uf[k][c] : (Real)0;
+            y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + q.v[c];
+        }
+        q.Q = q.alive ? g.beta_scale[h] * flux_value<Real, D>(gd, h, y, uf[k], uf[k]) *
+                            (Real)(gd->area[h] * ((double)n[k] / kVrTrials))
+                      : (Real)0;
+    }
+}
+
 // start (i = 0): y_0 uniform on dOmega_h (plain) or on dOmega_h^{+/-} (VR), Q = beta(y_0) |part|
 template <typename Real, int D, bool VR, bool STAR>
 __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int k, const StepWords &w,
@@ -1245,7 +1318,7 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
                 y0[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + ch.v[c];
             }
             const Real b = g.beta_scale[h] * flux_value<Real, D>(gd, h, y0, u, nrm);
-            if ((k == 0) != (b >= (Real)0)) {
+            if (k != vr_part<Real, D>(gd, h, w, b)) {
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
                     u[c] = -u[c];
@@ -1476,15 +1549,22 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
         const int h = schedule(g, i, hw);
         if (i > 0) S *= g.alpha_sign[h];
         const int rel = (i > 0) ? relation(g, hp, h) : 0;
+        bool trials = false;
+        if constexpr (VR && !STAR && D >= 3) {
+            if (i == 0 && gd->part_len[h][0] < 0.0) {
+                vr_trials_start<Real, D>(g, gd, h, w0, rng, ch);
+                trials = true;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < (VR ? 2 : 1); ++k) {
             StepWords w = w0;
-            if (k == 1) {
+            if (k == 1 && !trials) {
                 w.a = rng.words(i, 1, 0);
                 if constexpr (two_calls<D>()) w.b = rng.words(i, 1, 1);
             }
             if (i == 0) {
-                chain_start<Real, D, VR, STAR>(g, gd, h, k, w, rng, ch[k]);
+                if (!trials) chain_start<Real, D, VR, STAR>(g, gd, h, k, w, rng, ch[k]);
             } else if (ch[k].alive) {
                 chain_step<Real, D, STAR>(g, gd, h, rel, w, rng, i, k, ch[k]);
             }

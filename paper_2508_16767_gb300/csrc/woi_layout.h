@@ -22,6 +22,7 @@ constexpr int kMeshStack = 64;         // BVH traversal stack (the host caps the
 constexpr int kMaxHits = 32;           // intersections of one line with one mesh
 constexpr int kTriBuckets = 1024;      // per mesh: the triangle range of each top-10-bit word bucket
 constexpr int kEllAttempts = 64;       // rejection attempts for a uniform point on an ellipsoid
+constexpr int kVrTrials = 16;          // uniform trials of the VR start where |dOmega^+/-| has no closed form
 
 enum { kSphere = 0, kStar = 1, kEllipsoid = 2, kMesh = 3 };
 
@@ -62,7 +63,8 @@ struct DevGeom {
     const double *flux_coef;           // device array, device format (real-SH entries carry their
                                        // normalisation); FP32 copy in flux_coef_f
     const float *flux_coef_f;
-    double part_len[kMaxSurf][2];      // |dOmega^+|, |dOmega^-| (2D variance reduction)
+    double part_len[kMaxSurf][2];      // |dOmega^+|, |dOmega^-| (variance reduction); -1: by trials
+    double vr_tol[kMaxSurf];           // d >= 3 VR: |beta| below which its sign is taken in FP64
     int arc_off[kMaxSurf], arc_n[kMaxSurf];
     const double *arc_t0;              // device arrays of the beta-sign arcs
     const double *arc_t1;

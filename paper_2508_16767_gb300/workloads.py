@@ -144,6 +144,20 @@ def linear_3d_problem():
     }
 
 
+def zonal_3d_problem():
+    """Concentric spheres r = 1, 0.5, sigma = (1, 4) with degree-2 data Y_2^0 on the outer
+    sphere and the jump -0.5 Y_2^0 + 0.3 Y_2^2 on the inner one.  The sign parts are not
+    halves (Y_2^0 >= 0 on 1 - 1/sqrt(3) of the sphere) and have no closed form in general:
+    the case of the variance-reduced start by uniform trials."""
+    return {
+        "name": "3d-zonal", "dim": 3,
+        "surfaces": [_sphere([0, 0, 0], 1.0), _sphere([0, 0, 0], 0.5)],
+        "parent": [-1, 0], "sigma": [1.0, 4.0],
+        "flux": [real_sh({(2, 0): 1.0}, 2), real_sh({(2, 0): -0.5, (2, 2): 0.3}, 2)],
+        "M": 6,
+    }
+
+
 def ball_points(n, dim, seed, radius=1.0):
     """n points uniform in the ball of the given radius (r = R U^{1/d})."""
     rng = np.random.default_rng(seed)

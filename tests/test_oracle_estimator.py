@@ -97,6 +97,52 @@ def test_variance_reduced_hemispheres_nd(oracle_core):
         assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS
 
 
+def test_variance_reduced_by_trials(oracle_core):
+    """Algorithm 3 where |dOmega^+/-| has no closed form (degree-2 data on 3D spheres,
+    reading R22): the start by 16 shared uniform trials has the plain estimator's exact
+    mean, and a smaller SE on these workloads."""
+    for prob, x in ((wl.nested_3d_problem(), wl.ball_points(10, 3, 12)),
+                    (wl.zonal_3d_problem(), wl.ball_points(10, 3, 41, radius=0.95))):
+        res = oracle_core.estimate(prob, x, 60000, seed=0, M=6, variant="vr")
+        u_ex, g_ex = concentric_exact(prob, 6, x)
+        assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS
+        plain = oracle_core.estimate(prob, x, 60000, seed=0, M=6)
+        assert np.sqrt(np.mean(res["se_u"] ** 2)) < 0.8 * np.sqrt(np.mean(plain["se_u"] ** 2))
+
+
+def test_vr_trial_weight_is_the_part_fraction(oracle_core):
+    """The trial count C_k / K in the start weight Q = beta |dOmega| C_k / K: over many
+    walks started on the outer sphere of the zonal case (data Y_2^0) it averages the
+    exact part fractions 1 - 1/sqrt(3) and 1/sqrt(3)."""
+    prob = wl.zonal_3d_problem()
+    prep = oracle_core.Prepared(prob, "vr")
+    assert np.all(prep.part_len < 0)                      # flagged: parts by trials
+    ow = oracle_core.walks(prob, np.zeros(3), np.arange(4000, dtype=np.uint64), seed=2, M=0, variant="vr",
+                           prepared=prep)
+    on_outer = ow["H"][:, 0] == 0
+    area = prep.area[0]
+    for k, p_exact in ((0, 1 - 1 / np.sqrt(3)), (1, 1 / np.sqrt(3))):
+        y = ow["Y"][on_outer, k, 0]
+        beta = np.array([prep.beta_scale[0] * oracle_core.flux_at(prob, 0, yy, prepared=prep) for yy in y])
+        frac = ow["Q"][on_outer, k, 0] / (beta * area)
+        assert np.all(np.abs(frac * 16 - np.round(frac * 16)) < 1e-9)     # a count of 16 trials
+        assert np.all(np.sign(beta) == (1 if k == 0 else -1))
+        assert abs(frac.mean() - p_exact) < 5 * frac.std() / np.sqrt(len(frac))
+
+
+def test_vr_trial_weight_mistake_is_detected(oracle_core):
+    """A planted mistake: the trial start weighs beta by |dOmega| / 2 (as if the parts
+    were halves); the zonal case's parts are not, and the exact mean catches it."""
+    prob, x = wl.zonal_3d_problem(), wl.ball_points(10, 3, 41, radius=0.95)
+    oracle_core.set_mutant(11)
+    try:
+        res = oracle_core.estimate(prob, x, 60000, seed=0, M=6, variant="vr")
+    finally:
+        oracle_core.set_mutant(0)
+    u_ex, g_ex = concentric_exact(prob, 6, x)
+    assert np.abs(zscores(res, u_ex, g_ex)).max() > Z_CATCH
+
+
 def test_vr_without_reflection_is_detected(oracle_core):
     """A planted mistake: the part sampler keeps directions of the wrong sign (no
     reflection), so each chain draws from the whole sphere.  Each chain then averages

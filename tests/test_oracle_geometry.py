@@ -237,7 +237,10 @@ def test_vr_hemispheres(oracle_core, d):
         assert np.all(np.abs((u ** 2).mean(axis=0) - 1 / d) < 5 * (u ** 2).std(axis=0) / sqrt(n))
 
 
-def test_vr_parts_need_linear_data(oracle_core):
-    """Degree-2 data on a 3D sphere has no hemisphere parts: the VR variant refuses it."""
+def test_vr_parts_in_3d(oracle_core):
+    """Degree-2 data on a 3D sphere has no hemisphere parts: they are flagged for the start
+    by uniform trials (-1); an ellipsoid has no VR start at all."""
+    prep = oracle_core.Prepared(wl.nested_3d_problem(), "vr")
+    assert np.all(prep.part_len < 0)
     with pytest.raises(ValueError):
-        oracle_core.Prepared(wl.nested_3d_problem(), "vr")
+        oracle_core.Prepared(wl.ellipsoids_problem(3), "vr")
