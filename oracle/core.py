@@ -326,12 +326,10 @@ def linear_on_sphere(dim, s, flux):
 
 
 def vr_parts(dim, s, flux):
-    """|dOmega^+|, |dOmega^-| in d >= 3 (Sec. 4.4): zero data puts the whole sphere in the
-    beta >= 0 part; data linear in u splits it into two hemispheres; other data on a sphere
-    has parts of no closed form, marked (-1, -1): the start is then drawn from uniform
-    trials (reading R22).  None for other surfaces."""
-    if s["kind"] != "sphere":
-        return None
+    """|dOmega^+|, |dOmega^-| in d >= 3 (Sec. 4.4): zero data puts the whole surface in the
+    beta >= 0 part; data linear in u splits a sphere into two hemispheres; other data, and
+    every ellipsoid and mesh, has parts of no closed form, marked (-1, -1): the start is
+    then drawn from uniform trials (reading R22)."""
     A = surface_area(dim, s)
     if flux["basis"] == "zero":
         return (A, 0.0)
@@ -446,10 +444,7 @@ class Prepared:
         self.part_len = np.zeros((n, 2))
         for i in range(n):
             if variant == "vr" and d >= 3:
-                parts = vr_parts(d, surfs[i], fl[i])
-                if parts is None:
-                    raise ValueError("variance reduction in d >= 3 needs spheres on every surface")
-                self.part_len[i] = parts
+                self.part_len[i] = vr_parts(d, surfs[i], fl[i])
                 arc_off.append(len(t0))
                 arc_n.append(0)
                 continue

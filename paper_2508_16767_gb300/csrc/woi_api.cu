@@ -985,30 +985,30 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
         g->flux_dev = dev;
     }
     g->flux_dev_f.assign(g->flux_dev.begin(), g->flux_dev.end());
-    // Sec. 4.4 in d >= 3, spheres only.  Data linear in the unit vector u (degree-1 real
+    // Sec. 4.4 in d >= 3.  On a sphere, data linear in the unit vector u (degree-1 real
     // harmonics, harmonic polynomials of degree <= 1) is negative exactly on the mirror image
-    // of the half where it is positive: the parts are hemispheres of half the area.  Zero
-    // data puts the whole sphere in dOmega^+.  Other data in the quadratic device formats has
-    // parts of no closed form, marked -1: the start is drawn from uniform trials (the areas
-    // are estimated by the trials themselves).  vr_tol[i] bounds where an FP32 evaluation of
-    // beta may have the wrong sign: 1e-4 of a bound on the magnitude of its terms (the FP32
-    // error is about 1e-6 of it); below it the kernels decide the sign in FP64.
+    // of the half where it is positive: the parts are hemispheres of half the area.  Zero data
+    // puts the whole surface in dOmega^+.  Other data, and every ellipsoid and mesh, has parts
+    // of no closed form, marked -1: the start is drawn from uniform trials (the areas are
+    // estimated by the trials themselves).  vr_tol[i] (spheres with data in the quadratic
+    // device formats) bounds where an FP32 evaluation of beta may have the wrong sign: 1e-4
+    // of a bound on the magnitude of its terms (the FP32 error is about 1e-6 of it); below it
+    // the kernels decide the sign in FP64.  Elsewhere it is 0 and the kernels decide in their
+    // own precision.
     std::vector<double> vtol(n, 0.0);
     if (d >= 3) {
         vr_ok = true;
-        for (int i = 0; i < n && vr_ok; ++i) {
-            if (g->surf[i].type != WOI_SPHERE) { vr_ok = false; break; }
+        for (int i = 0; i < n; ++i) {
             if (basis[i] == WOI_FLUX_ZERO) { plen[2 * i] = g->area[i]; continue; }
+            plen[2 * i] = plen[2 * i + 1] = -1.0;
             const int fb = g->flux_basis_dev[i];
-            if (fb != kFluxSphQuad && fb != kFluxHarmonicQuad) { vr_ok = false; break; }
+            if (g->surf[i].type != WOI_SPHERE || (fb != kFluxSphQuad && fb != kFluxHarmonicQuad)) continue;
             const double *c = coef.data() + off[i];
-            bool linear = false;
+            bool linear = true;
             if (basis[i] == WOI_FLUX_REAL_SH) {
-                linear = true;
                 for (int idx = 0; idx < nc[i]; ++idx)
                     if ((idx < 1 || idx > 3) && c[idx] != 0.0) linear = false;
             } else {
-                linear = true;
                 const int T = (int)c[1];
                 for (int t = 0; t < T; ++t) {
                     double deg = 0.0;
@@ -1016,7 +1016,7 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
                     if (deg > 1.0) linear = false;
                 }
             }
-            plen[2 * i] = plen[2 * i + 1] = linear ? 0.5 * g->area[i] : -1.0;
+            if (linear) plen[2 * i] = plen[2 * i + 1] = 0.5 * g->area[i];
             // |terms| <= sum |q| rho^deg with rho = max |y_k| on the sphere (rho = 1 for u)
             const double *q = g->flux_dev.data() + g->flux_off_dev[i];
             double bound = 0.0;
@@ -1332,9 +1332,7 @@ woi_status check_opts(const woi_geometry *g, const woi_opts *o, int64_t n_pts, i
     if (n_walks % o->sched_group || walk_begin % o->sched_group)
         return fail(WOI_E_INVALID_ARG, "walk range must be a multiple of sched_group");
     if (o->variant == WOI_VR && !g->vr_ok)
-        return fail(WOI_E_UNSUPPORTED, "variance reduction needs 2D Fourier (or zero) flux on every surface, or in "
-                                        "d >= 3 spheres with real-harmonic data of degree <= 2 or harmonic-polynomial "
-                                        "data of degree <= 3 (or zero)");
+        return fail(WOI_E_UNSUPPORTED, "variance reduction in 2D needs Fourier (or zero) flux on every surface");
     if (o->block_size != 0 && (o->block_size % 32 || o->block_size < 32 || o->block_size > kMixedMaxBlock))
         return fail(WOI_E_INVALID_ARG, "block_size must be a multiple of 32 in [32, %d]", kMixedMaxBlock);
     if (o->walks_per_lane < 0 || o->walks_per_lane > 4096) return fail(WOI_E_INVALID_ARG, "walks_per_lane out of range");

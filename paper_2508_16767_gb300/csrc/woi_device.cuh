@@ -1159,37 +1159,59 @@ __device__ __forceinline__ int vr_part(const DevGeom *gd, int h, const StepWords
     return b >= (Real)0 ? 0 : 1;
 }
 
-// VR start on a d >= 3 sphere whose parts have no closed form: kVrTrials uniform trials on
-// dOmega_h shared by both chains (trial t draws the step-0 words of chain id t << 12; trial 0
-// is chain 0's own).  Chain k starts at the first trial of its sign with
-// Q = beta |dOmega| C_k / kVrTrials, C_k the trials of that sign: an unbiased estimate of
-// |dOmega^+/-| / |dOmega| that is independent of where the first trial of that sign lies,
-// so the chain's term has Algorithm 3's mean.  No trial of a sign: that chain is dead.
-template <typename Real, int D>
+// VR start in d >= 3 where the parts have no closed form: kVrTrials uniform points on
+// dOmega_h (sphere, ellipsoid or mesh sampler) shared by both chains (trial t draws the step-0
+// words of chain id t << 12; trial 0 is chain 0's own).  Chain k starts at the first trial of
+// its sign with Q = beta |dOmega| C_k / kVrTrials, C_k the trials of that sign: an unbiased
+// estimate of |dOmega^+/-| / |dOmega| that is independent of where the first trial of that
+// sign lies, so the chain's term has Algorithm 3's mean.  No trial of a sign: that chain is
+// dead.  On ellipsoids and meshes the sign is taken in the kernel's precision, like the
+// ellipsoid sampler's acceptance test.
+template <typename Real, int D, bool STAR>
 __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, const StepWords &w0, const Rng &rng,
                                 Chain<Real, D> *ch)
 {
-    int n[2] = {0, 0};
-    Real uf[2][D];
+    bool is_ell = false, is_mesh = false;
+    if constexpr (STAR && D >= 3) is_ell = g.type[h] == kEllipsoid;
+    if constexpr (STAR && D == 3) is_mesh = g.type[h] == kMesh;
+    int n[2] = {0, 0}, af[2] = {0, 0};
+    Real vf[2][D], nf[2][D];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int c = 0; c < D; ++c) uf[k][c] = 0;
+        for (int c = 0; c < D; ++c) vf[k][c] = nf[k][c] = 0;
     for (int t = 0; t < kVrTrials; ++t) {
+        const int cid = t << 12;
         StepWords w = w0;
         if (t > 0) {
-            w.a = rng.words(0, t << 12, 0);
-            if constexpr (two_calls<D>()) w.b = rng.words(0, t << 12, 1);
+            w.a = rng.words(0, cid, 0);
+            if constexpr (two_calls<D>()) w.b = rng.words(0, cid, 1);
         }
-        Real u[D], y[D];
-        direction<Real, D>(w, u);
+        Real v[D], nrm[D], y[D];
+        int aj = 0;
+        if (is_mesh) {
+            if constexpr (STAR && D == 3) mesh_uniform<Real>(gd, gd->mesh_slot[h], w, v, nrm, &aj);
+        } else if (is_ell) {
+            if constexpr (STAR && D >= 3) {
+                const SEll<Real> &E = static_cast<const SGeomE<Real> &>(g).ell;
+                ell_uniform<Real, D>(E, E.slot[h], rng, 0, cid, w, v, nrm);
+            }
+        } else {
+            direction<Real, D>(w, nrm);
 #pragma unroll
-        for (int c = 0; c < D; ++c) y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + g.radius[h] * u[c];
-        const Real b = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, u, u);
-        const int part = vr_part<Real, D>(gd, h, w, b);
+            for (int c = 0; c < D; ++c) v[c] = g.radius[h] * nrm[c];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + v[c];
+        const Real b = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, nrm, nrm);
+        const int part = (is_ell || is_mesh) ? (b >= (Real)0 ? 0 : 1) : vr_part<Real, D>(gd, h, w, b);
         if (n[part] == 0) {
 #pragma unroll
-            for (int c = 0; c < D; ++c) uf[part][c] = u[c];
+            for (int c = 0; c < D; ++c) {
+                vf[part][c] = v[c];
+                nf[part][c] = nrm[c];
+            }
+            af[part] = aj;
         }
         ++n[part];
     }
@@ -1198,16 +1220,16 @@ __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, 
         Chain<Real, D> &q = ch[k];
         q.T = 1;
         q.s = h;
-        q.aj = 0;
+        q.aj = af[k];
         q.ad = 0;
         q.alive = n[k] > 0 && gd->flux_basis[h] != kFluxZero;
         Real y[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            q.v[c] = q.alive ? g.radius[h] * uf[k][c] : (Real)0;
+            q.v[c] = q.alive ? vf[k][c] : (Real)0;
             y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + q.v[c];
         }
-        q.Q = q.alive ? g.beta_scale[h] * flux_value<Real, D>(gd, h, y, uf[k], uf[k]) *
+        q.Q = q.alive ? g.beta_scale[h] * flux_value<Real, D>(gd, h, y, nf[k], nf[k]) *
                             (Real)(gd->area[h] * ((double)n[k] / kVrTrials))
                       : (Real)0;
     }
@@ -1550,9 +1572,9 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
         if (i > 0) S *= g.alpha_sign[h];
         const int rel = (i > 0) ? relation(g, hp, h) : 0;
         bool trials = false;
-        if constexpr (VR && !STAR && D >= 3) {
+        if constexpr (VR && D >= 3) {
             if (i == 0 && gd->part_len[h][0] < 0.0) {
-                vr_trials_start<Real, D>(g, gd, h, w0, rng, ch);
+                vr_trials_start<Real, D, STAR>(g, gd, h, w0, rng, ch);
                 trials = true;
             }
         }

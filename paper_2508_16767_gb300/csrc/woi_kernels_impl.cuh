@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(128) k_walk_values(WalkValuesParams p)
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::mixed(bool vr, const MixedParams &p, int grid, int block, size_t smem, cudaStream_t s)
 {
-    if constexpr (D == 2 || !STAR) {
+    {
         if (vr) {
             k_walk_mixed<D, true, STAR><<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
@@ -491,7 +491,7 @@ template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::mixed_warp(bool vr, const MixedParams &p, int grid, int block, size_t smem,
                                              cudaStream_t s)
 {
-    if constexpr (D == 2 || !STAR) {
+    {
         if (vr) {
             k_walk_mixed_warp<D, true, STAR><<<grid, block, smem, s>>>(p);
             return cudaGetLastError();
@@ -504,7 +504,7 @@ cudaError_t DimLaunchers<D, STAR>::mixed_warp(bool vr, const MixedParams &p, int
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t smem, int *blocks_per_sm)
 {
-    if constexpr (D == 2 || !STAR) {
+    {
         if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, true, STAR>, block, smem);
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed_warp<D, false, STAR>, block, smem);
@@ -515,7 +515,7 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_warp(bool vr, int block, size_t sme
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::shared(bool vr, const MixedParams &p, int grid, size_t smem, cudaStream_t s)
 {
-    if constexpr (D == 2 || !STAR) {
+    {
         if (vr) {
             cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, true, STAR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -534,7 +534,7 @@ cudaError_t DimLaunchers<D, STAR>::shared(bool vr, const MixedParams &p, int gri
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *blocks_per_sm)
 {
-    if constexpr (D == 2 || !STAR) {
+    {
         if (vr) {
             cudaError_t e = cudaFuncSetAttribute(k_walk_shared<D, true, STAR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -551,7 +551,7 @@ cudaError_t DimLaunchers<D, STAR>::occupancy_shared(bool vr, size_t smem, int *b
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, size_t smem, int *blocks_per_sm)
 {
-    if constexpr (D == 2 || !STAR) {
+    {
         if (vr) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, true, STAR>, block, smem);
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_walk_mixed<D, false, STAR>, block, smem);
@@ -559,7 +559,7 @@ cudaError_t DimLaunchers<D, STAR>::occupancy(bool vr, int block, size_t smem, in
 template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::fp64_point(bool vr, const Fp64PointParams &p, int grid, cudaStream_t s)
     {
-        if constexpr (D == 2 || !STAR) {
+        {
             if (vr) {
                 k_walk_fp64_point<D, true, STAR><<<grid, 256, 0, s>>>(p);
                 return cudaGetLastError();
@@ -572,7 +572,7 @@ template <int D, bool STAR>
 cudaError_t DimLaunchers<D, STAR>::values(bool vr, bool fp64, const WalkValuesParams &p, cudaStream_t s)
     {
         const int grid = (int)((p.n + 127) / 128);
-        if constexpr (D == 2 || !STAR) {
+        {
             if (vr) {
                 if (fp64) k_walk_values<double, D, true, STAR><<<grid, 128, 0, s>>>(p);
                 else k_walk_values<float, D, true, STAR><<<grid, 128, 0, s>>>(p);

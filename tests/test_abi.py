@@ -96,12 +96,12 @@ def test_estimate_argument_checks_and_no_device(woi):
     with pytest.raises(woi.WoiError) as e:
         woi.woi_estimate(g, pts, 1000, sched_group=32)           # 1000 is not a multiple of 32
     assert e.value.status == 1
-    ge = woi.Geometry(wl.ellipsoids_problem(3))
+    g2 = woi.Geometry(wl.manufactured_instance(2, np.random.default_rng(3), k_max=4))
     with pytest.raises(woi.WoiError) as e:
-        woi.woi_estimate(ge, wl.ellipsoid_points(wl.ellipsoids_problem(3), 4, seed=1), 1024,
-                         variant="vr")                            # VR in 3D: spheres only
+        woi.woi_estimate(g2, wl.ball_points(4, 2, 1, radius=0.5), 1024,
+                         variant="vr")                            # VR in 2D needs Fourier data
     assert e.value.status == 4
-    ge.close()
+    g2.close()
     with pytest.raises(woi.WoiError) as e:
         woi.woi_estimate(g, pts, 1024, M=40)
     assert e.value.status == 1

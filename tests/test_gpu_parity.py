@@ -84,6 +84,11 @@ def cases():
         yield f"ellipsoids-{dim}d", ell, wl.ellipsoid_points(ell, 3, seed=50 + dim), "plain"
     rocks = wl.rocks_problem(n_rocks=3, subdiv_outer=3, subdiv_rock=2, M=4)
     yield "mesh-rocks", rocks, wl.mesh_points(rocks, 3, seed=61), "plain"
+    ell3 = wl.ellipsoids_problem(3)
+    yield "ellipsoids-3d-vr", ell3, wl.ellipsoid_points(ell3, 3, seed=62), "vr"
+    ell6 = wl.ellipsoids_problem(6)
+    yield "ellipsoids-6d-vr", ell6, wl.ellipsoid_points(ell6, 2, seed=63), "vr"
+    yield "mesh-rocks-vr", rocks, wl.mesh_points(rocks, 3, seed=64), "vr"
 
 
 CASES = list(cases())
@@ -178,7 +183,8 @@ def test_shared_schedules(W, O):
                                                       ("6d-nested", "plain", 1), ("ellipsoids-3d", "plain", 1),
                                                       ("mesh-rocks", "plain", 1), ("3d-linear-vr", "vr", 1),
                                                       ("6d-nested-vr", "vr", 32), ("3d-nested-vr", "vr", 1),
-                                                      ("6d-quad-vr", "vr", 32)])
+                                                      ("6d-quad-vr", "vr", 32), ("ellipsoids-3d-vr", "vr", 1),
+                                                      ("mesh-rocks-vr", "vr", 32)])
 def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
     estimate is still the mean over the same walks the oracle draws for that
@@ -369,7 +375,7 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
 
 
 @pytest.mark.parametrize("name", ["3d-nested", "ellipsoids-3d", "mesh-rocks", "star-3", "3d-linear-vr", "6d-nested-vr",
-                                  "3d-nested-vr", "3d-zonal-vr", "6d-quad-vr"])
+                                  "3d-nested-vr", "3d-zonal-vr", "6d-quad-vr", "ellipsoids-3d-vr", "mesh-rocks-vr"])
 def test_walk_trace_states_match_oracle(W, O, name):
     """woi_walk_trace (FP64): every state y_i, Q_i and T_i of every walk equals the
     oracle's (Eqs. naive_woi_Q, naive_woi_T) to 1e-12 of its magnitude scale times the
@@ -381,7 +387,9 @@ def test_walk_trace_states_match_oracle(W, O, name):
     g.close()
     ow = O.walks(prob, x[0], ids, seed=7, M=prob["M"], variant=variant, point_id=0)
     chains = 2 if variant == "vr" else 1
-    alive = ow["T"][:, :chains] != 0           # a chain that ended keeps its last state on both sides
+    # a chain that ended keeps its last state on both sides; a chain dead from the start (no
+    # start of its sign: Q = 0) has no state to compare
+    alive = (ow["T"][:, :chains] != 0) & (ow["Q"][:, :chains] != 0)
     cond = np.broadcast_to(ow["scale"][:, 3, None, None], alive.shape)[alive]
     dy = np.abs(tr["Y"] - ow["Y"][:, :chains]).max(axis=-1)
     assert np.all(dy[alive] <= 1e-12 * cond * (1 + np.abs(ow["Y"][:, :chains]).max(axis=-1)[alive])), name
