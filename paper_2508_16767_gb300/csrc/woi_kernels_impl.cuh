@@ -69,7 +69,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 // for good, so one round covers all the work.
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
-__global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams p)
+__global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed(MixedParams p)
 {
     __shared__ SGeomFor<float, D, STAR> g;
     __shared__ int left_sh;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed(MixedParams
 // point), each warp with its own x - c_s table, no block barrier per unit
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
-__global__ void __launch_bounds__(256, kMixedMinBlocks) k_walk_mixed_warp(MixedParams p)
+__global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed_warp(MixedParams p)
 {
     __shared__ SGeomFor<float, D, STAR> g;
     extern __shared__ float xc_all[];   // [warps][n][kMaxDim]
