@@ -329,7 +329,7 @@ def vr_parts(dim, s, flux):
     """|dOmega^+|, |dOmega^-| in d >= 3 (Sec. 4.4): zero data puts the whole surface in the
     beta >= 0 part; data linear in u splits a sphere into two hemispheres; other data, and
     every ellipsoid and mesh, has parts of no closed form, marked (-1, -1): the start is
-    then drawn from uniform trials (reading R22)."""
+    then drawn from uniform trials weighted by their fraction of each sign."""
     A = surface_area(dim, s)
     if flux["basis"] == "zero":
         return (A, 0.0)

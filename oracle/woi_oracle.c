@@ -823,9 +823,9 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     double cond0 = 1.0;
     int alive[2] = {1, 1};
     int tri[2] = {-1, -1};   /* mesh triangle of each chain's state (-1 elsewhere) */
-    int trial_n[2] = {0, 0}, trial_tri[2] = {-1, -1};   /* VR start by trials (reading R22) */
+    int trial_n[2] = {0, 0}, trial_tri[2] = {-1, -1};   /* VR start by uniform trials */
     double trial_y[2][OR_MAX_DIM] = {{0}};
-    double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m})  (reading R1) */
+    double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m}): alpha_{H_0} never enters the expansion */
     double Ai = 1.0;         /* ||alpha||_1^i */
     int h_prev = -1;
 
@@ -857,7 +857,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
                     if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
                 } else if (P->part_len[2 * h] < 0.0) {
-                    /* parts of no closed form (reading R22): K uniform trials on dOmega_h, shared by
+                    /* parts of no closed form: K uniform trials on dOmega_h, shared by
                      * both chains (trial t draws the step-0 words of chain id t << 12).  Chain k starts
                      * at the first trial of its sign and weighs beta by |dOmega| C_k / K, C_k the
                      * trials of that sign: C_k / K is an unbiased estimate of |dOmega^+/-| / |dOmega|,
@@ -904,7 +904,8 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                 double ynew[OR_MAX_DIM];
                 int tnew = -1;
                 if (rel == OR_REL_OTHER) {
-                    /* uniform on dOmega_h; Q *= K*(y_i, y_{i-1}) |dOmega_h|; T unchanged (R2, R3) */
+                    /* uniform on dOmega_h; Q *= K*(y_i, y_{i-1}) |dOmega_h| with the normal at the new
+                     * point; T unchanged (the sign is already in K*) */
                     or_uniform_point(P, h, &rng, i, k, ynew, &tnew);
                     double nrm[OR_MAX_DIM], dot = 0.0;
                     if (or_mutant == 5) {
@@ -926,7 +927,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     /* a line through a point of a mesh triangle skips that triangle */
                     int q = or_intersections(P, h, y[k], z, rel == OR_REL_DESC, ts,
                                              rel == OR_REL_SAME ? tri[k] : -1, hits);
-                    if (q == 0) {            /* reading R5 */
+                    if (q == 0) {            /* no admissible crossing (tangent line): the walk ends */
                         alive[k] = 0; T[k] = 0.0;
                         continue;
                     }

@@ -1115,7 +1115,7 @@ __device__ void mesh_step(const DevGeom *gd, Real area, int h, int rel, const St
         Real tt[kMaxHits];
         int tri[kMaxHits];
         const int q = mesh_hits<Real>(gd, m, dy, z, rel == 1, rel == 0 ? ch.aj : -1, tt, tri);
-        if (q == 0) {                          // reading R5
+        if (q == 0) {                          // no admissible crossing (tangent line): the walk ends
             ch.alive = false;
             ch.T = 0;
             return;
@@ -1405,7 +1405,7 @@ __device__ void ell_step(const SGeomE<Real> &g, int h, int rel, const StepWords 
         if (rel == 0) {
             t = (Real)-2 * b1 / a2;
             const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
-            if (O::fabs_(t) * E.jmax[e] <= tiny) {   // tangent: only y itself (reading R5)
+            if (O::fabs_(t) * E.jmax[e] <= tiny) {   // tangent: only y itself, the walk ends
                 ch.alive = false;
                 ch.T = 0;
                 return;

@@ -10,7 +10,8 @@ hemisphere parts in 3D and 6D, an invisible interface
 walkers per schedule).  The test statistic is z = (estimate - exact) / SE with
 the SE from the schedule-group means; with fixed seeds the outcome is
 deterministic.  Planted mistakes in the oracle (Sec. 3 signs and scalings,
-readings R1-R3, the truncation weight, the factor N) must be detected.
+the range of the sign product, T in the uniform case, the normal of K*, the
+truncation weight, the factor N) must be detected.
 """
 import numpy as np
 import pytest
@@ -98,9 +99,9 @@ def test_variance_reduced_hemispheres_nd(oracle_core):
 
 
 def test_variance_reduced_by_trials(oracle_core):
-    """Algorithm 3 where |dOmega^+/-| has no closed form (degree-2 data on 3D spheres,
-    reading R22): the start by 16 shared uniform trials has the plain estimator's exact
-    mean, and a smaller SE on these workloads."""
+    """Algorithm 3 where |dOmega^+/-| has no closed form (degree-2 data on 3D spheres):
+    the start by 16 shared uniform trials, weighted by their fraction of each sign, has the
+    plain estimator's exact mean, and a smaller SE on these workloads."""
     for prob, x in ((wl.nested_3d_problem(), wl.ball_points(10, 3, 12)),
                     (wl.zonal_3d_problem(), wl.ball_points(10, 3, 41, radius=0.95))):
         res = oracle_core.estimate(prob, x, 60000, seed=0, M=6, variant="vr")
