@@ -60,7 +60,7 @@ typedef enum {
     WOI_E_INVALID_ARG = 1,   /* bad pointer, size, option or range */
     WOI_E_GEOMETRY = 2,      /* surfaces overlap, are not nested as `parent` says, or a point lies outside */
     WOI_E_COMPAT = 3,        /* flux data violate the zero-mean compatibility condition of Sec. 1 */
-    WOI_E_UNSUPPORTED = 4,   /* a combination this build does not implement */
+    WOI_E_UNSUPPORTED = 4,   /* a combination the library does not implement */
     WOI_E_NO_DEVICE = 5,     /* no usable CUDA device */
     WOI_E_CUDA = 6,          /* a CUDA runtime call failed (message has the CUDA error string) */
     WOI_E_OOM = 7,           /* device or host allocation failed */
