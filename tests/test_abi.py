@@ -110,6 +110,18 @@ def test_estimate_argument_checks_and_no_device(woi):
         with pytest.raises(woi.WoiError) as e:
             woi.woi_estimate(g, pts, 1024)
         assert e.value.status == 5
+        # the variance-reduced walk passes the option checks in d >= 3 (hemispheres or
+        # trials) on spheres, ellipsoids and meshes: only the missing device stops it
+        ell = wl.ellipsoids_problem(3)
+        rocks = wl.rocks_problem(n_rocks=1, subdiv_outer=1, subdiv_rock=1, M=3)
+        for prob, x in ((wl.nested_3d_problem(), pts), (wl.linear_3d_problem(), pts),
+                        (wl.nested_6d_problem(), wl.ball_points(4, 6, 1)),
+                        (ell, wl.ellipsoid_points(ell, 4, seed=1)), (rocks, wl.mesh_points(rocks, 4, seed=1))):
+            gv = woi.Geometry(prob)
+            with pytest.raises(woi.WoiError) as e:
+                woi.woi_estimate(gv, x, 1024, variant="vr")
+            assert e.value.status == 5, prob.get("name")
+            gv.close()
     g.close()
 
 
