@@ -19,6 +19,8 @@ def cases():
     yield "3d-nested", wl.nested_3d_problem(), wl.ball_points(2, 3, 12), "plain", 6
     yield "star-3", wl.star_inclusions_problem(seed=3, n_incl=3), np.array([[0.1, 0.2], [-0.5, 0.3]]), "plain", 3
     yield "star-3-vr", wl.star_inclusions_problem(seed=3, n_incl=3), np.array([[0.6, -0.4]]), "vr", 3
+    yield "3d-linear-vr", wl.linear_3d_problem(), wl.ball_points(1, 3, 5, radius=0.9), "vr", 4
+    yield "3d-zonal-vr", wl.zonal_3d_problem(), wl.ball_points(1, 3, 6, radius=0.9), "vr", 4
 
 
 def main():

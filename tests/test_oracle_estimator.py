@@ -254,7 +254,8 @@ def test_oracle_reproduces_stored_replay(oracle_core):
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "replay_small.json")))
     probs = {"2d-concentric": wl.concentric_2d_problem(), "3d-nested": wl.nested_3d_problem(),
              "star-3": wl.star_inclusions_problem(seed=3, n_incl=3),
-             "star-3-vr": wl.star_inclusions_problem(seed=3, n_incl=3)}
+             "star-3-vr": wl.star_inclusions_problem(seed=3, n_incl=3),
+             "3d-linear-vr": wl.linear_3d_problem(), "3d-zonal-vr": wl.zonal_3d_problem()}
     for c in gold["cases"]:
         r = oracle_core.walks(probs[c["name"]], np.asarray(c["x"]), np.arange(32), seed=0, M=c["M"],
                               variant=c["variant"], point_id=c["point_id"])
