@@ -221,14 +221,16 @@ def test_invisible_interface(oracle_core):
     assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS
 
 
-def test_walk_ranges_merge(oracle_core):
+@pytest.mark.parametrize("variant", ["plain", "vr"])
+def test_walk_ranges_merge(oracle_core, variant):
     """Splitting the walks into ranges (resumption / sharding) and adding the
-    sums reproduces the single run."""
+    sums reproduces the single run (the variance-reduced start by trials draws
+    per walk too)."""
     prob = wl.nested_3d_problem()
     x = wl.ball_points(3, 3, 2)
-    a = oracle_core.estimate(prob, x, 4096, seed=2, M=6)
-    b1 = oracle_core.estimate(prob, x, 1024, seed=2, M=6)
-    b2 = oracle_core.estimate(prob, x, 3072, seed=2, M=6, walk_begin=1024)
+    a = oracle_core.estimate(prob, x, 4096, seed=2, M=6, variant=variant)
+    b1 = oracle_core.estimate(prob, x, 1024, seed=2, M=6, variant=variant)
+    b2 = oracle_core.estimate(prob, x, 3072, seed=2, M=6, walk_begin=1024, variant=variant)
     assert np.allclose(a["sum_f"], b1["sum_f"] + b2["sum_f"], rtol=1e-12, atol=1e-12)
     assert np.allclose(a["sum_gm2"], b1["sum_gm2"] + b2["sum_gm2"], rtol=1e-12, atol=1e-12)
 
