@@ -236,13 +236,18 @@ def test_full_size_3d_workload_sampled(W, O):
         assert abs(gr["se_u"][p] / orr["se_u"][0] - 1) < 1e-3
 
 
-def test_ranges_add_up(W):
-    prob = wl.concentric_2d_problem()
-    x = wl.concentric_2d_points()[:10]
+@pytest.mark.parametrize("name,variant", [("2d-concentric", "plain"), ("3d-nested", "vr")])
+def test_ranges_add_up(W, name, variant):
+    """Walk ranges (resumption / sharding) add up to the single run, also for the
+    variance-reduced walk with its start by trials."""
+    if name == "2d-concentric":
+        prob, x = wl.concentric_2d_problem(), wl.concentric_2d_points()[:10]
+    else:
+        prob, x = wl.nested_3d_problem(), wl.ball_points(6, 3, 9)
     g = W.Geometry(prob)
-    a = W.woi_estimate_range(g, x, 0, 6144, seed=5)
-    b1 = W.woi_estimate_range(g, x, 0, 2048, seed=5)
-    b2 = W.woi_estimate_range(g, x, 2048, 4096, seed=5)
+    a = W.woi_estimate_range(g, x, 0, 6144, seed=5, M=prob["M"], variant=variant)
+    b1 = W.woi_estimate_range(g, x, 0, 2048, seed=5, M=prob["M"], variant=variant)
+    b2 = W.woi_estimate_range(g, x, 2048, 4096, seed=5, M=prob["M"], variant=variant)
     g.close()
     assert np.allclose(a, b1 + b2, rtol=1e-12, atol=1e-14)
     f = W.finalize_moments(a, 6144)
