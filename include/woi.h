@@ -122,12 +122,12 @@ typedef struct {
 } woi_flux_desc;
 
 enum { WOI_PLAIN = 0,                 /* Algorithm 2 */
-       WOI_VR = 1 };                  /* Algorithm 3: two chains from dOmega^+ / dOmega^-.  2D: Fourier
-                                         (or zero) data, parts cut at the roots of beta (else
-                                         WOI_E_UNSUPPORTED).  d >= 3: hemispheres for data linear in the
-                                         unit vector on a sphere; otherwise the start is drawn from 16
-                                         uniform trials on the surface, weighted by the fraction of
-                                         trials of each sign (same mean, no areas needed) */
+       WOI_VR = 1 };                  /* Algorithm 3: two chains from dOmega^+ / dOmega^-.  2D Fourier
+                                         data: parts cut at the roots of beta; d >= 3 data linear in the
+                                         unit vector on a sphere: hemispheres; any other data and
+                                         surface: the start is drawn from 16 uniform trials on the
+                                         surface, weighted by the fraction of trials of each sign (same
+                                         mean, no areas needed) */
 enum { WOI_MIXED = 0,                 /* FP32 walks, compensated FP32 per-lane sums, FP64 reductions */
        WOI_FP64_PLAIN = 1 };          /* FP64 everywhere, one kernel launch per evaluation point */
 

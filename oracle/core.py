@@ -450,7 +450,11 @@ class Prepared:
                 continue
             arcs = vr_arcs(d, surfs[i], fl[i], self.beta_scale[i]) if variant == "vr" else None
             if variant == "vr" and arcs is None:
-                raise ValueError("variance reduction needs 2D Fourier (or zero) flux on every surface")
+                # 2D data other than a Fourier series: parts of no closed form, start by trials
+                self.part_len[i] = (-1.0, -1.0)
+                arc_off.append(len(t0))
+                arc_n.append(0)
+                continue
             arc_off.append(len(t0))
             arc_n.append(0 if arcs is None else len(arcs))
             for a, b, s_, L in (arcs or []):

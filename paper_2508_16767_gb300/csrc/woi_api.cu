@@ -824,7 +824,8 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
         th[i] = (uint64_t)std::floor(std::ldexp(C / A, 32));
     }
     th[n - 1] = 1ull << 32;
-    // Sec. 4.4: arcs of dOmega^+ = {beta >= 0} and dOmega^- = {beta < 0} (2D)
+    // Sec. 4.4: arcs of dOmega^+ = {beta >= 0} and dOmega^- = {beta < 0} (2D Fourier data;
+    // other 2D data is marked -1 and its start is drawn from uniform trials, as in d >= 3)
     bool vr_ok = (d == 2);
     std::vector<double> at0, at1, alen, as0, plen(2 * n, 0.0);
     std::vector<int> asg, aoff(n, 0), an(n, 0);
@@ -849,7 +850,11 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
             an[i] = 1;
             continue;
         }
-        if (basis[i] != WOI_FLUX_FOURIER) { vr_ok = false; break; }
+        if (basis[i] != WOI_FLUX_FOURIER) {
+            // other 2D data: parts of no closed form, the start is drawn from uniform trials
+            plen[2 * i] = plen[2 * i + 1] = -1.0;
+            continue;
+        }
         std::vector<double> c(coef.begin() + off[i], coef.begin() + off[i] + nc[i]);
         auto beta = [&](double t) { return bsc[i] * fourier_eval(c, t); };
         const int m = 8192;
@@ -985,7 +990,7 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
         g->flux_dev = dev;
     }
     g->flux_dev_f.assign(g->flux_dev.begin(), g->flux_dev.end());
-    // Sec. 4.4 in d >= 3.  On a sphere, data linear in the unit vector u (degree-1 real
+    // Sec. 4.4 in d >= 3 (and the sign tolerance of 2D trial starts).  On a sphere, data linear in the unit vector u (degree-1 real
     // harmonics, harmonic polynomials of degree <= 1) is negative exactly on the mirror image
     // of the half where it is positive: the parts are hemispheres of half the area.  Zero data
     // puts the whole surface in dOmega^+.  Other data, and every ellipsoid and mesh, has parts
@@ -996,6 +1001,25 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
     // the kernels decide the sign in FP64.  Elsewhere it is 0 and the kernels decide in their
     // own precision.
     std::vector<double> vtol(n, 0.0);
+    auto sign_tolerance = [&](int i) {
+        // |terms| <= sum |q| rho^deg with rho = max |y_k| on the sphere (rho = 1 for u)
+        const int fb = g->flux_basis_dev[i];
+        if (g->surf[i].type != WOI_SPHERE || (fb != kFluxSphQuad && fb != kFluxHarmonicQuad)) return 0.0;
+        const double *q = g->flux_dev.data() + g->flux_off_dev[i];
+        double bound = 0.0;
+        if (fb == kFluxSphQuad) {
+            for (int k = 0; k < 10; ++k) bound += std::fabs(q[k]);
+        } else {
+            double rho = 1.0;
+            for (int k = 0; k < d; ++k) rho = std::max(rho, std::fabs(g->surf[i].center[k]) + g->surf[i].radius);
+            for (int k = 1; k < g->flux_n_dev[i]; ++k) bound += std::fabs(q[k]);
+            bound *= std::fabs(q[0]) * rho * rho;
+        }
+        return 1e-4 * std::fabs(bsc[i]) * bound;
+    };
+    if (d == 2)
+        for (int i = 0; i < n; ++i)
+            if (plen[2 * i] < 0.0) vtol[i] = sign_tolerance(i);
     if (d >= 3) {
         vr_ok = true;
         for (int i = 0; i < n; ++i) {
@@ -1017,18 +1041,7 @@ woi_status woi_set_sigma_and_data(woi_geometry *g, const double *sigma, const wo
                 }
             }
             if (linear) plen[2 * i] = plen[2 * i + 1] = 0.5 * g->area[i];
-            // |terms| <= sum |q| rho^deg with rho = max |y_k| on the sphere (rho = 1 for u)
-            const double *q = g->flux_dev.data() + g->flux_off_dev[i];
-            double bound = 0.0;
-            if (fb == kFluxSphQuad) {
-                for (int k = 0; k < 10; ++k) bound += std::fabs(q[k]);
-            } else {
-                double rho = 1.0;
-                for (int k = 0; k < d; ++k) rho = std::max(rho, std::fabs(g->surf[i].center[k]) + g->surf[i].radius);
-                for (int k = 1; k < g->flux_n_dev[i]; ++k) bound += std::fabs(q[k]);
-                bound *= std::fabs(q[0]) * rho * rho;
-            }
-            vtol[i] = 1e-4 * std::fabs(bsc[i]) * bound;
+            vtol[i] = sign_tolerance(i);
         }
     }
     g->vr_tol = vtol;
@@ -1332,7 +1345,7 @@ woi_status check_opts(const woi_geometry *g, const woi_opts *o, int64_t n_pts, i
     if (n_walks % o->sched_group || walk_begin % o->sched_group)
         return fail(WOI_E_INVALID_ARG, "walk range must be a multiple of sched_group");
     if (o->variant == WOI_VR && !g->vr_ok)
-        return fail(WOI_E_UNSUPPORTED, "variance reduction in 2D needs Fourier (or zero) flux on every surface");
+        return fail(WOI_E_UNSUPPORTED, "variance reduction is not available for this geometry");
     if (o->block_size != 0 && (o->block_size % 32 || o->block_size < 32 || o->block_size > kMixedMaxBlock))
         return fail(WOI_E_INVALID_ARG, "block_size must be a multiple of 32 in [32, %d]", kMixedMaxBlock);
     if (o->walks_per_lane < 0 || o->walks_per_lane > 4096) return fail(WOI_E_INVALID_ARG, "walks_per_lane out of range");

@@ -1159,23 +1159,25 @@ __device__ __forceinline__ int vr_part(const DevGeom *gd, int h, const StepWords
     return b >= (Real)0 ? 0 : 1;
 }
 
-// VR start in d >= 3 where the parts have no closed form: kVrTrials uniform points on
-// dOmega_h (sphere, ellipsoid or mesh sampler) shared by both chains (trial t draws the step-0
+// VR start where the parts have no closed form (d >= 3, and 2D data other than a Fourier
+// series): kVrTrials uniform points on dOmega_h (the circle / sphere, star, ellipsoid or mesh
+// sampler) shared by both chains (trial t draws the step-0
 // words of chain id t << 12; trial 0 is chain 0's own).  Chain k starts at the first trial of
 // its sign with Q = beta |dOmega| C_k / kVrTrials, C_k the trials of that sign: an unbiased
 // estimate of |dOmega^+/-| / |dOmega| that is independent of where the first trial of that
 // sign lies, so the chain's term has Algorithm 3's mean.  No trial of a sign: that chain is
-// dead.  On ellipsoids and meshes the sign is taken in the kernel's precision, like the
+// dead.  On stars, ellipsoids and meshes the sign is taken in the kernel's precision, like the
 // ellipsoid sampler's acceptance test.
 template <typename Real, int D, bool STAR>
 __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, const StepWords &w0, const Rng &rng,
                                 Chain<Real, D> *ch)
 {
-    bool is_ell = false, is_mesh = false;
+    bool is_ell = false, is_mesh = false, is_star = false;
     if constexpr (STAR && D >= 3) is_ell = g.type[h] == kEllipsoid;
     if constexpr (STAR && D == 3) is_mesh = g.type[h] == kMesh;
+    if constexpr (STAR && D == 2) is_star = g.type[h] == kStar;
     int n[2] = {0, 0}, af[2] = {0, 0};
-    Real vf[2][D], nf[2][D];
+    Real vf[2][D], nf[2][D], adf[2] = {0, 0};
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
@@ -1187,9 +1189,16 @@ __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, 
             w.a = rng.words(0, cid, 0);
             if constexpr (two_calls<D>()) w.b = rng.words(0, cid, 1);
         }
-        Real v[D], nrm[D], y[D];
+        Real v[D], nrm[D], y[D], ad = 0;
         int aj = 0;
-        if (is_mesh) {
+        if (is_star) {
+            if constexpr (STAR && D == 2) {   // by arc length, as the plain start
+                Real ct, st;
+                star_at_arclen(g, (double)u01<Real>(w.a.y) * (double)g.area[h], &aj, &ad);
+                angle_cs(g, aj, ad, &ct, &st);
+                star_local(g, ct, st, v, nrm);
+            }
+        } else if (is_mesh) {
             if constexpr (STAR && D == 3) mesh_uniform<Real>(gd, gd->mesh_slot[h], w, v, nrm, &aj);
         } else if (is_ell) {
             if constexpr (STAR && D >= 3) {
@@ -1204,7 +1213,7 @@ __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, 
 #pragma unroll
         for (int c = 0; c < D; ++c) y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + v[c];
         const Real b = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, nrm, nrm);
-        const int part = (is_ell || is_mesh) ? (b >= (Real)0 ? 0 : 1) : vr_part<Real, D>(gd, h, w, b);
+        const int part = (is_ell || is_mesh || is_star) ? (b >= (Real)0 ? 0 : 1) : vr_part<Real, D>(gd, h, w, b);
         if (n[part] == 0) {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -1212,6 +1221,7 @@ __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, 
                 nf[part][c] = nrm[c];
             }
             af[part] = aj;
+            adf[part] = ad;
         }
         ++n[part];
     }
@@ -1221,7 +1231,7 @@ __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, 
         q.T = 1;
         q.s = h;
         q.aj = af[k];
-        q.ad = 0;
+        q.ad = adf[k];
         q.alive = n[k] > 0 && gd->flux_basis[h] != kFluxZero;
         Real y[D];
 #pragma unroll
@@ -1572,7 +1582,7 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
         if (i > 0) S *= g.alpha_sign[h];
         const int rel = (i > 0) ? relation(g, hp, h) : 0;
         bool trials = false;
-        if constexpr (VR && D >= 3) {
+        if constexpr (VR) {
             if (i == 0 && gd->part_len[h][0] < 0.0) {
                 vr_trials_start<Real, D, STAR>(g, gd, h, w0, rng, ch);
                 trials = true;

@@ -96,12 +96,6 @@ def test_estimate_argument_checks_and_no_device(woi):
     with pytest.raises(woi.WoiError) as e:
         woi.woi_estimate(g, pts, 1000, sched_group=32)           # 1000 is not a multiple of 32
     assert e.value.status == 1
-    g2 = woi.Geometry(wl.manufactured_instance(2, np.random.default_rng(3), k_max=4))
-    with pytest.raises(woi.WoiError) as e:
-        woi.woi_estimate(g2, wl.ball_points(4, 2, 1, radius=0.5), 1024,
-                         variant="vr")                            # VR in 2D needs Fourier data
-    assert e.value.status == 4
-    g2.close()
     with pytest.raises(woi.WoiError) as e:
         woi.woi_estimate(g, pts, 1024, M=40)
     assert e.value.status == 1
@@ -110,11 +104,14 @@ def test_estimate_argument_checks_and_no_device(woi):
         with pytest.raises(woi.WoiError) as e:
             woi.woi_estimate(g, pts, 1024)
         assert e.value.status == 5
-        # the variance-reduced walk passes the option checks in d >= 3 (hemispheres or
-        # trials) on spheres, ellipsoids and meshes: only the missing device stops it
+        # the variance-reduced walk passes the option checks everywhere (2D arcs or trials,
+        # d >= 3 hemispheres or trials) on circles, spheres, ellipsoids and meshes: only the
+        # missing device stops it
         ell = wl.ellipsoids_problem(3)
         rocks = wl.rocks_problem(n_rocks=1, subdiv_outer=1, subdiv_rock=1, M=3)
-        for prob, x in ((wl.nested_3d_problem(), pts), (wl.linear_3d_problem(), pts),
+        man2 = wl.manufactured_instance(2, np.random.default_rng(3), k_max=4)
+        for prob, x in ((man2, wl.ball_points(4, 2, 1, radius=0.5)),
+                        (wl.nested_3d_problem(), pts), (wl.linear_3d_problem(), pts),
                         (wl.nested_6d_problem(), wl.ball_points(4, 6, 1)),
                         (ell, wl.ellipsoid_points(ell, 4, seed=1)), (rocks, wl.mesh_points(rocks, 4, seed=1))):
             gv = woi.Geometry(prob)

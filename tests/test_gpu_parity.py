@@ -79,6 +79,7 @@ def cases():
     for dim in (2, 3):
         inst = wl.manufactured_instance(dim, rng, k_max=12)
         yield f"manufactured-{dim}d", inst, wl.ball_points(3, dim, 40 + dim, radius=0.9), "plain"
+        yield f"manufactured-{dim}d-vr", inst, wl.ball_points(2, dim, 50 + dim, radius=0.9), "vr"
     for dim in (3, 6):
         ell = wl.ellipsoids_problem(dim)
         yield f"ellipsoids-{dim}d", ell, wl.ellipsoid_points(ell, 3, seed=50 + dim), "plain"
