@@ -1140,7 +1140,7 @@ __device__ void mesh_step(const DevGeom *gd, Real area, int h, int rel, const St
     ch.s = h;
 }
 
-// the part (0: beta >= 0, 1: beta < 0) of a uniform start point on a d >= 3 sphere, from
+// the part (0: beta >= 0, 1: beta < 0) of a uniform start point on a circle or sphere, from
 // its direction's words w and beta b evaluated in Real.  In FP32, where |b| is within the
 // surface's tolerance of 0 (the FP32 error is far below it), the sign is taken again in
 // FP64 from the same words, so that the part is the one an FP64 evaluation gives.
@@ -1161,8 +1161,8 @@ __device__ __forceinline__ int vr_part(const DevGeom *gd, int h, const StepWords
 
 // VR start where the parts have no closed form (d >= 3, and 2D data other than a Fourier
 // series): kVrTrials uniform points on dOmega_h (the circle / sphere, star, ellipsoid or mesh
-// sampler) shared by both chains (trial t draws the step-0
-// words of chain id t << 12; trial 0 is chain 0's own).  Chain k starts at the first trial of
+// sampler) shared by both chains (trial t draws the step-0 words of chain id t << 12; trial 0
+// is chain 0's own).  Chain k starts at the first trial of
 // its sign with Q = beta |dOmega| C_k / kVrTrials, C_k the trials of that sign: an unbiased
 // estimate of |dOmega^+/-| / |dOmega| that is independent of where the first trial of that
 // sign lies, so the chain's term has Algorithm 3's mean.  No trial of a sign: that chain is
