@@ -163,6 +163,29 @@ def test_vr_trial_weight_is_the_part_fraction(oracle_core):
         assert abs(frac.mean() - p_exact) < 5 * frac.std() / np.sqrt(len(frac))
 
 
+def test_vr_trial_weight_on_a_circle(oracle_core):
+    """2D trial start on a circle with the harmonic-polynomial data n . grad(x_1 x_2) =
+    R sin 2 theta (zero mean; its sign parts are four quarter arcs, half the circle each):
+    the start weights average the part fraction 1/2, and every start lies on the circle
+    in the part of its sign."""
+    R = 0.8
+    prob = {"dim": 2, "surfaces": [wl._sphere([0.0, 0.0], R)], "parent": [-1], "sigma": [1.0],
+            "flux": [wl.harmonic_poly(1.0, [(1.0, (1, 1))], 2)], "M": 0}
+    prep = oracle_core.Prepared(prob, "vr")
+    assert np.all(prep.part_len < 0)
+    ow = oracle_core.walks(prob, np.array([0.1, 0.2]), np.arange(3000, dtype=np.uint64), seed=4, M=0,
+                           variant="vr", prepared=prep)
+    for k, sgn in ((0, 1.0), (1, -1.0)):
+        alive = ow["Q"][:, k, 0] != 0            # no trial of that sign (2^-16): the chain is dead
+        y = ow["Y"][alive, k, 0]
+        assert np.allclose(np.linalg.norm(y, axis=1), R, atol=1e-13)
+        beta = np.array([prep.beta_scale[0] * oracle_core.flux_at(prob, 0, yy, prepared=prep) for yy in y])
+        assert np.all(sgn * beta > 0)
+        frac = np.zeros(len(alive))
+        frac[alive] = ow["Q"][alive, k, 0] / (beta * prep.area[0])
+        assert abs(frac.mean() - 0.5) < 5 * frac.std() / np.sqrt(len(frac))
+
+
 def test_vr_trial_weight_mistake_is_detected(oracle_core):
     """A planted mistake: the trial start weighs beta by |dOmega| / 2 (as if the parts
     were halves); the zonal case's parts are not, and the exact mean catches it."""
