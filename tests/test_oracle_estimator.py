@@ -155,9 +155,11 @@ def test_vr_trial_weight_is_the_part_fraction(oracle_core):
     on_outer = ow["H"][:, 0] == 0
     area = prep.area[0]
     for k, p_exact in ((0, 1 - 1 / np.sqrt(3)), (1, 1 / np.sqrt(3))):
-        y = ow["Y"][on_outer, k, 0]
+        alive = ow["Q"][on_outer, k, 0] != 0     # no trial of that sign: the chain is dead
+        y = ow["Y"][on_outer, k, 0][alive]
         beta = np.array([prep.beta_scale[0] * oracle_core.flux_at(prob, 0, yy, prepared=prep) for yy in y])
-        frac = ow["Q"][on_outer, k, 0] / (beta * area)
+        frac = np.zeros(len(alive))
+        frac[alive] = ow["Q"][on_outer, k, 0][alive] / (beta * area)
         assert np.all(np.abs(frac * 16 - np.round(frac * 16)) < 1e-9)     # a count of 16 trials
         assert np.all(np.sign(beta) == (1 if k == 0 else -1))
         assert abs(frac.mean() - p_exact) < 5 * frac.std() / np.sqrt(len(frac))
