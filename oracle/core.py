@@ -76,8 +76,10 @@ def lib():
         _lib.or_walks.argtypes = [P(OrProblem), P(OrOpts), ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                  ctypes.c_void_p]
+                                  ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_set_mutant.argtypes = [ctypes.c_int]
+        _lib.or_set_mutant_bound.argtypes = [ctypes.c_int]
+        _lib.or_set_perturb.argtypes = [ctypes.c_double]
         _lib.or_threads.argtypes = [ctypes.c_int]
         _lib.or_threads.restype = ctypes.c_int
         _lib.or_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -117,6 +119,18 @@ class OrOpts(ctypes.Structure):
 def set_mutant(m: int) -> None:
     """Plant one of the numbered mistakes in the C oracle (tests only; 0 = none)."""
     lib().or_set_mutant(int(m))
+
+
+def set_mutant_bound(m: int) -> None:
+    """Plant a mistake in the per-walk error bound (tests only; 1 drops the states'
+    term, 0 = none)."""
+    lib().or_set_mutant_bound(int(m))
+
+
+def set_perturb(rel: float) -> None:
+    """Move every walk state y on surface s by rel |y - c_s| and the evaluation
+    point by rel |x - c_s| per tally (tests of the error bound only; 0 = exact)."""
+    lib().or_set_perturb(float(rel))
 
 
 def philox4x32_10(ctr, key):
@@ -532,7 +546,13 @@ def finalize(sf, sm, sm2, n_walks, G):
 def walks(problem, x, walk_ids, seed=0, M=None, variant="plain", sched_group=1, point_id=0, instance=0,
           prepared=None):
     """Per-walk values N * sum_i c_i Phi(x, y_i) and the gradient tally, with
-    the schedule, the states and the magnitude scales, for pathwise replay."""
+    the schedule, the states, Q and T, for pathwise replay.  "scale"[:, 0] and
+    [:, 1] are the walk's first-order error bounds B_u and B_g (a computation
+    of the walk rounded with unit roundoff u differs by about u B from the exact
+    one), [:, 2] the walk's conditioning (the largest amplification of a state
+    error by consecutive line / ray steps), [:, 3] the largest ratio of the start
+    flux's term magnitudes to its value; "E_y" and "E_Q" [n, 2, M+1] the error
+    bounds of each state y_i and of Q_i in the same units."""
     prep = prepared or Prepared(problem, variant)
     M = problem["M"] if M is None else M
     d = prep.dim
@@ -545,11 +565,13 @@ def walks(problem, x, walk_ids, seed=0, M=None, variant="plain", sched_group=1, 
     Y = np.zeros((n, 2, M + 1, d))
     sc = np.zeros((n, 4))
     QT = np.zeros((n, 2, M + 1, 2))
+    E = np.zeros((n, 2, M + 1, 2))
     o = _opts(M, variant, sched_group)
     lib().or_walks(ctypes.byref(prep.struct), ctypes.byref(o), x.ctypes.data, point_id, instance, ids.ctypes.data,
                    n, seed, fu.ctypes.data, fg.ctypes.data, H.ctypes.data, Y.ctypes.data, sc.ctypes.data,
-                   QT.ctypes.data)
-    return {"u": fu, "grad": fg, "H": H, "Y": Y, "scale": sc, "Q": QT[..., 0], "T": QT[..., 1]}
+                   QT.ctypes.data, E.ctypes.data)
+    return {"u": fu, "grad": fg, "H": H, "Y": Y, "scale": sc, "Q": QT[..., 0], "T": QT[..., 1],
+            "E_y": E[..., 0], "E_Q": E[..., 1]}
 
 
 def flux_at(problem, h, y, prepared=None, tri=-1):

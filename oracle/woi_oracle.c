@@ -423,6 +423,29 @@ static void or_uniform_point(const or_problem *P, int h, or_rng *r, int step, in
 
 /* uniform point on dOmega_h^+ (part = 0) or dOmega_h^- (part = 1): the arcs of
  * the requested sign are concatenated in increasing parameter angle */
+static double or_flux(const or_problem *P, int h, int tri, const double *y);
+
+/* |grad_y b_h(y)| by central differences of the flux as it is evaluated off the surface too
+ * (error bound of the tests only: how fast b_h changes when its point moves) */
+static double or_flux_grad_mag(const or_problem *P, int h, int tri, const double *y)
+{
+    const int d = P->dim;
+    const double *c = or_center(P, h);
+    double r = 0.0;
+    for (int k = 0; k < d; ++k) r += (y[k] - c[k]) * (y[k] - c[k]);
+    const double step = 1e-6 * fmax(sqrt(r), 1e-3);
+    double g2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double yp[OR_MAX_DIM], ym[OR_MAX_DIM];
+        for (int j = 0; j < d; ++j) yp[j] = ym[j] = y[j];
+        yp[k] += step;
+        ym[k] -= step;
+        const double g = (or_flux(P, h, tri, yp) - or_flux(P, h, tri, ym)) / (2.0 * step);
+        g2 += g * g;
+    }
+    return sqrt(g2);
+}
+
 static double or_beta(const or_problem *P, int h, int tri, const double *y);
 
 static void or_uniform_part_point(const or_problem *P, int h, int part, or_rng *r, int step, int chain,
@@ -507,6 +530,14 @@ static int or_intersections(const or_problem *P, int h, const double *y, const d
             b += z[k] * (y[k] - c[k]);
             c0 += (y[k] - c[k]) * (y[k] - c[k]);
         }
+        if (!ray) {
+            /* a line through y on the sphere: |y + t z - c|^2 = R^2 with |y - c| = R leaves
+             * t (t + 2 b) = 0, so the one intersection distinct from y is t = -2 b (the
+             * reflection of y - c in the plane normal to z) */
+            double t = -2.0 * b;
+            if (fabs(t) > tiny * R) ts[q++] = t;
+            return q;
+        }
         c0 -= R * R;
         double disc = b * b - c0;
         if (disc < 0.0) return 0;
@@ -532,6 +563,13 @@ static int or_intersections(const or_problem *P, int h, const double *y, const d
                 b1 += z[k] * Akj * dy[j];
                 c0 += dy[k] * Akj * dy[j];
             }
+        if (!ray) {
+            /* a line through y on the ellipsoid: c0 = 0 there, so a2 t^2 + 2 b1 t = 0 and the
+             * intersection distinct from y is t = -2 b1 / a2 */
+            double t = -2.0 * b1 / a2;
+            if (fabs(t) > tiny / P->ell_jmax[h]) ts[q++] = t;
+            return q;
+        }
         double disc = b1 * b1 - a2 * c0;
         if (disc < 0.0) return 0;
         double sq = sqrt(disc);
@@ -788,11 +826,59 @@ static double or_beta(const or_problem *P, int h, int tri, const double *y)
 typedef struct {
     int *H;          /* [M+1] scheduled interfaces (0-based), or NULL */
     double *Y;       /* [2][M+1][dim] states of each chain, or NULL */
-    double *scale;   /* [4]: sum_i |c_i Phi_i|, sum_i |c_i|, sum_i |c_i| |grad Phi_i| (both chains), and
-                        the walk's conditioning (>= 1): the larger of (term magnitude of beta(y_0)) /
-                        |beta(y_0)| and, over its chords on curved surfaces, (|y - c| + |y' - c|) / |t| */
+    double *scale;   /* [4], see the error bound below: B_u, B_g, the walk's conditioning
+                        (largest running amplification of a state error by line / ray steps) and
+                        the largest ratio (sum of the magnitudes of the start flux's terms) / |flux| */
     double *QT;      /* [2][M+1][2]: Q_i and T_i of each chain, or NULL */
+    double *E;       /* [2][M+1][2]: the error bounds e_i of y_i and Qe_i of Q_i (units of u), or NULL */
 } or_trace;
+
+/* Per-walk first-order error bound (test tolerance, not part of the estimator).
+ * A computation of the same walk whose every operation is rounded with unit
+ * roundoff u differs from the exact one by at most about u B_u in the u tally and
+ * u B_g in the gradient tally, where, summed over the tallied states of both chains,
+ *   B_u = sum |C_i T_i| [ Qe_i (|Phi_i| + 1) + |Q_i| (|Phi_i| + 1 + |grad Phi_i| (e_i + r_x)) ]
+ *   B_g = sum |C_i T_i| [ Qe_i |grad Phi_i| + |Q_i| (|grad Phi_i| + |D2 Phi_i| (e_i + r_x)) ]
+ * with C_i = N w_i ||alpha||_1^i prod sign(alpha), |D2 Phi| = (d - 1) / (omega_d r^d) the norm of
+ * the Hessian of Phi, r_x = |x - c_s| (x is rounded relative to the state's surface centre),
+ * and, in units of u:
+ *   e_i   a bound on the error of the state y_i: |y - c_s| for a fresh sample (start, uniform
+ *         transition); a reflection chord (line on a sphere or ellipsoid, t = -2 b) adds
+ *         |y' - c|; a line or ray whose intersection is found as a root multiplies the
+ *         incoming error by 1 + 1 / |n(y') . z| (moving the line by delta moves a crossing
+ *         at angle acos|n . z| to the normal by delta / |n . z| along it) and adds |y' - c|;
+ *   Qe_i  a bound on the error of Q_i: the start flux contributes |beta scale| (sum of the
+ *         magnitudes of its terms + |grad b| e_0) |part|, a uniform transition the first-order
+ *         change of K*(y', y) under the errors of y, y' and of the normal at y', a line step
+ *         halves it.
+ * The walk's conditioning is the largest product of root-step amplifications since the
+ * last fresh sample. */
+static int or_mutant_bound = 0;  /* test hook: 1 drops the states' term from the bound */
+void or_set_mutant_bound(int m) { or_mutant_bound = m; }
+
+/* Test hook: every new walk state y on surface s is moved by or_perturb |y - c_s| and the
+ * evaluation point by or_perturb |x - c_s| in each tally (a stand-in for rounding, in a
+ * pseudo-random direction), so that a test can compare the change of the tallies with the
+ * bound above.  0 (the default) leaves the walk exact. */
+static double or_perturb = 0.0;
+void or_set_perturb(double rel) { or_perturb = rel; }
+
+static void or_perturb_vec(int d, uint64_t walk, int i, int k, int tag, double mag, double *v)
+{
+    uint64_t z = (walk + 1) * 0x9E3779B97F4A7C15ull + (uint64_t)(i * 64 + k * 8 + tag + 1) * 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 31;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 29;
+    const double s = mag / sqrt((double)d);
+    for (int c = 0; c < d; ++c) v[c] += ((z >> (3 * c)) & 1) ? s : -s;
+}
+
+static double or_norm_rel(int d, const double *y, const double *c)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s += (y[k] - c[k]) * (y[k] - c[k]);
+    return sqrt(s);
+}
 
 /* H_i: 0-based index; i = 0 uniform over the N surfaces, i >= 1 by |alpha| */
 static int or_schedule_from_word(const or_problem *P, int i, uint32_t w)
@@ -817,10 +903,11 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     const int n_chain = o->variant == 1 ? 2 : 1;
     or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32) ^ instance}, walk, -1, -1, -1, {0}};
     uint64_t group = walk / (uint64_t)o->sched_group;
-    double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0}, sc_phi = 0.0, sc_c = 0.0, sc_g = 0.0;
+    double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0};
 
     double y[2][OR_MAX_DIM], Q[2], T[2];
-    double cond0 = 1.0;
+    double Qe[2] = {0.0, 0.0}, ey[2] = {0.0, 0.0}, amp[2] = {1.0, 1.0};   /* error bound, see above */
+    double B_u = 0.0, B_g = 0.0, cond = 1.0, flux_ratio = 1.0;
     int alive[2] = {1, 1};
     int tri[2] = {-1, -1};   /* mesh triangle of each chain's state (-1 elsewhere) */
     int trial_n[2] = {0, 0}, trial_tri[2] = {-1, -1};   /* VR start by uniform trials */
@@ -828,6 +915,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
     double S = 1.0;          /* prod_{m=1}^{i} sign(alpha_{H_m}): alpha_{H_0} never enters the expansion */
     double Ai = 1.0;         /* ||alpha||_1^i */
     int h_prev = -1;
+    const double omega = or_omega(d);
 
     for (int i = 0; i <= M; ++i) {
         const double weight = (i == M && or_mutant != 3) ? 0.5 : 1.0; /* w_i = 1 - delta_{iM}/2 */
@@ -841,6 +929,7 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
         }
         const int h = or_schedule_from_word(P, i, hw);
         if (tr && tr->H) tr->H[i] = h;
+        const double *ch = or_center(P, h);
 
         if (i > 0 || or_mutant == 2) {
             if (i > 0) Ai *= P->alpha_l1;
@@ -851,11 +940,10 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
             if (i == 0) {
                 /* p0: uniform on dOmega_{h0} (plain) or on dOmega^{+/-} (Alg. 3) */
                 T[k] = 1.0;
+                double L = P->area[h];
+                int start = 1;
                 if (o->variant == 0) {
                     or_uniform_point(P, h, &rng, 0, k, y[k], &tri[k]);
-                    Q[k] = or_beta(P, h, tri[k], y[k]) * P->area[h];
-                    double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
-                    if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
                 } else if (P->part_len[2 * h] < 0.0) {
                     /* parts of no closed form: K uniform trials on dOmega_h, shared by
                      * both chains (trial t draws the step-0 words of chain id t << 12).  Chain k starts
@@ -876,37 +964,47 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                         }
                     }
                     if (trial_n[k] == 0 || P->flux_basis[h] == OR_FLUX_ZERO) {
-                        alive[k] = 0; Q[k] = 0.0;
+                        alive[k] = 0; Q[k] = 0.0; start = 0;
                         for (int c = 0; c < d; ++c) y[k][c] = 0.0;
                     } else {
                         for (int c = 0; c < d; ++c) y[k][c] = trial_y[k][c];
                         tri[k] = trial_tri[k];
-                        const double frac = or_mutant == 11 ? 0.5 : (double)trial_n[k] / OR_VR_TRIALS;
-                        Q[k] = or_beta(P, h, tri[k], y[k]) * P->area[h] * frac;
-                        double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
-                        if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
+                        L *= or_mutant == 11 ? 0.5 : (double)trial_n[k] / OR_VR_TRIALS;
                     }
                 } else {
-                    double L = P->part_len[2 * h + k];
+                    L = P->part_len[2 * h + k];
                     if (L <= 0.0 || P->flux_basis[h] == OR_FLUX_ZERO) {
                         /* empty part, or beta = 0 on the whole surface: the chain carries no weight */
-                        alive[k] = 0; Q[k] = 0.0;
+                        alive[k] = 0; Q[k] = 0.0; start = 0;
                         for (int c = 0; c < d; ++c) y[k][c] = 0.0;
                     } else {
                         or_uniform_part_point(P, h, k, &rng, 0, k, y[k]);
-                        Q[k] = or_beta(P, h, -1, y[k]) * L;
-                        double b0 = fabs(or_flux(P, h, -1, y[k])), bm = or_flux_mag(P, h, -1, y[k]);
-                        if (b0 > 0.0 && bm / b0 > cond0) cond0 = bm / b0;
+                        tri[k] = -1;
                     }
+                }
+                if (start) {
+                    const double ry = or_norm_rel(d, y[k], ch);
+                    if (or_perturb > 0.0) or_perturb_vec(d, walk, i, k, 0, or_perturb * ry, y[k]);
+                    Q[k] = or_beta(P, h, tri[k], y[k]) * L;
+                    const double b0 = fabs(or_flux(P, h, tri[k], y[k])), bm = or_flux_mag(P, h, tri[k], y[k]);
+                    if (b0 > 0.0 && bm / b0 > flux_ratio) flux_ratio = bm / b0;
+                    /* the flux's rounding (its terms' magnitudes) and its change under the
+                     * start's own error |y - c_h| */
+                    Qe[k] = fabs(P->beta_scale[h]) * (bm + or_flux_grad_mag(P, h, tri[k], y[k]) * ry) * L;
+                    ey[k] = ry;
+                    amp[k] = 1.0;
                 }
             } else if (alive[k]) {
                 const int rel = or_relation(P, h_prev, h);
+                const double dc = or_dist(d, or_center(P, h_prev), ch);   /* centres: rounding of y - c_h */
                 double ynew[OR_MAX_DIM];
                 int tnew = -1;
                 if (rel == OR_REL_OTHER) {
                     /* uniform on dOmega_h; Q *= K*(y_i, y_{i-1}) |dOmega_h| with the normal at the new
                      * point; T unchanged (the sign is already in K*) */
                     or_uniform_point(P, h, &rng, i, k, ynew, &tnew);
+                    const double rn = or_norm_rel(d, ynew, ch);
+                    if (or_perturb > 0.0) or_perturb_vec(d, walk, i, k, 0, or_perturb * rn, ynew);
                     double nrm[OR_MAX_DIM], dot = 0.0;
                     if (or_mutant == 5) {
                         or_normal(P, h_prev, tri[k], y[k], nrm);
@@ -916,9 +1014,17 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                         for (int c = 0; c < d; ++c) dot += (ynew[c] - y[k][c]) * nrm[c];
                     }
                     double r = or_dist(d, ynew, y[k]);
-                    double kstar = dot / (or_omega(d) * pow(r, (double)d));
+                    double kstar = dot / (omega * pow(r, (double)d));
+                    /* error bound: the difference y' - y carries the errors of both states and of
+                     * the centres; the normal turns by (error of y') / |y' - c_h| = 1, which moves
+                     * the dot product by r */
+                    const double et = ey[k] + dc + rn;
+                    const double dK = (et + r + d * fabs(dot) * et / r) / (omega * pow(r, (double)d)) + fabs(kstar);
+                    Qe[k] = fabs(kstar * P->area[h]) * Qe[k] + fabs(Q[k]) * P->area[h] * dK;
                     Q[k] *= kstar * P->area[h];
                     if (or_mutant == 1) T[k] *= dot > 0.0 ? 1.0 : -1.0;
+                    ey[k] = rn;
+                    amp[k] = 1.0;
                 } else {
                     /* isotropic line (same interface) or ray (from a descendant) */
                     double z[OR_MAX_DIM], ts[OR_MAX_ROOTS];
@@ -935,25 +1041,32 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                     int j = (int)(((uint64_t)cw * (uint64_t)q) >> 32);
                     for (int c = 0; c < d; ++c) ynew[c] = y[k][c] + ts[j] * z[c];
                     tnew = P->type[h] == OR_MESH ? hits[j] : -1;
-                    double nrm[OR_MAX_DIM], dot = 0.0;
+                    const double rn = or_norm_rel(d, ynew, ch);
+                    double nrm[OR_MAX_DIM], dot = 0.0, nz = 0.0;
                     or_normal(P, h, tnew, ynew, nrm);
-                    for (int c = 0; c < d; ++c) dot += (ynew[c] - y[k][c]) * nrm[c];
-                    double sg = dot > 0.0 ? 1.0 : (dot < 0.0 ? -1.0 : 0.0);
-                    if (rel == OR_REL_SAME && or_mutant != 7) Q[k] *= 0.5;
-                    T[k] *= (double)q * sg;
-                    if (rel == OR_REL_SAME && P->type[h] != OR_MESH) {
-                        /* a chord nearly tangent to a curved surface moves its far end by
-                         * (|y - c| + |y' - c|) / |t| times any rounding of the start's distance
-                         * from the surface: a conditioning factor of the walk (replay tolerance) */
-                        const double *ch = or_center(P, h);
-                        double ra = 0.0, rb = 0.0;
-                        for (int c = 0; c < d; ++c) {
-                            ra += (y[k][c] - ch[c]) * (y[k][c] - ch[c]);
-                            rb += (ynew[c] - ch[c]) * (ynew[c] - ch[c]);
-                        }
-                        const double amp = (sqrt(ra) + sqrt(rb)) / fabs(ts[j]);
-                        if (amp > cond0) cond0 = amp;
+                    for (int c = 0; c < d; ++c) {
+                        dot += (ynew[c] - y[k][c]) * nrm[c];
+                        nz += z[c] * nrm[c];
                     }
+                    double sg = dot > 0.0 ? 1.0 : (dot < 0.0 ? -1.0 : 0.0);
+                    if (rel == OR_REL_SAME && or_mutant != 7) {
+                        Q[k] *= 0.5;
+                        Qe[k] *= 0.5;
+                    }
+                    T[k] *= (double)q * sg;
+                    /* error bound: a chord of a sphere or ellipsoid is the reflection t = -2 b, which
+                     * does not amplify an error of y; a crossing found as a root moves by the error
+                     * over |n . z| */
+                    const int reflect = rel == OR_REL_SAME && (P->type[h] == OR_SPHERE || P->type[h] == OR_ELLIPSOID);
+                    if (reflect) {
+                        ey[k] = ey[k] + rn;
+                    } else {
+                        const double a = 1.0 + 1.0 / fmax(fabs(nz), 1e-300);
+                        ey[k] = (ey[k] + dc) * a + rn;
+                        amp[k] *= a;
+                        if (amp[k] > cond) cond = amp[k];
+                    }
+                    if (or_perturb > 0.0) or_perturb_vec(d, walk, i, k, 0, or_perturb * rn, ynew);
                 }
                 for (int c = 0; c < d; ++c) y[k][c] = ynew[c];
                 tri[k] = tnew;
@@ -964,24 +1077,37 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                 tr->QT[((size_t)k * (M + 1) + i) * 2] = Q[k];
                 tr->QT[((size_t)k * (M + 1) + i) * 2 + 1] = T[k];
             }
+            if (tr && tr->E) {
+                tr->E[((size_t)k * (M + 1) + i) * 2] = ey[k];
+                tr->E[((size_t)k * (M + 1) + i) * 2 + 1] = Qe[k];
+            }
             if (!alive[k]) continue;
             /* tally: N w_i ||alpha||^i prod sign(alpha) Q T Phi(x, y_i), and grad_x Phi */
-            double coef = (or_mutant == 4 ? 1.0 : (double)N) * weight * Ai * S * Q[k] * T[k];
-            double phi = or_phi(d, x, y[k]), g[OR_MAX_DIM];
-            or_grad_phi(d, x, y[k], g);
+            const double C = (or_mutant == 4 ? 1.0 : (double)N) * weight * Ai * S;
+            double coef = C * Q[k] * T[k];
+            const double rx = or_norm_rel(d, x, ch);
+            double xp[OR_MAX_DIM];
+            for (int c = 0; c < d; ++c) xp[c] = x[c];
+            if (or_perturb > 0.0) or_perturb_vec(d, walk, i, k, 1, or_perturb * rx, xp);
+            double phi = or_phi(d, xp, y[k]), g[OR_MAX_DIM];
+            or_grad_phi(d, xp, y[k], g);
             acc_u += coef * phi;
             for (int c = 0; c < d; ++c) acc_g[c] += coef * g[c];
-            sc_phi += fabs(coef * phi);
-            sc_c += fabs(coef);
             double gn = 0.0;
             for (int c = 0; c < d; ++c) gn += g[c] * g[c];
-            sc_g += fabs(coef) * sqrt(gn);
+            gn = sqrt(gn);
+            const double r = or_dist(d, x, y[k]);
+            const double hess = (d - 1) / (omega * pow(r, (double)d));
+            const double near = or_mutant_bound == 1 ? 0.0 : ey[k] + rx;
+            const double CT = fabs(C * T[k]);
+            B_u += CT * (Qe[k] * (fabs(phi) + 1.0) + fabs(Q[k]) * (fabs(phi) + 1.0 + gn * near));
+            B_g += CT * (Qe[k] * gn + fabs(Q[k]) * (gn + hess * near));
         }
         h_prev = h;
     }
     *out_u = acc_u;
     for (int c = 0; c < d; ++c) out_g[c] = acc_g[c];
-    if (tr && tr->scale) { tr->scale[0] = sc_phi; tr->scale[1] = sc_c; tr->scale[2] = sc_g; tr->scale[3] = cond0; }
+    if (tr && tr->scale) { tr->scale[0] = B_u; tr->scale[1] = B_g; tr->scale[2] = cond; tr->scale[3] = flux_ratio; }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1027,12 +1153,15 @@ int or_estimate(const or_problem *P, const or_opts *o, const double *points, int
 /* per-walk values for pathwise replay: walks[w] for one point */
 void or_walks(const or_problem *P, const or_opts *o, const double *x, uint32_t point_id, uint32_t instance,
               const uint64_t *walks, int64_t n_walks, uint64_t seed, double *out_u, double *out_g, int *out_H,
-              double *out_Y, double *out_scale, double *out_QT)
+              double *out_Y, double *out_scale, double *out_QT, double *out_E)
 {
     const int d = P->dim, M = o->M;
+    /* walks are independent and write disjoint output slots */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t w = 0; w < n_walks; ++w) {
         or_trace tr = {out_H ? out_H + w * (M + 1) : NULL, out_Y ? out_Y + (size_t)w * 2 * (M + 1) * d : NULL,
-                       out_scale ? out_scale + 4 * w : NULL, out_QT ? out_QT + (size_t)w * 2 * (M + 1) * 2 : NULL};
+                       out_scale ? out_scale + 4 * w : NULL, out_QT ? out_QT + (size_t)w * 2 * (M + 1) * 2 : NULL,
+                       out_E ? out_E + (size_t)w * 2 * (M + 1) * 2 : NULL};
         or_walk(P, o, x, point_id, instance, walks[w], seed, out_u + w, out_g + w * d, &tr);
     }
 }

@@ -291,6 +291,32 @@ def star_inclusions_points(problem, n, seed=13, near_frac=0.3, band=0.01):
     return out[rng.permutation(len(out))]
 
 
+def near_surface_points(problem, i, deltas, side=-1, seed=0):
+    """One point per entry of `deltas`, at normal distance delta from surface i
+    (a circle, a d-sphere or a 2D star), on its inner side (side = -1) or its
+    outer side (side = +1), each at a random position along the surface."""
+    rng = np.random.default_rng(seed)
+    s = problem["surfaces"][i]
+    c = np.asarray(s["center"], dtype=np.float64)
+    out = []
+    for dl in deltas:
+        if s["kind"] == "sphere":
+            g = rng.standard_normal(len(c))
+            g /= np.linalg.norm(g)
+            out.append(c + (s["radius"] + side * dl) * g)
+        elif s["kind"] == "star":
+            a, b, R = s["star_a"], s["star_b"], s["radius"]
+            t = rng.uniform(0.0, 2.0 * np.pi)
+            r = R * _star_radius(a, b, np.array([t]))[0]
+            dr = R * sum(k * (b[k] * np.cos(k * t) - a[k] * np.sin(k * t)) for k in range(1, len(a)))
+            tang = np.array([dr * np.cos(t) - r * np.sin(t), dr * np.sin(t) + r * np.cos(t)])
+            nrm = np.array([tang[1], -tang[0]]) / np.linalg.norm(tang)
+            out.append(c + r * np.array([np.cos(t), np.sin(t)]) + side * dl * nrm)
+        else:
+            raise ValueError("near_surface_points takes circles, spheres and stars")
+    return np.ascontiguousarray(np.asarray(out, dtype=np.float64))
+
+
 # ---------------------------------------------------------------------------
 # batch of heterogeneous manufactured-solution instances
 # ---------------------------------------------------------------------------
