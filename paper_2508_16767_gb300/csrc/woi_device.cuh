@@ -224,8 +224,11 @@ struct SGeom {
     Real star_a[kMaxStar + 1], star_b[kMaxStar + 1];
     Real star_lmax;                      // bound on |gamma'|
     Real star_kpp;                       // bound on |gamma''|
+    Real star_k3;                        // bound on |gamma'''|
+    Real star_harm[kMaxStar + 2][4];     // gamma - centre = sum_m (X_m cos mt + Y_m sin mt, U_m cos mt + V_m sin mt)
     Real star_rmin, star_rmax;           // annulus that contains the star
     Real scan[kNodes][2];                // gamma(t_j) - centre
+    Real scan_d[kNodes][2];              // gamma'(t_j)
     double panel_s[kNodes + 1];          // arc length at t_j
 };
 
@@ -241,6 +244,7 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.star_K = src->star_K;
         g.star_lmax = (Real)src->star_lmax;
         g.star_kpp = (Real)src->star_kpp;
+        g.star_k3 = (Real)src->star_k3;
         g.star_rmin = (Real)src->star_rmin;
         g.star_rmax = (Real)src->star_rmax;
     }
@@ -274,8 +278,11 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         for (int j = tid; j < kNodes; j += nt) {
             g.scan[j][0] = (Real)src->star_scan[j][0];
             g.scan[j][1] = (Real)src->star_scan[j][1];
+            g.scan_d[j][0] = (Real)src->star_scan_d[j][0];
+            g.scan_d[j][1] = (Real)src->star_scan_d[j][1];
         }
         for (int j = tid; j <= kNodes; j += nt) g.panel_s[j] = src->star_panel_s[j];
+        for (int i = tid; i < (kMaxStar + 2) * 4; i += nt) g.star_harm[i / 4][i % 4] = (Real)src->star_harm[i / 4][i % 4];
     }
 }
 
@@ -370,27 +377,6 @@ __device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st
     const Real R = g.radius[g.star_idx];
     *r = R * s;
     *dr = R * ds;
-}
-
-// r, r' and r'' at the angle (ct, st)
-template <typename Real>
-__device__ __forceinline__ void star_eval2(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr, Real *ddr)
-{
-    Real ck = ct, sk = st, s = 1, ds = 0, dds = 0;
-    for (int k = 1; k <= g.star_K; ++k) {
-        const Real a = g.star_a[k], b = g.star_b[k];
-        const Real ca = a * ck + b * sk;
-        s += ca;
-        ds += (Real)k * (b * ck - a * sk);
-        dds -= (Real)(k * k) * ca;
-        const Real cn = ck * ct - sk * st;
-        sk = sk * ct + ck * st;
-        ck = cn;
-    }
-    const Real R = g.radius[g.star_idx];
-    *r = R * s;
-    *dr = R * ds;
-    *ddr = R * dds;
 }
 
 // local point r (cos t, sin t), outward unit normal and |gamma'| at the angle (ct, st)
@@ -491,30 +477,88 @@ __device__ __forceinline__ void star_line_f(const SGeom<Real> &g, int j, Real de
     *df = tx * z[1] - ty * z[0];
 }
 
-// f'(delta) = gamma' x z and f''(delta) = gamma'' x z
+// The line through the state y = gamma(s) on the star, in direction z: its other intersections
+// are the roots of g(t) = [(gamma(t) - gamma(s)) / (t - s)] x z, the divided difference of the
+// curve crossed with z (g(s) = gamma'(s) x z; no root at s itself).  With gamma a trigonometric
+// polynomial of degree K + 1,
+//   (cos mt - cos ms) / (t - s) = -m sin(m c) S(m h),  (sin mt - sin ms) / (t - s) = m cos(m c) S(m h),
+// c = (t + s) / 2, h = (t - s) / 2, S(x) = sin(x) / x, so every term is formed to relative
+// accuracy: no cancellation between gamma(t) and a rounded gamma(s) however close t is to s (a
+// near-tangent line).  t = t_j + delta, s = t_js + ds.  Returns g and g' in *gv, *gd, and in
+// *dz the divided difference dotted with z, so that t - s times it is the line parameter.
 template <typename Real>
-__device__ __forceinline__ void star_line_df(const SGeom<Real> &g, int j, Real delta, const Real *z, Real *df,
-                                             Real *ddf)
+__device__ void star_dd(const SGeom<Real> &g, int j, Real delta, int js, Real ds, const Real *z, Real *gv, Real *gd,
+                        Real *dz)
 {
-    Real ct, st, r, dr, ddr;
-    angle_cs(g, j, delta, &ct, &st);
-    star_eval2(g, ct, st, &r, &dr, &ddr);
-    const Real tx = dr * ct - r * st, ty = dr * st + r * ct;
-    const Real ax = (ddr - r) * ct - (Real)2 * dr * st, ay = (ddr - r) * st + (Real)2 * dr * ct;
-    *df = tx * z[1] - ty * z[0];
-    *ddf = ax * z[1] - ay * z[0];
+    using O = RealOps<Real>;
+    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
+    int dj = j - js;
+    if (dj > kNodes / 2) dj -= kNodes;
+    if (dj < -kNodes / 2) dj += kNodes;
+    const Real h = (Real)0.5 * ((Real)dj * H + (delta - ds));
+    Real cc, sc;                                             // c = t_j + (delta + ds - dj H) / 2
+    angle_cs(g, j, (Real)0.5 * (delta + ds - (Real)dj * H), &cc, &sc);
+    Real sh, ch;
+    O::sincos_(h, &sh, &ch);
+    Real cmc = cc, smc = sc, cmh = ch, smh = sh;             // cos / sin of m c and m h, m = 1
+    Real Dx = 0, Dy = 0, dDx = 0, dDy = 0;
+    for (int m = 1; m <= g.star_K + 1; ++m) {
+        const Real x = (Real)m * h, x2 = x * x;
+        Real S, Sp;                                          // S(x) and S'(x)
+        if (O::fabs_(x) < (Real)0.1) {
+            S = (Real)1 - x2 * ((Real)(1.0 / 6.0) - x2 * ((Real)(1.0 / 120.0) - x2 * (Real)(1.0 / 5040.0)));
+            Sp = -x * ((Real)(1.0 / 3.0) - x2 * ((Real)(1.0 / 30.0) - x2 * (Real)(1.0 / 840.0)));
+        } else {
+            S = smh / x;
+            Sp = (cmh - S) / x;
+        }
+        const Real *c = g.star_harm[m];
+        const Real Fx = -c[0] * smc + c[1] * cmc, Fxp = -c[0] * cmc - c[1] * smc;
+        const Real Fy = -c[2] * smc + c[3] * cmc, Fyp = -c[2] * cmc - c[3] * smc;
+        const Real mh = (Real)0.5 * (Real)m;
+        Dx += (Real)m * S * Fx;
+        Dy += (Real)m * S * Fy;
+        dDx += (Real)m * mh * (Sp * Fx + S * Fxp);
+        dDy += (Real)m * mh * (Sp * Fy + S * Fyp);
+        const Real cn = cmc * cc - smc * sc;                 // m + 1
+        smc = smc * cc + cmc * sc;
+        cmc = cn;
+        const Real hn = cmh * ch - smh * sh;
+        smh = smh * ch + cmh * sh;
+        cmh = hn;
+    }
+    *gv = Dx * z[1] - Dy * z[0];
+    *gd = dDx * z[1] - dDy * z[0];
+    if (dz) *dz = Dx * z[0] + Dy * z[1];
 }
 
-// root of f in (a, b) given sign(f(a)) (safeguarded Newton in delta)
+// the function whose roots in scan interval j are the crossings: f(delta) = (gamma - yc) x z
+// (a ray, or a line away from its start), or the divided difference g of the line through the
+// state (js, ds) (dd = true)
 template <typename Real>
-__device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa, const Real *yc, const Real *z,
-                           Real t0 = (Real)-1)
+struct StarLineEval {
+    const SGeom<Real> &g;
+    const Real *yc, *z;
+    int j;
+    bool dd;
+    int js;
+    Real ds;
+    __device__ __forceinline__ void operator()(Real delta, Real *v, Real *dv) const
+    {
+        if (dd) star_dd(g, j, delta, js, ds, z, v, dv, (Real *)nullptr);
+        else star_line_f(g, j, delta, yc, z, v, dv);
+    }
+};
+
+// root in (a, b) given sign(v(a)) (safeguarded Newton in delta)
+template <typename Real>
+__device__ Real star_refine(const StarLineEval<Real> &ev, Real a, Real b, Real fa, Real t0 = (Real)-1)
 {
     Real t = (t0 > a && t0 < b) ? t0 : (Real)0.5 * (a + b);
     const int iters = sizeof(Real) == 4 ? 40 : 90;
     for (int it = 0; it < iters; ++it) {
         Real f, df;
-        star_line_f(g, j, t, yc, z, &f, &df);
+        ev(t, &f, &df);
         if (f == (Real)0) break;
         if ((f < 0) == (fa < 0)) a = t; else b = t;
         const Real step = f / df;
@@ -530,60 +574,93 @@ __device__ Real star_refine(const SGeom<Real> &g, int j, Real a, Real b, Real fa
     return t;
 }
 
-// Roots of f in the scan interval [t_j, t_j+1] (j in [0, kNodes)) appended as candidates:
-// a sign change gives one root; otherwise, where |f| may reach 0 (|f'| <= lmax) and f'
-// changes sign, the extremum decides whether a pair of roots hides in the interval.
+// rounding level of f = (gamma - y) x z and of f' = gamma' x z in the kernel's precision
+template <typename Real>
+__device__ __forceinline__ Real star_f_noise(const SGeom<Real> &g)
+{
+    return (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_rmax;
+}
+// |f| below which a computed value's sign is not trusted (a few units of the rounding of gamma)
+template <typename Real>
+__device__ __forceinline__ Real star_dip_noise(const SGeom<Real> &g)
+{
+    return (sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-14) * g.star_rmax;
+}
+template <typename Real>
+__device__ __forceinline__ Real star_df_noise(const SGeom<Real> &g)
+{
+    return (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_lmax;
+}
+
 // f = (gamma - y) x z has |f''| <= |gamma''| <= K, so on a scan interval [0, H] f stays
 // above the chord minus K H^2 / 8: with f(0), f(H) of one sign and both beyond that (plus
-// the rounding of f), the interval holds no root; only the others need the search for an
-// extremum
+// the rounding of f), the interval holds no root; only the others need a search for a pair
 template <typename Real>
 __device__ __forceinline__ Real star_guard(const SGeom<Real> &g)
 {
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
-    return g.star_kpp * H * H * (Real)0.125 + (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_rmax;
+    return g.star_kpp * H * H * (Real)0.125 + star_f_noise(g);
 }
 
+// The roots of f (the evaluator's function: (gamma - y) x z, or the divided difference g) in the
+// scan interval [t_j, t_j+1] (j in [0, kNodes)), appended to cand in scan order (at most
+// kIntervalRoots), by depth-first subdivision.  f'' is bounded by K (|gamma''| for f,
+// |gamma'''| / 3 for g), so a piece of width w, with f and f' known at its ends,
+//   - holds exactly one root if its end values differ in sign and f' has one sign at both
+//     ends with min |f'| > K w (f' cannot change sign inside: f is monotone); it is refined;
+//   - holds none if its end values share a sign and either min |f| > K w^2 / 8 (f stays above
+//     its chord minus that) or f is monotone;
+//   - is split at its midpoint otherwise; a midpoint of the other sign between ends of one sign
+//     leaves a sign change in each half, unless |f| there is within the rounding of f (then
+//     the piece is a tangency and holds no root).
+// Any number of extrema in the interval is handled (a near-tangent line close to an inflection
+// of the curve puts three roots in one interval, or two with two extrema of f).  Pieces narrower
+// than pair_min_width (a tangency within the rounding of f) count one root for a sign change
+// and none otherwise.  fa, fb and da, db are f and f' at the interval's ends; nf, nd and ndip
+// the rounding levels of f and f' and the |f| below which a sign is not trusted.
+constexpr int kPairStack = 40;
+constexpr int kIntervalRoots = 4;
+template <typename Real> __host__ __device__ constexpr Real pair_min_width() { return sizeof(Real) == 4 ? (Real)4e-6 : (Real)1e-12; }
+
 template <typename Real>
-__device__ __forceinline__ int star_interval_roots(const SGeom<Real> &g, int j, Real fa, Real fb, const Real *yc,
-                                                   const Real *z, Real *cand)
+__device__ int star_interval_roots(const StarLineEval<Real> &ev, Real fa, Real fb, Real da, Real db, Real K, Real nf,
+                                   Real nd, Real ndip, Real *cand)
 {
+    using O = RealOps<Real>;
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
-    const Real guard = star_guard(g);
-    int nc = 0;
-    if ((fa < 0) != (fb < 0)) {
-        cand[nc++] = star_refine(g, j, (Real)0, H, fa, yc, z, H * fa / (fa - fb));   // secant start
-    } else if (RealOps<Real>::fabs_(fa) < guard || RealOps<Real>::fabs_(fb) < guard) {
-        Real d1, dd1, d2, dd2;
-        star_line_df(g, j, (Real)0, z, &d1, &dd1);
-        star_line_df(g, j, H, z, &d2, &dd2);
-        if ((d1 < 0) != (d2 < 0)) {
-            // extremum of f in (0, H): safeguarded Newton on f' = 0
-            Real lo = 0, hi = H, dlo = d1;
-            Real te = H * d1 / (d1 - d2);
-            for (int it = 0; it < (sizeof(Real) == 4 ? 30 : 60); ++it) {
-                Real dm, ddm;
-                star_line_df(g, j, te, z, &dm, &ddm);
-                if (dm == (Real)0) break;
-                if ((dm < 0) == (dlo < 0)) { lo = te; dlo = dm; } else hi = te;
-                const Real step = dm / ddm;
-                if (RealOps<Real>::fabs_(step) <= eps_tol<Real>()) {
-                    te -= step;
-                    break;
-                }
-                Real tn = te - step;
-                if (!(tn > lo && tn < hi)) tn = (Real)0.5 * (lo + hi);
-                te = tn;
-                if (hi - lo <= bracket_tol<Real>()) break;
-            }
-            if (!(te > (Real)0 && te < H)) te = (Real)0.5 * H;
-            Real fe, de;
-            star_line_f(g, j, te, yc, z, &fe, &de);
-            if ((fe < 0) != (fa < 0)) {
-                cand[nc++] = star_refine(g, j, (Real)0, te, fa, yc, z);
-                cand[nc++] = star_refine(g, j, te, H, fe, yc, z);
-            }
+    Real lo_[kPairStack], hi_[kPairStack], flo_[kPairStack], fhi_[kPairStack], dlo_[kPairStack], dhi_[kPairStack];
+    lo_[0] = 0;
+    hi_[0] = H;
+    flo_[0] = fa;
+    fhi_[0] = fb;
+    dlo_[0] = da;
+    dhi_[0] = db;
+    int sp = 1, nc = 0;
+    while (sp > 0 && nc < kIntervalRoots) {
+        --sp;
+        const Real lo = lo_[sp], hi = hi_[sp], flo = flo_[sp], fhi = fhi_[sp], dlo = dlo_[sp], dhi = dhi_[sp];
+        const Real w = hi - lo;
+        const Real dmin = O::fabs_(dlo) < O::fabs_(dhi) ? O::fabs_(dlo) : O::fabs_(dhi);
+        const bool mono = (dlo < 0) == (dhi < 0) && dmin > K * w + nd;
+        const bool last = w <= pair_min_width<Real>() || sp + 2 > kPairStack;
+        if ((flo < 0) == (fhi < 0)) {
+            const Real fmin_ = O::fabs_(flo) < O::fabs_(fhi) ? O::fabs_(flo) : O::fabs_(fhi);
+            if (mono || fmin_ > K * w * w * (Real)0.125 + nf || last) continue;
+        } else if (mono || last) {
+            cand[nc++] = star_refine(ev, lo, hi, flo, lo + w * flo / (flo - fhi));   // secant start
+            continue;
         }
+        const Real m = (Real)0.5 * (lo + hi);
+        Real fm, dm;
+        ev(m, &fm, &dm);
+        // a dip through zero between ends of one sign brackets roots in both halves, unless the
+        // dip is within the rounding of f (a tangency: no root)
+        if ((flo < 0) == (fhi < 0) && (fm < 0) != (flo < 0) && O::fabs_(fm) <= ndip) continue;
+        // the right half below the left one: the left one is searched first (scan order)
+        lo_[sp] = m; hi_[sp] = hi; flo_[sp] = fm; fhi_[sp] = fhi; dlo_[sp] = dm; dhi_[sp] = dhi;
+        ++sp;
+        lo_[sp] = lo; hi_[sp] = m; flo_[sp] = flo; fhi_[sp] = fm; dlo_[sp] = dlo; dhi_[sp] = dm;
+        ++sp;
     }
     return nc;
 }
@@ -619,10 +696,13 @@ __device__ __forceinline__ void star_mark_window(const Real *yc, const Real *z, 
 // relative to the star centre) with the star.  A root is a point of the curve on
 // the line, so it lies where the line is inside the annulus rmin <= |p| <= rmax:
 // at most two windows of polar angle, scanned node by node (roots as in
-// star_interval_roots).  For a line, the start point is itself on the curve at
-// angle (sj, sd): exactly one root, the one nearest to that angle, is the start
-// point and is dropped.  Returns q; tt[] the line parameters, jj[] / dd[] the
-// roots as (node, offset).
+// star_interval_roots, of f = (gamma - yc) x z).  For a line, whose start is the
+// state itself on the curve at angle (sj, sd), the three scan intervals around that
+// angle hold only the start unless the line is close to tangent there; then they are
+// searched for the roots of the divided difference g of star_dd instead of f: g has no
+// root at the start, and a crossing close to it is found to the accuracy of g's terms,
+// not of f's cancelling difference.  Returns q;
+// tt[] the line parameters, jj[] / dd[] the roots as (node, offset).
 template <typename Real>
 __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Real *z, bool ray, int sj, Real sd,
                                   Real *tt, int *jj, Real *dd)
@@ -643,12 +723,56 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
         star_mark_window(yc, z, e, sf - outer, sf - inner, mask);
         star_mark_window(yc, z, e, sf + inner, sf + outer, mask);
     }
-    int q = 0, self = -1;
-    Real self_dist = (Real)1e30;
-    // the roots of one candidate interval, appended in scan order
+    int q = 0;
+    const Real unit = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-14;    // sign trust, relative
+    bool near_start = false;
+    if (!ray) {
+        // the intervals sj - 1, sj, sj + 1 around the start hold no crossing but the start itself
+        // unless the line is close to tangent there: |g'| <= |gamma''| / 2 = K / 2, so g keeps the
+        // sign of g(s) = gamma'(s) x z within 2 H of s when |g(s)| > K H (plus rounding)
+        for (int n = 0; n < 3; ++n) {
+            const int j = (sj - 1 + n) & (kNodes - 1);
+            mask[j >> 5] &= ~(1u << (j & 31));
+        }
+        Real ct, st, r, dr;
+        angle_cs(g, sj, sd, &ct, &st);
+        star_eval(g, ct, st, &r, &dr);
+        const Real gs = (dr * ct - r * st) * z[1] - (dr * st + r * ct) * z[0];
+        near_start = RealOps<Real>::fabs_(gs) <= g.star_kpp * H + star_df_noise(g);
+    }
+    if (near_start) {
+        // near-tangent line: the roots of g in those intervals, with |g''| <= |gamma'''| / 3
+        StarLineEval<Real> ev{g, yc, z, 0, true, sj, sd};
+        Real gv[4], gd[4];
+        for (int n = 0; n < 4; ++n) {
+            ev.j = (sj - 1 + n) & (kNodes - 1);
+            ev((Real)0, &gv[n], &gd[n]);
+        }
+        const Real nf = star_df_noise(g), nd = (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_kpp;
+        for (int o = 0; o < 3; ++o) {
+            ev.j = (sj - 1 + o) & (kNodes - 1);
+            Real cand[kIntervalRoots];
+            const int nc = star_interval_roots(ev, gv[o], gv[o + 1], gd[o], gd[o + 1], g.star_k3 * (Real)(1.0 / 3.0), nf,
+                                               nd, unit * g.star_lmax, cand);
+            for (int c = 0; c < nc && q < kMaxRoots; ++c) {
+                Real gg, gdd, dz;
+                star_dd(g, ev.j, cand[c], sj, sd, z, &gg, &gdd, &dz);
+                tt[q] = dz * ((Real)(o - 1) * H + (cand[c] - sd));  // (gamma(t) - gamma(s)) . z
+                jj[q] = ev.j;
+                dd[q] = cand[c];
+                ++q;
+            }
+        }
+    }
+    // the roots of one candidate interval of f, appended in scan order
     auto roots_of = [&](int j, Real fa, Real fb) {
-        Real cand[2];
-        const int nc = star_interval_roots(g, j, fa, fb, yc, z, cand);
+        Real cand[kIntervalRoots];
+        const int jn = (j + 1 == kNodes) ? 0 : j + 1;
+        const Real da = g.scan_d[j][0] * z[1] - g.scan_d[j][1] * z[0];     // f' at the nodes
+        const Real db = g.scan_d[jn][0] * z[1] - g.scan_d[jn][1] * z[0];
+        const StarLineEval<Real> ev{g, yc, z, j, false, 0, (Real)0};
+        const int nc = star_interval_roots(ev, fa, fb, da, db, g.star_kpp, star_f_noise(g), star_df_noise(g),
+                                           star_dip_noise(g), cand);
         for (int c = 0; c < nc; ++c) {
             Real ct, st, p[2];
             angle_cs(g, j, cand[c], &ct, &st);
@@ -659,16 +783,6 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
                 tt[q] = s;
                 jj[q] = j;
                 dd[q] = cand[c];
-                if (!ray) {
-                    int dj = j - sj;  // cyclic angular distance to the start point
-                    if (dj > kNodes / 2) dj -= kNodes;
-                    if (dj < -kNodes / 2) dj += kNodes;
-                    const Real dist = RealOps<Real>::fabs_((Real)dj * H + (cand[c] - sd));
-                    if (dist < self_dist) {
-                        self_dist = dist;
-                        self = q;
-                    }
-                }
                 ++q;
             }
         }
@@ -702,14 +816,6 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
         }
         for (int c = 0; c < n_cand; ++c) roots_of(cj[c], cfa[c], cfb[c]);
         if (bits == 0u) break;   // the mask is exhausted
-    }
-    if (!ray && self >= 0) {  // drop the start point
-        for (int a = self; a + 1 < q; ++a) {
-            tt[a] = tt[a + 1];
-            jj[a] = jj[a + 1];
-            dd[a] = dd[a + 1];
-        }
-        --q;
     }
     return q;
 }

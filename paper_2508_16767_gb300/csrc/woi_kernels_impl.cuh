@@ -61,6 +61,86 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 }
 
 // ---------------------------------------------------------------------------
+// one warp-level work unit: the walks [w_base, w_base + 32 L) of one point (lane l runs walks
+// w_base + 32 j + l), summed per lane with compensation and reduced over the warp (TwoSum) into
+// one partial row (sum of f, sum of squared schedule-group means) written by lane 0
+// ---------------------------------------------------------------------------
+template <int D, bool VR, bool STAR>
+__device__ __forceinline__ void run_unit(const SGeomFor<float, D, STAR> &g, const DevGeom *geom,
+                                         const float (*xc)[kMaxDim], Rng &rng, int64_t w_base, int64_t w_end, int L,
+                                         int sched_group, int lane, double *row)
+{
+    float s1[D + 1], c1[D + 1], s2[D + 1];
+#pragma unroll
+    for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
+    // the plain variant on spheres in d <= 3 with per-walk schedules advances rounds j and j + 1
+    // together (two independent walks per lane overlap their dependency chains); in higher
+    // dimensions, and with the larger code of stars, ellipsoids and meshes, the second walk's
+    // state does not fit in the registers
+    constexpr bool PAIR = !VR && !STAR && D <= 3;
+    int j = 0;
+    if (PAIR && sched_group == 1) {
+        for (; j + 1 < L; j += 2) {
+            const int64_t wa = w_base + (int64_t)j * 32 + lane, wb = wa + 32;
+            float f2[2][D + 1];
+            Rng r2[2] = {rng, rng};
+            r2[0].w0 = (uint32_t)wa;
+            r2[0].w1 = (uint32_t)((uint64_t)wa >> 32);
+            r2[1].w0 = (uint32_t)wb;
+            r2[1].w1 = (uint32_t)((uint64_t)wb >> 32);
+            const uint64_t grp[2] = {(uint64_t)wa / 32u, (uint64_t)wb / 32u};
+            if (wa < w_end) walk_pair<float, D, STAR>(g, geom, xc, r2, 1, grp, f2);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const bool valid = (q == 0 ? wa : wb) < w_end;
+#pragma unroll
+                for (int c = 0; c <= D; ++c) {
+                    const float fv = valid ? f2[q][c] : 0.f;
+                    kahan_add(s1[c], c1[c], fv);
+                    s2[c] += fv * fv;
+                }
+            }
+        }
+    }
+    for (; j < L; ++j) {
+        const int64_t w = w_base + (int64_t)j * 32 + lane;
+        float f[D + 1];
+        const bool valid = w < w_end;
+        if (valid) {
+            rng.w0 = (uint32_t)w;
+            rng.w1 = (uint32_t)((uint64_t)w >> 32);
+            walk<float, D, VR, STAR>(g, geom, xc, rng, sched_group, (uint64_t)w / 32u, f);
+        } else {
+#pragma unroll
+            for (int c = 0; c <= D; ++c) f[c] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
+        if (sched_group == 1) {
+#pragma unroll
+            for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
+        } else {
+            // the 32 lanes share one schedule; a warp's round is all valid or all past the end
+#pragma unroll
+            for (int c = 0; c <= D; ++c) {
+                const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
+                if (lane == 0 && valid) s2[c] += gm * gm;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c <= D; ++c) {
+        float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
+        warp_sum_pair(h1, l1);
+        warp_sum_pair(h2, l2);
+        if (lane == 0) {
+            row[c] = (double)h1 + (double)l1;
+            row[D + 1 + c] = (double)h2 + (double)l2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // batched walk kernel: warp-level work units (point, 32 x L walks) of many
 // instances.  A block serves one instance at a time (its geometry staged in
 // shared memory); its warps take units from that instance's own queue head
@@ -107,46 +187,8 @@ __global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed
             __syncwarp();
             rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
             const int64_t w_base = id.walk_begin + chunk * 32LL * L;
-            float s1[D + 1], c1[D + 1], s2[D + 1];
-#pragma unroll
-            for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
-            for (int j = 0; j < L; ++j) {
-                const int64_t w = w_base + (int64_t)j * 32 + lane;
-                float f[D + 1];
-                const bool valid = w < w_end;
-                if (valid) {
-                    rng.w0 = (uint32_t)w;
-                    rng.w1 = (uint32_t)((uint64_t)w >> 32);
-                    walk<float, D, VR, STAR>(g, id.geom, xc, rng, id.sched_group, (uint64_t)w / 32u, f);
-                } else {
-#pragma unroll
-                    for (int c = 0; c <= D; ++c) f[c] = 0.f;
-                }
-#pragma unroll
-                for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
-                if (id.sched_group == 1) {
-#pragma unroll
-                    for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
-                } else {
-                    // the 32 lanes share one schedule; a warp's round is all valid or all past the end
-#pragma unroll
-                    for (int c = 0; c <= D; ++c) {
-                        const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
-                        if (lane == 0 && valid) s2[c] += gm * gm;
-                    }
-                }
-            }
-            const int64_t row = id.unit_begin + local;
-#pragma unroll
-            for (int c = 0; c <= D; ++c) {
-                float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
-                warp_sum_pair(h1, l1);
-                warp_sum_pair(h2, l2);
-                if (lane == 0) {
-                    p.partials[row * (2 * (D + 1)) + c] = (double)h1 + (double)l1;
-                    p.partials[row * (2 * (D + 1)) + D + 1 + c] = (double)h2 + (double)l2;
-                }
-            }
+            run_unit<D, VR, STAR>(g, id.geom, xc, rng, w_base, w_end, L, id.sched_group, lane,
+                                  p.partials + (id.unit_begin + local) * (2 * (D + 1)));
             __syncwarp();   // the table is rewritten for the next unit
         }
         __syncthreads();    // every warp is done with this instance before its geometry is replaced
@@ -187,73 +229,8 @@ __global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed
         __syncwarp();
         rng.k0 = (uint32_t)p.seed ^ (uint32_t)point;
         const int64_t w_base = id.walk_begin + chunk * 32LL * L;
-        float s1[D + 1], c1[D + 1], s2[D + 1];
-#pragma unroll
-        for (int c = 0; c <= D; ++c) s1[c] = c1[c] = s2[c] = 0.f;
-        // the plain variant on spheres in d <= 3 with per-walk schedules advances rounds j and j + 1
-        // together (two independent walks per lane overlap their dependency chains); in higher
-        // dimensions, and with the larger code of stars, ellipsoids and meshes, the second walk's
-        // state does not fit in the registers
-        constexpr bool PAIR = !VR && !STAR && D <= 3;
-        int j = 0;
-        if (PAIR && id.sched_group == 1) {
-            for (; j + 1 < L; j += 2) {
-                const int64_t wa = w_base + (int64_t)j * 32 + lane, wb = wa + 32;
-                float f2[2][D + 1];
-                Rng r2[2] = {rng, rng};
-                r2[0].w0 = (uint32_t)wa;
-                r2[0].w1 = (uint32_t)((uint64_t)wa >> 32);
-                r2[1].w0 = (uint32_t)wb;
-                r2[1].w1 = (uint32_t)((uint64_t)wb >> 32);
-                const uint64_t grp[2] = {(uint64_t)wa / 32u, (uint64_t)wb / 32u};
-                if (wa < w_end) walk_pair<float, D, STAR>(g, id.geom, xc, r2, 1, grp, f2);
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const bool valid = (q == 0 ? wa : wb) < w_end;
-#pragma unroll
-                    for (int c = 0; c <= D; ++c) {
-                        const float fv = valid ? f2[q][c] : 0.f;
-                        kahan_add(s1[c], c1[c], fv);
-                        s2[c] += fv * fv;
-                    }
-                }
-            }
-        }
-        for (; j < L; ++j) {
-            const int64_t w = w_base + (int64_t)j * 32 + lane;
-            float f[D + 1];
-            const bool valid = w < w_end;
-            if (valid) {
-                rng.w0 = (uint32_t)w;
-                rng.w1 = (uint32_t)((uint64_t)w >> 32);
-                walk<float, D, VR, STAR>(g, id.geom, xc, rng, id.sched_group, (uint64_t)w / 32u, f);
-            } else {
-#pragma unroll
-                for (int c = 0; c <= D; ++c) f[c] = 0.f;
-            }
-#pragma unroll
-            for (int c = 0; c <= D; ++c) kahan_add(s1[c], c1[c], f[c]);
-            if (id.sched_group == 1) {
-#pragma unroll
-                for (int c = 0; c <= D; ++c) s2[c] += f[c] * f[c];
-            } else {
-#pragma unroll
-                for (int c = 0; c <= D; ++c) {
-                    const float gm = warp_sum_all(f[c]) * (1.0f / 32.0f);
-                    if (lane == 0 && valid) s2[c] += gm * gm;
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c <= D; ++c) {
-            float h1 = s1[c], l1 = c1[c], h2 = s2[c], l2 = 0.f;
-            warp_sum_pair(h1, l1);
-            warp_sum_pair(h2, l2);
-            if (lane == 0) {
-                p.partials[unit * (2 * (D + 1)) + c] = (double)h1 + (double)l1;
-                p.partials[unit * (2 * (D + 1)) + D + 1 + c] = (double)h2 + (double)l2;
-            }
-        }
+        run_unit<D, VR, STAR>(g, id.geom, xc, rng, w_base, w_end, L, id.sched_group, lane,
+                              p.partials + unit * (2 * (D + 1)));
         __syncwarp();   // the table is rewritten for the next unit
     }
 }

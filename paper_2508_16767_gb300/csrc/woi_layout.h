@@ -44,6 +44,10 @@ struct DevGeom {
     int star_idx, star_K;              // star_idx = -1: no star in this instance
     double star_lmax;                  // bound on |gamma'| of the star
     double star_kpp;                   // bound on |gamma''| of the star
+    double star_k3;                    // bound on |gamma'''| of the star
+    // gamma(t) - centre = sum_{m=0}^{K+1} (X_m cos mt + Y_m sin mt, U_m cos mt + V_m sin mt):
+    // star_harm[m] = (X_m, Y_m, U_m, V_m)
+    double star_harm[kMaxStar + 2][4];
     double star_rmin, star_rmax;       // bounds on r(t): every point of the star lies in this annulus
     uint32_t sched_tm1[kMaxSurfPad];   // T_n - 1, padded with 0xFFFFFFFF
     int sched_bucket[kSchedBuckets + 1]; // first n with T_n - 1 >= b 2^24 (N - 1 if none)
@@ -58,6 +62,7 @@ struct DevGeom {
     double star_a[kMaxStar + 1], star_b[kMaxStar + 1];
     double node_cs[kNodes][2];         // cos t_j, sin t_j
     double star_scan[kNodes][2];       // gamma(t_j) - centre
+    double star_scan_d[kNodes][2];     // gamma'(t_j)
     double star_panel_s[kNodes + 1];   // arc length at t_j
     int flux_basis[kMaxSurf], flux_off[kMaxSurf], flux_n[kMaxSurf];
     const double *flux_coef;           // device array, device format (real-SH entries carry their
