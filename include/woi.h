@@ -83,7 +83,9 @@ enum { WOI_SPHERE = 0,     /* circle (2D) or (d-1)-sphere: centre, radius */
                               triangles with opposite orientations, triangles counter-clockwise
                               seen from outside (positive enclosed volume); `center` is the
                               reference point of the surface's local coordinates (any point near
-                              it).  A line crossing one mesh more than 32 times is not supported.
+                              it).  A line crossing one mesh more than 32 times is not supported:
+                              the call reports WOI_E_GEOMETRY (asynchronous calls through
+                              woi_check_status).
                               At most WOI_MAX_MESHES per geometry */
 
 typedef struct {
@@ -208,6 +210,28 @@ WOI_API woi_status woi_estimate_range(woi_geometry *geometry, const woi_opts *op
                               int64_t walk_begin, int64_t n_walks, uint64_t seed, double *moments);
 
 /*
+ * Mean and standard error from raw moments (Algorithm 1: the estimate is the mean
+ * of the walk tallies, its standard error the one of the schedule-group means).
+ * moments[n_pts][2][dim+1] as woi_estimate_range returns them -- for f = (u tally,
+ * grad tally), the sum of f over n_walks walks and the sum over the
+ * G = n_walks / sched_group schedule groups of (group mean of f)^2 -- typically the
+ * element-wise sum of the moments of disjoint walk ranges (shards, resumed runs)
+ * that together cover n_walks walks of every point.  Writes u[n_pts] = sum / n_walks,
+ * grad[n_pts][dim] likewise, and se_u[n_pts], se_grad[n_pts][dim] = sqrt(s^2 / G)
+ * with s^2 the sample variance of the G group means (0 when G = 1); each output
+ * may be NULL.  moments and outputs may be host or device memory (detected per
+ * pointer); with only device pointers the call is asynchronous on cuda_stream (a
+ * cudaStream_t, NULL = the legacy default stream) and allocates nothing, otherwise
+ * it stages through temporary device memory and returns after the results are
+ * copied back.  Errors: WOI_E_INVALID_ARG for dim outside [2, 6], n_pts < 0,
+ * n_walks < 1, sched_group not 1 or 32, n_walks not a multiple of sched_group, or a
+ * null moments array with n_pts > 0; WOI_E_NO_DEVICE without a CUDA device.
+ */
+WOI_API woi_status woi_finalize_moments(int dim, int64_t n_pts, int64_t n_walks, int sched_group,
+                                        const double *moments, void *cuda_stream, double *u, double *grad,
+                                        double *se_u, double *se_grad);
+
+/*
  * Per-walk values for pathwise replay: for one point x[dim] (host) with
  * stream ids point_id and instance_id (the instance index of a batch, 0 otherwise), the walks walk_ids[n] (host) give f_u[n] and
  * f_grad[n][dim] (host), each the full walk tally N sum_i c_i Phi(x, y_i)
@@ -249,6 +273,19 @@ WOI_API woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geometrie
                               double *const *se_grad);
 
 /*
+ * Outcome of the last asynchronous estimate on this geometry (an estimate or
+ * range call with device points and device outputs, which returns before its
+ * kernels finish).  Waits for that call's work on its stream and returns
+ * WOI_E_GEOMETRY if a line or ray of one of its walks crossed a mesh surface
+ * more than 32 times (the crossing lists are bounded: the extra crossings were
+ * dropped and that call's estimates are invalid), WOI_OK otherwise or if there
+ * is nothing to check.  The counter is reset by every call and read once.
+ * Synchronous calls (host points or outputs), woi_walk_values / woi_walk_trace
+ * and woi_estimate_batch report the same condition in their own status.
+ */
+WOI_API woi_status woi_check_status(woi_geometry *geometry);
+
+/*
  * Duration in milliseconds of the walk kernel(s) of the last estimate on this
  * handle that ran with opts->timing = 1 (CUDA events on its launch stream;
  * waits for the stop event).  WOI_E_STATE if no timed estimate ran.
@@ -273,8 +310,10 @@ WOI_API woi_status woi_last_kernel_ms(woi_geometry *geometry, float *ms);
  * se_grad[n_pts][dim] must be device pointers (outputs may be NULL).  The
  * call is asynchronous on opts->cuda_stream.  Sizes whose scratch would exceed
  * the array are rejected with WOI_E_INVALID_ARG (about 16 MiB / (16 (dim+1))
- * work units of 32 x walks_per_lane walks each -- 2048 by default -- e.g.
- * 4096 points x 1e5 walks in 3D fits).
+ * work units of 32 x walks_per_lane walks each -- e.g. 4096 points x 1e5 walks
+ * in 3D fits with 64 walks per lane).  The launch shape is chosen as for
+ * woi_estimate (explicit options, else the woi_autotune table), except that the
+ * default is 64 walks per lane (fewer, larger work units).
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream

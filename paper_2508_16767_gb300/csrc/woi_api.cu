@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -123,8 +124,10 @@ struct woi_geometry {
     StarCurve star;
     std::vector<double> star_panel_s;          // kNodes + 1
     std::vector<double> star_scan;             // kNodes * 2
+    std::vector<double> star_scan_d;           // kNodes * 2: gamma'(t_j)
     double star_lmax = 0.0;
     double star_kpp = 0.0;                     // bound on |gamma''|
+    double star_k3 = 0.0;                      // bound on |gamma'''|
     double star_rmin = 0.0, star_rmax = 0.0;
     struct Ellipsoid {
         double A[kMaxDim][kMaxDim];            // (y - c)^T A (y - c) = 1
@@ -176,6 +179,8 @@ struct woi_geometry {
     bool general() const { return star_idx >= 0 || !ell.empty() || !mesh.empty(); }
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     bool timed = false;
+    cudaEvent_t ev_done = nullptr;             // end of the last asynchronous estimate on a mesh geometry
+    bool check_pending = false;                // its overflow counter has not been read yet
 
     ~woi_geometry() { release(); }
     void release()
@@ -202,8 +207,10 @@ struct woi_geometry {
         cudaFree(d_scratch);
         if (ev_start) cudaEventDestroy(ev_start);
         if (ev_stop) cudaEventDestroy(ev_stop);
-        ev_start = ev_stop = nullptr;
+        if (ev_done) cudaEventDestroy(ev_done);
+        ev_start = ev_stop = ev_done = nullptr;
         timed = false;
+        check_pending = false;
         if (cur >= 0) cudaSetDevice(cur);
         d_blob = nullptr;
         d_flux = d_arc_t0 = d_arc_t1 = d_arc_len = d_arc_s0 = nullptr;
@@ -675,11 +682,14 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
             g->star_panel_s[j + 1] = g->star_panel_s[j] + star_length(g->star, j * H, (j + 1) * H, 4);
         g->area[g->star_idx] = g->star_panel_s[kNodes];
         g->star_scan.assign(2 * kNodes, 0.0);
+        g->star_scan_d.assign(2 * kNodes, 0.0);
         for (int j = 0; j < kNodes; ++j) {
             double r, dr, t = 2.0 * kPi * j / kNodes;
             g->star.eval(t, &r, &dr);
             g->star_scan[2 * j] = r * std::cos(t);
             g->star_scan[2 * j + 1] = r * std::sin(t);
+            g->star_scan_d[2 * j] = dr * std::cos(t) - r * std::sin(t);
+            g->star_scan_d[2 * j + 1] = dr * std::sin(t) + r * std::cos(t);
         }
         double lm = 0.0, rmin = 1e300, rmax = 0.0, b1 = 0.0, b2 = 0.0;
         for (int k = 1; k <= g->star.K; ++k) {
@@ -703,6 +713,11 @@ woi_status woi_create_geometry(int dim, int n_surf, const woi_surface_desc *surf
         g->star_rmax = rmax + margin;
         // gamma'' = (r'' - r) e_r + 2 r' e_t, so |gamma''| <= |r''| + r + 2 |r'|
         g->star_kpp = b2 + g->star_rmax + 2.0 * b1;
+        // gamma''' = (r''' - 3 r') e_r + (3 r'' - r) e_t
+        double b3 = 0.0;
+        for (int k = 1; k <= g->star.K; ++k)
+            b3 += (double)k * k * k * (std::fabs(g->star.a[k]) + std::fabs(g->star.b[k]));
+        g->star_k3 = b3 * g->star.R + 3.0 * b1 + 3.0 * b2 + g->star_rmax;
     }
     *out = g;
     return WOI_OK;
@@ -1164,6 +1179,21 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
     b.star_K = g.star_idx >= 0 ? g.star.K : 0;
     b.star_lmax = g.star_lmax;
     b.star_kpp = g.star_kpp;
+    b.star_k3 = g.star_k3;
+    if (g.star_idx >= 0) {
+        // r(t) (cos t, sin t) as a trigonometric polynomial of degree K + 1: cos kt cos t =
+        // (cos (k+1)t + cos (k-1)t) / 2 and the like
+        const double R = g.star.R;
+        b.star_harm[1][0] += R;                            // R cos t
+        b.star_harm[1][3] += R;                            // R sin t
+        for (int k = 1; k <= g.star.K; ++k) {
+            const double a = 0.5 * R * g.star.a[k], c = 0.5 * R * g.star.b[k];
+            b.star_harm[k + 1][0] += a;  b.star_harm[k - 1][0] += a;    // a_k cos kt cos t
+            b.star_harm[k + 1][1] += c;  b.star_harm[k - 1][1] += c;    // b_k sin kt cos t
+            b.star_harm[k + 1][3] += a;  b.star_harm[k - 1][3] -= a;    // a_k cos kt sin t
+            b.star_harm[k - 1][2] += c;  b.star_harm[k + 1][2] -= c;    // b_k sin kt sin t
+        }
+    }
     b.star_rmin = g.star_rmin;
     b.star_rmax = g.star_rmax;
     for (int i = 0; i < kMaxSurfPad; ++i) b.sched_tm1[i] = i < g.n ? (uint32_t)(g.thresh[i] - 1) : 0xFFFFFFFFu;
@@ -1212,6 +1242,8 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
         for (int j = 0; j < kNodes; ++j) {
             b.star_scan[j][0] = g.star_scan[2 * j];
             b.star_scan[j][1] = g.star_scan[2 * j + 1];
+            b.star_scan_d[j][0] = g.star_scan_d[2 * j];
+            b.star_scan_d[j][1] = g.star_scan_d[2 * j + 1];
         }
         for (int j = 0; j <= kNodes; ++j) b.star_panel_s[j] = g.star_panel_s[j];
     }
@@ -1372,6 +1404,19 @@ woi_status stage_points(woi_geometry *g, const double *points, int64_t n_pts, co
     return WOI_OK;
 }
 
+// lines of the last call that crossed a mesh more than kMaxHits times (the crossing lists were
+// truncated): read after the call's work has finished, cleared, and reported as WOI_E_GEOMETRY
+woi_status take_mesh_overflow(woi_geometry *g)
+{
+    g->check_pending = false;
+    if (!g->d_mesh_overflow) return WOI_OK;
+    unsigned int over = 0;
+    WOI_CUDA(cudaMemcpy(&over, g->d_mesh_overflow, sizeof(over), cudaMemcpyDeviceToHost));
+    if (!over) return WOI_OK;
+    WOI_CUDA(cudaMemset(g->d_mesh_overflow, 0, sizeof(over)));
+    return fail(WOI_E_GEOMETRY, "%u lines crossed a mesh more than %d times; estimates are invalid", over, kMaxHits);
+}
+
 struct OutBuf {
     double *user;
     bool on_dev;
@@ -1392,6 +1437,8 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
     const int d = g->dim, C = d + 1;
     const bool vr = o->variant == WOI_VR, star = g->general(), fp64 = o->precision == WOI_FP64_PLAIN;
     if ((st = stage_geometry(g, o->M, s)) != WOI_OK) return st;
+    // the mesh crossing-overflow counter counts this call's lines only
+    if (g->d_mesh_overflow) WOI_CUDA(cudaMemsetAsync(g->d_mesh_overflow, 0, sizeof(unsigned int), s));
 
     int block, L;
     launch_shape(o, d, star, &block, &L);
@@ -1523,15 +1570,13 @@ woi_status run_estimate(woi_geometry *g, const woi_opts *o, const double *points
     }
     if (any_host || !pointer_on_device(points)) {
         WOI_CUDA(cudaStreamSynchronize(s));
-        if (g->d_mesh_overflow) {
-            unsigned int over = 0;
-            WOI_CUDA(cudaMemcpy(&over, g->d_mesh_overflow, sizeof(over), cudaMemcpyDeviceToHost));
-            if (over) {
-                WOI_CUDA(cudaMemset(g->d_mesh_overflow, 0, sizeof(over)));
-                return fail(WOI_E_GEOMETRY, "%u lines crossed a mesh more than %d times; estimates are invalid", over,
-                            kMaxHits);
-            }
-        }
+        return take_mesh_overflow(g);
+    }
+    if (g->d_mesh_overflow) {
+        // asynchronous call on a mesh geometry: woi_check_status waits for this event and reads the counter
+        if (!g->ev_done) WOI_CUDA(cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming));
+        WOI_CUDA(cudaEventRecord(g->ev_done, s));
+        g->check_pending = true;
     }
     return WOI_OK;
 }
@@ -1772,6 +1817,8 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
         }
         g_batch.key = key;
     }
+    for (int k = 0; k < n_inst; ++k)
+        if (geoms[k]->d_mesh_overflow) WOI_CUDA(cudaMemsetAsync(geoms[k]->d_mesh_overflow, 0, sizeof(unsigned int), s));
     if (o->timing) {
         // events of the first geometry time the whole batch launch
         woi_geometry *g0 = geoms[0];
@@ -1794,6 +1841,8 @@ woi_status run_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, 
     }
     // the batch scratch and the captured graph are shared by batch calls: finish before returning
     WOI_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < n_inst; ++k)
+        if ((st = take_mesh_overflow(geoms[k])) != WOI_OK) return st;
     return WOI_OK;
 }
 
@@ -1857,12 +1906,13 @@ static woi_status walk_values_impl(woi_geometry *g, const woi_opts *o, const dou
     p.f_grad = (double *)(base + o_g);
     p.trace = trace ? (double *)(base + o_t) : nullptr;
     if (trace) WOI_CUDA(cudaMemsetAsync(p.trace, 0, trace_count * sizeof(double), s));
+    if (g->d_mesh_overflow) WOI_CUDA(cudaMemsetAsync(g->d_mesh_overflow, 0, sizeof(unsigned int), s));
     WOI_CUDA(launch_walk_values(d, o->variant == WOI_VR, g->general(), o->precision == WOI_FP64_PLAIN, p, s));
     WOI_CUDA(cudaMemcpyAsync(f_u, p.f_u, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     WOI_CUDA(cudaMemcpyAsync(f_grad, p.f_grad, n * d * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (trace) WOI_CUDA(cudaMemcpyAsync(trace, p.trace, trace_count * sizeof(double), cudaMemcpyDeviceToHost, s));
     WOI_CUDA(cudaStreamSynchronize(s));
-    return WOI_OK;
+    return take_mesh_overflow(g);
 }
 
 woi_status woi_walk_values(woi_geometry *g, const woi_opts *o, const double *x, uint32_t point_id,
@@ -1940,6 +1990,15 @@ woi_status woi_autotune(woi_geometry *g, const woi_opts *o, const double *points
     return WOI_OK;
 }
 
+woi_status woi_check_status(woi_geometry *g)
+{
+    g_last_error.clear();
+    if (!g) return fail(WOI_E_INVALID_ARG, "null geometry");
+    if (!g->check_pending) return WOI_OK;
+    WOI_CUDA(cudaEventSynchronize(g->ev_done));
+    return take_mesh_overflow(g);
+}
+
 woi_status woi_last_kernel_ms(woi_geometry *g, float *ms)
 {
     g_last_error.clear();
@@ -1948,6 +2007,66 @@ woi_status woi_last_kernel_ms(woi_geometry *g, float *ms)
     WOI_CUDA(cudaEventSynchronize(g->ev_stop));
     WOI_CUDA(cudaEventElapsedTime(ms, g->ev_start, g->ev_stop));
     return WOI_OK;
+}
+
+woi_status woi_finalize_moments(int dim, int64_t n_pts, int64_t n_walks, int sched_group, const double *moments,
+                                void *cuda_stream, double *u, double *grad, double *se_u, double *se_grad)
+{
+    g_last_error.clear();
+    if (dim < 2 || dim > WOI_MAX_DIM) return fail(WOI_E_INVALID_ARG, "dim = %d outside [2, %d]", dim, WOI_MAX_DIM);
+    if (n_pts < 0 || n_walks < 1) return fail(WOI_E_INVALID_ARG, "need n_pts >= 0, n_walks >= 1");
+    if (sched_group != 1 && sched_group != 32) return fail(WOI_E_INVALID_ARG, "sched_group must be 1 or 32");
+    if (n_walks % sched_group) return fail(WOI_E_INVALID_ARG, "n_walks must be a multiple of sched_group");
+    if (n_pts > 0 && !moments) return fail(WOI_E_INVALID_ARG, "null moments");
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(WOI_E_NO_DEVICE, "no CUDA device");
+    }
+    if (n_pts == 0) return WOI_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int C = dim + 1;
+    // host arrays go through one temporary device buffer: [moments][u][grad][se_u][se_grad]
+    double *user[5] = {const_cast<double *>(moments), u, grad, se_u, se_grad};
+    const size_t count_of[5] = {(size_t)n_pts * 2 * C, (size_t)n_pts, (size_t)n_pts * dim, (size_t)n_pts,
+                                (size_t)n_pts * dim};
+    bool host[5];
+    size_t off[5], bytes = 0;
+    for (int k = 0; k < 5; ++k) {
+        host[k] = user[k] && !pointer_on_device(user[k]);
+        off[k] = bytes;
+        if (host[k]) bytes = align_up(bytes + count_of[k] * sizeof(double), 256);
+    }
+    char *tmp = nullptr;
+    if (bytes && cudaMalloc((void **)&tmp, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WOI_E_OOM, "device staging allocation of %zu bytes failed", bytes);
+    }
+    double *dev[5];
+    for (int k = 0; k < 5; ++k) dev[k] = !user[k] ? nullptr : (host[k] ? (double *)(tmp + off[k]) : user[k]);
+    woi_status st = WOI_OK;
+    cudaError_t e = cudaSuccess;
+    if (host[0]) e = cudaMemcpyAsync(dev[0], moments, count_of[0] * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        FinalizeParams fp{};
+        fp.dim = dim;
+        fp.n_pts = n_pts;
+        fp.n_walks = n_walks;
+        fp.sched_group = sched_group;
+        fp.partials = dev[0];
+        fp.u = dev[1];
+        fp.grad = dev[2];
+        fp.se_u = dev[3];
+        fp.se_grad = dev[4];
+        fp.moments = nullptr;
+        e = launch_finalize(fp, true, s);    // one row of accumulated moments per point
+    }
+    for (int k = 1; k < 5 && e == cudaSuccess; ++k)
+        if (host[k]) e = cudaMemcpyAsync(user[k], dev[k], count_of[k] * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(WOI_E_CUDA, "woi_finalize_moments: %s", cudaGetErrorString(e));
+    if (tmp) cudaFree(tmp);
+    return st;
 }
 
 woi_status woi_estimate_batch(int n_inst, woi_geometry *const *geoms, const woi_opts *o, const int *m_per_inst,
@@ -1976,20 +2095,22 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[WOI_NOALLOC_SCR
 namespace {
 
 constexpr int kNoallocMaxDevices = 64;
-void *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+std::atomic<void *> g_noalloc_addr[kNoallocMaxDevices];   // zero-initialised (static storage)
 thread_local DevGeom g_noalloc_blob;   // host image of the blob (no heap allocation)
 
+// device address of the scratch array on device `dev` (current); looked up once per device.
+// Two threads may look it up at the same time: both get the same address and store it.
 woi_status noalloc_scratch_address(int dev, char **out)
 {
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(WOI_E_UNSUPPORTED, "device ordinal %d too large", dev);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
+    void *p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return fail(WOI_E_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
+        g_noalloc_addr[dev].store(p, std::memory_order_release);
     }
-    *out = (char *)g_noalloc_addr[dev];
+    *out = (char *)p;
     return WOI_OK;
 }
 
@@ -2025,8 +2146,8 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     const int d = g->dim, C = d + 1, M = o->M;
     const bool vr = o->variant == WOI_VR, star = g->general();
-    const int block = o->block_size ? o->block_size : 256;
-    const int L = o->walks_per_lane ? o->walks_per_lane : 64;
+    int block, L;
+    launch_shape(o, d, star, &block, &L, 64);  // explicit options, else the tuned table, else 256 x 64
     const int64_t unit_walks = 32LL * L;       // warp-level work units
     const int64_t chunks = (n_walks + unit_walks - 1) / unit_walks;
     const int64_t units = n_pts * chunks;
@@ -2089,7 +2210,7 @@ extern "C" woi_status woi_estimate_noalloc(woi_geometry *g, const woi_opts *o, c
     int per_sm = 0;
     const size_t smem = (size_t)(block / 32) * g->n * kMaxDim * sizeof(float);
     WOI_CUDA(mixed_warp_occupancy(d, vr, star, block, smem, &per_sm));
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm < 1) return fail(WOI_E_UNSUPPORTED, "walk kernel does not fit on an SM (M = %d)", M);
     const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, (units + block / 32 - 1) / (block / 32));
     MixedParams mp{};
     mp.inst = (const InstDesc *)(base + o_desc);

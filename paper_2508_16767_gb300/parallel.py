@@ -41,12 +41,8 @@ def allreduce_moments(moments, group=None):
     return t if isinstance(moments, torch.Tensor) else t.numpy()
 
 
-def finalize(moments, n_walks, sched_group=1):
-    """Mean and SE of merged moments (the library's finalize formulas)."""
-    m = np.asarray(moments)
-    S1, S2 = m[:, 0, :], m[:, 1, :]
-    G = n_walks / sched_group
-    mean = S1 / n_walks
-    var = np.maximum(S2 - G * mean * mean, 0.0) / max(G - 1, 1)
-    se = np.sqrt(var / G)
-    return {"u": mean[:, 0], "grad": mean[:, 1:], "se_u": se[:, 0], "se_grad": se[:, 1:]}
+def finalize(moments, n_walks, sched_group=1, stream=None):
+    """Mean and SE of merged moments [P, 2, dim+1] (host or device) by the library's
+    finalize kernel (woi_finalize_moments)."""
+    from . import woi
+    return woi.woi_finalize_moments(moments, n_walks, sched_group, stream=stream)

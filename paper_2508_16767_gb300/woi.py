@@ -30,7 +30,8 @@ STATUS = {0: "WOI_OK", 1: "WOI_E_INVALID_ARG", 2: "WOI_E_GEOMETRY", 3: "WOI_E_CO
           5: "WOI_E_NO_DEVICE", 6: "WOI_E_CUDA", 7: "WOI_E_OOM", 8: "WOI_E_TIMEOUT", 9: "WOI_E_STATE"}
 EXPORTED = ["woi_default_opts", "woi_create_geometry", "woi_set_sigma_and_data", "woi_estimate",
             "woi_estimate_range", "woi_walk_values", "woi_walk_trace", "woi_estimate_batch", "woi_last_kernel_ms",
-            "woi_estimate_noalloc", "woi_autotune", "woi_surface_area",
+            "woi_estimate_noalloc", "woi_autotune", "woi_surface_area", "woi_finalize_moments",
+            "woi_check_status",
             "woi_destroy_geometry", "woi_last_error", "woi_version"]
 
 
@@ -74,6 +75,8 @@ def _load():
     lib.woi_set_sigma_and_data.argtypes = [vp, P(ctypes.c_double), P(FluxDesc)]
     lib.woi_estimate.argtypes = [vp, P(Opts), dp, i64, i64, u64, dp, dp, dp, dp]
     lib.woi_estimate_range.argtypes = [vp, P(Opts), dp, i64, i64, i64, u64, dp]
+    lib.woi_check_status.argtypes = [vp]
+    lib.woi_finalize_moments.argtypes = [ctypes.c_int, i64, i64, ctypes.c_int, dp, vp, dp, dp, dp, dp]
     lib.woi_walk_values.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, ctypes.c_uint32, dp, i64, u64, dp, dp]
     lib.woi_walk_trace.argtypes = [vp, P(Opts), dp, ctypes.c_uint32, ctypes.c_uint32, dp, i64, u64, dp, dp, dp]
     lib.woi_estimate_batch.argtypes = [ctypes.c_int, P(vp), P(Opts), P(ctypes.c_int), P(vp), P(i64), P(i64), u64,
@@ -148,6 +151,12 @@ def make_opts(M=4, variant="plain", precision="mixed", sched_group=1, stream=Non
     o.timing = int(bool(timing))
     o.tile_points = int(tile_points)
     return o
+
+
+def woi_check_status(geom) -> None:
+    """Waits for the last asynchronous estimate on `geom` and raises WoiError
+    (WOI_E_GEOMETRY) if one of its lines crossed a mesh more than 32 times."""
+    _check(lib.woi_check_status(geom.handle))
 
 
 def woi_last_kernel_ms(geom) -> float:
@@ -332,11 +341,12 @@ def woi_autotune(geom: Geometry, points, n_walks, seed=0, stream=None, **opt):
     return b.value, l.value
 
 
-def woi_estimate_batch(instances, seed=0, stream=None, **opt):
+def woi_estimate_batch(instances, seed=0, stream=None, out=None, **opt):
     """Batched estimate.  instances: list of (Geometry, points, n_walks[, M]);
-    points numpy (host) or torch CUDA tensors.  Instance k uses random-stream
-    instance id k.  Returns a list of dicts like woi_estimate, with outputs
-    allocated like each instance's points."""
+    points numpy (host) or torch tensors (host, e.g. pinned, or CUDA).  Instance k
+    uses random-stream instance id k.  Returns a list of dicts like woi_estimate,
+    with outputs allocated like each instance's points unless out[k] =
+    (u, grad, se_u, se_grad) is given."""
     n = len(instances)
     P = ctypes.POINTER
     geoms = (ctypes.c_void_p * n)()
@@ -350,29 +360,39 @@ def woi_estimate_batch(instances, seed=0, stream=None, **opt):
         geom, points, n_walks = inst[0], _as_input(inst[1]), inst[2]
         M = inst[3] if len(inst) > 3 else geom.problem.get("M", 4)
         Pk = int(points.shape[0])
-        out = (_alloc_like(points, (Pk,)), _alloc_like(points, (Pk, geom.dim)), _alloc_like(points, (Pk,)),
-               _alloc_like(points, (Pk, geom.dim)))
-        keep += [points, *out]
+        res_k = out[k] if out is not None else (_alloc_like(points, (Pk,)), _alloc_like(points, (Pk, geom.dim)),
+                                                _alloc_like(points, (Pk,)), _alloc_like(points, (Pk, geom.dim)))
+        keep += [points, *res_k]
         geoms[k], pts[k], npts[k], nw[k], ms[k] = geom.handle, _ptr(points), Pk, int(n_walks), int(M)
         for j in range(4):
-            outs[j][k] = _ptr(out[j])
-        results.append({"u": out[0], "grad": out[1], "se_u": out[2], "se_grad": out[3]})
+            outs[j][k] = _ptr(res_k[j])
+        results.append({"u": res_k[0], "grad": res_k[1], "se_u": res_k[2], "se_grad": res_k[3]})
     arrays = [inst[1] for inst in instances]
     o = make_opts(M=4, stream=_stream_of(arrays, stream), **opt)
     _check(lib.woi_estimate_batch(n, geoms, ctypes.byref(o), ms, pts, npts, nw, int(seed), *outs))
     return results
 
 
+def woi_finalize_moments(moments, n_walks, sched_group=1, out=None, stream=None):
+    """u, grad, se_u, se_grad from raw moments [P, 2, dim+1] (numpy or torch, host or
+    CUDA) of n_walks walks per point -- e.g. the sum of the moments of disjoint walk
+    ranges -- computed by the library's finalize kernel."""
+    if not _is_torch(moments):
+        moments = np.ascontiguousarray(moments, dtype=np.float64)
+    P, two, C = (int(v) for v in moments.shape)
+    assert two == 2
+    dim = C - 1
+    if out is None:
+        out = (_alloc_like(moments, (P,)), _alloc_like(moments, (P, dim)), _alloc_like(moments, (P,)),
+               _alloc_like(moments, (P, dim)))
+    _check(lib.woi_finalize_moments(dim, P, int(n_walks), int(sched_group), _ptr(moments),
+                                    _stream_of([moments, *out], stream), *[_ptr(a) for a in out]))
+    return {"u": out[0], "grad": out[1], "se_u": out[2], "se_grad": out[3]}
+
+
 def finalize_moments(mom, n_walks, sched_group=1):
-    """Mean and SE from raw moments (host, numpy) -- the same formulas as the
-    library's finalize step, for merged ranges."""
-    mom = np.asarray(mom)
-    S1, S2 = mom[:, 0, :], mom[:, 1, :]
-    G = n_walks / sched_group
-    mean = S1 / n_walks
-    var = np.maximum(S2 - G * mean * mean, 0.0) / max(G - 1, 1)
-    se = np.sqrt(var / G)
-    return {"u": mean[:, 0], "grad": mean[:, 1:], "se_u": se[:, 0], "se_grad": se[:, 1:]}
+    """Mean and SE of merged raw moments through the library (woi_finalize_moments)."""
+    return woi_finalize_moments(mom, n_walks, sched_group)
 
 
 def woi_estimate_noalloc(geom: Geometry, points, n_walks, seed=0, out=None, stream=None, **opt):
