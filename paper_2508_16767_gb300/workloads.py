@@ -538,6 +538,18 @@ def radial_mesh(center, radius, subdiv, amp, seed):
     return Vr, F
 
 
+def bellows_problem(subdiv=6, k=80.0, amp=0.3, M=3):
+    """One closed radial mesh shaped like a bellows along z, r(u) = 1 + amp cos(k u_z)
+    (20 4^subdiv triangles), with zero flux: lines through it cross it many times (at
+    the defaults about 5 % of random lines through a point of it cross it more than 32
+    times), the case in which a library must report that it truncated a crossing list."""
+    V, F = icosphere(subdiv)
+    V = np.asarray(V, dtype=np.float64)
+    Vr = (1.0 + amp * np.cos(k * V[:, 2]))[:, None] * V
+    return {"name": "bellows", "dim": 3, "surfaces": [_mesh(Vr, F, [0.0, 0.0, 0.0])], "parent": [-1],
+            "sigma": [1.0], "flux": [{"basis": "zero", "coef": []}], "M": M}
+
+
 def _mesh(V, F, center):
     return {"kind": "mesh", "center": [float(c) for c in center],
             "vertices": np.asarray(V, dtype=np.float64).tolist(), "triangles": np.asarray(F, dtype=np.int64).tolist()}

@@ -1,13 +1,18 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 * Pathwise replay: the same Philox streams give the same walks; per-walk
-  tallies agree to 1e-12 (FP64 path) and 1e-5 (FP32 path) relative to the
-  walk's magnitude scale (sum_i |c_i| (|Phi_i| + 1) for u, sum_i |c_i| |grad Phi_i|
-  for grad u, each times the walk's conditioning: the larger of the start flux's
-  sum of term magnitudes over its value and, for a chord nearly tangent to a
-  curved surface, (|y - c| + |y' - c|) / |t|, by which it amplifies any rounding of
-  the start's distance from the surface), apart from a bounded fraction of FP32
-  walks whose discrete choices flip at a near-tangency (star curves and meshes).
+  tallies agree to 1e-12 (FP64 path) and 1e-5 (FP32 path) of the walk's error
+  bound B (the oracle's first-order bound of the change of the tallies under a
+  unit relative error of every state, of x and of every factor: the terms'
+  magnitudes, the start flux's term magnitudes and slope, the sensitivity of
+  Phi and grad Phi to the states near an interface, and the amplification of a
+  state error by line / ray steps; pinned by a perturbation experiment in
+  test_oracle_error_bound.py).  The first point of every case replays 2e4 walks.
+  Walks whose line / ray amplification (the walk's conditioning) exceeds 1e3 are
+  ill-conditioned: their count is reported and they are held to the FP64 bar
+  only.  Among the others, a walk beyond the FP32 bar is a branch flip (a
+  discrete choice of the walk taken differently at FP32 rounding): each must
+  follow the oracle in FP64, and there may be at most a 1e-4 fraction of them.
 * Per-point estimates over the same walks: the FP32 path's mean differs from
   the oracle's by far less than the Monte Carlo standard error (1e-2 SE), the
   FP64 path's by rounding only; sizes span several work units and a ragged tail.
@@ -102,44 +107,61 @@ def walk_ids(n=96):
     return ids
 
 
-def replay(W, O, prob, x, variant, precision, point_id):
+COND_CAP = 1e3        # FP32 per-walk claims hold for walks whose conditioning is at most this
+FLIP_FRACTION = 1e-4  # branch flips allowed among the well-conditioned FP32 walks
+N_LARGE = 20000       # walks replayed at the first point of every case
+
+
+def replay(W, O, prob, x, variant, point_id, n):
+    """Per-walk errors of both GPU paths relative to the oracle's error bound, and the
+    walks' conditioning."""
     g = W.Geometry(prob)
-    ids = walk_ids()
-    gv = W.woi_walk_values(g, x, ids, seed=7, point_id=point_id, M=prob["M"], variant=variant, precision=precision)
+    ids = walk_ids(n)
+    out = {}
+    for precision in ("fp64", "mixed"):
+        gv = W.woi_walk_values(g, x, ids, seed=7, point_id=point_id, M=prob["M"], variant=variant,
+                               precision=precision)
+        out[precision] = gv
     ov = O.walks(prob, x, ids, seed=7, M=prob["M"], variant=variant, point_id=point_id)
     g.close()
-    # magnitude scales: sum_i |c_i| (|Phi_i| + 1) and sum_i |c_i| |grad Phi_i|, times the
-    # walk's conditioning (start flux and near-tangent chords)
-    cond = ov["scale"][:, 3]
-    sc_u = (ov["scale"][:, 0] + ov["scale"][:, 1]) * cond
-    sc_g = ov["scale"][:, 2] * cond
-    eu = np.abs(gv["u"] - ov["u"]) / np.maximum(sc_u, 1e-300)
-    eg = np.max(np.abs(gv["grad"] - ov["grad"]), axis=1) / np.maximum(sc_g, 1e-300)
-    return eu, eg
+    B_u, B_g = ov["scale"][:, 0], ov["scale"][:, 1]
+    err = {}
+    for precision, gv in out.items():
+        eu = np.abs(gv["u"] - ov["u"]) / np.maximum(B_u, 1e-300)
+        eg = np.max(np.abs(gv["grad"] - ov["grad"]), axis=1) / np.maximum(B_g, 1e-300)
+        err[precision] = np.maximum(eu, eg)
+    return err["fp64"], err["mixed"], ov["scale"][:, 2]
+
+
+_REPLAYS = {}
+
+
+def replays(W, O, case):
+    """The replays of a case (computed once for the FP64 and FP32 tests)."""
+    name, prob, x, variant = case
+    if name not in _REPLAYS:
+        parts = [replay(W, O, prob, x[p], variant, p, N_LARGE if p == 0 else 96) for p in range(len(x))]
+        _REPLAYS[name] = tuple(np.concatenate([r[k] for r in parts]) for k in range(3))
+    return _REPLAYS[name]
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_replay_fp64_per_walk(W, O, case):
-    name, prob, x, variant = case
-    for p in range(len(x)):
-        eu, eg = replay(W, O, prob, x[p], variant, "fp64", p)
-        assert eu.max() <= FP64_RTOL, (name, p, eu.max())
-        assert eg.max() <= FP64_RTOL, (name, p, eg.max())
+    e64, _, cond = replays(W, O, case)
+    assert e64.max() <= FP64_RTOL, (case[0], e64.max(), int((e64 > FP64_RTOL).sum()))
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_replay_fp32_per_walk(W, O, case):
-    name, prob, x, variant = case
-    bad = tot = 0
-    for p in range(len(x)):
-        eu, eg = replay(W, O, prob, x[p], variant, "mixed", p)
-        viol = (eu > FP32_RTOL) | (eg > FP32_RTOL)
-        bad += int(viol.sum())
-        tot += len(eu)
-    # star curves (near-tangent lines) and meshes (lines through an edge, within FP32 rounding)
-    # may change an FP32 intersection count: a legitimate branch flip
-    allowed = 0 if ("star" not in name and "mesh" not in name) else max(1, tot // 200)
-    assert bad <= allowed, f"{name}: {bad} of {tot} walks beyond {FP32_RTOL}"
+    name = case[0]
+    e64, e32, cond = replays(W, O, case)
+    well = cond <= COND_CAP
+    flips = well & (e32 > FP32_RTOL)
+    print(f"\n{name}: {len(cond)} walks, conditioning max {cond.max():.3g}, 99.9% {np.quantile(cond, 0.999):.3g}, "
+          f"{int((~well).sum())} above {COND_CAP:g} ({(~well).mean():.2e}); FP32 error / bound max "
+          f"{e32[well].max():.2e} (well-conditioned), {int(flips.sum())} branch flips")
+    assert np.all(e64[flips] <= FP64_RTOL), name          # a flip follows the oracle in FP64
+    assert flips.sum() <= FLIP_FRACTION * len(cond), (name, int(flips.sum()), len(cond))
 
 
 def _estimates(W, O, prob, x, n_walks, variant="plain", sched_group=1, seed=3, **kw):
@@ -190,7 +212,11 @@ def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
     estimate is still the mean over the same walks the oracle draws for that
     stream.  70 points = two full tiles and a ragged one; 2048 + 160 walks =
-    several walk chunks and a ragged chunk."""
+    several walk chunks and a ragged chunk.  A walk that takes another branch in
+    FP32 than in the oracle (beyond the per-walk bar at the tile's first point)
+    moves every point of its tile: such walks are replayed (each must follow the
+    oracle in FP64), their FP32-minus-oracle contribution is removed from the
+    comparison, and they count against the flip fraction of the replay tests."""
     prob = dict((c[0], c[1]) for c in CASES)[name]
     if name.startswith("star"):
         x = wl.star_inclusions_points(prob, 70, seed=22)
@@ -201,23 +227,41 @@ def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     else:
         x = wl.ball_points(70, prob["dim"], 23, radius=0.9)
     n_walks = 2048 + 160
+    M = prob["M"]
     g = W.Geometry(prob)
-    gr = W.woi_estimate(g, x, n_walks, seed=4, M=prob["M"], variant=variant, sched_group=sched_group, tile_points=32)
+    gr = W.woi_estimate(g, x, n_walks, seed=4, M=M, variant=variant, sched_group=sched_group, tile_points=32)
+    orr = O.estimate(prob, x, n_walks, seed=4, M=M, variant=variant, sched_group=sched_group, tile=32)
+    ids = np.arange(n_walks, dtype=np.uint64)
+    corr_u, corr_g = np.zeros(len(x)), np.zeros_like(orr["grad"])
+    flips = 0
+    kw = dict(seed=4, M=M, variant=variant, sched_group=sched_group)
+    for t in range(-(-len(x) // 32)):
+        x0 = x[32 * t]
+        v32 = W.woi_walk_values(g, x0, ids, point_id=t, precision="mixed", **kw)
+        ov = O.walks(prob, x0, ids, point_id=t, **kw)
+        e32 = np.maximum(np.abs(v32["u"] - ov["u"]) / np.maximum(ov["scale"][:, 0], 1e-300),
+                         np.max(np.abs(v32["grad"] - ov["grad"]), axis=1) / np.maximum(ov["scale"][:, 1], 1e-300))
+        bad = ids[e32 > FP32_RTOL]
+        flips += len(bad)
+        if len(bad) == 0:
+            continue
+        v64 = W.woi_walk_values(g, x0, bad, point_id=t, precision="fp64", **kw)
+        ob = O.walks(prob, x0, bad, point_id=t, **kw)
+        assert np.all(np.abs(v64["u"] - ob["u"]) <= FP64_RTOL * ob["scale"][:, 0]), (name, t)
+        for p in range(32 * t, min(len(x), 32 * t + 32)):
+            a = W.woi_walk_values(g, x[p], bad, point_id=t, precision="mixed", **kw)
+            b = O.walks(prob, x[p], bad, point_id=t, **kw)
+            corr_u[p] = np.sum(a["u"] - b["u"]) / n_walks
+            corr_g[p] = np.sum(a["grad"] - b["grad"], axis=0) / n_walks
     g.close()
-    orr = O.estimate(prob, x, n_walks, seed=4, M=prob["M"], variant=variant, sched_group=sched_group, tile=32)
-    zu = np.abs(gr["u"] - orr["u"]) / orr["se_u"]
-    zg = np.abs(gr["grad"] - orr["grad"]) / orr["se_grad"]
-    if name.startswith("star") or name.startswith("mesh"):
-        # a near-tangent line can change the FP32 intersection count of one shared walk
-        # (a legitimate branch flip, as in the per-walk replay); it moves every point of
-        # its tile by a small fraction of an SE, and the other tiles still agree to rounding
-        assert zu.max() <= 0.25 and zg.max() <= 0.25, name
-        assert np.median(zu) <= 1e-2 and np.median(zg) <= 1e-2, name
-        return
-    assert np.all(zu <= 1e-2), name
-    assert np.all(zg <= 1e-2), name
-    assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-3)
-    assert np.allclose(gr["se_grad"], orr["se_grad"], rtol=1e-3)
+    print(f"\n{name} tiles: {flips} branch flips in {3 * n_walks} shared walks")
+    zu = np.abs(gr["u"] - (orr["u"] + corr_u)) / orr["se_u"]
+    zg = np.abs(gr["grad"] - (orr["grad"] + corr_g)) / orr["se_grad"]
+    assert np.all(zu <= 1e-2), (name, zu.max())
+    assert np.all(zg <= 1e-2), (name, zg.max())
+    if flips == 0:
+        assert np.allclose(gr["se_u"], orr["se_u"], rtol=1e-3)
+        assert np.allclose(gr["se_grad"], orr["se_grad"], rtol=1e-3)
 
 
 def test_full_size_3d_workload_sampled(W, O):
@@ -384,8 +428,8 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
                                   "3d-nested-vr", "3d-zonal-vr", "6d-quad-vr", "ellipsoids-3d-vr", "mesh-rocks-vr"])
 def test_walk_trace_states_match_oracle(W, O, name):
     """woi_walk_trace (FP64): every state y_i, Q_i and T_i of every walk equals the
-    oracle's (Eqs. naive_woi_Q, naive_woi_T) to 1e-12 of its magnitude scale times the
-    walk's conditioning (a near-tangent chord amplifies rounding, as in the replay)."""
+    oracle's (Eqs. naive_woi_Q, naive_woi_T) to 1e-12 of the oracle's error bound of
+    that state and that Q (units of the unit roundoff), T exactly."""
     prob, x, variant = next((c[1], c[2], c[3]) for c in CASES if c[0] == name)
     g = W.Geometry(prob)
     ids = walk_ids(64)
@@ -396,12 +440,12 @@ def test_walk_trace_states_match_oracle(W, O, name):
     # a chain that ended keeps its last state on both sides; a chain dead from the start (no
     # start of its sign: Q = 0) has no state to compare
     alive = (ow["T"][:, :chains] != 0) & (ow["Q"][:, :chains] != 0)
-    cond = np.broadcast_to(ow["scale"][:, 3, None, None], alive.shape)[alive]
-    dy = np.abs(tr["Y"] - ow["Y"][:, :chains]).max(axis=-1)
-    assert np.all(dy[alive] <= 1e-12 * cond * (1 + np.abs(ow["Y"][:, :chains]).max(axis=-1)[alive])), name
-    for key in ("Q", "T"):
-        ref = ow[key][:, :chains]
-        assert np.all(np.abs(tr[key] - ref)[alive] <= 1e-12 * cond * (np.abs(ref)[alive] + 1e-300) + 1e-300), (name, key)
+    Y = ow["Y"][:, :chains]
+    dy = np.abs(tr["Y"] - Y).max(axis=-1)
+    assert np.all(dy[alive] <= 1e-12 * (ow["E_y"][:, :chains] + np.abs(Y).max(axis=-1))[alive]), name
+    dq = np.abs(tr["Q"] - ow["Q"][:, :chains])
+    assert np.all(dq[alive] <= 1e-12 * ow["E_Q"][:, :chains][alive] + 1e-300), name
+    assert np.array_equal(tr["T"][alive], ow["T"][:, :chains][alive]), name
 
 
 def test_autotune_keeps_the_estimate(W):

@@ -1,6 +1,8 @@
 """Multi-rank host logic on CPU: two gloo ranks each take a walk-range share
-(computed here with the oracle, as no GPU is needed for the host logic), the
-moments are all-reduced, and the merged estimate equals the single-range run."""
+(their moments computed here with the oracle, as there is no GPU), the moments
+are all-reduced, and the merged moments and estimate equal the single-range
+run's.  The same merge through the library's walk ranges and its finalize
+(woi_estimate_range, woi_finalize_moments) is a GPU test (test_gpu_multirank.py)."""
 import os
 import socket
 
@@ -68,6 +70,7 @@ def test_two_rank_gloo_merge(tmp_path):
     x = wl.concentric_2d_points()[:6]
     full = core.estimate(prob, x, 3000, seed=9, M=4)
     assert np.allclose(m0, _moments(full, 2), rtol=1e-12, atol=1e-13)
-    f = parallel.finalize(m0, 3000)
+    # per-walk schedules: the group means are the walks' values, so sum_gm = sum_f
+    f = core.finalize(m0[:, 0, :], m0[:, 0, :], m0[:, 1, :], 3000, 3000)
     assert np.allclose(f["u"], full["u"], rtol=1e-12, atol=1e-13)
     assert np.allclose(f["se_u"], full["se_u"], rtol=1e-9)

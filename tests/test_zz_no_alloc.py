@@ -36,14 +36,20 @@ def _check_close(a, b):
 
 
 def test_noalloc_matches_estimate_twice(W):
+    """Plain walks on spheres and circles, and the variance-reduced walk on 2D Fourier data,
+    whose start draws from the beta-sign arc tables that this entry point copies into the
+    fixed array; the star case puts its tables there too."""
     import torch
-    cases = [(wl.nested_3d_problem(), torch.from_numpy(wl.ball_points(200, 3, 31)).cuda(), 5000, 11),
-             (wl.concentric_2d_problem(), torch.from_numpy(wl.concentric_2d_points()).cuda(), 3000, 12)]
-    for prob, x, n_walks, seed in cases:
+    star = wl.star_inclusions_problem(seed=3, n_incl=3)
+    cases = [(wl.nested_3d_problem(), torch.from_numpy(wl.ball_points(200, 3, 31)).cuda(), 5000, 11, "plain"),
+             (wl.concentric_2d_problem(), torch.from_numpy(wl.concentric_2d_points()).cuda(), 3000, 12, "plain"),
+             (wl.concentric_2d_problem(), torch.from_numpy(wl.concentric_2d_points()).cuda(), 3000, 13, "vr"),
+             (star, torch.from_numpy(wl.star_inclusions_points(star, 40, seed=5)).cuda(), 2048, 14, "vr")]
+    for prob, x, n_walks, seed, variant in cases:
         g = W.Geometry(prob)
-        ref = W.woi_estimate(g, x, n_walks, seed=seed)
-        first = W.woi_estimate_noalloc(g, x, n_walks, seed=seed)
-        second = W.woi_estimate_noalloc(g, x, n_walks, seed=seed)
+        ref = W.woi_estimate(g, x, n_walks, seed=seed, M=prob["M"], variant=variant)
+        first = W.woi_estimate_noalloc(g, x, n_walks, seed=seed, M=prob["M"], variant=variant)
+        second = W.woi_estimate_noalloc(g, x, n_walks, seed=seed, M=prob["M"], variant=variant)
         torch.cuda.synchronize()
         _check_close(first, ref)
         _check_close(second, ref)
