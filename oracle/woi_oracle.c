@@ -42,15 +42,18 @@
  *     line / ray intersections by testing every triangle (no acceleration
  *     structure); a line through a point of triangle j skips triangle j.
  *
- * Readings of the paper taken here (each one is listed with its reason in
- * the design notes of the repository):
- *   R1 the alpha-sign product runs over m = 1..i (Thm 4.2), not m = 0..i;
+ * Readings of the paper taken here, each with its reason:
+ *   R1 the alpha-sign product runs over m = 1..i (Thm 4.2 and its proof), not
+ *      m = 0..i as the algorithms print it: alpha_{h_0} never appears in the
+ *      Neumann-series expansion of Sec. 3;
  *   R2 in the "otherwise" (uniform) transition T is left unchanged: the sign
  *      already lives in the signed K* inside Q (Thm 4.1 needs Q*T = prod K* / p);
- *   R3 K* is evaluated as K*(y_i, y_{i-1}) with the normal at the new point;
- *   R4 "descendant" means strict descendant at any depth;
+ *   R3 K* is evaluated as K*(y_i, y_{i-1}) with the normal at the new point, as
+ *      K*_ij is defined in Sec. 3 (Sec. 4.2.2 prints the arguments swapped);
+ *   R4 "descendant" means strict descendant at any depth: a ray from inside
+ *      any region nested in the target's meets the target from inside;
  *   R5 a line/ray that finds no admissible intersection (q = 0, a tangency of
- *      measure zero) ends the walk: T = 0 from then on.
+ *      measure zero) ends the walk: T = 0 from then on, as T *= q gives.
  */
 #include <math.h>
 #include <stdint.h>
@@ -164,7 +167,8 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Random-number protocol (documented in the design notes; both sides follow it):
+/* Random-number protocol (the oracle and the library each implement it from this
+ * definition; it is not in the paper, which draws its random numbers freely):
  *   key     = (seed_lo ^ point_id, seed_hi ^ instance)
  *   counter = (walk_lo, walk_hi, step, (chain << 4) | sub)      per-walk words
  *   counter = (group_lo, group_hi, step, 0x100)                 shared schedule words
