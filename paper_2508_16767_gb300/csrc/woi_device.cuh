@@ -618,16 +618,20 @@ __device__ __forceinline__ Real star_guard(const SGeom<Real> &g)
 // than pair_min_width (a tangency within the rounding of f) count one root for a sign change
 // and none otherwise.  fa, fb and da, db are f and f' at the interval's ends; nf, nd and ndip
 // the rounding levels of f and f' and the |f| below which a sign is not trusted.
-constexpr int kPairStack = 40;
+// depth-first stack: one pending piece per level; pieces stop at pair_min_width, so
+// log2(H / pair_min_width) + 2 levels suffice (13 + 2 in FP32, 35 + 2 in FP64)
+template <typename Real> __host__ __device__ constexpr int pair_stack() { return sizeof(Real) == 4 ? 16 : 40; }
 constexpr int kIntervalRoots = 4;
 template <typename Real> __host__ __device__ constexpr Real pair_min_width() { return sizeof(Real) == 4 ? (Real)4e-6 : (Real)1e-12; }
 
+// (the common case, a sign change with f monotone, is refined at the call site)
 template <typename Real>
-__device__ int star_interval_roots(const StarLineEval<Real> &ev, Real fa, Real fb, Real da, Real db, Real K, Real nf,
-                                   Real nd, Real ndip, Real *cand)
+__device__ int star_interval_roots(const StarLineEval<Real> &ev, Real fa, Real fb, Real da, Real db, Real K,
+                                                Real nf, Real nd, Real ndip, Real *cand)
 {
     using O = RealOps<Real>;
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
+    constexpr int kPairStack = pair_stack<Real>();
     Real lo_[kPairStack], hi_[kPairStack], flo_[kPairStack], fhi_[kPairStack], dlo_[kPairStack], dhi_[kPairStack];
     lo_[0] = 0;
     hi_[0] = H;
@@ -771,8 +775,16 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
         const Real da = g.scan_d[j][0] * z[1] - g.scan_d[j][1] * z[0];     // f' at the nodes
         const Real db = g.scan_d[jn][0] * z[1] - g.scan_d[jn][1] * z[0];
         const StarLineEval<Real> ev{g, yc, z, j, false, 0, (Real)0};
-        const int nc = star_interval_roots(ev, fa, fb, da, db, g.star_kpp, star_f_noise(g), star_df_noise(g),
-                                           star_dip_noise(g), cand);
+        int nc;
+        const Real dmin = RealOps<Real>::fabs_(da) < RealOps<Real>::fabs_(db) ? RealOps<Real>::fabs_(da)
+                                                                                : RealOps<Real>::fabs_(db);
+        if ((fa < 0) != (fb < 0) && (da < 0) == (db < 0) && dmin > g.star_kpp * H + star_df_noise(g)) {
+            cand[0] = star_refine(ev, (Real)0, H, fa, H * fa / (fa - fb));   // one crossing, f monotone
+            nc = 1;
+        } else {
+            nc = star_interval_roots(ev, fa, fb, da, db, g.star_kpp, star_f_noise(g), star_df_noise(g),
+                                     star_dip_noise(g), cand);
+        }
         for (int c = 0; c < nc; ++c) {
             Real ct, st, p[2];
             angle_cs(g, j, cand[c], &ct, &st);
