@@ -65,7 +65,7 @@ def alg_tally_flops(dim: int) -> float:
 # DRAM bytes per launch of the walk kernel(s) from an ncu capture of the named workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), scaled to one full launch; None once
 # the kernel has changed since the counters were taken.
-TRAFFIC = {"3d-nested": None, "batch": 289_699_840}   # batch: both group launches of one step
+TRAFFIC = {"3d-nested": 625_152, "batch": 289_699_840}   # batch: both group launches of one step
 
 # Warp instructions (all pipes, and the XU pipe: transcendentals, conversions) per walk-step of
 # the walk kernels, from an ncu capture of the same kernels (sm__inst_executed.sum and
