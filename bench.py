@@ -434,7 +434,7 @@ def measure_single(name, args, local, steps, warmup, extras=True):
            "clocks": clk.summary(), "gpu_launches": steps * (2 if args.precision == "mixed" else P + 1)}
     res["accuracy"] = accuracy(outs[0].cpu().numpy(), outs[1].cpu().numpy(), outs[2].cpu().numpy(),
                                outs[3].cpu().numpy(), ws * Wk)
-    if not extras or rank != 0 or ws != 1 or args.precision != "mixed" or args.tile_points:
+    if not extras or rank != 0 or ws != 1 or args.precision != "mixed" or args.tile_points or args.no_vr:
         geom.close()
         return res, problem, points
 
@@ -694,6 +694,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (extra_workloads)")
+    ap.add_argument("--no-vr", action="store_true", help="skip the variance-reduced comparison")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--walks-per-lane", type=int, default=0)
     ap.add_argument("--sched-group", type=int, default=0, help="walkers per schedule (default: the workload's)")
