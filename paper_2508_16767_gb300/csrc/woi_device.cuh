@@ -775,16 +775,8 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
         const Real da = g.scan_d[j][0] * z[1] - g.scan_d[j][1] * z[0];     // f' at the nodes
         const Real db = g.scan_d[jn][0] * z[1] - g.scan_d[jn][1] * z[0];
         const StarLineEval<Real> ev{g, yc, z, j, false, 0, (Real)0};
-        int nc;
-        const Real dmin = RealOps<Real>::fabs_(da) < RealOps<Real>::fabs_(db) ? RealOps<Real>::fabs_(da)
-                                                                                : RealOps<Real>::fabs_(db);
-        if ((fa < 0) != (fb < 0) && (da < 0) == (db < 0) && dmin > g.star_kpp * H + star_df_noise(g)) {
-            cand[0] = star_refine(ev, (Real)0, H, fa, H * fa / (fa - fb));   // one crossing, f monotone
-            nc = 1;
-        } else {
-            nc = star_interval_roots(ev, fa, fb, da, db, g.star_kpp, star_f_noise(g), star_df_noise(g),
-                                     star_dip_noise(g), cand);
-        }
+        const int nc = star_interval_roots(ev, fa, fb, da, db, g.star_kpp, star_f_noise(g), star_df_noise(g),
+                                           star_dip_noise(g), cand);
         for (int c = 0; c < nc; ++c) {
             Real ct, st, p[2];
             angle_cs(g, j, cand[c], &ct, &st);
