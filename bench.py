@@ -466,6 +466,31 @@ def measure_single(name, args, local, steps, warmup, extras=True):
                                    "value_at_plain_rms_error": P / (t_v * ratio), "accuracy": acc_v,
                                    "note": "two chains per walk; value_at_plain_rms_error scales the walks by "
                                            "(se_vr / se_plain)^2"}
+    # shared trajectories (Sec. 4.6: tiles of 32 points share their walks) on the 3D nested workload
+    if name == "3d-nested":
+        so = dict(opt, tile_points=32, block_size=0, walks_per_lane=0)
+        step(False, so)
+        sms = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(True, so)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sms.append((e0.elapsed_time(e1), woi.woi_last_kernel_ms(geom)))
+        t_s = float(np.mean([a for a, _ in sms])) / 1000.0
+        k_s = float(np.mean([b for _, b in sms]))
+        n_tiles = -(-P // 32)
+        fl = Wk * (M + 1) * (n_tiles * (alg_flops_per_walk_step(d, ell) - alg_tally_flops(d)) + P * alg_tally_flops(d))
+        res["shared_trajectories"] = {
+            "value": P / t_s, "unit": "estimates/s", "ms_per_step": 1000.0 * t_s, "tile_points": 32, "kernel_ms": k_s,
+            "roofline_frac": fl / (k_s / 1000.0) / 1e12 / peak,
+            "accuracy": accuracy(outs[0].cpu().numpy(), outs[1].cpu().numpy(), outs[2].cpu().numpy(),
+                                 outs[3].cpu().numpy(), Wk),
+            "note": "each tile's 32 points share one walk stream: the SE of every point is its own, the errors "
+                    "of points in a tile are correlated"}
     geom.close()
     return res, problem, points
 
@@ -506,7 +531,8 @@ def run_single_line(args, ws, rank, local):
                 "config": dict(res["config"], l2="flushed between steps (512 MiB write outside the step events)",
                                parallelism=f"replicas x{ws}, disjoint walk ranges, moments all-reduced"),
                 "walk_steps_per_s": res["walk_steps_per_s"], "accuracy": res["accuracy"], "roofline": res["roofline"],
-                "cpu_baseline": cpu, "variance_reduced": res.get("variance_reduced"), "e2e": e2e,
+                "cpu_baseline": cpu, "variance_reduced": res.get("variance_reduced"),
+                "shared_trajectories": res.get("shared_trajectories"), "e2e": e2e,
                 "clocks": res["clocks"], "gpu_launches": res["gpu_launches"]}
     return line
 
