@@ -115,6 +115,24 @@ template <> struct RealOps<float> {
         *s = (k & 2) ? -a : a;
         *c = ((k + 1) & 2) ? -b : b;
     }
+    // sin and cos of x radians: x / 2 pi rounded once (relative 6e-8, within the rounding of x
+    // itself for |x| <= pi), then sincos2pi; no large-argument path
+    __device__ static __forceinline__ void sincos_rad(float x, float *s, float *c)
+    {
+        sincos2pi(x * 0.159154943091895336f, s, c);
+    }
+    // sin and cos of a small angle: Taylor series to d^7 and d^8 for |d| <= 1/4 (the first
+    // omitted terms, d^9/9! and d^10/10!, are below 4e-11 relative); larger d through sincos_rad
+    __device__ static __forceinline__ void sincos_small(float d, float *s, float *c)
+    {
+        if (fabsf(d) <= 0.25f) {
+            const float d2 = d * d;
+            *s = fmaf(d * d2, fmaf(d2, fmaf(d2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), d);
+            *c = fmaf(d2, fmaf(d2, fmaf(d2, fmaf(d2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
+        } else {
+            sincos_rad(d, s, c);
+        }
+    }
     __device__ static __forceinline__ float sqrt_(float v) { return sqrtf(v); }
     // sqrt of a strictly positive argument through the reciprocal square root
     __device__ static __forceinline__ float sqrt_pos(float v) { return v * rsqrtf(v); }
@@ -122,7 +140,6 @@ template <> struct RealOps<float> {
     __device__ static __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
     __device__ static __forceinline__ float log_(float v) { return logf(v); }
     __device__ static __forceinline__ float fast_log(float v) { return __logf(v); }
-    __device__ static __forceinline__ void sincos_(float t, float *s, float *c) { sincosf(t, s, c); }
     __device__ static __forceinline__ float fabs_(float v) { return fabsf(v); }
     __device__ static __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
     __device__ static __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
@@ -135,7 +152,8 @@ template <> struct RealOps<double> {
     __device__ static __forceinline__ double rsqrt_(double v) { return 1.0 / sqrt(v); }
     __device__ static __forceinline__ double log_(double v) { return log(v); }
     __device__ static __forceinline__ double fast_log(double v) { return log(v); }
-    __device__ static __forceinline__ void sincos_(double t, double *s, double *c) { sincos(t, s, c); }
+    __device__ static __forceinline__ void sincos_rad(double t, double *s, double *c) { sincos(t, s, c); }
+    __device__ static __forceinline__ void sincos_small(double t, double *s, double *c) { sincos(t, s, c); }
     __device__ static __forceinline__ double fabs_(double v) { return fabs(v); }
     __device__ static __forceinline__ double rcp(double v) { return 1.0 / v; }
     __device__ static __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
@@ -356,7 +374,7 @@ template <typename Real>
 __device__ __forceinline__ void angle_cs(const SGeom<Real> &g, int j, Real delta, Real *ct, Real *st)
 {
     Real sd, cd;
-    RealOps<Real>::sincos_(delta, &sd, &cd);
+    RealOps<Real>::sincos_small(delta, &sd, &cd);
     const Real cj = g.node_cs[j][0], sj = g.node_cs[j][1];
     *ct = cj * cd - sj * sd;
     *st = sj * cd + cj * sd;
@@ -366,6 +384,7 @@ template <typename Real>
 __device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr)
 {
     Real ck = ct, sk = st, s = 1, ds = 0;
+#pragma unroll 1
     for (int k = 1; k <= g.star_K; ++k) {
         const Real a = g.star_a[k], b = g.star_b[k];
         s += a * ck + b * sk;
@@ -417,16 +436,31 @@ __device__ __forceinline__ double gl8_w(int q)
     return w[q];
 }
 
-// arc length from node j to node j + delta
+// Gauss-Legendre 4-point rule on [-1, 1] (positive half)
+__device__ __forceinline__ float gl4_x(int q) { return q == 0 ? 0.33998104358485626f : 0.86113631159405258f; }
+__device__ __forceinline__ float gl4_w(int q) { return q == 0 ? 0.65214515486254614f : 0.34785484513745386f; }
+
+// arc length from node j to node j + delta (|delta| <= 2 pi / kNodes): Gauss-Legendre with 8
+// points in FP64 and 4 in FP32, whose error on the panel, delta^9 (4!)^4 / (9 (8!)^3) times
+// max |speed^(8)| (at most 16^8 times the curve's size for degree <= 16), is below 1e-10 of
+// the panel's length, far below the FP32 rounding
 template <typename Real>
 __device__ Real star_local_arclen(const SGeom<Real> &g, int j, Real delta)
 {
     const Real half = (Real)0.5 * delta;
     Real s = 0;
+    if constexpr (sizeof(Real) == 4) {
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {   // nodes half -+ x_0 half, half -+ x_1 half
+            const Real xq = gl4_x(q >> 1) * half;
+            s += gl4_w(q >> 1) * star_speed_at(g, j, (q & 1) ? half + xq : half - xq);
+        }
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const Real xq = (Real)gl8_x(q) * half;
-        s += (Real)gl8_w(q) * (star_speed_at(g, j, half - xq) + star_speed_at(g, j, half + xq));
+        for (int q = 0; q < 4; ++q) {
+            const Real xq = (Real)gl8_x(q) * half;
+            s += (Real)gl8_w(q) * (star_speed_at(g, j, half - xq) + star_speed_at(g, j, half + xq));
+        }
     }
     return half * s;
 }
@@ -446,6 +480,7 @@ __device__ void star_at_arclen(const SGeom<Real> &g, double s_abs, int *jo, Real
     Real delta = ds / star_speed_at(g, lo, (Real)0);
     if (!(delta > d_lo && delta < d_hi)) delta = (Real)0.5 * H;
     const int iters = sizeof(Real) == 4 ? 12 : 30;
+#pragma unroll 1
     for (int it = 0; it < iters; ++it) {
         const Real f = star_local_arclen(g, lo, delta) - ds;
         if (f == (Real)0) break;
@@ -499,9 +534,10 @@ __device__ void star_dd(const SGeom<Real> &g, int j, Real delta, int js, Real ds
     Real cc, sc;                                             // c = t_j + (delta + ds - dj H) / 2
     angle_cs(g, j, (Real)0.5 * (delta + ds - (Real)dj * H), &cc, &sc);
     Real sh, ch;
-    O::sincos_(h, &sh, &ch);
+    O::sincos_rad(h, &sh, &ch);
     Real cmc = cc, smc = sc, cmh = ch, smh = sh;             // cos / sin of m c and m h, m = 1
     Real Dx = 0, Dy = 0, dDx = 0, dDy = 0;
+#pragma unroll 1
     for (int m = 1; m <= g.star_K + 1; ++m) {
         const Real x = (Real)m * h, x2 = x * x;
         Real S, Sp;                                          // S(x) and S'(x)
@@ -534,28 +570,29 @@ __device__ void star_dd(const SGeom<Real> &g, int j, Real delta, int js, Real ds
 
 // the function whose roots in scan interval j are the crossings: f(delta) = (gamma - yc) x z
 // (a ray, or a line away from its start), or the divided difference g of the line through the
-// state (js, ds) (dd = true)
-template <typename Real>
+// state (js, ds) (DD = true); a compile-time choice, so that each search is compiled with
+// its own evaluator only
+template <typename Real, bool DD>
 struct StarLineEval {
     const SGeom<Real> &g;
     const Real *yc, *z;
     int j;
-    bool dd;
     int js;
     Real ds;
     __device__ __forceinline__ void operator()(Real delta, Real *v, Real *dv) const
     {
-        if (dd) star_dd(g, j, delta, js, ds, z, v, dv, (Real *)nullptr);
+        if constexpr (DD) star_dd(g, j, delta, js, ds, z, v, dv, (Real *)nullptr);
         else star_line_f(g, j, delta, yc, z, v, dv);
     }
 };
 
 // root in (a, b) given sign(v(a)) (safeguarded Newton in delta)
-template <typename Real>
-__device__ Real star_refine(const StarLineEval<Real> &ev, Real a, Real b, Real fa, Real t0 = (Real)-1)
+template <typename Real, typename Ev>
+__device__ Real star_refine(const Ev &ev, Real a, Real b, Real fa, Real t0 = (Real)-1)
 {
     Real t = (t0 > a && t0 < b) ? t0 : (Real)0.5 * (a + b);
     const int iters = sizeof(Real) == 4 ? 40 : 90;
+#pragma unroll 1
     for (int it = 0; it < iters; ++it) {
         Real f, df;
         ev(t, &f, &df);
@@ -619,52 +656,55 @@ __device__ __forceinline__ Real star_guard(const SGeom<Real> &g)
 // and none otherwise.  fa, fb and da, db are f and f' at the interval's ends; nf, nd and ndip
 // the rounding levels of f and f' and the |f| below which a sign is not trusted.
 // depth-first stack: one pending piece per level; pieces stop at pair_min_width, so
-// log2(H / pair_min_width) + 2 levels suffice (13 + 2 in FP32, 35 + 2 in FP64)
+// log2(H / pair_min_width) + 1 levels suffice (13 + 1 in FP32, 35 + 1 in FP64)
 template <typename Real> __host__ __device__ constexpr int pair_stack() { return sizeof(Real) == 4 ? 16 : 40; }
 constexpr int kIntervalRoots = 4;
 template <typename Real> __host__ __device__ constexpr Real pair_min_width() { return sizeof(Real) == 4 ? (Real)4e-6 : (Real)1e-12; }
 
-// (the common case, a sign change with f monotone, is refined at the call site)
-template <typename Real>
-__device__ int star_interval_roots(const StarLineEval<Real> &ev, Real fa, Real fb, Real da, Real db, Real K,
-                                                Real nf, Real nd, Real ndip, Real *cand)
+// The piece under test is held in registers; the stack holds the right halves still pending
+// (one per level), so a piece that needs no split touches no local memory.
+template <typename Real, typename Ev>
+__device__ int star_interval_roots(const Ev &ev, Real fa, Real fb, Real da, Real db, Real K,
+                                   Real nf, Real nd, Real ndip, Real *cand)
 {
     using O = RealOps<Real>;
-    const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
     constexpr int kPairStack = pair_stack<Real>();
     Real lo_[kPairStack], hi_[kPairStack], flo_[kPairStack], fhi_[kPairStack], dlo_[kPairStack], dhi_[kPairStack];
-    lo_[0] = 0;
-    hi_[0] = H;
-    flo_[0] = fa;
-    fhi_[0] = fb;
-    dlo_[0] = da;
-    dhi_[0] = db;
-    int sp = 1, nc = 0;
-    while (sp > 0 && nc < kIntervalRoots) {
-        --sp;
-        const Real lo = lo_[sp], hi = hi_[sp], flo = flo_[sp], fhi = fhi_[sp], dlo = dlo_[sp], dhi = dhi_[sp];
+    Real lo = 0, hi = (Real)(2.0 * 3.14159265358979323846 / kNodes), flo = fa, fhi = fb, dlo = da, dhi = db;
+    int sp = 0, nc = 0;
+    for (;;) {
         const Real w = hi - lo;
         const Real dmin = O::fabs_(dlo) < O::fabs_(dhi) ? O::fabs_(dlo) : O::fabs_(dhi);
         const bool mono = (dlo < 0) == (dhi < 0) && dmin > K * w + nd;
-        const bool last = w <= pair_min_width<Real>() || sp + 2 > kPairStack;
+        const bool last = w <= pair_min_width<Real>() || sp + 1 > kPairStack;
+        bool split = false;
         if ((flo < 0) == (fhi < 0)) {
             const Real fmin_ = O::fabs_(flo) < O::fabs_(fhi) ? O::fabs_(flo) : O::fabs_(fhi);
-            if (mono || fmin_ > K * w * w * (Real)0.125 + nf || last) continue;
+            split = !(mono || fmin_ > K * w * w * (Real)0.125 + nf || last);
         } else if (mono || last) {
             cand[nc++] = star_refine(ev, lo, hi, flo, lo + w * flo / (flo - fhi));   // secant start
-            continue;
+        } else {
+            split = true;
         }
-        const Real m = (Real)0.5 * (lo + hi);
-        Real fm, dm;
-        ev(m, &fm, &dm);
-        // a dip through zero between ends of one sign brackets roots in both halves, unless the
-        // dip is within the rounding of f (a tangency: no root)
-        if ((flo < 0) == (fhi < 0) && (fm < 0) != (flo < 0) && O::fabs_(fm) <= ndip) continue;
-        // the right half below the left one: the left one is searched first (scan order)
-        lo_[sp] = m; hi_[sp] = hi; flo_[sp] = fm; fhi_[sp] = fhi; dlo_[sp] = dm; dhi_[sp] = dhi;
-        ++sp;
-        lo_[sp] = lo; hi_[sp] = m; flo_[sp] = flo; fhi_[sp] = fm; dlo_[sp] = dlo; dhi_[sp] = dm;
-        ++sp;
+        if (split) {
+            const Real m = (Real)0.5 * (lo + hi);
+            Real fm, dm;
+            ev(m, &fm, &dm);
+            // a dip through zero between ends of one sign brackets roots in both halves, unless
+            // the dip is within the rounding of f (a tangency: no root)
+            if (!((flo < 0) == (fhi < 0) && (fm < 0) != (flo < 0) && O::fabs_(fm) <= ndip)) {
+                // the right half waits; the left one is searched first (scan order)
+                lo_[sp] = m; hi_[sp] = hi; flo_[sp] = fm; fhi_[sp] = fhi; dlo_[sp] = dm; dhi_[sp] = dhi;
+                ++sp;
+                hi = m;
+                fhi = fm;
+                dhi = dm;
+                continue;
+            }
+        }
+        if (sp == 0 || nc >= kIntervalRoots) break;
+        --sp;
+        lo = lo_[sp]; hi = hi_[sp]; flo = flo_[sp]; fhi = fhi_[sp]; dlo = dlo_[sp]; dhi = dhi_[sp];
     }
     return nc;
 }
@@ -699,7 +739,9 @@ __device__ __forceinline__ void star_mark_window(const Real *yc, const Real *z, 
 // Intersections of the line (ray = false) or ray (ray = true) yc + s z (yc
 // relative to the star centre) with the star.  A root is a point of the curve on
 // the line, so it lies where the line is inside the annulus rmin <= |p| <= rmax:
-// at most two windows of polar angle, scanned node by node (roots as in
+// at most two windows of polar angle (for a ray, their parts with s > 0; a window
+// cut at s = 0 holds yc, so |yc| >= rmin > 0 and its polar angle is defined),
+// scanned node by node (roots as in
 // star_interval_roots, of f = (gamma - yc) x z).  For a line, whose start is the
 // state itself on the curve at angle (sj, sd), the three scan intervals around that
 // angle hold only the start unless the line is close to tangent there; then they are
@@ -724,8 +766,14 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
         const Real outer = RealOps<Real>::sqrt_(g.star_rmax * g.star_rmax - e * e);
         const Real in2 = g.star_rmin * g.star_rmin - e * e;
         const Real inner = in2 > (Real)0 ? RealOps<Real>::sqrt_(in2) : (Real)0;
-        star_mark_window(yc, z, e, sf - outer, sf - inner, mask);
-        star_mark_window(yc, z, e, sf + inner, sf + outer, mask);
+        Real a0 = sf - outer, a1 = sf + inner;
+        const Real b0 = sf - inner, b1 = sf + outer;
+        if (ray) {   // only s > 0 is on the ray: the windows are cut at the start
+            a0 = a0 > (Real)0 ? a0 : (Real)0;
+            a1 = a1 > (Real)0 ? a1 : (Real)0;
+        }
+        if (!ray || b0 > (Real)0) star_mark_window(yc, z, e, a0, b0, mask);
+        if (!ray || b1 > (Real)0) star_mark_window(yc, z, e, a1, b1, mask);
     }
     int q = 0;
     const Real unit = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-14;    // sign trust, relative
@@ -746,13 +794,15 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
     }
     if (near_start) {
         // near-tangent line: the roots of g in those intervals, with |g''| <= |gamma'''| / 3
-        StarLineEval<Real> ev{g, yc, z, 0, true, sj, sd};
+        StarLineEval<Real, true> ev{g, yc, z, 0, sj, sd};
         Real gv[4], gd[4];
+#pragma unroll 1
         for (int n = 0; n < 4; ++n) {
             ev.j = (sj - 1 + n) & (kNodes - 1);
             ev((Real)0, &gv[n], &gd[n]);
         }
         const Real nf = star_df_noise(g), nd = (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_kpp;
+#pragma unroll 1
         for (int o = 0; o < 3; ++o) {
             ev.j = (sj - 1 + o) & (kNodes - 1);
             Real cand[kIntervalRoots];
@@ -774,7 +824,7 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
         const int jn = (j + 1 == kNodes) ? 0 : j + 1;
         const Real da = g.scan_d[j][0] * z[1] - g.scan_d[j][1] * z[0];     // f' at the nodes
         const Real db = g.scan_d[jn][0] * z[1] - g.scan_d[jn][1] * z[0];
-        const StarLineEval<Real> ev{g, yc, z, j, false, 0, (Real)0};
+        const StarLineEval<Real, false> ev{g, yc, z, j, 0, (Real)0};
         const int nc = star_interval_roots(ev, fa, fb, da, db, g.star_kpp, star_f_noise(g), star_df_noise(g),
                                            star_dip_noise(g), cand);
         for (int c = 0; c < nc; ++c) {
