@@ -1748,7 +1748,9 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
                 trials = true;
             }
         }
-#pragma unroll
+        // with general surfaces one copy of the transition code serves both chains (the
+        // instruction footprint, not the work, bounds those kernels)
+#pragma unroll(STAR ? 1 : 2)
         for (int k = 0; k < (VR ? 2 : 1); ++k) {
             StepWords w = w0;
             if (k == 1 && !trials) {
