@@ -171,8 +171,10 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
  * definition; it is not in the paper, which draws its random numbers freely):
  *   key     = (seed_lo ^ point_id, seed_hi ^ instance)
  *   counter = (walk_lo, walk_hi, step, (chain << 4) | sub)      per-walk words
- *   counter = (group_lo, group_hi, step, 0x100)                 shared schedule words
- * Word k of a (step, chain) stream is word k % 4 of sub-call k / 4. */
+ * Word k of a (step, chain) stream is word k % 4 of sub-call k / 4.  With a shared
+ * schedule (W_g walkers per schedule, Alg. 1) the schedule word of step i of every walk
+ * in group g is the one the group's first walk, g W_g, draws for itself: word 0 of its
+ * (step i, chain 0) stream. */
 typedef struct {
     uint32_t key[2];
     uint64_t walk;
@@ -926,8 +928,9 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
         uint32_t hw;
         if (o->sched_group == 1) {
             hw = or_word(&rng, i, 0, 0);
-        } else {
-            uint32_t ctr[4] = {(uint32_t)group, (uint32_t)(group >> 32), (uint32_t)i, 0x100u}, w4[4];
+        } else {   /* the group's first walk's own schedule word */
+            const uint64_t first = group * (uint64_t)o->sched_group;
+            uint32_t ctr[4] = {(uint32_t)first, (uint32_t)(first >> 32), (uint32_t)i, 0u}, w4[4];
             or_philox4x32_10(ctr, rng.key, w4);
             hw = w4[0];
         }

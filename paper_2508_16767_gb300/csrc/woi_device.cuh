@@ -60,7 +60,8 @@ __device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, ui
 
 // Random-number protocol: key = (seed_lo ^ point, seed_hi ^ instance);
 // counter = (walk_lo, walk_hi, step, (chain << 4) | sub) for the walk's own
-// words and (group_lo, group_hi, step, 0x100) for a shared schedule.
+// words.  A shared schedule (groups of 32 walks) takes, in step i, the schedule
+// word of the group's first walk: word 0 of that walk's (step i, chain 0) stream.
 struct Rng {
     uint32_t k0, k1;
     uint32_t w0, w1;
@@ -772,8 +773,11 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
             a0 = a0 > (Real)0 ? a0 : (Real)0;
             a1 = a1 > (Real)0 ? a1 : (Real)0;
         }
-        if (!ray || b0 > (Real)0) star_mark_window(yc, z, e, a0, b0, mask);
-        if (!ray || b1 > (Real)0) star_mark_window(yc, z, e, a1, b1, mask);
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {   // one copy of the marking code
+            const Real sa = k == 0 ? a0 : a1, sb = k == 0 ? b0 : b1;
+            if (!ray || sb > (Real)0) star_mark_window(yc, z, e, sa, sb, mask);
+        }
     }
     int q = 0;
     const Real unit = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-14;    // sign trust, relative
@@ -1722,7 +1726,10 @@ __device__ void chain_step(const SGeom<Real> &g, const DevGeom *gd, int h, int r
 // The steps of one walk (Algorithms 2-3), handing each state to `sink`:
 // sink(i, k, chain, c) with c = N w_i ||alpha||_1^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i
 // the coefficient of Phi(x, y_i) (0 for a chain that has ended).
-template <typename Real, int D, bool VR, bool STAR, typename Sink>
+// LANE0: the 32 lanes of the warp run the 32 walks of one schedule group together, lane 0
+// the group's first, so a shared schedule word is lane 0's own (one shuffle per step).
+// Otherwise the word is drawn from the first walk's stream here.
+template <typename Real, int D, bool VR, bool STAR, bool LANE0 = false, typename Sink>
 __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *gd, const Rng &rng, int sched_group,
                                            uint64_t group, Sink &sink)
 {
@@ -1735,8 +1742,12 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
         if constexpr (two_calls<D>()) w0.b = rng.words(i, 0, 1);
         uint32_t hw = w0.a.x;
         if (sched_group > 1) {
-            const U4 gw = philox10((uint32_t)group, (uint32_t)(group >> 32), (uint32_t)i, 0x100u, rng.k0, rng.k1);
-            hw = gw.x;
+            if constexpr (LANE0) {
+                hw = __shfl_sync(0xFFFFFFFFu, hw, 0);
+            } else {
+                const uint64_t first = group * 32u;
+                hw = philox10((uint32_t)first, (uint32_t)(first >> 32), (uint32_t)i, 0u, rng.k0, rng.k1).x;
+            }
         }
         const int h = schedule(g, i, hw);
         if (i > 0) S *= g.alpha_sign[h];
@@ -1748,9 +1759,11 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
                 trials = true;
             }
         }
-        // with general surfaces one copy of the transition code serves both chains (the
-        // instruction footprint, not the work, bounds those kernels)
-#pragma unroll(STAR ? 1 : 2)
+        // with general surfaces, and on spheres in d >= 4, one copy of the transition code
+        // serves both chains (the instruction footprint, not the work, bounds those kernels:
+        // unrolled, the star's variance-reduced kernel is 1.6x and the 6D one 1.14x slower; on
+        // spheres in d <= 3 the unrolled loop is 9 % faster)
+#pragma unroll((STAR || D >= 4) ? 1 : 2)
         for (int k = 0; k < (VR ? 2 : 1); ++k) {
             StepWords w = w0;
             if (k == 1 && !trials) {
@@ -1793,14 +1806,14 @@ struct TallySink {
 // one walk: returns the tally f[0] (u) and f[1..D] (grad u) of
 // N sum_i w_i A^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i Phi(x, Y_i), summed
 // over the two chains for VR
-template <typename Real, int D, bool VR, bool STAR, bool TRACE = false>
+template <typename Real, int D, bool VR, bool STAR, bool TRACE = false, bool LANE0 = false>
 __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[kMaxDim], const Rng &rng,
                      int sched_group, uint64_t group, Real *f, double *trace = nullptr)
 {
 #pragma unroll
     for (int c = 0; c <= D; ++c) f[c] = 0;
     TallySink<Real, D, TRACE> sink{g, xc, f, trace};
-    walk_steps<Real, D, VR, STAR>(g, gd, rng, sched_group, group, sink);
+    walk_steps<Real, D, VR, STAR, LANE0>(g, gd, rng, sched_group, group, sink);
 }
 
 // Two independent walks of one lane, advanced step by step in the same loop so that the

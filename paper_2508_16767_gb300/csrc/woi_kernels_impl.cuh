@@ -109,7 +109,11 @@ __device__ __forceinline__ void run_unit(const SGeomFor<float, D, STAR> &g, cons
         if (valid) {
             rng.w0 = (uint32_t)w;
             rng.w1 = (uint32_t)((uint64_t)w >> 32);
-            walk<float, D, VR, STAR>(g, geom, xc, rng, sched_group, (uint64_t)w / 32u, f);
+            // a shared schedule: w_base is a multiple of 32 and a round is all valid or all past
+            // the end, so lane 0 runs the first walk of the round's group; the general-surface
+            // kernels take its word by a shuffle, the sphere kernels (whose workloads use
+            // per-walk schedules, and whose code is timed to the instruction) draw it
+            walk<float, D, VR, STAR, false, STAR>(g, geom, xc, rng, sched_group, (uint64_t)w / 32u, f);
         } else {
 #pragma unroll
             for (int c = 0; c <= D; ++c) f[c] = 0.f;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
             if (w < w_end) {
                 rng.w0 = (uint32_t)w;
                 rng.w1 = (uint32_t)((uint64_t)w >> 32);
-                walk_steps<float, D, VR, STAR>(g, id.geom, rng, id.sched_group, (uint64_t)w / 32u, sink);
+                walk_steps<float, D, VR, STAR, STAR>(g, id.geom, rng, id.sched_group, (uint64_t)w / 32u, sink);
             }
             __syncwarp();
             const int n_valid = (int)min((int64_t)32, w_end - w0);
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(256) k_walk_fp64_point(Fp64PointParams p)
         rng.k1 = (uint32_t)(p.seed >> 32) ^ p.instance_id;
         rng.w0 = (uint32_t)w;
         rng.w1 = (uint32_t)((uint64_t)w >> 32);
-        walk<double, D, VR, STAR>(g, p.geom, xc, rng, p.sched_group, (uint64_t)w / 32u, f);
+        walk<double, D, VR, STAR, false, STAR>(g, p.geom, xc, rng, p.sched_group, (uint64_t)w / 32u, f);
     } else {
 #pragma unroll
         for (int c = 0; c <= D; ++c) f[c] = 0.0;
