@@ -710,12 +710,13 @@ __device__ int star_interval_roots(const Ev &ev, Real fa, Real fb, Real da, Real
     return nc;
 }
 
-// mark the scan intervals of the nodes whose angles lie between the polar angles of
-// the points yc + sa z and yc + sb z (the angle is monotone along a line that misses
-// the centre; it increases when e = yc x z > 0), padded by one node on each side
+// the scan intervals of the nodes whose angles lie between the polar angles of the points
+// yc + sa z and yc + sb z (the angle is monotone along a line that misses the centre; it
+// increases when e = yc x z > 0), padded by one node on each side: the cyclic node range
+// [j0, j0 + count)
 template <typename Real>
-__device__ __forceinline__ void star_mark_window(const Real *yc, const Real *z, Real e, Real sa, Real sb,
-                                                 uint32_t *mask)
+__device__ __forceinline__ void star_window(const Real *yc, const Real *z, Real e, Real sa, Real sb, int *j0,
+                                            int *count)
 {
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes), TWO_PI = (Real)(2.0 * 3.14159265358979323846);
     Real pa = RealOps<Real>::atan2_(yc[1] + sa * z[1], yc[0] + sa * z[0]);
@@ -729,12 +730,9 @@ __device__ __forceinline__ void star_mark_window(const Real *yc, const Real *z, 
     if (pb < 0) pb += TWO_PI;
     Real span = pb - pa;
     if (span < 0) span += TWO_PI;
-    int j0 = (int)(pa / H) - 1;
-    const int count = (int)(span / H) + 3;
-    for (int c = 0; c < count && c < kNodes; ++c) {
-        const int j = (j0 + c) & (kNodes - 1);   // kNodes is a power of two
-        mask[j >> 5] |= 1u << (j & 31);
-    }
+    *j0 = ((int)(pa / H) - 1) & (kNodes - 1);   // kNodes is a power of two
+    const int c = (int)(span / H) + 3;
+    *count = c < kNodes ? c : kNodes;
 }
 
 // Intersections of the line (ray = false) or ray (ray = true) yc + s z (yc
@@ -759,9 +757,9 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
     const Real tiny = sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-9;
     const Real ae = RealOps<Real>::fabs_(e);
     if (ae >= g.star_rmax) return 0;
-    uint32_t mask[kNodes / 32];
-#pragma unroll
-    for (int w = 0; w < kNodes / 32; ++w) mask[w] = 0u;
+    // the windows as at most two cyclic node ranges [s0, s0 + c0) and [s1, s1 + c1), merged where
+    // they overlap or touch, so that every interval is scanned once
+    int s0 = 0, c0 = 0, s1 = 0, c1 = 0, nr = 0;
     {
         const Real sf = -(yc[0] * z[0] + yc[1] * z[1]);          // foot of the perpendicular from the centre
         const Real outer = RealOps<Real>::sqrt_(g.star_rmax * g.star_rmax - e * e);
@@ -774,9 +772,32 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
             a1 = a1 > (Real)0 ? a1 : (Real)0;
         }
 #pragma unroll 1
-        for (int k = 0; k < 2; ++k) {   // one copy of the marking code
+        for (int k = 0; k < 2; ++k) {   // one copy of the window code
             const Real sa = k == 0 ? a0 : a1, sb = k == 0 ? b0 : b1;
-            if (!ray || sb > (Real)0) star_mark_window(yc, z, e, sa, sb, mask);
+            if (ray && !(sb > (Real)0)) continue;
+            int jw, cw;
+            star_window(yc, z, e, sa, sb, &jw, &cw);
+            if (nr == 0) {
+                s0 = jw;
+                c0 = cw;
+            } else {
+                s1 = jw;
+                c1 = cw;
+            }
+            ++nr;
+        }
+        if (nr == 2) {
+            const int d01 = (s1 - s0) & (kNodes - 1), d10 = (s0 - s1) & (kNodes - 1);
+            if (d01 <= c0) {            // the second starts inside the first or where it ends
+                const int u = d01 + c1 > c0 ? d01 + c1 : c0;
+                c0 = u < kNodes ? u : kNodes;
+                nr = 1;
+            } else if (d10 <= c1) {     // the first starts inside the second or where it ends
+                const int u = d10 + c0 > c1 ? d10 + c0 : c1;
+                s0 = s1;
+                c0 = u < kNodes ? u : kNodes;
+                nr = 1;
+            }
         }
     }
     int q = 0;
@@ -785,11 +806,8 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
     if (!ray) {
         // the intervals sj - 1, sj, sj + 1 around the start hold no crossing but the start itself
         // unless the line is close to tangent there: |g'| <= |gamma''| / 2 = K / 2, so g keeps the
-        // sign of g(s) = gamma'(s) x z within 2 H of s when |g(s)| > K H (plus rounding)
-        for (int n = 0; n < 3; ++n) {
-            const int j = (sj - 1 + n) & (kNodes - 1);
-            mask[j >> 5] &= ~(1u << (j & 31));
-        }
+        // sign of g(s) = gamma'(s) x z within 2 H of s when |g(s)| > K H (plus rounding); the
+        // scan of f skips them
         Real ct, st, r, dr;
         angle_cs(g, sj, sd, &ct, &st);
         star_eval(g, ct, st, &r, &dr);
@@ -853,15 +871,19 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
     int cj[kCand];
     Real cfa[kCand], cfb[kCand];
     const Real guard = star_guard(g);
-    int w = 0;
-    uint32_t bits = mask[0];
+    int r = 0, t = 0;   // the range being scanned and the position in it
     for (int round = 0; round <= kNodes / kCand; ++round) {
         int n_cand = 0;
         for (;;) {
-            while (bits == 0u && w + 1 < kNodes / 32) bits = mask[++w];
-            if (bits == 0u || n_cand == kCand) break;
-            const int j = w * 32 + __ffs(bits) - 1;
-            bits &= bits - 1;
+            if (r >= nr || n_cand == kCand) break;
+            if (t >= (r == 0 ? c0 : c1)) {
+                ++r;
+                t = 0;
+                continue;
+            }
+            const int j = ((r == 0 ? s0 : s1) + t) & (kNodes - 1);
+            ++t;
+            if (!ray && ((j - sj + 1) & (kNodes - 1)) < 3) continue;   // the three around the start
             const int jn = (j + 1 == kNodes) ? 0 : j + 1;
             const Real fa = g.scan[j][0] * z[1] - g.scan[j][1] * z[0] - e;
             const Real fb = g.scan[jn][0] * z[1] - g.scan[jn][1] * z[0] - e;
@@ -873,7 +895,7 @@ __device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Re
             }
         }
         for (int c = 0; c < n_cand; ++c) roots_of(cj[c], cfa[c], cfb[c]);
-        if (bits == 0u) break;   // the mask is exhausted
+        if (r >= nr) break;   // the ranges are exhausted
     }
     return q;
 }
