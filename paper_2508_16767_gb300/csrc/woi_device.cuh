@@ -908,7 +908,88 @@ template <typename Real> __device__ __forceinline__ const Real *flux_coefs(const
 template <> __device__ __forceinline__ const float *flux_coefs<float>(const DevGeom *gd) { return gd->flux_coef_f; }
 template <> __device__ __forceinline__ const double *flux_coefs<double>(const DevGeom *gd) { return gd->flux_coef; }
 
+// the general real spherical harmonics (3D) and harmonic polynomials (the workloads' degree-2
+// data take the quadratic forms in flux_value; inlined, these loops are half of a kernel's
+// code), with out-of-line copies
+template <typename Real>
+__device__ __forceinline__ Real flux_real_sh_body(const Real *c, int nc, const Real *u)
+{
+    // associated Legendre P_l^m(x) without the (-1)^m phase, x = cos(polar); the
+    // coefficients already carry the normalisation of the real harmonics
+    const Real x = u[2];
+    Real sx2 = (Real)1 - x * x;
+    sx2 = sx2 > (Real)0 ? sx2 : (Real)0;
+    const Real sx = RealOps<Real>::sqrt_(sx2);
+    Real ca = 1, sa = 0;  // cos / sin of the azimuth
+    if (sx > (Real)0) {
+        const Real inv = (Real)1 / sx;
+        ca = u[0] * inv;
+        sa = u[1] * inv;
+    }
+    int L = 0;
+    while ((L + 2) * (L + 2) <= nc) ++L;
+    Real v = 0;
+    Real pmm = 1, cm = 1, sm = 0;  // P_m^m, cos(m az), sin(m az)
+    for (int m = 0; m <= L; ++m) {
+        if (m > 0) {
+            pmm *= (Real)(2 * m - 1) * sx;
+            const Real cn = cm * ca - sm * sa;
+            sm = sm * ca + cm * sa;
+            cm = cn;
+        }
+        Real p_prev = 0, p_cur = pmm;
+        for (int l = m; l <= L; ++l) {
+            if (l > m) {
+                const Real p_next = (l == m + 1) ? x * (Real)(2 * m + 1) * pmm
+                                                 : ((Real)(2 * l - 1) * x * p_cur - (Real)(l + m - 1) * p_prev) / (Real)(l - m);
+                p_prev = p_cur;
+                p_cur = p_next;
+            }
+            if (m == 0) v += c[l * l + l] * p_cur;
+            else v += (c[l * l + l + m] * cm + c[l * l + l - m] * sm) * p_cur;
+        }
+    }
+    return v;
+}
 template <typename Real, int D>
+__device__ __forceinline__ Real flux_harmonic_poly_body(const Real *c, const Real *y, const Real *n)
+{
+    const Real s = c[0];
+    const int T = (int)c[1];
+    Real grad[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) grad[k] = 0;
+    for (int t = 0; t < T; ++t) {
+        const Real *row = c + 2 + t * (D + 1);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int ek = (int)row[1 + k];
+            if (ek == 0) continue;
+            Real term = row[0] * (Real)ek;
+            for (int j = 0; j < D; ++j) {
+                const int e = (int)row[1 + j] - (j == k ? 1 : 0);
+                for (int p = 0; p < e; ++p) term *= y[j];
+            }
+            grad[k] += term;
+        }
+    }
+    Real v = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) v += n[k] * grad[k];
+    return s * v;
+}
+template <typename Real>
+__device__ __noinline__ Real flux_real_sh(const Real *c, int nc, const Real *u) { return flux_real_sh_body<Real>(c, nc, u); }
+template <typename Real, int D>
+__device__ __noinline__ Real flux_harmonic_poly(const Real *c, const Real *y, const Real *n)
+{
+    return flux_harmonic_poly_body<Real, D>(c, y, n);
+}
+
+// OUT: the general real spherical harmonics and harmonic polynomials are called out of line
+// (the plain general-surface kernels, which their instruction footprint bounds); elsewhere
+// inlined (the sphere and variance-reduced kernels measured 1.5-15 % slower with the calls)
+template <typename Real, int D, bool OUT = false>
 __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *u, const Real *n)
 {
     const int basis = gd->flux_basis[h];
@@ -925,71 +1006,11 @@ __device__ Real flux_value(const DevGeom *gd, int h, const Real *y, const Real *
         return v;
     }
     if (basis == kFluxRealSH) {
-        if constexpr (D == 3) {
-            // associated Legendre P_l^m(x) without the (-1)^m phase, x = cos(polar); the
-            // coefficients already carry the normalisation of the real harmonics
-            const Real x = u[2];
-            Real sx2 = (Real)1 - x * x;
-            sx2 = sx2 > (Real)0 ? sx2 : (Real)0;
-            const Real sx = RealOps<Real>::sqrt_(sx2);
-            Real ca = 1, sa = 0;  // cos / sin of the azimuth
-            if (sx > (Real)0) {
-                const Real inv = (Real)1 / sx;
-                ca = u[0] * inv;
-                sa = u[1] * inv;
-            }
-            int L = 0;
-            while ((L + 2) * (L + 2) <= nc) ++L;
-            Real v = 0;
-            Real pmm = 1, cm = 1, sm = 0;  // P_m^m, cos(m az), sin(m az)
-            for (int m = 0; m <= L; ++m) {
-                if (m > 0) {
-                    pmm *= (Real)(2 * m - 1) * sx;
-                    const Real cn = cm * ca - sm * sa;
-                    sm = sm * ca + cm * sa;
-                    cm = cn;
-                }
-                Real p_prev = 0, p_cur = pmm;
-                for (int l = m; l <= L; ++l) {
-                    if (l > m) {
-                        const Real p_next = (l == m + 1) ? x * (Real)(2 * m + 1) * pmm
-                                                         : ((Real)(2 * l - 1) * x * p_cur - (Real)(l + m - 1) * p_prev) / (Real)(l - m);
-                        p_prev = p_cur;
-                        p_cur = p_next;
-                    }
-                    if (m == 0) v += c[l * l + l] * p_cur;
-                    else v += (c[l * l + l + m] * cm + c[l * l + l - m] * sm) * p_cur;
-                }
-            }
-            return v;
-        }
+        if constexpr (D == 3) return OUT ? flux_real_sh<Real>(c, nc, u) : flux_real_sh_body<Real>(c, nc, u);
         return 0;
     }
-    if (basis == kFluxHarmonicPoly) {
-        const Real s = c[0];
-        const int T = (int)c[1];
-        Real grad[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) grad[k] = 0;
-        for (int t = 0; t < T; ++t) {
-            const Real *row = c + 2 + t * (D + 1);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const int ek = (int)row[1 + k];
-                if (ek == 0) continue;
-                Real term = row[0] * (Real)ek;
-                for (int j = 0; j < D; ++j) {
-                    const int e = (int)row[1 + j] - (j == k ? 1 : 0);
-                    for (int p = 0; p < e; ++p) term *= y[j];
-                }
-                grad[k] += term;
-            }
-        }
-        Real v = 0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) v += n[k] * grad[k];
-        return s * v;
-    }
+    if (basis == kFluxHarmonicPoly)
+        return OUT ? flux_harmonic_poly<Real, D>(c, y, n) : flux_harmonic_poly_body<Real, D>(c, y, n);
     if (basis == kFluxSphQuad) {
         if constexpr (D == 3) {
             const Real x = u[0], yv = u[1], z = u[2];
@@ -1549,7 +1570,7 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
     Real y[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) y[c] = (g.c_hi[h][c] + g.c_lo[h][c]) + ch.v[c];
-    ch.Q = g.beta_scale[h] * flux_value<Real, D>(gd, h, y, u, nrm) * (Real)part_len;
+    ch.Q = g.beta_scale[h] * flux_value<Real, D, STAR && !VR>(gd, h, y, u, nrm) * (Real)part_len;
 }
 
 // transition i >= 1 from an ellipsoid-bound state to ellipsoid h (relation rel); dy = y - c_h.
