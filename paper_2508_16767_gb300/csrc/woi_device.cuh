@@ -1544,7 +1544,7 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
             }
             u[0] = ct;
             u[1] = st;
-        } else {
+        } else if constexpr (VR) {   // (in 3-6D only the variance-reduced walk reaches here)
             // VR on a d >= 3 sphere whose data is linear in u: the two parts are mirror-image
             // hemispheres, so a uniform direction that lands in the part of the wrong sign is
             // reflected, u -> -u, which leaves it uniform on the requested one
