@@ -55,6 +55,18 @@ struct Builder {
         return b;
     }
 
+    int bin_of(int t, int axis, double lo, double ext, int nb) const
+    {
+        const int bi = (int)((cen[(size_t)t * 3 + axis] - lo) / ext * nb);
+        return bi < 0 ? 0 : (bi >= nb ? nb - 1 : bi);
+    }
+    static double area(const Box &x)
+    {
+        if (x.hi[0] < x.lo[0]) return 0.0;
+        const double dx = x.hi[0] - x.lo[0], dy = x.hi[1] - x.lo[1], dz = x.hi[2] - x.lo[2];
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    }
+
     // node for ids[b, e); children built depth-first, the left child right after its parent
     int build(int b, int e, int depth)
     {
@@ -76,14 +88,71 @@ struct Builder {
             nodes[me] = node;
             return me;
         }
-        int axis = 0;
-        for (int k = 1; k < 3; ++k)
-            if (cbox.hi[k] - cbox.lo[k] > cbox.hi[axis] - cbox.lo[axis]) axis = k;
-        const int mid = (b + e) / 2;
-        std::nth_element(ids.begin() + b, ids.begin() + mid, ids.begin() + e, [&](int x, int y) {
-            const double cx = cen[(size_t)x * 3 + axis], cy = cen[(size_t)y * 3 + axis];
-            return cx < cy || (cx == cy && x < y);
-        });
+        // surface-area heuristic over kBins centroid bins per axis: the split that minimises
+        // area(L) N_L + area(R) N_R, the expected number of triangle tests below this node for
+        // lines in random directions (every crossing of a line is wanted, so every box the line
+        // meets is opened); the median of the widest axis where the centroids coincide
+        constexpr int kBins = 16;
+        int best_axis = -1, best_split = 0;
+        double best_cost = 1e300;
+        for (int k = 0; k < 3; ++k) {
+            const double ext = cbox.hi[k] - cbox.lo[k];
+            if (!(ext > 0.0)) continue;
+            Box bins[kBins];
+            int cnt[kBins] = {0};
+            for (int i = b; i < e; ++i) {
+                const int bi = bin_of(ids[i], k, cbox.lo[k], ext, kBins);
+                Box tb = tri_box(ids[i]);
+                bins[bi].add(tb.lo);
+                bins[bi].add(tb.hi);
+                ++cnt[bi];
+            }
+            double right_area[kBins];
+            int right_n[kBins];
+            Box acc;
+            int n = 0;
+            for (int i = kBins - 1; i > 0; --i) {      // right side of split i: bins i .. kBins-1
+                if (cnt[i]) {
+                    acc.add(bins[i].lo);
+                    acc.add(bins[i].hi);
+                }
+                n += cnt[i];
+                right_area[i] = area(acc);
+                right_n[i] = n;
+            }
+            Box left;
+            int nl = 0;
+            for (int i = 1; i < kBins; ++i) {           // left side: bins 0 .. i-1
+                if (cnt[i - 1]) {
+                    left.add(bins[i - 1].lo);
+                    left.add(bins[i - 1].hi);
+                }
+                nl += cnt[i - 1];
+                if (nl == 0 || right_n[i] == 0) continue;
+                const double cost = area(left) * nl + right_area[i] * right_n[i];
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_axis = k;
+                    best_split = i;
+                }
+            }
+        }
+        int mid;
+        if (best_axis >= 0) {
+            const double lo = cbox.lo[best_axis], ext = cbox.hi[best_axis] - cbox.lo[best_axis];
+            mid = (int)(std::partition(ids.begin() + b, ids.begin() + e,
+                                       [&](int t) { return bin_of(t, best_axis, lo, ext, kBins) < best_split; }) -
+                        ids.begin());
+        } else {
+            int axis = 0;
+            for (int k = 1; k < 3; ++k)
+                if (cbox.hi[k] - cbox.lo[k] > cbox.hi[axis] - cbox.lo[axis]) axis = k;
+            mid = (b + e) / 2;
+            std::nth_element(ids.begin() + b, ids.begin() + mid, ids.begin() + e, [&](int x, int y) {
+                const double cx = cen[(size_t)x * 3 + axis], cy = cen[(size_t)y * 3 + axis];
+                return cx < cy || (cx == cy && x < y);
+            });
+        }
         const int l = build(b, mid, depth + 1);
         const int r = build(mid, e, depth + 1);
         node.a = l;
@@ -184,7 +253,7 @@ std::string mesh_prepare(const double *V, int nv, const int *T, int nt, const do
         const uint64_t th = (t == nt - 1) ? (1ull << 32) : (uint64_t)std::floor(std::ldexp(C / A, 32));
         m.tm1[t] = (uint32_t)(th - 1);
     }
-    // the hierarchy: median split of the centroids along the widest axis, leaves of <= 4
+    // the hierarchy: surface-area-heuristic splits of the centroids, leaves of <= 4
     m.nodes.clear();
     m.leaf_tri.resize(nt);
     for (int t = 0; t < nt; ++t) m.leaf_tri[t] = t;
