@@ -57,6 +57,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -171,15 +172,18 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
  * definition; it is not in the paper, which draws its random numbers freely):
  *   key     = (seed_lo ^ point_id, seed_hi ^ instance)
  *   counter = (walk_lo, walk_hi, step, (chain << 4) | sub)      per-walk words
- * Word k of a (step, chain) stream is word k % 4 of sub-call k / 4.  With a shared
- * schedule (W_g walkers per schedule, Alg. 1) the schedule word of step i of every walk
- * in group g is the one the group's first walk, g W_g, draws for itself: word 0 of its
- * (step i, chain 0) stream. */
+ * Word k of a (step, chain) stream is word k % 4 of sub-call k / 4, except on 2D instances
+ * whose surfaces are all circles: a step there draws two words (the schedule word and the
+ * angle or arc position), and steps 2j and 2j + 1 share one call, (step j, chain, sub 0),
+ * step 2j taking its words 0 and 1 and step 2j + 1 its words 2 and 3.  With a shared
+ * schedule (W_g walkers per schedule, Alg. 1) the schedule word of step i of every walk in
+ * group g is the one the group's first walk, g W_g, draws for itself. */
 typedef struct {
     uint32_t key[2];
     uint64_t walk;
     int cached_step, cached_chain, cached_sub;
     uint32_t words[4];
+    int pair2;   /* 2D instance of circles only: two steps per call */
 } or_rng;
 
 /* word k of attempt `attempt` of a (step, chain) stream: counter word 3 is
@@ -187,6 +191,14 @@ typedef struct {
  * attempts serve rejection sampling */
 static uint32_t or_word_at(or_rng *r, int step, int chain, int attempt, int k)
 {
+    if (r->pair2) {   /* words 0, 1 of step 2j + e are words 2e, 2e + 1 of call j */
+        if (attempt != 0 || k > 1) {
+            fprintf(stderr, "oracle: word %d (attempt %d) drawn on an instance of circles\n", k, attempt);
+            abort();
+        }
+        k += 2 * (step & 1);
+        step >>= 1;
+    }
     int sub = (attempt << 5) | (k >> 2);
     if (r->cached_step != step || r->cached_chain != chain || r->cached_sub != sub) {
         uint32_t ctr[4] = {(uint32_t)r->walk, (uint32_t)(r->walk >> 32), (uint32_t)step,
@@ -907,7 +919,12 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
 {
     const int d = P->dim, M = o->M, N = P->n_surf;
     const int n_chain = o->variant == 1 ? 2 : 1;
-    or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32) ^ instance}, walk, -1, -1, -1, {0}};
+    or_rng rng = {{(uint32_t)seed ^ point_id, (uint32_t)(seed >> 32) ^ instance}, walk, -1, -1, -1, {0}, 0};
+    if (d == 2) {
+        rng.pair2 = 1;
+        for (int s = 0; s < N; ++s)
+            if (P->type[s] != OR_SPHERE) rng.pair2 = 0;
+    }
     uint64_t group = walk / (uint64_t)o->sched_group;
     double acc_u = 0.0, acc_g[OR_MAX_DIM] = {0};
 
@@ -929,10 +946,10 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
         if (o->sched_group == 1) {
             hw = or_word(&rng, i, 0, 0);
         } else {   /* the group's first walk's own schedule word */
-            const uint64_t first = group * (uint64_t)o->sched_group;
-            uint32_t ctr[4] = {(uint32_t)first, (uint32_t)(first >> 32), (uint32_t)i, 0u}, w4[4];
-            or_philox4x32_10(ctr, rng.key, w4);
-            hw = w4[0];
+            or_rng first = rng;
+            first.walk = group * (uint64_t)o->sched_group;
+            first.cached_step = -1;
+            hw = or_word(&first, i, 0, 0);
         }
         const int h = or_schedule_from_word(P, i, hw);
         if (tr && tr->H) tr->H[i] = h;
@@ -1044,8 +1061,8 @@ void or_walk(const or_problem *P, const or_opts *o, const double *x, uint32_t po
                         alive[k] = 0; T[k] = 0.0;
                         continue;
                     }
-                    uint32_t cw = or_word(&rng, i, k, or_choice_word(d));
-                    int j = (int)(((uint64_t)cw * (uint64_t)q) >> 32);
+                    /* the pick among q crossings (a single crossing needs no word) */
+                    int j = q == 1 ? 0 : (int)(((uint64_t)or_word(&rng, i, k, or_choice_word(d)) * (uint64_t)q) >> 32);
                     for (int c = 0; c < d; ++c) ynew[c] = y[k][c] + ts[j] * z[c];
                     tnew = P->type[h] == OR_MESH ? hits[j] : -1;
                     const double rn = or_norm_rel(d, ynew, ch);

@@ -60,8 +60,9 @@ __device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, ui
 
 // Random-number protocol: key = (seed_lo ^ point, seed_hi ^ instance);
 // counter = (walk_lo, walk_hi, step, (chain << 4) | sub) for the walk's own
-// words.  A shared schedule (groups of 32 walks) takes, in step i, the schedule
-// word of the group's first walk: word 0 of that walk's (step i, chain 0) stream.
+// words; on 2D instances of circles only, steps 2j and 2j + 1 share the call of
+// step j (ChainWords).  A shared schedule (groups of 32 walks) takes, in step i,
+// the schedule word of the group's first walk.
 struct Rng {
     uint32_t k0, k1;
     uint32_t w0, w1;
@@ -1769,6 +1770,50 @@ __device__ void chain_step(const SGeom<Real> &g, const DevGeom *gd, int h, int r
 // The steps of one walk (Algorithms 2-3), handing each state to `sink`:
 // sink(i, k, chain, c) with c = N w_i ||alpha||_1^i prod_{m=1}^{i} sign(alpha_{H_m}) Q_i T_i
 // the coefficient of Phi(x, y_i) (0 for a chain that has ended).
+// The words of step i of one chain: one generator call per step, except on 2D instances of
+// circles only (the sphere kernels of dimension 2), whose steps use two words (the schedule
+// word and the angle or arc position): steps 2j and 2j + 1 share the call (j, chain, 0), step
+// 2j taking its words x, y and step 2j + 1 its z, w, so that half the calls are made.  The
+// call of the current pair is kept from one step to the next.
+template <int D, bool STAR>
+struct ChainWords {
+    static constexpr bool kPair = D == 2 && !STAR;
+    U4 c;
+    int j = -1;
+    __device__ __forceinline__ StepWords step(const Rng &rng, int i, int chain)
+    {
+        StepWords w;
+        if constexpr (kPair) {
+            if ((i >> 1) != j) {
+                c = rng.words(i >> 1, chain, 0);
+                j = i >> 1;
+            }
+            const bool odd = (i & 1) != 0;
+            w.a.x = odd ? c.z : c.x;
+            w.a.y = odd ? c.w : c.y;
+            w.a.z = 0u;
+            w.a.w = 0u;
+        } else {
+            w.a = rng.words(i, chain, 0);
+            if constexpr (two_calls<D>()) w.b = rng.words(i, chain, 1);
+        }
+        return w;
+    }
+};
+
+// the schedule word of step i of the walk `first` (a shared schedule's group leader), in the
+// same layout
+template <int D, bool STAR>
+__device__ __forceinline__ uint32_t first_walk_schedule_word(const Rng &rng, uint64_t first, int i)
+{
+    if constexpr (ChainWords<D, STAR>::kPair) {
+        const U4 c = philox10((uint32_t)first, (uint32_t)(first >> 32), (uint32_t)(i >> 1), 0u, rng.k0, rng.k1);
+        return (i & 1) ? c.z : c.x;
+    } else {
+        return philox10((uint32_t)first, (uint32_t)(first >> 32), (uint32_t)i, 0u, rng.k0, rng.k1).x;
+    }
+}
+
 // LANE0: the 32 lanes of the warp run the 32 walks of one schedule group together, lane 0
 // the group's first, so a shared schedule word is lane 0's own (one shuffle per step).
 // Otherwise the word is drawn from the first walk's stream here.
@@ -1777,20 +1822,15 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
                                            uint64_t group, Sink &sink)
 {
     Chain<Real, D> ch[VR ? 2 : 1];
+    ChainWords<D, STAR> cw[VR ? 2 : 1];
     Real S = 1;
     int hp = 0;
     for (int i = 0; i <= g.M; ++i) {
-        StepWords w0;
-        w0.a = rng.words(i, 0, 0);
-        if constexpr (two_calls<D>()) w0.b = rng.words(i, 0, 1);
+        const StepWords w0 = cw[0].step(rng, i, 0);
         uint32_t hw = w0.a.x;
         if (sched_group > 1) {
-            if constexpr (LANE0) {
-                hw = __shfl_sync(0xFFFFFFFFu, hw, 0);
-            } else {
-                const uint64_t first = group * 32u;
-                hw = philox10((uint32_t)first, (uint32_t)(first >> 32), (uint32_t)i, 0u, rng.k0, rng.k1).x;
-            }
+            if constexpr (LANE0) hw = __shfl_sync(0xFFFFFFFFu, hw, 0);
+            else hw = first_walk_schedule_word<D, STAR>(rng, group * 32u, i);
         }
         const int h = schedule(g, i, hw);
         if (i > 0) S *= g.alpha_sign[h];
@@ -1809,9 +1849,8 @@ __device__ __forceinline__ void walk_steps(const SGeom<Real> &g, const DevGeom *
 #pragma unroll((STAR || D >= 4) ? 1 : 2)
         for (int k = 0; k < (VR ? 2 : 1); ++k) {
             StepWords w = w0;
-            if (k == 1 && !trials) {
-                w.a = rng.words(i, 1, 0);
-                if constexpr (two_calls<D>()) w.b = rng.words(i, 1, 1);
+            if constexpr (VR) {
+                if (k == 1 && !trials) w = cw[1].step(rng, i, 1);
             }
             if (i == 0) {
                 if (!trials) chain_start<Real, D, VR, STAR>(g, gd, h, k, w, rng, ch[k]);
@@ -1860,13 +1899,15 @@ __device__ void walk(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[k
 }
 
 // Two independent walks of one lane, advanced step by step in the same loop so that the
-// scheduler can overlap their dependency chains (plain variant; each walk has its own
-// stream, schedule and state, exactly as if walked alone): f[q] receives walk q's tally
+// scheduler can overlap their dependency chains (plain variant with per-walk schedules; each
+// walk has its own stream, schedule and state, exactly as if walked alone): f[q] receives walk
+// q's tally
 template <typename Real, int D, bool STAR>
 __device__ void walk_pair(const SGeom<Real> &g, const DevGeom *gd, const Real (*xc)[kMaxDim], const Rng *rng,
-                          int sched_group, const uint64_t *group, Real (*f)[D + 1])
+                          Real (*f)[D + 1])
 {
     Chain<Real, D> ch[2];
+    ChainWords<D, STAR> cw[2];
     Real S[2] = {1, 1};
     int hp[2] = {0, 0};
 #pragma unroll
@@ -1876,13 +1917,8 @@ __device__ void walk_pair(const SGeom<Real> &g, const DevGeom *gd, const Real (*
     for (int i = 0; i <= g.M; ++i) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            StepWords w;
-            w.a = rng[q].words(i, 0, 0);
-            if constexpr (two_calls<D>()) w.b = rng[q].words(i, 0, 1);
-            uint32_t hw = w.a.x;
-            if (sched_group > 1)
-                hw = philox10((uint32_t)group[q], (uint32_t)(group[q] >> 32), (uint32_t)i, 0x100u, rng[q].k0, rng[q].k1).x;
-            const int h = schedule(g, i, hw);
+            const StepWords w = cw[q].step(rng[q], i, 0);
+            const int h = schedule(g, i, w.a.x);
             if (i > 0) S[q] *= g.alpha_sign[h];
             const int rel = (i > 0) ? relation(g, hp[q], h) : 0;
             if (i == 0) chain_start<Real, D, false, STAR>(g, gd, h, 0, w, rng[q], ch[q]);

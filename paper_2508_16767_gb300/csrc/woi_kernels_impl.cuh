@@ -88,8 +88,7 @@ __device__ __forceinline__ void run_unit(const SGeomFor<float, D, STAR> &g, cons
             r2[0].w1 = (uint32_t)((uint64_t)wa >> 32);
             r2[1].w0 = (uint32_t)wb;
             r2[1].w1 = (uint32_t)((uint64_t)wb >> 32);
-            const uint64_t grp[2] = {(uint64_t)wa / 32u, (uint64_t)wb / 32u};
-            if (wa < w_end) walk_pair<float, D, STAR>(g, geom, xc, r2, 1, grp, f2);
+            if (wa < w_end) walk_pair<float, D, STAR>(g, geom, xc, r2, f2);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const bool valid = (q == 0 ? wa : wb) < w_end;

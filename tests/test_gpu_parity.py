@@ -383,9 +383,9 @@ def test_batch_variance_reduced_matches_oracle(W, O):
         g.close()
 
 
-@pytest.mark.parametrize("name,n_pts,n_walks,precision,variant", [("2d-concentric", 64, 10_000, "fp64", "plain"),
-                                                                  ("2d-concentric", 64, 10_000, "mixed", "plain"),
-                                                                  ("2d-concentric", 64, 10_000, "mixed", "vr"),
+@pytest.mark.parametrize("name,n_pts,n_walks,precision,variant", [("2d-concentric", 256, 10_000, "fp64", "plain"),
+                                                                  ("2d-concentric", 256, 10_000, "mixed", "plain"),
+                                                                  ("2d-concentric", 256, 10_000, "mixed", "vr"),
                                                                   ("3d-nested", 256, 100_000, "mixed", "plain"),
                                                                   ("3d-linear", 256, 100_000, "mixed", "vr"),
                                                                   ("3d-nested", 256, 100_000, "mixed", "vr"),
@@ -396,10 +396,14 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
     """The GPU estimates at the workloads' sizes against the exact mean of the truncated
     estimator on concentric spheres (the per-mode series of the oracle's closed forms):
     every point within 4.5 SE, and the RMS error over the points consistent with the RMS
-    standard error (between 0.7 and 1.3 times it).  Algorithm 3 has the same mean."""
+    standard error (between 0.7 and 1.3 times it).  Algorithm 3 has the same mean.  The 2D
+    case takes 256 points uniform in the disk of radius 0.95: over the 64 grid points of the
+    workload the ratio has, for the variance-reduced estimator (heavy-tailed per-point errors),
+    a spread of 0.11-0.16 between seeds by the oracle itself, so the band would be about 2
+    standard deviations; over 256 points the spread is 0.045."""
     from oracle import closed_form as cf
     if name == "2d-concentric":
-        prob, x = wl.concentric_2d_problem(), wl.concentric_2d_points()
+        prob, x = wl.concentric_2d_problem(), wl.ball_points(256, 2, 12, radius=0.95)
     elif name == "3d-nested":
         prob, x = wl.nested_3d_problem(), wl.ball_points(4096, 3, 12)
     elif name == "3d-linear":
