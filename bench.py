@@ -65,7 +65,7 @@ def alg_tally_flops(dim: int) -> float:
 # DRAM bytes per launch of the walk kernel(s) from an ncu capture of the named workload
 # (dram__bytes_read.sum + dram__bytes_write.sum), scaled to one full launch; None once
 # the kernel has changed since the counters were taken.
-TRAFFIC = {"3d-nested": 625_152, "batch": 289_699_840}   # batch: both group launches of one step
+TRAFFIC = {"3d-nested": 625_152, "batch": 284_768_768}   # batch: both group launches of one step
 
 # Warp instructions (all pipes, and the XU pipe: transcendentals, conversions) per walk-step of
 # the walk kernels, from an ncu capture of the same kernels (sm__inst_executed.sum and
@@ -74,7 +74,7 @@ TRAFFIC = {"3d-nested": 625_152, "batch": 289_699_840}   # batch: both group lau
 # sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active).  With the live walk-step rate they
 # give the fraction of the issue slots (4 warp instructions per SM per cycle) and of the XU pipe
 # the kernel uses; None until measured for the current kernel.
-INST_PER_STEP = {"batch": {2: {"inst": 7.807, "xu": 0.2010}, 3: {"inst": 9.226, "xu": 0.2062}}}
+INST_PER_STEP = {"batch": {2: {"inst": 7.539, "xu": 0.2010}, 3: {"inst": 9.226, "xu": 0.2062}}}
 XU_PEAK_PER_SM_CYCLE = 0.99
 
 WORKLOADS = {
