@@ -247,6 +247,47 @@ def star_inclusions_problem(seed=3, n_incl=32, star_amp=0.15, star_k=5):
             "parent": [-1] + [0] * (n - 1), "sigma": [float(s) for s in sigma], "flux": flux, "M": 4}
 
 
+def star_degree_problem(seed=21, degree=16, n_incl=4, top=0.012):
+    """A star of the given Fourier degree, r(t) = 1 + sum_{k<=degree} a_k cos kt + b_k sin kt
+    with a_k, b_k ~ N(0, (0.03 / k)^2) and the top harmonic's cosine set to `top` (the curve
+    is wiggly at every scale up to the degree, and r > 0.8), with n_incl circles inside
+    (radii U[0.05, 0.12], gap >= 0.03), sigma_1 = 1, sigma_i log-uniform on [0.2, 5], and
+    flux data as in star_inclusions_problem (trig polynomials of degree <= 4, zero mean)."""
+    rng = np.random.default_rng(seed)
+    a = [0.0] + [float(rng.normal(0.0, 0.03 / k)) for k in range(1, degree + 1)]
+    b = [0.0] + [float(rng.normal(0.0, 0.03 / k)) for k in range(1, degree + 1)]
+    a[degree] = top
+    _, curve = _star_curve(a, b)
+    assert np.min(np.linalg.norm(curve, axis=1)) > 0.8
+    circles = []
+    tries = 0
+    while len(circles) < n_incl and tries < 100000:
+        tries += 1
+        rad = rng.uniform(0.05, 0.12)
+        c = rng.uniform(-0.8, 0.8, size=2)
+        if not _inside_star(a, b, c):
+            continue
+        if np.min(np.linalg.norm(curve - c, axis=1)) < rad + 0.03:
+            continue
+        if any(np.linalg.norm(c - c2) < rad + r2 + 0.03 for c2, r2 in circles):
+            continue
+        circles.append((c, rad))
+    surfaces = [_star([0, 0], 1.0, a, b)] + [_sphere(c, r) for c, r in circles]
+    n = len(surfaces)
+    sigma = [1.0] + list(np.exp(rng.uniform(math.log(0.2), math.log(5.0), n - 1)))
+    t = np.linspace(0.0, 2 * np.pi, 8192, endpoint=False)
+    r = _star_radius(a, b, t)
+    dr = sum(-k * a[k] * np.sin(k * t) + k * b[k] * np.cos(k * t) for k in range(1, len(a)))
+    speed = np.sqrt(r * r + dr * dr)
+    ca, cb = rng.standard_normal(4), rng.standard_normal(4)
+    bt = sum(ca[k - 1] * np.cos(k * t) + cb[k - 1] * np.sin(k * t) for k in range(1, 5))
+    flux = [fourier(ca, cb, a0=-float(np.sum(bt * speed) / np.sum(speed)))]
+    for _ in range(n - 1):
+        flux.append(fourier(rng.standard_normal(4), rng.standard_normal(4)))
+    return {"name": f"star-degree-{degree}", "dim": 2, "surfaces": surfaces, "parent": [-1] + [0] * (n - 1),
+            "sigma": [float(x) for x in sigma], "flux": flux, "M": 4}
+
+
 def star_inclusions_points(problem, n, seed=13, near_frac=0.3, band=0.01):
     """n points in the star domain: (1 - near_frac) uniform by rejection and
     near_frac within `band` of a surface (a random surface chosen by length, a
@@ -365,13 +406,13 @@ def eval_poly(terms, x):
     return v, g
 
 
-def manufactured_instance(dim, rng, k_max=64, r_lo=0.02, r_hi=0.15, gap=0.01, max_tries=10000):
-    """Unit disk/ball with k ~ U{1..k_max} non-overlapping circles/spheres
-    (radii U[r_lo, r_hi]; on rejection failure the count is reduced and
-    recorded), sigma_1 = 1, sigma_i log-uniform on [0.05, 20], and flux data
-    of the manufactured solution u_h (harmonic, degree <= 3):
+def manufactured_instance(dim, rng, k_max=64, r_lo=0.02, r_hi=0.15, gap=0.01, max_tries=10000, k_exact=None):
+    """Unit disk/ball with k ~ U{1..k_max} (or k_exact) non-overlapping
+    circles/spheres (radii U[r_lo, r_hi]; on rejection failure the count is
+    reduced and recorded), sigma_1 = 1, sigma_i log-uniform on [0.05, 20], and
+    flux data of the manufactured solution u_h (harmonic, degree <= 3):
     b_1 = sigma_1 dn u_h, b_i = (sigma_parent - sigma_i) dn u_h."""
-    k_req = int(rng.integers(1, k_max + 1))
+    k_req = int(rng.integers(1, k_max + 1)) if k_exact is None else int(k_exact)
     incl = []
     tries = 0
     while len(incl) < k_req and tries < max_tries:
