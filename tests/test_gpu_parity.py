@@ -373,6 +373,35 @@ def test_batch_matches_oracle_and_fp64_path(W, O):
         g.close()
 
 
+def test_batch_ragged_and_empty_instances(W, O):
+    """woi_estimate_batch with walk counts that end inside a work unit (1000, 2080 and 33 walks),
+    an instance with no points, one with a single point and a truncation M of its own per
+    instance: every estimate within 1e-2 SE of the oracle's over the same walks, twice (the
+    second call replays the captured graph), and the empty instance's outputs empty."""
+    rng = np.random.default_rng(44)
+    specs = [(2, 7, 1000, 3), (3, 0, 512, 6), (3, 5, 2080, 5), (2, 1, 33, 4), (3, 4, 1056, 2)]
+    insts = []
+    for k, (dim, n_pts, n_walks, M) in enumerate(specs):
+        prob = wl.manufactured_instance(dim, rng, k_max=10)
+        x = wl.ball_points(n_pts, dim, 200 + k, radius=0.9) if n_pts else np.zeros((0, dim))
+        insts.append((prob, x, n_walks, M))
+    geoms = [W.Geometry(p) for p, _, _, _ in insts]
+    args = [(g, x, n, M) for g, (p, x, n, M) in zip(geoms, insts)]
+    for _ in range(2):
+        res = W.woi_estimate_batch(args, seed=8)
+        for k, (prob, x, n, M) in enumerate(insts):
+            u = np.asarray(res[k]["u"])
+            assert u.shape == (len(x),), k
+            if len(x) == 0:
+                continue
+            orr = O.estimate(prob, x, n, seed=8, M=M, instance=k)
+            assert np.all(np.abs(u - orr["u"]) <= 1e-2 * orr["se_u"] + 1e-12), (k, u, orr["u"])
+            g = np.asarray(res[k]["grad"])
+            assert np.all(np.abs(g - orr["grad"]) <= 1e-2 * orr["se_grad"] + 1e-12), k
+    for g in geoms:
+        g.close()
+
+
 def test_batch_variance_reduced_matches_oracle(W, O):
     """woi_estimate_batch with Algorithm 3 over instances of three dimensions (2D arcs,
     3D and 6D hemispheres, 3D starts by trials): one persistent launch per dimension
