@@ -497,6 +497,24 @@ def ellipsoids_problem(dim, M=None):
             "parent": parent, "sigma": sigma, "flux": flux, "M": {3: 5, 4: 6, 5: 7, 6: 8}[dim] if M is None else M}
 
 
+def ellipsoid_chain_problem(dim, n=8, shrink=0.8, M=4):
+    """n concentric nested ellipsoids: the outer one of ellipsoids_problem (centre (1.3, 0,
+    ...), diag(A) = [1, 0.9, 1.2, ...]), each next one the previous scaled by `shrink` about
+    the centre; sigma alternating 1 and log-uniform values on [0.3, 3] (seed 0), and the
+    point-charge data of u = |x|^{2-dim} (the origin lies outside the outer ellipsoid)."""
+    rng = np.random.default_rng(0)
+    c = [1.3] + [0.0] * (dim - 1)
+    A0 = np.diag(np.asarray([1.0, 0.9] + [1.2] * (dim - 2), dtype=np.float64))
+    surfaces = [_ellipsoid(c, A0 / shrink ** (2 * i)) for i in range(n)]
+    sigma = [1.0] + [float(np.exp(rng.uniform(math.log(0.3), math.log(3.0)))) for _ in range(n - 1)]
+    zero = [0.0] * dim
+    flux = [{"basis": "point_charge", "coef": [sigma[0]] + zero}]
+    for i in range(1, n):
+        flux.append({"basis": "point_charge", "coef": [sigma[i - 1] - sigma[i]] + zero})
+    return {"name": f"{dim}d-ellipsoid-chain", "dim": dim, "surfaces": surfaces,
+            "parent": [-1] + list(range(n - 1)), "sigma": sigma, "flux": flux, "M": M}
+
+
 def inside_ellipsoid(s, p):
     c = np.asarray(s["center"], dtype=np.float64)
     A = np.asarray(s["matrix"], dtype=np.float64)

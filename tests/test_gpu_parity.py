@@ -18,9 +18,9 @@
   FP64 path's by rounding only; sizes span several work units and a ragged tail.
 * The full-size 3D workload (4096 points x 1e5 walks, the benchmark's launch
   configuration) on sampled points.
-* Edge cases: no points, M = 0, the maximum M, the maximum star degree and number of
-  surfaces, shared schedules, resumable walk ranges, device pointers,
-  bit-reproducibility, and host-side errors.
+* Edge cases: no points, M = 0, the maximum M, the maximum star degree and numbers of
+  surfaces, ellipsoids and meshes, ragged and empty batch instances, shared schedules,
+  resumable walk ranges, device pointers, bit-reproducibility, and host-side errors.
 """
 import numpy as np
 import pytest
@@ -82,14 +82,19 @@ def cases():
     star = wl.star_inclusions_problem()
     yield "star-32", star, wl.star_inclusions_points(star, 4, seed=13), "plain"
     yield "star-32-vr", star, wl.star_inclusions_points(star, 3, seed=14), "vr"
-    # the largest sizes: a star of the maximum Fourier degree (16; up to 34 crossings per line)
-    # and an instance of the maximum number of surfaces (128)
+    # the largest sizes: a star of the maximum Fourier degree (16; up to 34 crossings per line),
+    # an instance of the maximum number of surfaces (128), of ellipsoids (8) and of meshes (16)
     deg = wl.star_degree_problem()
     yield "star-degree-16", deg, wl.star_inclusions_points(deg, 3, seed=23), "plain"
     yield "star-degree-16-vr", deg, wl.star_inclusions_points(deg, 2, seed=24), "vr"
     many = wl.manufactured_instance(3, np.random.default_rng(31), r_lo=0.02, r_hi=0.05, gap=0.005, k_exact=127)
     yield "surfaces-128", many, wl.ball_points(3, 3, 33, radius=0.9), "plain"
     yield "surfaces-128-vr", many, wl.ball_points(2, 3, 34, radius=0.9), "vr"
+    chain = wl.ellipsoid_chain_problem(3)            # 8 ellipsoids, the maximum per instance
+    yield "ellipsoids-8", chain, wl.ellipsoid_points(chain, 3, seed=70), "plain"
+    yield "ellipsoids-8-vr", chain, wl.ellipsoid_points(chain, 2, seed=72), "vr"
+    meshes = wl.rocks_problem(n_rocks=15, seed=9, subdiv_outer=3, subdiv_rock=1, M=4)   # 16 meshes
+    yield "meshes-16", meshes, wl.mesh_points(meshes, 3, seed=71), "plain"
     for dim in (2, 3):
         inst = wl.manufactured_instance(dim, rng, k_max=12)
         yield f"manufactured-{dim}d", inst, wl.ball_points(3, dim, 40 + dim, radius=0.9), "plain"
