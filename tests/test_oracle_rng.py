@@ -63,3 +63,46 @@ def test_directions_isotropic(oracle_core, d):
     assert np.abs(z.mean(axis=0)).max() < 5.0 / np.sqrt(n)
     C = z.T @ z / n
     assert np.abs(C - np.eye(d) / d).max() < 6.0 * np.sqrt(2.0 / (d * d * n)) + 1e-3
+
+
+def _schedule_from_word(thresh, n, i, w):
+    """Thm 4.2's schedule from a 32-bit word: H_0 uniform over the n surfaces, H_i (i >= 1)
+    the first surface whose threshold exceeds the word."""
+    if i == 0:
+        return (w * n) >> 32
+    for k in range(n):
+        if w < int(thresh[k]):
+            return k
+    return n - 1
+
+
+@pytest.mark.parametrize("name,sched_group", [("2d-circles", 1), ("2d-circles", 32), ("2d-star", 1), ("3d", 1),
+                                              ("3d", 32)])
+def test_schedule_words_follow_the_protocol(oracle_core, name, sched_group):
+    """The oracle's schedules H_i against the random-number protocol written out here from its
+    definition: key = (seed_lo ^ point, seed_hi ^ instance); the schedule word of step i of a
+    walk is word 0 of the call (walk, i, chain 0 | sub 0), except on 2D instances whose surfaces
+    are all circles, where steps 2j and 2j + 1 share the call (walk, j, 0) and take its words 0
+    and 2; with W_g = 32 every walk of a group takes the group leader's (walk 32 g) word."""
+    from paper_2508_16767_gb300 import workloads as wl
+    if name == "2d-circles":
+        prob, x = wl.concentric_2d_problem(), np.array([0.3, -0.2])
+    elif name == "2d-star":
+        prob, x = wl.star_inclusions_problem(seed=3, n_incl=3), np.array([0.1, 0.2])
+    else:
+        prob, x = wl.nested_3d_problem(), np.array([0.1, 0.2, -0.3])
+    paired = prob["dim"] == 2 and all(s["kind"] == "sphere" for s in prob["surfaces"])
+    M, seed, point_id, instance = prob["M"], (5 << 32) | 77, 3, 2
+    walks = np.concatenate([np.arange(64), 2 ** 33 + np.arange(32)]).astype(np.uint64)
+    tr = oracle_core.walks(prob, x, walks, seed=seed, M=M, sched_group=sched_group, point_id=point_id,
+                           instance=instance)
+    alpha, _ = oracle_core.alpha_beta_scale(np.asarray(prob["sigma"]), prob["parent"])
+    thresh, _ = oracle_core.schedule_thresholds(alpha)
+    n = len(prob["surfaces"])
+    key = [(seed ^ point_id) & 0xFFFFFFFF, ((seed >> 32) ^ instance) & 0xFFFFFFFF]
+    for r, w in enumerate(walks):
+        lead = int(w) // sched_group * sched_group
+        for i in range(M + 1):
+            step, word = (i >> 1, 2 * (i & 1)) if paired else (i, 0)
+            words = oracle_core.philox4x32_10([lead & 0xFFFFFFFF, lead >> 32, step, 0], key)
+            assert tr["H"][r, i] == _schedule_from_word(thresh, n, i, int(words[word])), (name, int(w), i)
