@@ -15,9 +15,11 @@ constexpr int kMixedMinBlocks = 3;    // resident blocks per SM the walk kernels
 // the general-surface kernels of 2D and 3D (star curves, meshes) wait on long dependent
 // chains (root refinement, hierarchy loads) and gain more from a fourth resident block
 // (64 registers) than they lose to spills: 9 % (star) and 15 % (meshes) faster; in 4-6D
-// (ellipsoids) the spills cost more (12 % slower), and on spheres 2-4 % slower
-template <int D, bool STAR>
-constexpr int mixed_min_blocks() { return (STAR && D <= 3) ? 4 : kMixedMinBlocks; }
+// (ellipsoids) the spills cost more (12 % slower), and on spheres 2-4 % slower.  The
+// variance-reduced kernels of 4-6D carry two chains of d-vectors and are compiled for two
+// blocks (128 registers): 6D spheres 512 -> 417 ms (in 2-3D two blocks were slower)
+template <int D, bool STAR, bool VR = false>
+constexpr int mixed_min_blocks() { return (VR && D >= 4) ? 2 : ((STAR && D <= 3) ? 4 : kMixedMinBlocks); }
 constexpr int kSharedBlock = 128;     // threads per block of the shared-trajectory kernel
 constexpr int kTile = 32;             // points per shared-trajectory tile
 

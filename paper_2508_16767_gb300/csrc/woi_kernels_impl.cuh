@@ -152,7 +152,7 @@ __device__ __forceinline__ void run_unit(const SGeomFor<float, D, STAR> &g, cons
 // for good, so one round covers all the work.
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
-__global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed(MixedParams p)
+__global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR, VR>()) k_walk_mixed(MixedParams p)
 {
     __shared__ SGeomFor<float, D, STAR> g;
     __shared__ int left_sh;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed
 // point), each warp with its own x - c_s table, no block barrier per unit
 // ---------------------------------------------------------------------------
 template <int D, bool VR, bool STAR>
-__global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR>()) k_walk_mixed_warp(MixedParams p)
+__global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR, VR>()) k_walk_mixed_warp(MixedParams p)
 {
     __shared__ SGeomFor<float, D, STAR> g;
     extern __shared__ float xc_all[];   // [warps][n][kMaxDim]
