@@ -239,8 +239,12 @@ struct SGeom {
     int tin[kMaxSurf], tout[kMaxSurf];
     int type[kMaxSurf];
     Real coef[kMaxM + 1];                // N w_i ||alpha||_1^i
-    Real node_cs[kNodes][2];             // cos, sin of t_j = 2 pi j / kNodes
-    // star (at most one per instance)
+    Real node_cs[kNodes][2];             // cos, sin of t_j = 2 pi j / kNodes (circle arcs too)
+};
+
+// the star curve's tables (at most one star per instance)
+template <typename Real>
+struct SGeomS : SGeom<Real> {
     Real star_a[kMaxStar + 1], star_b[kMaxStar + 1];
     Real star_lmax;                      // bound on |gamma'|
     Real star_kpp;                       // bound on |gamma''|
@@ -252,8 +256,16 @@ struct SGeom {
     double panel_s[kNodes + 1];          // arc length at t_j
 };
 
+// the star view of a geometry that a 2D general-surface kernel staged as SGeomS
 template <typename Real>
-__device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
+__device__ __forceinline__ const SGeomS<Real> &star_geom(const SGeom<Real> &g)
+{
+    return static_cast<const SGeomS<Real> &>(g);
+}
+
+// stages the common tables, and the star's with TABS (g is then an SGeomS)
+template <typename Real, bool TABS>
+__device__ void load_geometry_tables(SGeom<Real> &g, const DevGeom *src)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) {
@@ -262,11 +274,14 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.M = src->M;
         g.star_idx = src->star_idx;
         g.star_K = src->star_K;
-        g.star_lmax = (Real)src->star_lmax;
-        g.star_kpp = (Real)src->star_kpp;
-        g.star_k3 = (Real)src->star_k3;
-        g.star_rmin = (Real)src->star_rmin;
-        g.star_rmax = (Real)src->star_rmax;
+        if constexpr (TABS) {
+            SGeomS<Real> &gs = static_cast<SGeomS<Real> &>(g);
+            gs.star_lmax = (Real)src->star_lmax;
+            gs.star_kpp = (Real)src->star_kpp;
+            gs.star_k3 = (Real)src->star_k3;
+            gs.star_rmin = (Real)src->star_rmin;
+            gs.star_rmax = (Real)src->star_rmax;
+        }
     }
     for (int i = tid; i < kMaxSurfPad; i += nt) g.sched_tm1[i] = src->sched_tm1[i];
     for (int i = tid; i <= kSchedBuckets; i += nt) g.sched_bucket[i] = src->sched_bucket[i];
@@ -290,20 +305,36 @@ __device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
         g.node_cs[j][0] = (Real)src->node_cs[j][0];
         g.node_cs[j][1] = (Real)src->node_cs[j][1];
     }
-    if (src->star_idx >= 0) {
-        for (int k = tid; k <= kMaxStar; k += nt) {
-            g.star_a[k] = (Real)src->star_a[k];
-            g.star_b[k] = (Real)src->star_b[k];
+    if constexpr (TABS) {
+        SGeomS<Real> &gs = static_cast<SGeomS<Real> &>(g);
+        if (src->star_idx >= 0) {
+            for (int k = tid; k <= kMaxStar; k += nt) {
+                gs.star_a[k] = (Real)src->star_a[k];
+                gs.star_b[k] = (Real)src->star_b[k];
+            }
+            for (int j = tid; j < kNodes; j += nt) {
+                gs.scan[j][0] = (Real)src->star_scan[j][0];
+                gs.scan[j][1] = (Real)src->star_scan[j][1];
+                gs.scan_d[j][0] = (Real)src->star_scan_d[j][0];
+                gs.scan_d[j][1] = (Real)src->star_scan_d[j][1];
+            }
+            for (int j = tid; j <= kNodes; j += nt) gs.panel_s[j] = src->star_panel_s[j];
+            for (int i = tid; i < (kMaxStar + 2) * 4; i += nt)
+                gs.star_harm[i / 4][i % 4] = (Real)src->star_harm[i / 4][i % 4];
         }
-        for (int j = tid; j < kNodes; j += nt) {
-            g.scan[j][0] = (Real)src->star_scan[j][0];
-            g.scan[j][1] = (Real)src->star_scan[j][1];
-            g.scan_d[j][0] = (Real)src->star_scan_d[j][0];
-            g.scan_d[j][1] = (Real)src->star_scan_d[j][1];
-        }
-        for (int j = tid; j <= kNodes; j += nt) g.panel_s[j] = src->star_panel_s[j];
-        for (int i = tid; i < (kMaxStar + 2) * 4; i += nt) g.star_harm[i / 4][i % 4] = (Real)src->star_harm[i / 4][i % 4];
     }
+}
+
+template <typename Real>
+__device__ void load_geometry(SGeom<Real> &g, const DevGeom *src)
+{
+    load_geometry_tables<Real, false>(g, src);
+}
+
+template <typename Real>
+__device__ void load_geometry(SGeomS<Real> &g, const DevGeom *src)
+{
+    load_geometry_tables<Real, true>(g, src);
 }
 
 // ellipsoids of an instance (d >= 3), staged only by kernels compiled for them
@@ -316,19 +347,26 @@ struct SEll {
 };
 
 template <typename Real>
-struct SGeomE : SGeom<Real> {
+struct SGeomE : SGeomS<Real> {
     SEll<Real> ell;
 };
 
-// the staged geometry of a kernel: with the ellipsoid tables when it serves general
-// surfaces in d >= 3 (STAR is the kernels' flag for "not only spheres")
+// the staged geometry of a per-point kernel: every table, with the ellipsoids' when it serves
+// general surfaces in d >= 3 (STAR is the kernels' flag for "not only spheres"). The sphere
+// kernels run at the occupancy their registers allow, so the unused star tables cost them
+// nothing; staging only the common tables there measured 1 % slower (its code differs).
 template <typename Real, int D, bool STAR>
-using SGeomFor = typename std::conditional<(STAR && D >= 3), SGeomE<Real>, SGeom<Real>>::type;
+using SGeomFor = typename std::conditional<(STAR && D >= 3), SGeomE<Real>, SGeomS<Real>>::type;
+
+// the staged geometry of a shared-trajectory kernel, whose occupancy is bounded by shared
+// memory: spheres stage only the common tables
+template <typename Real, int D, bool STAR>
+using SGeomTile = typename std::conditional<STAR, SGeomFor<Real, D, STAR>, SGeom<Real>>::type;
 
 template <typename Real>
 __device__ void load_geometry(SGeomE<Real> &g, const DevGeom *src)
 {
-    load_geometry(static_cast<SGeom<Real> &>(g), src);
+    load_geometry(static_cast<SGeomS<Real> &>(g), src);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < kMaxSurf; i += nt) g.ell.slot[i] = i < src->n ? src->ell_slot[i] : -1;
     for (int i = tid; i < src->n_ell * kMaxDim * kMaxDim; i += nt) {
@@ -383,7 +421,7 @@ __device__ __forceinline__ void angle_cs(const SGeom<Real> &g, int j, Real delta
 }
 
 template <typename Real>
-__device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st, Real *r, Real *dr)
+__device__ __forceinline__ void star_eval(const SGeomS<Real> &g, Real ct, Real st, Real *r, Real *dr)
 {
     Real ck = ct, sk = st, s = 1, ds = 0;
 #pragma unroll 1
@@ -402,7 +440,7 @@ __device__ __forceinline__ void star_eval(const SGeom<Real> &g, Real ct, Real st
 
 // local point r (cos t, sin t), outward unit normal and |gamma'| at the angle (ct, st)
 template <typename Real>
-__device__ __forceinline__ Real star_local(const SGeom<Real> &g, Real ct, Real st, Real *v, Real *n)
+__device__ __forceinline__ Real star_local(const SGeomS<Real> &g, Real ct, Real st, Real *v, Real *n)
 {
     Real r, dr;
     star_eval(g, ct, st, &r, &dr);
@@ -418,7 +456,7 @@ __device__ __forceinline__ Real star_local(const SGeom<Real> &g, Real ct, Real s
 }
 
 template <typename Real>
-__device__ __forceinline__ Real star_speed_at(const SGeom<Real> &g, int j, Real delta)
+__device__ __forceinline__ Real star_speed_at(const SGeomS<Real> &g, int j, Real delta)
 {
     Real ct, st, r, dr;
     angle_cs(g, j, delta, &ct, &st);
@@ -447,7 +485,7 @@ __device__ __forceinline__ float gl4_w(int q) { return q == 0 ? 0.65214515486254
 // max |speed^(8)| (at most 16^8 times the curve's size for degree <= 16), is below 1e-10 of
 // the panel's length, far below the FP32 rounding
 template <typename Real>
-__device__ Real star_local_arclen(const SGeom<Real> &g, int j, Real delta)
+__device__ Real star_local_arclen(const SGeomS<Real> &g, int j, Real delta)
 {
     const Real half = (Real)0.5 * delta;
     Real s = 0;
@@ -469,7 +507,7 @@ __device__ Real star_local_arclen(const SGeom<Real> &g, int j, Real delta)
 
 // (node, offset) of the point at arc length s_abs (FP64 split of the target)
 template <typename Real>
-__device__ void star_at_arclen(const SGeom<Real> &g, double s_abs, int *jo, Real *delta_o)
+__device__ void star_at_arclen(const SGeomS<Real> &g, double s_abs, int *jo, Real *delta_o)
 {
     int lo = 0, hi = kNodes;
     while (hi - lo > 1) {
@@ -502,7 +540,7 @@ __device__ void star_at_arclen(const SGeom<Real> &g, double s_abs, int *jo, Real
 
 // f(delta) = (gamma_loc(t_j + delta) - yc) x z and its derivative
 template <typename Real>
-__device__ __forceinline__ void star_line_f(const SGeom<Real> &g, int j, Real delta, const Real *yc, const Real *z,
+__device__ __forceinline__ void star_line_f(const SGeomS<Real> &g, int j, Real delta, const Real *yc, const Real *z,
                                             Real *f, Real *df)
 {
     Real ct, st, r, dr;
@@ -524,7 +562,7 @@ __device__ __forceinline__ void star_line_f(const SGeom<Real> &g, int j, Real de
 // near-tangent line).  t = t_j + delta, s = t_js + ds.  Returns g and g' in *gv, *gd, and in
 // *dz the divided difference dotted with z, so that t - s times it is the line parameter.
 template <typename Real>
-__device__ void star_dd(const SGeom<Real> &g, int j, Real delta, int js, Real ds, const Real *z, Real *gv, Real *gd,
+__device__ void star_dd(const SGeomS<Real> &g, int j, Real delta, int js, Real ds, const Real *z, Real *gv, Real *gd,
                         Real *dz)
 {
     using O = RealOps<Real>;
@@ -576,7 +614,7 @@ __device__ void star_dd(const SGeom<Real> &g, int j, Real delta, int js, Real ds
 // its own evaluator only
 template <typename Real, bool DD>
 struct StarLineEval {
-    const SGeom<Real> &g;
+    const SGeomS<Real> &g;
     const Real *yc, *z;
     int j;
     int js;
@@ -615,18 +653,18 @@ __device__ Real star_refine(const Ev &ev, Real a, Real b, Real fa, Real t0 = (Re
 
 // rounding level of f = (gamma - y) x z and of f' = gamma' x z in the kernel's precision
 template <typename Real>
-__device__ __forceinline__ Real star_f_noise(const SGeom<Real> &g)
+__device__ __forceinline__ Real star_f_noise(const SGeomS<Real> &g)
 {
     return (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_rmax;
 }
 // |f| below which a computed value's sign is not trusted (a few units of the rounding of gamma)
 template <typename Real>
-__device__ __forceinline__ Real star_dip_noise(const SGeom<Real> &g)
+__device__ __forceinline__ Real star_dip_noise(const SGeomS<Real> &g)
 {
     return (sizeof(Real) == 4 ? (Real)1e-6 : (Real)1e-14) * g.star_rmax;
 }
 template <typename Real>
-__device__ __forceinline__ Real star_df_noise(const SGeom<Real> &g)
+__device__ __forceinline__ Real star_df_noise(const SGeomS<Real> &g)
 {
     return (sizeof(Real) == 4 ? (Real)2e-6 : (Real)1e-12) * g.star_lmax;
 }
@@ -635,7 +673,7 @@ __device__ __forceinline__ Real star_df_noise(const SGeom<Real> &g)
 // above the chord minus K H^2 / 8: with f(0), f(H) of one sign and both beyond that (plus
 // the rounding of f), the interval holds no root; only the others need a search for a pair
 template <typename Real>
-__device__ __forceinline__ Real star_guard(const SGeom<Real> &g)
+__device__ __forceinline__ Real star_guard(const SGeomS<Real> &g)
 {
     const Real H = (Real)(2.0 * 3.14159265358979323846 / kNodes);
     return g.star_kpp * H * H * (Real)0.125 + star_f_noise(g);
@@ -750,7 +788,7 @@ __device__ __forceinline__ void star_window(const Real *yc, const Real *z, Real 
 // not of f's cancelling difference.  Returns q;
 // tt[] the line parameters, jj[] / dd[] the roots as (node, offset).
 template <typename Real>
-__device__ int star_intersections(const SGeom<Real> &g, const Real *yc, const Real *z, bool ray, int sj, Real sd,
+__device__ int star_intersections(const SGeomS<Real> &g, const Real *yc, const Real *z, bool ray, int sj, Real sd,
                                   Real *tt, int *jj, Real *dd)
 {
     const Real e = yc[0] * z[1] - yc[1] * z[0];
@@ -1402,9 +1440,10 @@ __device__ void vr_trials_start(const SGeom<Real> &g, const DevGeom *gd, int h, 
         if (is_star) {
             if constexpr (STAR && D == 2) {   // by arc length, as the plain start
                 Real ct, st;
-                star_at_arclen(g, (double)u01<Real>(w.a.y) * (double)g.area[h], &aj, &ad);
+                const SGeomS<Real> &gs = star_geom(g);
+                star_at_arclen(gs, (double)u01<Real>(w.a.y) * (double)g.area[h], &aj, &ad);
                 angle_cs(g, aj, ad, &ct, &st);
-                star_local(g, ct, st, v, nrm);
+                star_local(gs, ct, st, v, nrm);
             }
         } else if (is_mesh) {
             if constexpr (STAR && D == 3) mesh_uniform<Real>(gd, gd->mesh_slot[h], w, v, nrm, &aj);
@@ -1500,7 +1539,7 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
             nrm[c] = u[c];
         }
     } else {
-        if constexpr (D == 2) {
+        if constexpr (D == 2 && (VR || STAR)) {   // (the plain walk on circles never gets here)
             // target position (FP64) along the surface, or along the concatenated
             // arcs of the requested sign (VR)
             const double s_target = (double)u01<Real>(w.a.y) * part_len;
@@ -1519,8 +1558,10 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
                 }
                 if (s > gd->arc_len[a_sel]) s = gd->arc_len[a_sel];
                 if (is_star) {
-                    star_at_arclen(g, gd->arc_s0[a_sel] + s, &j_sel, &d_sel);
-                    angle_cs(g, j_sel, d_sel, &ct, &st);
+                    if constexpr (STAR) {
+                        star_at_arclen(star_geom(g), gd->arc_s0[a_sel] + s, &j_sel, &d_sel);
+                        angle_cs(g, j_sel, d_sel, &ct, &st);
+                    }
                 } else {
                     // t = t0 + s / R, split into a node and an offset in FP64
                     const double t = gd->arc_t0[a_sel] + s / (double)gd->radius[h];
@@ -1529,12 +1570,12 @@ __device__ void chain_start(const SGeom<Real> &g, const DevGeom *gd, int h, int 
                     j = j < 0 ? 0 : (j >= kNodes ? kNodes - 1 : j);
                     angle_cs(g, j, (Real)(t - j * H), &ct, &st);
                 }
-            } else {
-                star_at_arclen(g, s_target, &j_sel, &d_sel);
+            } else if constexpr (STAR) {   // (only a star reaches here in the plain walk)
+                star_at_arclen(star_geom(g), s_target, &j_sel, &d_sel);
                 angle_cs(g, j_sel, d_sel, &ct, &st);
             }
             if (is_star) {
-                star_local(g, ct, st, ch.v, nrm);
+                if constexpr (STAR) star_local(star_geom(g), ct, st, ch.v, nrm);
                 ch.aj = j_sel;
                 ch.ad = d_sel;
             } else {
@@ -1670,15 +1711,16 @@ __device__ void chain_step(const SGeom<Real> &g, const DevGeom *gd, int h, int r
         }
     }
     if (STAR && g.type[h] == kStar) {
-        if constexpr (D == 2) {
+        if constexpr (STAR && D == 2) {
+            const SGeomS<Real> &gs = star_geom(g);
             Real vn[2], nrm[2];
             if (rel == 2) {
                 // uniform on the star by arc length; Q *= K*(y_i, y_{i-1}) |dOmega_h|
                 int j;
                 Real delta, ct, st;
-                star_at_arclen(g, (double)u01<Real>(w.a.y) * (double)g.panel_s[kNodes], &j, &delta);
+                star_at_arclen(gs, (double)u01<Real>(w.a.y) * (double)gs.panel_s[kNodes], &j, &delta);
                 angle_cs(g, j, delta, &ct, &st);
-                star_local(g, ct, st, vn, nrm);
+                star_local(gs, ct, st, vn, nrm);
                 ch.aj = j;
                 ch.ad = delta;
                 const Real dx = vn[0] - dy[0], dyy = vn[1] - dy[1];
@@ -1689,7 +1731,7 @@ __device__ void chain_step(const SGeom<Real> &g, const DevGeom *gd, int h, int r
                 direction<Real, 2>(w, z);
                 Real tt[kMaxRoots], dd[kMaxRoots];
                 int jj[kMaxRoots];
-                const int q = star_intersections(g, dy, z, rel == 1, ch.aj, ch.ad, tt, jj, dd);
+                const int q = star_intersections(gs, dy, z, rel == 1, ch.aj, ch.ad, tt, jj, dd);
                 if (q == 0) {
                     ch.alive = false;
                     ch.T = 0;
@@ -1705,7 +1747,7 @@ __device__ void chain_step(const SGeom<Real> &g, const DevGeom *gd, int h, int r
                 }
                 Real ct, st;
                 angle_cs(g, jj[sel], dd[sel], &ct, &st);
-                star_local(g, ct, st, vn, nrm);
+                star_local(gs, ct, st, vn, nrm);
                 ch.aj = jj[sel];
                 ch.ad = dd[sel];
                 const Real dot = (vn[0] - dy[0]) * nrm[0] + (vn[1] - dy[1]) * nrm[1];

@@ -278,7 +278,7 @@ struct RecordSink {
 template <int D, bool VR, bool STAR>
 __global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
 {
-    __shared__ SGeomFor<float, D, STAR> g;
+    __shared__ SGeomTile<float, D, STAR> g;
     extern __shared__ float4 rec_all4[];
     float *rec_all = reinterpret_cast<float *>(rec_all4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
