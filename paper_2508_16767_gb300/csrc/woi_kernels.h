@@ -117,7 +117,8 @@ cudaError_t launch_mixed_warp(int dim, bool vr, bool star, const MixedParams &p,
 cudaError_t mixed_warp_occupancy(int dim, bool vr, bool star, int block, size_t smem, int *blocks_per_sm);
 // shared-trajectory kernel (tiles of kTile points share walks); dynamic shared memory:
 // (kSharedBlock / 32) * chains * (M + 1) * 32 * shared_record_floats(dim) * 4 bytes
-constexpr int shared_record_floats(int dim) { return ((2 * dim + 1) + 3) / 4 * 4; }
+// (a record: yhi, ylo and the coefficient; in odd dim padded to whole float4 vectors)
+constexpr int shared_record_floats(int dim) { return dim % 2 == 0 ? 2 * dim + 1 : ((2 * dim + 1) + 3) / 4 * 4; }
 cudaError_t launch_shared(int dim, bool vr, bool star, const MixedParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t shared_occupancy(int dim, bool vr, bool star, size_t smem, int *blocks_per_sm);
 cudaError_t launch_finalize(const FinalizeParams &p, bool from_acc, cudaStream_t s);

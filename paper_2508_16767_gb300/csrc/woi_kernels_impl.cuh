@@ -245,20 +245,29 @@ __global__ void __launch_bounds__(256, mixed_min_blocks<D, STAR, VR>()) k_walk_m
 // lane tallies its point against the 32 recorded walks (broadcast reads).
 // ---------------------------------------------------------------------------
 // record of one walk state for the tile: y = c_s + v as an unevaluated FP32 sum
-// yhi + ylo (TwoSum, then c_lo), and the coefficient c; kRec<D> floats, 16-byte
-// aligned so that the 32 lanes read a record with kRec<D> / 4 broadcast vector loads
+// yhi + ylo (TwoSum, then c_lo), and the coefficient c. The vector part holds kRec<D>
+// floats, 16-byte aligned, so that the 32 lanes read it with kRec<D> / 4 broadcast vector
+// loads. In even d the 2d floats of yhi, ylo fill whole vectors and c goes to an array of
+// its own after the vector parts (2d + 1 floats a record); in odd d c pads the last vector.
 template <int D>
-constexpr int kRec = ((2 * D + 1) + 3) / 4 * 4;
+constexpr bool kRecSplit = D % 2 == 0;
+template <int D>
+constexpr int kRec = kRecSplit<D> ? 2 * D : ((2 * D + 1) + 3) / 4 * 4;
+static_assert(shared_record_floats(2) == kRec<2> + 1 && shared_record_floats(3) == kRec<3> &&
+                  shared_record_floats(4) == kRec<4> + 1 && shared_record_floats(5) == kRec<5> &&
+                  shared_record_floats(6) == kRec<6> + 1,
+              "host and kernel record sizes differ");
 
 template <int D>
 struct RecordSink {
     const SGeom<float> &g;
     float *rec;    // [chains][M+1][32 walks][kRec<D>]
+    float *rec_c;  // [chains][M+1][32 walks] (even d)
     int M1, lane;
     __device__ __forceinline__ void operator()(int i, int k, const Chain<float, D> &ch, float c)
     {
         float *r = rec + ((size_t)(k * M1 + i) * 32 + lane) * kRec<D>;
-        float out[kRec<D>];
+        float out[kRec<D> + (kRecSplit<D> ? 1 : 0)];
 #pragma unroll
         for (int q = 0; q < D; ++q) {
             const float a = g.c_hi[ch.s][q], b = ch.v[q];
@@ -272,6 +281,7 @@ struct RecordSink {
 #pragma unroll
         for (int q = 0; q < kRec<D>; q += 4)
             *reinterpret_cast<float4 *>(r + q) = make_float4(out[q], out[q + 1], out[q + 2], out[q + 3]);
+        if constexpr (kRecSplit<D>) rec_c[(size_t)(k * M1 + i) * 32 + lane] = c;
     }
 };
 
@@ -289,8 +299,9 @@ __global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
     constexpr int R = kRec<D>;
     const int M1 = g.M + 1;
     const int n_rec = chains * M1;
-    float *rec = rec_all + (size_t)warp * n_rec * 32 * R;
-    RecordSink<D> sink{g, rec, M1, lane};
+    float *rec = rec_all + (size_t)warp * n_rec * 32 * (R + (kRecSplit<D> ? 1 : 0));
+    float *rec_c = rec + (size_t)n_rec * 32 * R;   // (even d)
+    RecordSink<D> sink{g, rec, rec_c, M1, lane};
     const int L = p.walks_per_lane;
     const int64_t w_end = id.walk_begin + id.n_walks;
     Rng rng;
@@ -337,7 +348,11 @@ __global__ void __launch_bounds__(kSharedBlock) k_walk_shared(MixedParams p)
                 for (int c = 0; c <= D; ++c) f[c] = 0.f;
                 for (int e = 0; e < n_rec; ++e) {
                     const float *r = rec + ((size_t)e * 32 + ww) * R;
-                    float y[R];
+                    float y[R + (kRecSplit<D> ? 1 : 0)];
+                    if constexpr (kRecSplit<D>) {   // the coefficient first: a zero skips the vector loads
+                        y[2 * D] = rec_c[e * 32 + ww];
+                        if (y[2 * D] == 0.f) continue;
+                    }
 #pragma unroll
                     for (int q = 0; q < R; q += 4) {
                         const float4 t = *reinterpret_cast<const float4 *>(r + q);

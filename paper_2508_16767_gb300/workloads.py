@@ -167,19 +167,24 @@ def ball_points(n, dim, seed, radius=1.0):
     return g * r[:, None]
 
 
-def nested_6d_problem():
-    """6D hyperspheres r = 1, 0.6, sigma = (1, 4); Neumann flux x_1 on |x| = 1
-    and flux jump x_2 on the inner sphere (0.6 x_2/|x| there)."""
-    d = 6
+def nested_nd_problem(dim, M=8):
+    """Hyperspheres r = 1, 0.6 in d dimensions (3 <= d <= 6), sigma = (1, 4); Neumann
+    flux x_1 on |x| = 1 and flux jump x_2 on the inner sphere (0.6 x_2/|x| there)."""
+    d = dim
     e1 = tuple(1 if k == 0 else 0 for k in range(d))
     e2 = tuple(1 if k == 1 else 0 for k in range(d))
     return {
-        "name": "6d-nested", "dim": d,
+        "name": f"{d}d-nested", "dim": d,
         "surfaces": [_sphere([0] * d, 1.0), _sphere([0] * d, 0.6)],
         "parent": [-1, 0], "sigma": [1.0, 4.0],
         "flux": [harmonic_poly(1.0, [(1.0, e1)], d), harmonic_poly(0.6, [(1.0, e2)], d)],
-        "M": 8,
+        "M": M,
     }
+
+
+def nested_6d_problem():
+    """The 6D workload: nested_nd_problem in six dimensions, M = 8."""
+    return nested_nd_problem(6)
 
 
 # ---------------------------------------------------------------------------

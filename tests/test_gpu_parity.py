@@ -66,6 +66,10 @@ def cases():
     yield "e3b", e3b_problem(), wl.ball_points(3, 3, 5), "plain"
     yield "6d-nested", wl.nested_6d_problem(), wl.ball_points(3, 6, 14), "plain"
     yield "6d-nested-vr", wl.nested_6d_problem(), wl.ball_points(3, 6, 15), "vr"
+    for dim in (4, 5):
+        nd = wl.nested_nd_problem(dim)
+        yield f"{dim}d-nested", nd, wl.ball_points(3, dim, 60 + dim), "plain"
+        yield f"{dim}d-nested-vr", nd, wl.ball_points(2, dim, 65 + dim), "vr"
     yield "3d-linear-vr", wl.linear_3d_problem(), wl.ball_points(3, 3, 16, radius=0.95), "vr"
     yield "3d-nested-vr", wl.nested_3d_problem(), wl.ball_points(3, 3, 17), "vr"
     yield "3d-zonal-vr", wl.zonal_3d_problem(), wl.ball_points(3, 3, 18, radius=0.95), "vr"
@@ -99,7 +103,7 @@ def cases():
         inst = wl.manufactured_instance(dim, rng, k_max=12)
         yield f"manufactured-{dim}d", inst, wl.ball_points(3, dim, 40 + dim, radius=0.9), "plain"
         yield f"manufactured-{dim}d-vr", inst, wl.ball_points(2, dim, 50 + dim, radius=0.9), "vr"
-    for dim in (3, 6):
+    for dim in (3, 4, 5, 6):
         ell = wl.ellipsoids_problem(dim)
         yield f"ellipsoids-{dim}d", ell, wl.ellipsoid_points(ell, 3, seed=50 + dim), "plain"
     rocks = wl.rocks_problem(n_rocks=3, subdiv_outer=3, subdiv_rock=2, M=4)
@@ -221,7 +225,10 @@ def test_shared_schedules(W, O):
                                                       ("mesh-rocks", "plain", 1), ("3d-linear-vr", "vr", 1),
                                                       ("6d-nested-vr", "vr", 32), ("3d-nested-vr", "vr", 1),
                                                       ("6d-quad-vr", "vr", 32), ("ellipsoids-3d-vr", "vr", 1),
-                                                      ("mesh-rocks-vr", "vr", 32)])
+                                                      ("mesh-rocks-vr", "vr", 32), ("4d-nested", "plain", 1),
+                                                      ("4d-nested-vr", "vr", 32), ("5d-nested", "plain", 32),
+                                                      ("5d-nested-vr", "vr", 1), ("ellipsoids-4d", "plain", 1),
+                                                      ("ellipsoids-5d", "plain", 32)])
 def test_shared_trajectory_tiles(W, O, name, variant, sched_group):
     """Sec. 4.6: the 32 points of a tile share one walk stream; every point's
     estimate is still the mean over the same walks the oracle draws for that
@@ -434,7 +441,9 @@ def test_batch_variance_reduced_matches_oracle(W, O):
                                                                   ("3d-nested", 256, 100_000, "mixed", "vr"),
                                                                   ("3d-zonal", 256, 100_000, "mixed", "vr"),
                                                                   ("6d-nested", 64, 100_000, "mixed", "plain"),
-                                                                  ("6d-nested", 64, 100_000, "mixed", "vr")])
+                                                                  ("6d-nested", 64, 100_000, "mixed", "vr"),
+                                                                  ("4d-nested", 64, 100_000, "mixed", "plain"),
+                                                                  ("5d-nested", 64, 100_000, "mixed", "vr")])
 def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, precision, variant):
     """The GPU estimates at the workloads' sizes against the exact mean of the truncated
     estimator on concentric spheres (the per-mode series of the oracle's closed forms):
@@ -454,7 +463,8 @@ def test_estimates_match_the_exact_truncated_mean(W, name, n_pts, n_walks, preci
     elif name == "3d-zonal":
         prob, x = wl.zonal_3d_problem(), wl.ball_points(4096, 3, 12, radius=0.95)
     else:
-        prob, x = wl.nested_6d_problem(), wl.ball_points(1024, 6, 14)
+        dim = int(name[0])
+        prob, x = wl.nested_nd_problem(dim), wl.ball_points(1024, dim, 14)
     x = np.ascontiguousarray(x[:n_pts])
     radii = [s["radius"] for s in prob["surfaces"]]
     u_ex, g_ex = cf.concentric_truncated_mean(prob["dim"], radii, prob["sigma"], prob["parent"],

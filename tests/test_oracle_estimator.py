@@ -98,6 +98,19 @@ def test_variance_reduced_hemispheres_nd(oracle_core):
         assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS
 
 
+@pytest.mark.parametrize("dim", [4, 5])
+def test_nested_4d_5d_match_exact_mean(oracle_core, dim):
+    """Dimensions 4 and 5 (directions from Gaussian pairs, the d-dimensional kernels and the
+    hemisphere parts of Algorithm 3): the plain and the variance-reduced estimator against
+    the exact mean of the truncated estimator on two nested hyperspheres."""
+    prob = wl.nested_nd_problem(dim)
+    x = wl.ball_points(8, dim, 40 + dim)
+    for variant, seed in (("plain", 0), ("vr", 5)):
+        res = oracle_core.estimate(prob, x, 60000, seed=seed, M=8, variant=variant)
+        u_ex, g_ex = concentric_exact(prob, 8, x)
+        assert np.abs(zscores(res, u_ex, g_ex)).max() < Z_PASS, variant
+
+
 def test_variance_reduced_by_trials(oracle_core):
     """Algorithm 3 where |dOmega^+/-| has no closed form (degree-2 data on 3D spheres):
     the start by 16 shared uniform trials, weighted by their fraction of each sign, has the
