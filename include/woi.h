@@ -316,11 +316,10 @@ WOI_API woi_status woi_last_kernel_ms(woi_geometry *geometry, float *ms);
  * default is 64 walks per lane (fewer, larger work units).
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and it keeps the contents of the
- * last call, so calls that may overlap on the GPU (different streams, or
- * different host threads) race with each other and must be serialised by the
- * caller.
+ * device, with that device current).  All calls share the one array and it
+ * keeps the contents of the last call, so calls that may overlap on the GPU
+ * (different streams, or different host threads) race with each other and
+ * must be serialised by the caller.
  */
 #define WOI_NOALLOC_SCRATCH_BYTES (16u << 20)
 WOI_API woi_status woi_estimate_noalloc(woi_geometry *geometry, const woi_opts *opts, const double *points,
