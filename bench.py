@@ -466,8 +466,8 @@ def measure_single(name, args, local, steps, warmup, extras=True):
                                    "value_at_plain_rms_error": P / (t_v * ratio), "accuracy": acc_v,
                                    "note": "two chains per walk; value_at_plain_rms_error scales the walks by "
                                            "(se_vr / se_plain)^2"}
-    # shared trajectories (Sec. 4.6: tiles of 32 points share their walks) on the 3D nested workload
-    if name == "3d-nested":
+    # shared trajectories (Sec. 4.6: tiles of 32 points share their walks) on the nested spheres
+    if name in ("3d-nested", "6d-nested"):
         so = dict(opt, tile_points=32, block_size=0, walks_per_lane=0)
         step(False, so)
         sms = []
