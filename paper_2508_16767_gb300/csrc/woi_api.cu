@@ -165,8 +165,7 @@ struct woi_geometry {
     double *d_tri_d = nullptr;
     uint32_t *d_tri_tm1 = nullptr;
     int *d_tri_bucket = nullptr;
-    BvhNode *d_bvh = nullptr;
-    int *d_bvh_tri = nullptr;
+    BvhWide *d_bvh = nullptr;
     unsigned int *d_mesh_overflow = nullptr;
     int blob_M = -1;
     // grow-only scratch
@@ -202,7 +201,6 @@ struct woi_geometry {
         cudaFree(d_tri_tm1);
         cudaFree(d_tri_bucket);
         cudaFree(d_bvh);
-        cudaFree(d_bvh_tri);
         cudaFree(d_mesh_overflow);
         cudaFree(d_scratch);
         if (ev_start) cudaEventDestroy(ev_start);
@@ -221,7 +219,6 @@ struct woi_geometry {
         d_tri_tm1 = nullptr;
         d_tri_bucket = nullptr;
         d_bvh = nullptr;
-        d_bvh_tri = nullptr;
         d_mesh_overflow = nullptr;
         d_scratch = nullptr;
         scratch_bytes = 0;
@@ -1257,7 +1254,7 @@ void fill_blob(const woi_geometry &g, int M, DevGeom &b)
             b.mesh_node_off[m] = node_off;
             b.mesh_scale[m] = g.mesh[m].scale;
             tri_off += g.mesh[m].ntri;
-            node_off += (int)g.mesh[m].nodes.size();
+            node_off += (int)g.mesh[m].wide.size();
         }
     }
     b.n_ell = (int)g.ell.size();
@@ -1285,13 +1282,12 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
         if ((st = upload(&g->d_arc_s0, g->arc_s0, s)) != WOI_OK) return st;
         if ((st = upload(&g->d_arc_sign, g->arc_sign, s)) != WOI_OK) return st;
         if (!g->mesh.empty()) {
-            // all meshes concatenated: triangle rows, thresholds, nodes (children and leaf ranges
-            // shifted by the mesh's offsets) and leaf-triangle lists (global triangle indices)
+            // all meshes concatenated: triangle rows, thresholds and hierarchies (internal
+            // children shifted by the mesh's entry offset, leaf triangles by its triangle offset)
             std::vector<double> tri_d;
             std::vector<uint32_t> tm1;
             std::vector<int> bucket;
-            std::vector<BvhNode> nodes;
-            std::vector<int> leaf;
+            std::vector<BvhWide> nodes;
             for (const MeshHost &mh : g->mesh) {
                 const int tri_off = (int)tm1.size(), node_off = (int)nodes.size();
                 tri_d.insert(tri_d.end(), mh.tri.begin(), mh.tri.end());
@@ -1303,12 +1299,15 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
                     while (j < mh.ntri && (uint64_t)mh.tm1[j] < start) ++j;
                     bucket.push_back(tri_off + std::min(j, mh.ntri - 1));
                 }
-                for (BvhNode nd : mh.nodes) {
-                    if (nd.b < 0) nd.a += tri_off;
-                    else { nd.a += node_off; nd.b += node_off; }
+                for (BvhWide nd : mh.wide) {
+                    for (int c = 0; c < 2; ++c) {   // internal: entry + node_off; leaf: -(t + tri_off + 1)
+                        const int ch = nd.child[c];
+                        if (ch >= (int)mh.wide.size() || ch < -mh.ntri)
+                            return fail(WOI_E_GEOMETRY, "mesh hierarchy reference %d out of range", ch);
+                        nd.child[c] = ch >= 0 ? ch + node_off : ch - tri_off;
+                    }
                     nodes.push_back(nd);
                 }
-                for (int t : mh.leaf_tri) leaf.push_back(t + tri_off);
             }
             std::vector<float> tri_f(tri_d.begin(), tri_d.end());
             if ((st = upload(&g->d_tri_d, tri_d, s)) != WOI_OK) return st;
@@ -1316,7 +1315,6 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
             if ((st = upload(&g->d_tri_tm1, tm1, s)) != WOI_OK) return st;
             if ((st = upload(&g->d_tri_bucket, bucket, s)) != WOI_OK) return st;
             if ((st = upload(&g->d_bvh, nodes, s)) != WOI_OK) return st;
-            if ((st = upload(&g->d_bvh_tri, leaf, s)) != WOI_OK) return st;
             if (!g->d_mesh_overflow) WOI_CUDA(cudaMalloc((void **)&g->d_mesh_overflow, sizeof(unsigned int)));
             WOI_CUDA(cudaMemsetAsync(g->d_mesh_overflow, 0, sizeof(unsigned int), s));
             // the host vectors die at the end of this block: finish the pageable copies first
@@ -1338,7 +1336,6 @@ woi_status stage_geometry(woi_geometry *g, int M, cudaStream_t s)
     b.tri_tm1 = g->d_tri_tm1;
     b.tri_bucket = g->d_tri_bucket;
     b.bvh = g->d_bvh;
-    b.bvh_tri = g->d_bvh_tri;
     b.mesh_overflow = g->d_mesh_overflow;
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     WOI_CUDA(cudaMemcpyAsync(g->d_blob, &b, sizeof(DevGeom), cudaMemcpyHostToDevice, s));

@@ -1258,48 +1258,59 @@ __device__ int mesh_hits(const DevGeom *gd, int m, const Real *o, const Real *z,
                          int *tri)
 {
     const Real *rows = tri_rows<Real>(gd);
-    const BvhNode *nodes = gd->bvh;
+    const BvhWide *nodes = gd->bvh;
     const Real iz[3] = {(Real)1 / z[0], (Real)1 / z[1], (Real)1 / z[2]};
+    const Real t_lo = ray ? (Real)0 : (Real)-1e30;
+    // the padded box with corners (b0, b1, b2) and (b3, b4, b5) against the line (or the
+    // ray's t >= 0 part)
+    auto meets = [&](float b0, float b1, float b2, float b3, float b4, float b5) {
+        const float lo[3] = {b0, b1, b2}, hi[3] = {b3, b4, b5};
+        Real t0 = t_lo, t1 = (Real)1e30;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const Real ta = ((Real)lo[k] - o[k]) * iz[k], tb = ((Real)hi[k] - o[k]) * iz[k];
+            const Real tmn = ta < tb ? ta : tb, tmx = ta < tb ? tb : ta;
+            t0 = tmn > t0 ? tmn : t0;
+            t1 = tmx < t1 ? tmx : t1;
+        }
+        return t0 <= t1;
+    };
     int stack[kMeshStack];
     int sp = 0, q = 0;
     bool over = false;
+    // the line starts on or inside the mesh, so it meets the root's box: the root is taken
+    // without a test
     stack[sp++] = gd->mesh_node_off[m];
-    // "while-while" order: each lane walks inner nodes until it holds a leaf (or its stack
-    // is empty), then the lanes test their leaves' triangles together, so that the leaf
-    // code is not run once per lane while the other lanes wait in the node code
+    // "while-while" order: each lane walks internal entries until it holds a leaf (or its
+    // stack is empty), then the lanes test their leaves' triangles together, so that the leaf
+    // code is not run once per lane while the other lanes wait in the node code. An entry
+    // holds both children's boxes: one load per entry tests two boxes, and only the children
+    // the line meets go on the stack (a leaf child as -(triangle + 1)).
     for (;;) {
-        int leaf_first = 0, leaf_count = 0;
+        int t = -1;
         while (sp > 0) {
-            const int ni = stack[--sp];
-            const float4 n0 = __ldg(reinterpret_cast<const float4 *>(nodes + ni));
-            const float4 n1 = __ldg(reinterpret_cast<const float4 *>(nodes + ni) + 1);
-            const float lo[3] = {n0.x, n0.y, n0.z}, hi[3] = {n0.w, n1.x, n1.y};
-            const int na = __float_as_int(n1.z), nb = __float_as_int(n1.w);
-            // slab test against the padded box
-            Real t0 = ray ? (Real)0 : (Real)-1e30, t1 = (Real)1e30;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const Real ta = ((Real)lo[k] - o[k]) * iz[k], tb = ((Real)hi[k] - o[k]) * iz[k];
-                const Real tmn = ta < tb ? ta : tb, tmx = ta < tb ? tb : ta;
-                t0 = tmn > t0 ? tmn : t0;
-                t1 = tmx < t1 ? tmx : t1;
-            }
-            if (!(t0 <= t1)) continue;
-            if (nb < 0) {
-                leaf_first = na;
-                leaf_count = -nb;
+            const int ref = stack[--sp];
+            if (ref < 0) {
+                t = -ref - 1;
                 break;
             }
-            if (sp + 2 <= kMeshStack) {
-                stack[sp++] = na;
-                stack[sp++] = nb;
-            } else {
-                over = true;
+            const float4 *np = reinterpret_cast<const float4 *>(nodes + ref);
+            const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+            const bool h0 = meets(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+            const bool h1 = meets(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w);
+            // child 1 is taken first: the crossings come out in the depth-first order of the
+            // build, right subtree first
+            if (h0) {
+                if (sp < kMeshStack) stack[sp++] = __float_as_int(n3.x);
+                else over = true;
+            }
+            if (h1) {
+                if (sp < kMeshStack) stack[sp++] = __float_as_int(n3.y);
+                else over = true;
             }
         }
-        if (leaf_count == 0) break;              // the stack ran empty without another leaf
-        for (int i = leaf_first; i < leaf_first + leaf_count; ++i) {
-            const int t = __ldg(gd->bvh_tri + i);
+        if (t < 0) break;                        // the stack ran empty without another leaf
+        {
             if (t == exclude) continue;
             const Real *r = rows + (size_t)t * 12;
             const Real e1[3] = {__ldg(r + 3), __ldg(r + 4), __ldg(r + 5)};

@@ -33,7 +33,15 @@ struct BvhNode {
     float lo[3], hi[3];
     int a, b;
 };
-static_assert(sizeof(BvhNode) == 32, "nodes are read as two float4");
+// the device form of the hierarchy: one entry per internal node, holding the boxes of both
+// children (lo, hi of child 0, then of child 1) and their references: the entry index of an
+// internal child, or -(triangle + 1) for a leaf (every leaf holds one triangle)
+struct BvhWide {
+    float box[2][6];
+    int child[2];
+    int pad[2];
+};
+static_assert(sizeof(BvhWide) == 64, "entries are read as four float4");
 enum { kFluxZero = 0, kFluxFourier = 1, kFluxRealSH = 2, kFluxHarmonicPoly = 3, kFluxPointCharge = 4,
        kFluxHarmonicQuad = 16,     // device only: [s, (a_k, b_k[d], c_k[d(d+1)/2]) x d], grad P quadratic
        kFluxSphQuad = 17 };        // device only, 3D spheres: real harmonics of degree <= 2 as
@@ -93,8 +101,7 @@ struct DevGeom {
     const double *tri_d;               // [n_tri][12]
     const uint32_t *tri_tm1;           // [n_tri] T_j - 1 of the area-proportional triangle choice
     const int *tri_bucket;             // [n_mesh][kTriBuckets + 1]: first j with T_j - 1 >= b 2^22 (global j)
-    const BvhNode *bvh;                // all meshes' nodes
-    const int *bvh_tri;                // leaf-triangle lists (indices into the triangle rows)
+    const BvhWide *bvh;                // all meshes' hierarchies (mesh m's root at mesh_node_off[m])
     unsigned int *mesh_overflow;       // device counter of lines with more than kMaxHits crossings
 };
 

@@ -170,6 +170,38 @@ struct Builder {
     }
 };
 
+// the device form of a built hierarchy: internal nodes numbered in build order (the root
+// first), each with its children's boxes; a leaf child becomes -(its triangle + 1)
+std::string widen(MeshHost &m)
+{
+    std::vector<int> entry(m.nodes.size(), -1);
+    int n = 0;
+    for (size_t i = 0; i < m.nodes.size(); ++i)
+        if (m.nodes[i].b >= 0) entry[i] = n++;
+    if (m.nodes.empty() || entry[0] != 0) return "the mesh hierarchy has no internal root";
+    m.wide.assign(n, BvhWide{});
+    for (size_t i = 0; i < m.nodes.size(); ++i) {
+        const BvhNode &p = m.nodes[i];
+        if (p.b < 0) continue;
+        BvhWide &w = m.wide[entry[i]];
+        const int ch[2] = {p.a, p.b};
+        for (int c = 0; c < 2; ++c) {
+            const BvhNode &k = m.nodes[ch[c]];
+            for (int j = 0; j < 3; ++j) {
+                w.box[c][j] = k.lo[j];
+                w.box[c][3 + j] = k.hi[j];
+            }
+            if (k.b < 0) {
+                if (k.b != -1) return "a leaf of the mesh hierarchy holds more than one triangle";
+                w.child[c] = -(m.leaf_tri[k.a] + 1);
+            } else {
+                w.child[c] = entry[ch[c]];
+            }
+        }
+    }
+    return std::string();
+}
+
 // ray / triangle (Moller-Trumbore) in FP64 on a local-coordinate row; t > 0 hits counted
 bool ray_tri(const double *r, const double *o, const double *z, double *t_out)
 {
@@ -273,7 +305,7 @@ std::string mesh_prepare(const double *V, int nv, const int *T, int nt, const do
     bld.build(0, nt, 0);
     m.depth = bld.max_depth;
     if (m.depth + 2 >= kMeshStack) return "the mesh hierarchy is too deep";
-    return std::string();
+    return widen(m);
 }
 
 bool mesh_inside(const MeshHost &m, const double *x)
@@ -281,28 +313,28 @@ bool mesh_inside(const MeshHost &m, const double *x)
     // a direction with no special relation to the mesh; odd crossing count means inside
     const double z[3] = {0.5773502691896258 + 1.234e-3, 0.5773502691896258 - 2.345e-3, 0.5773502691896258 + 0.987e-3};
     const double o[3] = {x[0] - m.center[0], x[1] - m.center[1], x[2] - m.center[2]};
+    // through the device form of the hierarchy, as the kernels traverse it
     int count = 0;
     int stack[kMeshStack], sp = 0;
     stack[sp++] = 0;
     while (sp > 0) {
-        const BvhNode &n = m.nodes[stack[--sp]];
-        double t0 = 0.0, t1 = 1e300;
-        bool miss = false;
-        for (int k = 0; k < 3 && !miss; ++k) {
-            const double ta = ((double)n.lo[k] - o[k]) / z[k], tb = ((double)n.hi[k] - o[k]) / z[k];
-            t0 = std::max(t0, std::min(ta, tb));
-            t1 = std::min(t1, std::max(ta, tb));
-            miss = t0 > t1;
+        const int ref = stack[--sp];
+        if (ref < 0) {
+            double t;
+            if (ray_tri(&m.tri[(size_t)(-ref - 1) * 12], o, z, &t) && t > 0.0) ++count;
+            continue;
         }
-        if (miss) continue;
-        if (n.b < 0) {
-            for (int i = n.a; i < n.a - n.b; ++i) {
-                double t;
-                if (ray_tri(&m.tri[(size_t)m.leaf_tri[i] * 12], o, z, &t) && t > 0.0) ++count;
+        const BvhWide &n = m.wide[ref];
+        for (int c = 0; c < 2; ++c) {
+            double t0 = 0.0, t1 = 1e300;
+            bool miss = false;
+            for (int k = 0; k < 3 && !miss; ++k) {
+                const double ta = ((double)n.box[c][k] - o[k]) / z[k], tb = ((double)n.box[c][3 + k] - o[k]) / z[k];
+                t0 = std::max(t0, std::min(ta, tb));
+                t1 = std::min(t1, std::max(ta, tb));
+                miss = t0 > t1;
             }
-        } else {
-            stack[sp++] = n.a;
-            stack[sp++] = n.b;
+            if (!miss && sp < kMeshStack) stack[sp++] = n.child[c];
         }
     }
     return (count & 1) == 1;

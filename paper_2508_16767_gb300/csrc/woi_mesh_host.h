@@ -21,6 +21,7 @@ struct MeshHost {
     std::vector<uint32_t> tm1;      // [ntri] floor(2^32 C_j / A) - 1, the last 2^32 - 1
     std::vector<BvhNode> nodes;     // root first
     std::vector<int> leaf_tri;      // triangle indices (0..ntri-1) in leaf order
+    std::vector<BvhWide> wide;      // the same hierarchy as the device reads it, root first
     int depth = 0;
 };
 
