@@ -26,9 +26,9 @@ constexpr int kVrTrials = 16;          // uniform trials of the VR start where |
 
 enum { kSphere = 0, kStar = 1, kEllipsoid = 2, kMesh = 3 };
 
-// a node of a mesh's bounding-volume hierarchy (local coordinates of the surface, FP32 bounds
-// rounded outward and padded): internal node a, b = children; leaf a = first entry of the
-// leaf-triangle list, b = -(number of triangles)
+// a node of a mesh's bounding-volume hierarchy as the host builds it (local coordinates of
+// the surface, FP32 bounds rounded outward and padded): internal node a, b = children; leaf
+// a = first entry of the leaf-triangle list, b = -(number of triangles)
 struct BvhNode {
     float lo[3], hi[3];
     int a, b;
