@@ -21,6 +21,11 @@ def cases():
     yield "star-3-vr", wl.star_inclusions_problem(seed=3, n_incl=3), np.array([[0.6, -0.4]]), "vr", 3
     yield "3d-linear-vr", wl.linear_3d_problem(), wl.ball_points(1, 3, 5, radius=0.9), "vr", 4
     yield "3d-zonal-vr", wl.zonal_3d_problem(), wl.ball_points(1, 3, 6, radius=0.9), "vr", 4
+    yield "4d-nested", wl.nested_nd_problem(4), wl.ball_points(1, 4, 7), "plain", 4
+    yield "5d-nested-vr", wl.nested_nd_problem(5), wl.ball_points(1, 5, 8, radius=0.9), "vr", 4
+    yield "6d-nested", wl.nested_6d_problem(), wl.ball_points(1, 6, 9), "plain", 4
+    ell4 = wl.ellipsoids_problem(4)
+    yield "ellipsoids-4d", ell4, wl.ellipsoid_points(ell4, 1, seed=10), "plain", 3
 
 
 def main():

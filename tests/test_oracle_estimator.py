@@ -311,7 +311,9 @@ def test_oracle_reproduces_stored_replay(oracle_core):
     probs = {"2d-concentric": wl.concentric_2d_problem(), "3d-nested": wl.nested_3d_problem(),
              "star-3": wl.star_inclusions_problem(seed=3, n_incl=3),
              "star-3-vr": wl.star_inclusions_problem(seed=3, n_incl=3),
-             "3d-linear-vr": wl.linear_3d_problem(), "3d-zonal-vr": wl.zonal_3d_problem()}
+             "3d-linear-vr": wl.linear_3d_problem(), "3d-zonal-vr": wl.zonal_3d_problem(),
+             "4d-nested": wl.nested_nd_problem(4), "5d-nested-vr": wl.nested_nd_problem(5),
+             "6d-nested": wl.nested_6d_problem(), "ellipsoids-4d": wl.ellipsoids_problem(4)}
     for c in gold["cases"]:
         r = oracle_core.walks(probs[c["name"]], np.asarray(c["x"]), np.arange(32), seed=0, M=c["M"],
                               variant=c["variant"], point_id=c["point_id"])
