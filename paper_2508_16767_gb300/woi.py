@@ -108,6 +108,26 @@ def version() -> str:
     return lib.woi_version().decode()
 
 
+def woi_version() -> str:
+    return lib.woi_version().decode()
+
+
+def woi_last_error() -> str:
+    return lib.woi_last_error().decode()
+
+
+def woi_default_opts() -> "Opts":
+    o = Opts()
+    lib.woi_default_opts(ctypes.byref(o))
+    return o
+
+
+def woi_surface_area(handle, i) -> float:
+    a = ctypes.c_double()
+    _check(lib.woi_surface_area(handle, int(i), ctypes.byref(a)))
+    return a.value
+
+
 # ---------------------------------------------------------------------------
 # array marshalling
 # ---------------------------------------------------------------------------
@@ -204,6 +224,10 @@ def woi_create_geometry(dim, surfaces, parent):
     h = ctypes.c_void_p()
     _check(lib.woi_create_geometry(int(dim), n, arr, par, ctypes.byref(h)))
     return h
+
+
+def woi_destroy_geometry(handle):
+    lib.woi_destroy_geometry(handle)
 
 
 def woi_set_sigma_and_data(handle, sigma, flux):

@@ -164,6 +164,43 @@ def test_ellipsoid_host_geometry(woi):
     assert e.value.status == 3
 
 
+def test_binding_has_every_entry_point(woi):
+    """The Python binding keeps the C ABI's names: one function per declared entry point,
+    and the host-only ones answer without a GPU."""
+    for n in declared_entry_points():
+        assert callable(getattr(woi, n, None)), n
+    assert woi.woi_version()
+    assert woi.woi_default_opts().M == 4
+    h = woi.woi_create_geometry(3, [wl._sphere([0.0, 0.0, 0.0], 0.5)], [-1])
+    try:
+        assert woi.woi_surface_area(h, 0) == pytest.approx(np.pi, rel=1e-13)   # 4 pi r^2
+    finally:
+        woi.woi_destroy_geometry(h)
+    with pytest.raises(woi.WoiError):
+        woi.woi_create_geometry(3, [wl._sphere([0.0, 0.0, 0.0], -1.0)], [-1])
+    assert woi.woi_last_error()
+
+
+def test_mesh_inside_test_through_the_hierarchy(woi):
+    """The host's inside test walks a mesh's hierarchy in the form the kernels read (both
+    children's boxes in the parent's entry, a leaf child by its triangle). A sphere nested in
+    a mesh is accepted only if all of its 16,384 sample points test inside: spheres within
+    the polyhedron's inradius are accepted, spheres reaching beyond its circumradius are
+    rejected."""
+    V, F = wl.icosphere(3)                   # 1280 triangles, inradius 0.9955, circumradius 1
+    for k in range(16):
+        c = wl.ball_points(1, 3, 100 + k, radius=0.6)[0]
+        inside = k % 2 == 0
+        r = (0.985 if inside else 1.03) - float(np.linalg.norm(c))
+        surfaces = [wl._mesh(V, F, [0, 0, 0]), wl._sphere(list(c), r)]
+        if inside:
+            woi.woi_destroy_geometry(woi.woi_create_geometry(3, surfaces, [-1, 0]))
+        else:
+            with pytest.raises(woi.WoiError) as e:
+                woi.woi_create_geometry(3, surfaces, [-1, 0])
+            assert e.value.status == 2
+
+
 def test_mesh_host_geometry(woi):
     """Triangle meshes on the host side of the library: areas equal the oracle's,
     the rock workload is accepted, and open, inverted or crossing meshes are
